@@ -1,0 +1,109 @@
+"""Seeded synthetic inputs shared by the GPU library's tests/bench and the CPU oracle.
+
+This module holds none of the estimator's arithmetic: it only makes locations, limits, seeds
+and problem lists (numpy PCG64 generators), plus the data preparation of the paper's synthetic
+protocol (posterior mean/covariance from noisy observations, Sec. V-B Eqs. 7-8), which acts on a
+covariance matrix handed to it.
+
+Workloads (the paper's Sec. V uses fields on regular grids in [0,1]^2; its datasets are not
+available, so these seeded inputs stand in for them):
+  W1  n=256   : 16x16 grid, exponential (Matern nu=1/2) sigma2=1, range 0.1; a=-inf,
+                b_i ~ U(-1,1) (seed 1); tile 64; 10,000 lattice points x 20 shifts.
+  W2  n=16384 : 128x128 grid, Matern nu=3/2, range 0.05, nugget 1e-4; a=-inf, b_i=0.5;
+                tile 512; 20,000 paths = 10 shifts x 2,000 points.
+  W3  n=4096  : 64x64 grid, Matern nu=1/2, range 0.1; posterior field from 640 noisy
+                observations (noise sd 0.5); threshold u=0.8, level 0.95; 256 prefix problems
+                with dims ~ U{64..4096} (seed 3); 10,000 paths = 10 x 1,000.
+  W4  n=4096  : 64x64 grid, Matern nu=3/2, sigma2=1, range 0.1, nugget 1e-4; a=-inf, b_i=0.5;
+                10,000 paths = 10 x 1,000.
+  W5  n=65536 : 256x256 grid (Morton order), exponential range 0.05; tile 1024; TLR acc 1e-5,
+                max rank 256; a=-inf, b_i=0.5; 10,000 paths = 10 x 1,000.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def grid_coords(g: int, order: str = "row") -> np.ndarray:
+    """Locations s = (i/(g-1), j/(g-1)) of a g x g regular grid in [0,1]^2, shape (g*g, 2).
+    order="row": row-major (i outer); order="morton": Z-order of (i, j)."""
+    if g == 1:
+        return np.zeros((1, 2))
+    i, j = np.meshgrid(np.arange(g), np.arange(g), indexing="ij")
+    i = i.ravel()
+    j = j.ravel()
+    if order == "morton":
+        key = np.zeros(g * g, dtype=np.int64)
+        for bit in range(int(np.ceil(np.log2(max(g, 2)))) + 1):
+            key |= ((i >> bit) & 1) << (2 * bit + 1)
+            key |= ((j >> bit) & 1) << (2 * bit)
+        perm = np.argsort(key, kind="stable")
+        i, j = i[perm], j[perm]
+    elif order != "row":
+        raise ValueError(order)
+    return np.stack([i / (g - 1), j / (g - 1)], axis=1).astype(np.float64)
+
+
+def random_coords(n: int, seed: int) -> np.ndarray:
+    """n uniform locations in [0,1]^2 (irregular set, Table I "geom")."""
+    return np.random.default_rng(seed).random((n, 2))
+
+
+def uniform_limits(n: int, lo: float, hi: float, seed: int) -> np.ndarray:
+    return np.random.default_rng(seed).uniform(lo, hi, size=n)
+
+
+def prefix_problem_dims(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
+    """Problem dimensions k ~ U{lo..hi} (inclusive), int32."""
+    return np.random.default_rng(seed).integers(lo, hi + 1, size=count).astype(np.int32)
+
+
+def standard_normals(shape, seed: int) -> np.ndarray:
+    return np.random.default_rng(seed).standard_normal(shape)
+
+
+def posterior_field(Sigma_prior: np.ndarray, n_obs: int, noise_sd: float, seed: int):
+    """Synthetic posterior protocol of Sec. V-B (Eqs. 7-8) on a given prior covariance:
+    draw a truth field x ~ N(0, Sigma_prior), observe n_obs random locations with additive
+    N(0, noise_sd^2) noise, and return (mu_post, Sigma_post, obs_index).  Eq. 7 is evaluated in
+    Woodbury form Sigma - Sigma A^T (A Sigma A^T + s^2 I)^-1 A Sigma, Eq. 8 with mu = 0."""
+    rng = np.random.default_rng(seed)
+    n = Sigma_prior.shape[0]
+    C = np.linalg.cholesky(Sigma_prior + 1e-10 * np.eye(n))
+    x = C @ rng.standard_normal(n)
+    idx = np.sort(rng.choice(n, size=n_obs, replace=False))
+    y = x[idx] + noise_sd * rng.standard_normal(n_obs)
+    SAt = Sigma_prior[:, idx]                                  # Sigma A^T
+    K = Sigma_prior[np.ix_(idx, idx)] + noise_sd ** 2 * np.eye(n_obs)
+    Kc = np.linalg.cholesky(K)
+    T = np.linalg.solve(Kc, SAt.T)                             # Kc^-1 A Sigma
+    Sigma_post = Sigma_prior - T.T @ T
+    Sigma_post = 0.5 * (Sigma_post + Sigma_post.T)
+    mu_post = SAt @ np.linalg.solve(Kc.T, np.linalg.solve(Kc, y))
+    return mu_post, Sigma_post, idx
+
+
+WORKLOADS = {
+    "W1": dict(name="sov-n256-exp", g=16, nu=0.5, sigma2=1.0, range=0.1, nugget=0.0, tile=64,
+               Ns=10_000, M=20, seed=11, limits="uniform", b_seed=1),
+    "W2": dict(name="sov-n16384-matern32", g=128, nu=1.5, sigma2=1.0, range=0.05, nugget=1e-4,
+               tile=512, Ns=2_000, M=10, seed=12, limits="b=0.5"),
+    "W3": dict(name="excursion-n4096-exp", g=64, nu=0.5, sigma2=1.0, range=0.1, nugget=0.0,
+               Ns=1_000, M=10, seed=13, u=0.8, level=0.95, nprob=256, dims_lo=64,
+               dims_hi=4096, dims_seed=3, n_obs=640, noise_sd=0.5, field_seed=30),
+    "W4": dict(name="adjoint-n4096-matern32", g=64, nu=1.5, sigma2=1.0, range=0.1, nugget=1e-4,
+               Ns=1_000, M=10, seed=14, limits="b=0.5"),
+    "W5": dict(name="tlr-n65536-exp", g=256, nu=0.5, sigma2=1.0, range=0.05, nugget=0.0,
+               tile=1024, acc=1e-5, max_rank=256, Ns=1_000, M=10, seed=15, limits="b=0.5",
+               order="morton"),
+}
+
+
+def limits_for(w: dict, n: int):
+    """(a, b) of a workload: a = -inf; b as the workload states."""
+    a = np.full(n, -np.inf)
+    if w.get("limits") == "uniform":
+        b = uniform_limits(n, -1.0, 1.0, w["b_seed"])
+    else:
+        b = np.full(n, 0.5)
+    return a, b

@@ -1,0 +1,454 @@
+"""Pins of the CPU oracle against things other than itself: textbook values, closed forms,
+quadrature, brute-force Monte Carlo, library routines of a different implementation, and
+invariants of the method.  Each test names the paper passage the pinned function follows."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_14892_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ----------------------------------------------------------------- Phi, Q, Phi^-1 (Eq. 2)
+
+def test_normal_textbook_values():
+    for kind, arg, val in _read_golden("normal_quantiles.txt"):
+        x, v = float(arg), float(val)
+        got = oracle.Phinv([x])[0] if kind == "quantile" else oracle.Phi([x])[0]
+        # Phi(x) has relative condition number ~ x^2 in the tail (the x/sqrt(2) scaling is
+        # rounded before erfc), so the tolerance grows with x^2
+        rtol = 2e-15 if kind == "quantile" else 4e-16 * (4 + x * x)
+        assert abs(got - v) <= rtol * abs(v) + 1e-300, (kind, arg, got, v)
+
+
+def test_phinv_round_trip_and_other_implementation():
+    from scipy.special import ndtr, ndtri
+    u = np.concatenate([10.0 ** -np.linspace(300, 1, 400), np.linspace(0.01, 0.99, 199)])
+    z = oracle.Phinv(u)
+    # round trip through Phi (lower tail): exact to a few ulps of u times the condition
+    # number of Phi at z (~ z^2 in the tail)
+    assert np.all(np.abs(oracle.Phi(z) - u) <= 5e-16 * (8 + 2 * z * z) * u)
+    # a different implementation (Cephes ndtri / ndtr)
+    np.testing.assert_allclose(z, ndtri(u), rtol=2e-15, atol=1e-300)
+    x = np.linspace(-37, 8, 1000)
+    assert np.all(np.abs(oracle.Phi(x) - ndtr(x)) <= 5e-16 * (8 + 2 * x * x) * ndtr(x))
+    # symmetry Q(x) = Phi(-x), and the upper-tail form is accurate where 1-Phi cancels
+    np.testing.assert_array_equal(oracle.Q(x), oracle.Phi(-x))
+    assert oracle.Phi([0.0])[0] == 0.5
+    assert oracle.Phinv([0.5])[0] == 0.0
+    assert oracle.Phinv([0.0])[0] == -np.inf and oracle.Phinv([1.0])[0] == np.inf
+
+
+# ----------------------------------------------------------------- lattice (Alg. 2 "R")
+
+def test_splitmix64_reference_outputs():
+    for c, h in _read_golden("splitmix64.txt"):
+        assert oracle.splitmix64(0, int(c)) == int(h, 16)
+
+
+def test_lattice_alpha_exact():
+    from decimal import Decimal, getcontext
+    getcontext().prec = 60
+    al = oracle.lattice_alpha(200)
+    ps = oracle.primes(200)
+    assert ps[:10] == [2, 3, 5, 7, 11, 13, 17, 19, 23, 29] and ps[-1] == 1223
+    for p, a in zip(ps, al):
+        s = Decimal(p).sqrt()
+        frac = s - int(s)
+        assert int(a) == int(frac * (Decimal(2) ** 64))
+
+
+def test_lattice_points_fixed_point_rule():
+    rng = np.random.default_rng(0)
+    j = rng.integers(1, 10 ** 6, size=1000).astype(np.uint64)
+    al = oracle.lattice_alpha(1000)
+    de = rng.integers(0, 2 ** 63, size=1000).astype(np.uint64) * np.uint64(2)
+    w = oracle.lattice_points(j, al, de)
+    for t in range(0, 1000, 37):
+        W = (int(j[t]) * int(al[t]) + int(de[t])) % 2 ** 64
+        assert w[t] == ((W >> 11) + 0.5) / 2.0 ** 53
+    assert np.all((w > 0) & (w < 1))
+
+
+def test_lattice_rank1_structure():
+    # for one dimension, the Ns points of a shift are an equispaced-in-the-torus orbit:
+    # sorted fractional parts have gaps taking at most 3 distinct values (three-gap theorem)
+    al = oracle.lattice_alpha(3)
+    w = np.sort(oracle.lattice_points(np.arange(1, 1001, dtype=np.uint64), al[2], np.uint64(0)))
+    gaps = np.diff(np.concatenate([w, [w[0] + 1]]))
+    assert len(np.unique(np.round(gaps, 12))) <= 3
+
+
+# ----------------------------------------------------------------- Cholesky (Alg. 1 dpotrf)
+
+def _spd(n, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n))
+    return A @ A.T / n + np.eye(n)
+
+
+def test_cholesky_vs_lapack_and_backward_error():
+    A = _spd(150, 1)
+    L, info = oracle.cholesky(A)
+    assert info == 0
+    np.testing.assert_allclose(L, np.linalg.cholesky(A), rtol=1e-12, atol=1e-13)
+    assert np.linalg.norm(L @ L.T - A) / np.linalg.norm(A) < 150 * 2.2e-16
+
+
+def test_cholesky_equicorrelated_closed_form():
+    n, rho = 40, 0.37
+    A = (1 - rho) * np.eye(n) + rho * np.ones((n, n))
+    L, info = oracle.cholesky(A)
+    assert info == 0
+    for j in range(n):
+        ljj = math.sqrt((1 - rho) * (1 + j * rho) / (1 + (j - 1) * rho))
+        assert abs(L[j, j] - ljj) < 1e-14
+        lij = rho * (1 - rho) / ((1 + (j - 1) * rho) * ljj)
+        np.testing.assert_allclose(L[j + 1:, j], lij, rtol=1e-13)
+
+
+def test_cholesky_not_pd_info():
+    A = np.diag([1.0, 2.0, -1.0, 1.0])
+    assert oracle.cholesky(A)[1] == 3
+    B = np.array([[1.0, 2.0], [2.0, 1.0]])
+    assert oracle.cholesky(B)[1] == 2
+
+
+def test_cholesky_grad_vs_finite_differences():
+    n = 7
+    A = _spd(n, 2)
+    G = np.tril(np.random.default_rng(3).standard_normal((n, n)))
+    L, _ = oracle.cholesky(A)
+    Abar = oracle.cholesky_grad(L, G)
+    h = 1e-6
+    for (i, j) in [(0, 0), (3, 1), (6, 6), (5, 2), (6, 0)]:
+        E = np.zeros((n, n))
+        E[i, j] = h
+        if i != j:
+            pass  # the factorisation reads only the lower triangle
+        Lp, _ = oracle.cholesky(A + E)
+        Lm, _ = oracle.cholesky(A - E)
+        fd = ((Lp - Lm) * G).sum() / (2 * h)
+        assert abs(fd - Abar[i, j]) < 1e-7 * max(1, abs(fd)), (i, j, fd, Abar[i, j])
+    # n = 1: L = sqrt(A), dL/dA = 1/(2 sqrt A)
+    g = oracle.cholesky_grad(np.array([[2.0]]), np.array([[1.0]]))
+    assert abs(g[0, 0] - 1 / (2 * 2.0)) < 1e-16
+
+
+# ----------------------------------------------------------------- Matern (Eq. 6)
+
+def test_matern_bessel_form_matches_closed_forms():
+    c = inputs.random_coords(30, 5)
+    h = np.sqrt(((c[:, None] - c[None]) ** 2).sum(-1))
+    for nu, f in [(0.5, lambda x: np.exp(-x)), (1.5, lambda x: (1 + x) * np.exp(-x)),
+                  (2.5, lambda x: (1 + x + x * x / 3) * np.exp(-x))]:
+        C = oracle.matern(c, 1.7, 0.2, nu)
+        np.testing.assert_allclose(C, 1.7 * f(h / 0.2), rtol=1e-12, atol=1e-15)
+
+
+def test_matern_param_grad_vs_fd():
+    c = inputs.random_coords(12, 6)
+    for nu in (0.5, 1.5):
+        base, dA = oracle.matern_grad_params(c, 1.3, 0.15, nu)
+        h = 1e-6
+        fd = (oracle.matern(c, 1.3, 0.15 + h, nu) - oracle.matern(c, 1.3, 0.15 - h, nu)) / (2 * h)
+        np.testing.assert_allclose(dA, fd, rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(base * 1.3, oracle.matern(c, 1.3, 0.15, nu), rtol=1e-12)
+
+
+# ----------------------------------------------------------------- SOV (Eqs. 2-3, Alg. 2-3)
+
+Q1 = oracle.QMC(256, 8, 77)
+
+
+def test_sov_n1_exact_per_path():
+    for a, b, l in [(-np.inf, 0.3, 1.0), (-0.7, 1.2, 2.0), (3.0, 9.0, 1.0), (-9.0, -6.0, 1.5)]:
+        lw = oracle.sov_logw([a], [b], np.array([[l]]), Q1)
+        ex = math.log(oracle.Phi([b / l])[0] - oracle.Phi([a / l])[0]) if a / l <= 0 else \
+            math.log(oracle.Q([a / l])[0] - oracle.Q([b / l])[0])
+        np.testing.assert_array_equal(lw, ex)
+
+
+def test_sov_independent_product_per_path():
+    n = 12
+    rng = np.random.default_rng(4)
+    sd = rng.uniform(0.5, 2.0, n)
+    a = rng.uniform(-3, 0, n)
+    b = a + rng.uniform(0.1, 4, n)
+    a[::3] = -np.inf
+    lw = oracle.sov_logw(a, b, np.diag(sd), Q1)
+    ex = sum(math.log(oracle.Phi([b[i] / sd[i]])[0] - oracle.Phi([a[i] / sd[i]])[0])
+             if a[i] / sd[i] <= 0 else
+             math.log(oracle.Q([a[i] / sd[i]])[0] - oracle.Q([b[i] / sd[i]])[0]) for i in range(n))
+    np.testing.assert_allclose(lw, ex, rtol=1e-14)
+
+
+def _bvn_quad(a1, b1, a2, b2, rho):
+    from scipy.integrate import quad
+    from scipy.special import ndtr
+    s = math.sqrt(1 - rho * rho)
+    f = lambda x: math.exp(-0.5 * x * x) / math.sqrt(2 * math.pi) * (
+        ndtr((b2 - rho * x) / s) - ndtr((a2 - rho * x) / s))
+    return quad(f, a1, b1, epsabs=1e-14, epsrel=1e-13, limit=200)[0]
+
+
+def test_sov_bivariate_vs_quadrature():
+    for (a1, b1, a2, b2, rho) in [(-1.0, 0.5, -0.3, 2.0, 0.6), (-np.inf, 0.0, -np.inf, 0.0, -0.4),
+                                  (0.2, 3.0, -1.0, 1.0, 0.9)]:
+        S = np.array([[1.0, rho], [rho, 1.0]])
+        L, _ = oracle.cholesky(S)
+        lo1 = a1 if np.isfinite(a1) else -40
+        lo2 = a2 if np.isfinite(a2) else -40
+        ref = _bvn_quad(lo1, b1, lo2, b2, rho)
+        logP, P, err = oracle.sov([a1, a2], [b1, b2], L, oracle.QMC(4096, 10, 3))
+        assert abs(P - ref) <= max(err, 1e-12), (P, ref, err)
+
+
+def test_sov_trivariate_orthant_closed_form():
+    for r12, r13, r23 in [(0.5, 0.3, 0.2), (-0.3, 0.4, 0.1), (0.8, 0.7, 0.6)]:
+        S = np.array([[1, r12, r13], [r12, 1, r23], [r13, r23, 1.0]])
+        L, info = oracle.cholesky(S)
+        assert info == 0
+        ref = 0.125 + (math.asin(r12) + math.asin(r13) + math.asin(r23)) / (4 * math.pi)
+        logP, P, err = oracle.sov(np.full(3, -np.inf), np.zeros(3), L, oracle.QMC(4096, 10, 5))
+        assert abs(P - ref) <= err and err < 2e-3, (P, ref, err)
+
+
+def _equi(n, rho):
+    return (1 - rho) * np.eye(n) + rho * np.ones((n, n))
+
+
+@pytest.mark.parametrize("n", [5, 20, 100])
+def test_sov_equicorrelated_half_orthant(n):
+    # rho = 1/2: P(X <= 0) = 1/(n+1)
+    L, _ = oracle.cholesky(_equi(n, 0.5))
+    logP, P, err = oracle.sov(np.full(n, -np.inf), np.zeros(n), L, oracle.QMC(2000, 10, 9))
+    assert abs(P - 1 / (n + 1)) <= err, (P, 1 / (n + 1), err)
+
+
+def _equi_quad(a, b, rho):
+    """P(a <= X <= b), X equicorrelated rho >= 0, by 1-D quadrature over the common factor
+    X_i = sqrt(rho) Z + sqrt(1-rho) E_i (log domain inside the integrand)."""
+    from scipy.integrate import quad
+    from scipy.special import log_ndtr, ndtr
+    r, s = math.sqrt(rho), math.sqrt(1 - rho)
+
+    def f(z):
+        hi = (b - r * z) / s
+        lo = (a - r * z) / s
+        lg = np.sum(np.log(np.maximum(ndtr(hi) - ndtr(lo), 1e-300)))
+        return math.exp(lg - 0.5 * z * z) / math.sqrt(2 * math.pi)
+    return quad(f, -12, 12, epsabs=0, epsrel=1e-12, limit=400)[0]
+
+
+def test_sov_equicorrelated_quadrature_n200():
+    n, rho = 200, 0.3
+    rng = np.random.default_rng(8)
+    b = rng.uniform(1.0, 3.0, n)
+    a = np.full(n, -np.inf)
+    a[:50] = -b[:50]
+    ref = _equi_quad(a, b, rho)
+    L, _ = oracle.cholesky(_equi(n, rho))
+    logP, P, err = oracle.sov(a, b, L, oracle.QMC(1000, 10, 10))
+    assert abs(P - ref) <= err, (P, ref, err)
+
+
+def test_sov_bruteforce_mc_small_n():
+    n = 6
+    c = inputs.random_coords(n, 11)
+    S = oracle.matern(c, 1.0, 0.3, 0.5)
+    L, _ = oracle.cholesky(S)
+    rng = np.random.default_rng(12)
+    a = rng.uniform(-2.0, -0.5, n)
+    b = rng.uniform(0.5, 2.0, n)
+    a[0] = -np.inf
+    hits = 0
+    tot = 0
+    for _ in range(10):
+        x = rng.standard_normal((1_000_000, n)) @ L.T
+        hits += np.count_nonzero(np.all((x >= a) & (x <= b), axis=1))
+        tot += x.shape[0]
+    pmc = hits / tot
+    se_mc = math.sqrt(pmc * (1 - pmc) / tot)
+    logP, P, err = oracle.sov(a, b, L, oracle.QMC(4096, 10, 13))
+    assert abs(P - pmc) <= 4 * math.hypot(se_mc, err / 3), (P, pmc, se_mc, err)
+
+
+def test_sov_invariants():
+    n = 30
+    c = inputs.random_coords(n, 14)
+    S = oracle.matern(c, 1.0, 0.2, 1.5, nugget=1e-3)
+    L, _ = oracle.cholesky(S)
+    rng = np.random.default_rng(15)
+    a = rng.uniform(-2, 0, n)
+    b = a + rng.uniform(0.5, 3, n)
+    a[::4] = -np.inf
+    lw = oracle.sov_logw(a, b, L, Q1)
+    assert np.all(lw <= 0.0) and np.all(np.isfinite(lw))  # 0 <= e^logw <= 1
+    # diagonal scaling: D Sigma D with D a, D b gives the same weights per path
+    d = rng.uniform(0.3, 3.0, n)
+    Ld, _ = oracle.cholesky(S * np.outer(d, d))
+    lw2 = oracle.sov_logw(a * d, b * d, Ld, Q1)
+    np.testing.assert_allclose(lw2, lw, rtol=1e-10, atol=1e-10)
+    # prefix: trailing dimensions with both limits infinite leave the weights unchanged exactly
+    S3 = oracle.matern(np.vstack([c, inputs.random_coords(5, 16)]), 1.0, 0.2, 1.5, nugget=1e-3)
+    L3, _ = oracle.cholesky(S3)
+    lw3 = oracle.sov_logw(np.concatenate([a, np.full(5, -np.inf)]),
+                          np.concatenate([b, np.full(5, np.inf)]), L3, Q1)
+    np.testing.assert_array_equal(lw3, lw)
+    # monotone in b for steps well above the error
+    p1 = oracle.sov(a, b, L, Q1)
+    p2 = oracle.sov(a, b + 0.5, L, Q1)
+    assert p2[1] - p1[1] > p1[2] + p2[2]
+
+
+def test_estimate_log_domain():
+    rng = np.random.default_rng(17)
+    lw = rng.uniform(-5, 0, 40)
+    logP, P, err = oracle.estimate(lw, 4)
+    pq = np.exp(lw).reshape(4, 10).mean(1)
+    assert abs(P - pq.mean()) < 1e-15
+    assert abs(err - 3 * pq.std(ddof=1) / 2) < 1e-15
+    # underflow-safe: the same set shifted by -2000 in log space
+    logP2, P2, _ = oracle.estimate(lw - 2000, 4)
+    assert abs(logP2 - (logP - 2000)) < 1e-12 and P2 == 0.0
+    assert oracle.estimate(np.full(8, -np.inf), 2) == (-np.inf, 0.0, 0.0)
+
+
+# ----------------------------------------------------------------- SOV adjoint
+
+def test_sov_grad_n1_closed_form():
+    for a, b in [(-np.inf, 0.4), (-1.0, 0.7)]:
+        logP, ga, gb, gL = oracle.sov_grad([a], [b], np.array([[1.0]]), Q1)
+        den = oracle.Phi([b])[0] - oracle.Phi([a])[0]
+        phi = lambda x: math.exp(-x * x / 2) / math.sqrt(2 * math.pi)
+        # all paths carry the same weight; summing 2048 softmax weights costs ~1e-14
+        assert abs(gb[0] - phi(b) / den) < 1e-13
+        assert abs(ga[0] - (-phi(a) / den if np.isfinite(a) else 0.0)) < 1e-13
+
+
+def test_sov_grad_independent_closed_form():
+    n = 6
+    sd = np.array([0.5, 1.0, 2.0, 1.5, 0.8, 1.2])
+    b = np.array([0.2, 1.0, -0.3, 0.5, 2.0, 0.0])
+    a = np.full(n, -np.inf)
+    logP, ga, gb, gL = oracle.sov_grad(a, b, np.diag(sd), Q1)
+    from scipy.special import ndtr
+    phi = np.exp(-0.5 * (b / sd) ** 2) / math.sqrt(2 * math.pi)
+    np.testing.assert_allclose(gb, phi / ndtr(b / sd) / sd, rtol=1e-13)
+    # d/dsd_i of log Phi(b/sd) = -phi b / (Phi sd^2)
+    np.testing.assert_allclose(np.diag(gL), -phi * b / ndtr(b / sd) / sd ** 2, rtol=1e-12,
+                               atol=1e-15)
+
+
+def test_sov_grad_vs_central_fd():
+    n = 10
+    c = inputs.random_coords(n, 18)
+    S = oracle.matern(c, 1.0, 0.25, 1.5, nugget=1e-3)
+    L, _ = oracle.cholesky(S)
+    rng = np.random.default_rng(19)
+    a = rng.uniform(-2, 0, n)
+    a[::2] = -np.inf
+    b = a + rng.uniform(1, 3, n)
+    b[np.isinf(a)] = rng.uniform(-0.5, 1.5, np.count_nonzero(np.isinf(a)))
+    q = oracle.QMC(64, 4, 20)
+    logP, ga, gb, gL = oracle.sov_grad(a, b, L, q)
+    h = 1e-5
+    f = lambda aa, bb, LL: oracle.sov(aa, bb, LL, q)[0]
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = h
+        fd = (f(a, b + e, L) - f(a, b - e, L)) / (2 * h)
+        assert abs(fd - gb[i]) < 1e-6 * max(1, abs(fd)), (i, fd, gb[i])
+        if np.isfinite(a[i]):
+            fd = (f(a + e, b, L) - f(a - e, b, L)) / (2 * h)
+            assert abs(fd - ga[i]) < 1e-6 * max(1, abs(fd))
+    for (i, k) in [(3, 3), (5, 2), (9, 0), (9, 8)]:
+        E = np.zeros((n, n))
+        E[i, k] = h
+        fd = (f(a, b, L + E) - f(a, b, L - E)) / (2 * h)
+        assert abs(fd - gL[i, k]) < 1e-6 * max(1, abs(fd)), (i, k, fd, gL[i, k])
+
+
+def test_theta_grad_chain_vs_fd():
+    """d logP / d(sigma2, range) through Sigma -> L -> SOV, vs central FD on the whole chain."""
+    g = 4
+    c = inputs.grid_coords(g)
+    n = g * g
+    b = np.full(n, 0.5)
+    a = np.full(n, -np.inf)
+    q = oracle.QMC(64, 4, 21)
+
+    def logp(s2, rg):
+        L, _ = oracle.cholesky(oracle.matern(c, s2, rg, 1.5, nugget=1e-4))
+        return oracle.sov(a, b, L, q)[0]
+    s2, rg = 1.0, 0.3
+    L, _ = oracle.cholesky(oracle.matern(c, s2, rg, 1.5, nugget=1e-4))
+    _, ga, gb, gL = oracle.sov_grad(a, b, L, q)
+    Sbar = oracle.cholesky_grad(L, gL)
+    d_s2, d_rg = oracle.matern_theta_grad(Sbar, c, s2, rg, 1.5)
+    h = 1e-5
+    fd_s2 = (logp(s2 + h, rg) - logp(s2 - h, rg)) / (2 * h)
+    fd_rg = (logp(s2, rg + h) - logp(s2, rg - h)) / (2 * h)
+    assert abs(fd_s2 - d_s2) < 1e-5 * max(1, abs(fd_s2)), (fd_s2, d_s2)
+    assert abs(fd_rg - d_rg) < 1e-5 * max(1, abs(fd_rg)), (fd_rg, d_rg)
+
+
+# ----------------------------------------------------------------- Alg. 1 (confidence region)
+
+def test_excursion_prefix_identity_and_monotone():
+    g = 8
+    c = inputs.grid_coords(g)
+    S = oracle.matern(c, 1.0, 0.2, 0.5)
+    mu = inputs.standard_normals(g * g, 22) * 0.8 + 0.9
+    q = oracle.QMC(128, 8, 23)
+    ks = [1, 5, 17, 40, 64]
+    r = oracle.excursion(mu, S, 0.8, 0.95, q, prefix_dims=ks)
+    # marginals: P(X_i > u) and descending order
+    from scipy.special import ndtr
+    np.testing.assert_allclose(r["marginal"], 1 - ndtr((0.8 - mu) / np.sqrt(np.diag(S))),
+                               rtol=1e-12, atol=1e-15)
+    assert np.all(np.diff(r["marginal"][r["order"]]) <= 0)
+    # F_k is exactly the k-prefix SOV problem on the same lattice (Alg. 1 loop)
+    L = r["L"]
+    a = 0.8 - mu[r["order"]]
+    for t, k in enumerate(ks):
+        P = oracle.sov(a[:k], np.full(k, np.inf), L[:k, :k], q)[1]
+        assert P == r["F"][t]
+    assert np.all(np.diff(r["F"]) <= 0)
+    K = max([k for k, f in zip(ks, r["F"]) if f >= 0.95], default=0)
+    assert r["region"].sum() == K
+    assert np.all(r["region"][r["order"][:K]] == 1)
+
+
+def test_excursion_mc_validation():
+    """Sec. V-C MC validation: the detected region D at level 1-alpha satisfies
+    P(X > u on all of D) ~ 1 - alpha (checked on D for a few levels by brute-force sampling)."""
+    g = 6
+    c = inputs.grid_coords(g)
+    S = oracle.matern(c, 1.0, 0.3, 0.5)
+    mu = 1.6 + 0.5 * inputs.standard_normals(g * g, 24)
+    q = oracle.QMC(1024, 10, 25)
+    r = oracle.excursion(mu, S, 0.8, 0.9, q)
+    Lc = np.linalg.cholesky(S)
+    rng = np.random.default_rng(26)
+    x = mu + rng.standard_normal((200_000, g * g)) @ Lc.T
+    for k in (3, 10, 20):
+        D = r["order"][:k]
+        pmc = np.mean(np.all(x[:, D] > 0.8, axis=1))
+        se = math.sqrt(pmc * (1 - pmc) / x.shape[0])
+        assert abs(pmc - r["F"][k - 1]) < 4 * se + 3e-3, (k, pmc, r["F"][k - 1])

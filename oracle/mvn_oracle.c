@@ -33,6 +33,7 @@
  *     Delta = Phi(b') - Phi(a') and y = Phi^-1(Phi(a') + w Delta).
  *   - If Delta underflows to 0 the path weight is 0 (log-weight -inf) and y is set to the
  *     finite limit (a' if a' > 0, else b') so no NaN is produced.
+ *   - An argument of Phi^-1 rounded to exactly 0 or 1 is moved to the nearest interior double.
  */
 #include <math.h>
 #include <stdint.h>
@@ -199,6 +200,15 @@ void orc_cholesky_grad(int n, const double* L, int64_t ld, double* Lbar) {
 
 /* ---------------------------------------------------------------- SOV, one path */
 
+/* The argument of Phi^-1 in Eq. 2 lies strictly inside (0,1) for w in (0,1); rounding can push
+ * it to exactly 0 or 1 (probability ~2^-53 per step), which would make y infinite.  Such a
+ * value is moved to the nearest interior double. */
+static double orc_interior(double p) {
+    if (p <= 0.0) return 4.9406564584124654e-324;
+    if (p >= 1.0) return 0.99999999999999988898; /* 1 - 2^-53 */
+    return p;
+}
+
 /* One SOV path (Eq. 2, Alg. 3): returns the log-weight sum_i log(Phi(b'_i) - Phi(a'_i)).
  * w[i] are the path's uniforms, y[i] receives the transformed variables.
  * If kprefix != NULL, logw_prefix[t] receives the log-weight after kprefix[t] dimensions. */
@@ -218,11 +228,11 @@ static double orc_sov_one(int n, const double* a, const double* b, const double*
         if (ap > 0.0) {
             double qa = orc_Q(ap), qb = orc_Q(bp);
             delta = qa - qb;
-            yi = (delta > 0.0) ? -orc_Phinv(qa - w[i] * delta) : ap;
+            yi = (delta > 0.0) ? -orc_Phinv(orc_interior(qa - w[i] * delta)) : ap;
         } else {
             double pa = orc_Phi(ap), pb = orc_Phi(bp);
             delta = pb - pa;
-            yi = (delta > 0.0) ? orc_Phinv(pa + w[i] * delta) : bp;
+            yi = (delta > 0.0) ? orc_Phinv(orc_interior(pa + w[i] * delta)) : bp;
         }
         logw += (delta > 0.0) ? log(delta) : -INFINITY;
         y[i] = yi;

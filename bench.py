@@ -1,0 +1,319 @@
+"""Benchmark: one step = the whole hot path on workload W2 (n=16,384 Matern 3/2 field on a
+128 x 128 grid, range 0.05, nugget 1e-4, b = 0.5, a = -inf; 20,000 lattice paths = 10 shifts x
+2,000 points): Matern covariance generation (Eq. 6) -> tile Cholesky -> blocked SOV sweep
+(Eqs. 2-3, Algs. 2-3) -> log-domain estimate.
+
+Metric: SOV sample-dims/s (n * paths / step time) and MVN probabilities/s (1 / step time).
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64|mixed_simt]
+       [--impl reference]  (the CPU oracle on a bounded sample of the same workload)
+Under torchrun (N > 1) every rank runs its own independent problem (a different shift seed):
+weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MVN probs/sec and SOV sample-dims/sec at n=16k, mixed vs FP64 GPU at |dP|<=1e-4"
+UNIT = "sample-dims/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _clock_sampler():
+    try:
+        return subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+             "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except Exception:
+        return None
+
+
+def _clock_summary(proc, gpu_index: int):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except Exception:
+        proc.kill()
+        out = ""
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9 or not f[0].isdigit() or int(f[0]) != gpu_index:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for k, nm in enumerate(names):
+            if f[5 + k].lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def workload():
+    from paper_2405_14892_gb300 import inputs
+    w = dict(inputs.WORKLOADS["W2"])
+    c = inputs.grid_coords(w["g"])
+    a, b = inputs.limits_for(w, c.shape[0])
+    return w, c, a, b
+
+
+# ----------------------------------------------------------------------------- CPU oracle arm
+
+def cpu_oracle_throughput(sample_paths: int = 48, chol_n: int = 2048):
+    """The oracle as it stands on this host's cores, on a bounded sample of W2:
+    SOV on `sample_paths` paths of the full n=16,384 problem (exactly linear in the path count)
+    plus the plain Cholesky loop on the leading chol_n x chol_n block (scaled by (n/chol_n)^3).
+    Returns (sample-dims/s for a whole W2 step, details)."""
+    import oracle
+    w, c, a, b = workload()
+    n = c.shape[0]
+    Ntot = w["Ns"] * w["M"]
+    S = oracle.matern_closed(c, w["sigma2"], w["range"], w["nu"], w["nugget"])
+    L = oracle.cholesky_lapack(S)  # input of the timed SOV sample (not timed)
+    q = oracle.QMC(w["Ns"], w["M"], w["seed"])
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.sov_logw(a, b, L, q, paths=(0, sample_paths))
+    t_sov = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.cholesky(S[:chol_n, :chol_n])
+    t_chol = time.perf_counter() - t0
+    t_step = t_chol * (n / chol_n) ** 3 + t_sov * Ntot / sample_paths
+    det = {"cores": cores, "kind": "oracle",
+           "sample": f"SOV: {sample_paths} of {Ntot} paths at n={n} ({t_sov:.1f} s, OpenMP over "
+                     f"paths); Cholesky: plain loop on the leading {chol_n}^2 block ({t_chol:.1f} s,"
+                     f" one thread), scaled by (n/{chol_n})^3; step time {t_step:.0f} s",
+           "t_step_s": t_step}
+    return n * Ntot / t_step, det
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w, c, a, b = workload()
+    vals = []
+    det = None
+    for _ in range(max(1, args.steps)):
+        v, det = cpu_oracle_throughput(sample_paths=16, chol_n=1024)
+        vals.append(v)
+    v = statistics.median(vals)
+    n = c.shape[0]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "n": n, "paths": w["Ns"] * w["M"],
+                       "l2": "inputs larger than L2 (n^2 FP64 = 2.1 GB)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
+                             "sample": det["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_2405_14892_gb300 import mvn
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 and not os.path.exists(mvn.LIB_PATH):
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    w, c, a, b = workload()
+    n = c.shape[0]
+    Ns, M = w["Ns"], w["M"]
+    Ntot = Ns * M
+    seed = w["seed"] + 1000 * rank
+    prec = args.prec
+    coords = torch.tensor(c, device=dev)
+    a_d = torch.tensor(a, device=dev)
+    b_d = torch.tensor(b, device=dev)
+    S = mvn.colmajor_empty(n, n, dev)
+    out3 = torch.empty(3, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = mvn.context(local)
+
+    ev = {k: torch.cuda.Event(enable_timing=True) for k in ("s0", "s1", "s2", "s3")}
+    phase = {"matern": [], "cholesky": [], "sov": []}
+
+    def step(timed_phases: bool):
+        if timed_phases:
+            ev["s0"].record(stream)
+        mvn.mvn_matern(coords, w["sigma2"], w["range"], w["nu"], w["nugget"], out=S)
+        if timed_phases:
+            ev["s1"].record(stream)
+        mvn.mvn_cholesky(S, prec=prec, check=False)
+        if timed_phases:
+            ev["s2"].record(stream)
+        mvn.mvn_sov(a_d, b_d, S, Ns, M, seed, prec=prec, out3=out3)
+        if timed_phases:
+            ev["s3"].record(stream)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    st, info = ctx.sync()
+    if st != 0:
+        raise RuntimeError(f"device error {st} info {info}: {mvn.lib().mvn_last_error(ctx.h)}")
+
+    # ---- timed region: device clock, inputs resident in HBM
+    clocks_proc = _clock_sampler() if rank == 0 else None
+    launches0 = ctx.launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(True)
+        torch.cuda.synchronize()  # per-phase events read back between steps
+        phase["matern"].append(ev["s0"].elapsed_time(ev["s1"]))
+        phase["cholesky"].append(ev["s1"].elapsed_time(ev["s2"]))
+        phase["sov"].append(ev["s2"].elapsed_time(ev["s3"]))
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = ctx.launches() - launches0
+    ms = t_start.elapsed_time(t_end) / args.steps
+    clocks = _clock_summary(clocks_proc, local) if rank == 0 else None
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st, info = ctx.sync()
+    if st != 0:
+        raise RuntimeError(f"device error {st} info {info}")
+    res = out3.cpu().numpy()
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    c_h = torch.tensor(c).pin_memory()
+    a_h = torch.tensor(a).pin_memory()
+    b_h = torch.tensor(b).pin_memory()
+    res_h = torch.empty(3, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        coords.copy_(c_h, non_blocking=True)
+        a_d.copy_(a_h, non_blocking=True)
+        b_d.copy_(b_h, non_blocking=True)
+        step(False)
+        res_h.copy_(out3, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    h2d = c_h.numel() * 8 + a_h.numel() * 8 + b_h.numel() * 8
+    d2h = 3 * 8
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks, peak_src = _peaks()
+    sov_ms = statistics.median(phase["sov"])
+    chol_ms = statistics.median(phase["cholesky"])
+    value = world * n * Ntot / (ms * 1e-3)
+    # roofline of the dominant kernel (the SOV sweep): algorithmic flops of the limit GEMM
+    # n(n-1) per path (multiply-add = 2 flops) over the measured sweep time
+    sov_flops = float(n) * (n - 1) * Ntot
+    if prec == "fp64":
+        peak, bound, unit = 1.25, "alu", "TFLOP/s"      # nominal FP64 (recipe table)
+        peak_note = "nominal FP64 1.25 TFLOP/s (recipe table)"
+    elif prec == "mixed_simt":
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        bound, unit = "alu", "TFLOP/s"
+        peak_note = "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops x max SM clock"
+    else:
+        peak, bound, unit = peaks["bf16_tflops_sustained"], "tensor", "TFLOP/s"
+        peak_note = f"{peak_src} bf16 sustained"
+    achieved = sov_flops / (sov_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f64+f32+bf16x3",
+                                       "mixed_simt": "f64+f32"}[prec],
+        "data": "synthetic",
+        "config": {"workload": w["name"], "n": n, "paths": Ntot, "shifts": M, "points": Ns,
+                   "prec": prec, "l2": "inputs larger than L2 (Sigma n^2 FP64 = 2.1 GB)",
+                   "parallelism": f"replicas{world}"},
+        "probs_per_sec": world / (ms * 1e-3),
+        "phases_ms": {"matern": statistics.median(phase["matern"]), "cholesky": chol_ms,
+                      "sov": sov_ms},
+        "sov_sample_dims_per_sec": n * Ntot / (sov_ms * 1e-3),
+        "logP": float(res[0]), "P": float(res[1]), "err": float(res[2]),
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak, "traffic": None, "kernel": "SOV sweep",
+                     "peak_source": peak_note},
+        "e2e": {"value": world * n * Ntot / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        v, det = cpu_oracle_throughput()
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": det["cores"],
+                                "kind": "oracle", "sample": det["sample"]}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed_simt", choices=["mixed", "fp64", "mixed_simt"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

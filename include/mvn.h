@@ -1,0 +1,195 @@
+/*
+ * mvn.h -- C ABI of the GB300 (sm_103a) library for Separation-of-Variables (SOV) estimation
+ * of multivariate normal probabilities and the confidence-region loop built on it.
+ *
+ * Paper: "Parallel Approximations for High-Dimensional Multivariate Normal Probability
+ * Computation in Confidence Region Detection Applications" (arXiv 2405.14892).
+ *
+ * Conventions (all entry points):
+ *   - Array arguments are DEVICE pointers (e.g. torch.Tensor.data_ptr() of a CUDA tensor) unless
+ *     a comment says "host".  Scalars are host values.  Matrices are column-major with leading
+ *     dimension `ld` (in elements, ld >= n), FP64.
+ *   - The caller owns every input and output buffer.  The context owns its workspace, which
+ *     grows on demand (cudaMalloc) and is kept until mvn_destroy; after a first call of a given
+ *     size, later calls of that size allocate nothing.
+ *   - Work is enqueued on the context's stream and is asynchronous unless stated otherwise.
+ *     The returned status reports host-side validation and launch errors.  Errors found on
+ *     the device (a non-positive pivot, a numeric failure, a wait that timed out) are written to
+ *     a device status word; mvn_sync waits for the stream and returns it.
+ *   - No exception or exit crosses the ABI.  A context is not thread-safe; separate contexts
+ *     are independent.
+ */
+#ifndef MVN_H
+#define MVN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mvn_ctx mvn_ctx;
+typedef struct mvn_tlr mvn_tlr;
+
+typedef enum {
+    MVN_OK = 0,
+    MVN_ERR_ARG = 1,             /* invalid argument (size, pointer, NaN limit, a > b ...)      */
+    MVN_ERR_NOT_PD = 2,          /* matrix not positive definite (see `info`)                   */
+    MVN_ERR_CUDA = 3,            /* CUDA runtime error (message in mvn_last_error)              */
+    MVN_ERR_OOM = 4,             /* workspace allocation failed                                 */
+    MVN_ERR_TIMEOUT = 5,         /* a bounded device-side wait expired                          */
+    MVN_ERR_NUMERIC = 6,         /* every path has weight 0 (P-hat = 0, log P-hat = -inf)       */
+    MVN_ERR_NOT_IMPLEMENTED = 7
+} mvn_status;
+
+/* Arithmetic of the compute path.
+ *   MVN_FP64       : every step in FP64 (the plain FP64 GPU path).
+ *   MVN_MIXED      : Cholesky in FP64; SOV limit-update GEMM on the tcgen05 tensor cores with
+ *                    operands split into three BF16 slices (FP32 accumulation in TMEM), limits
+ *                    and transformed variables in FP32, the running log-weight in FP64, deep
+ *                    tails of Phi and Phi^-1 in FP64.
+ *   MVN_MIXED_SIMT : as MVN_MIXED with the limit-update GEMM in FP32 on the CUDA cores. */
+typedef enum { MVN_FP64 = 0, MVN_MIXED = 1, MVN_MIXED_SIMT = 2 } mvn_prec;
+
+/* Randomly shifted rank-1 (Richtmyer) lattice rule that replaces the uniforms R of Alg. 2:
+ *   w_{q,j,i} = frac(j * alpha_i + Delta_{q,i}) in 64-bit fixed point, j = 1..n_points,
+ *   alpha_i = floor(sqrt(p_i) 2^64) mod 2^64 (p_i the i-th prime, p_0 = 2),
+ *   Delta_{q,i} = SplitMix64(seed, counter q*2^32 + i), q = 0..n_shifts-1.
+ * Path p = q * n_points + (j - 1).  The estimate is P-hat = mean over all paths of exp(logw_p);
+ * err = err_k * sd_q(P-hat_q) / sqrt(n_shifts). */
+typedef struct {
+    int64_t n_points; /* points per shift (>= 1)                                     */
+    int32_t n_shifts; /* number of random shifts M (>= 1; >= 2 for an error estimate) */
+    int32_t reserved;
+    uint64_t seed;    /* key of the shift generator                                  */
+    double err_k;     /* error multiplier (3 = three standard errors)                */
+} mvn_qmc;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`, enqueuing on `cuda_stream` (a cudaStream_t; NULL =
+ * the legacy default stream).  *out receives the context.  Errors: MVN_ERR_ARG, MVN_ERR_CUDA. */
+mvn_status mvn_create(mvn_ctx** out, int device, void* cuda_stream);
+mvn_status mvn_destroy(mvn_ctx* ctx);
+/* Switch the stream later calls enqueue on. */
+mvn_status mvn_set_stream(mvn_ctx* ctx, void* cuda_stream);
+/* Message of the last error on this context (never NULL; "" if none). */
+const char* mvn_last_error(const mvn_ctx* ctx);
+/* Wait for the stream; return (and clear) the device status word.  If info != NULL (host),
+ * *info receives the LAPACK-style failing column of the last failed factorisation, else 0. */
+mvn_status mvn_sync(mvn_ctx* ctx, int* info);
+/* Number of kernels this context has launched since creation (host counter). */
+int64_t mvn_launch_count(const mvn_ctx* ctx);
+
+/* ------------------------------------------------------------------ covariance (Eq. 6) */
+
+/* Matern covariance of Eq. 6 for nu in {0.5, 1.5, 2.5} (closed forms of the Bessel K_nu):
+ *   Sigma_ij = C(||s_i - s_j||; sigma2, range, nu) + nugget * [i == j].
+ * coords: n x 2 row-major FP64 (x_i, y_i).  Sigma: n x n column-major (ld); only the lower
+ * triangle (i >= j) is written.  Errors: MVN_ERR_ARG (nu not supported, n < 0, ld < n). */
+mvn_status mvn_matern(mvn_ctx* ctx, int n, const double* coords, double sigma2, double range,
+                      double nu, double nugget, double* Sigma, int64_t ld);
+
+/* Contraction of a lower-triangle gradient with the Matern parameter derivatives:
+ *   out[0] = sum_{i>=j} Sbar_ij dSigma_ij/dsigma2,  out[1] = sum_{i>=j} Sbar_ij dSigma_ij/drange,
+ * for nu in {0.5, 1.5}.  Sbar: n x n column-major (ld), lower triangle read.  out: device
+ * double[2].  Deterministic (fixed reduction order). */
+mvn_status mvn_matern_grad(mvn_ctx* ctx, int n, const double* coords, double sigma2,
+                           double range, double nu, const double* Sbar, int64_t ld,
+                           double* out);
+
+/* ------------------------------------------------------------------ Cholesky (Alg. 1, "dpotrf") */
+
+/* In-place lower Cholesky factorisation A = L L^T (Alg. 1 "dpotrf"), tile algorithm with tile
+ * size `tile` (0 = automatic).  Only the lower triangle of A is read and written.
+ * prec: MVN_FP64 (every update in FP64).  Other values are accepted and also run in FP64 (the
+ * factor needs FP64 accuracy for the SOV estimate at the stated tolerance).
+ * info (host, optional): if non-NULL the call waits for completion and *info = 0 or the 1-based
+ * index of the first non-positive pivot (LAPACK convention), returning MVN_ERR_NOT_PD in that
+ * case.  If NULL the call is asynchronous and a failure is reported by mvn_sync. */
+mvn_status mvn_cholesky(mvn_ctx* ctx, int n, double* A, int64_t ld, int tile, mvn_prec prec,
+                        int* info);
+
+/* Reverse mode of mvn_cholesky (blocked form of the column algorithm's adjoint; Murray 2016).
+ * L: the factor (lower, ld).  Lbar: on entry dF/dL (lower triangle, ld); on exit dF/dA for the
+ * lower-triangle entries A_ij (i >= j) read by the factorisation (strict upper part untouched). */
+mvn_status mvn_cholesky_grad(mvn_ctx* ctx, int n, const double* L, int64_t ld, double* Lbar);
+
+/* ------------------------------------------------------------------ SOV (Eqs. 2-3, Algs. 2-3) */
+
+/* P(a <= X <= b), X ~ N(0, L L^T), by the blocked SOV sweep on the shifted lattice rule.
+ * a, b: device n-vectors (a_i = -INFINITY / b_i = +INFINITY allowed; a_i <= b_i, no NaN).
+ * L: lower Cholesky factor, n x n column-major (ld), FP64 (only the lower triangle is read).
+ * out3: device double[3] = {log P-hat, P-hat, err}.
+ * path_logw: optional device double[n_points * n_shifts], the per-path log-weights.
+ * Errors: MVN_ERR_ARG; MVN_ERR_NUMERIC (via mvn_sync) if every path has weight 0. */
+mvn_status mvn_sov(mvn_ctx* ctx, int n, const double* a, const double* b, const double* L,
+                   int64_t ld, const mvn_qmc* qmc, mvn_prec prec, double* out3,
+                   double* path_logw);
+
+/* SOV estimate and its gradient (reverse mode of the per-path recurrence; not in the paper):
+ *   dlogp_da, dlogp_db: device n-vectors of d log P-hat / d a_i, d b_i (either may be NULL);
+ *   dlogp_dL: optional device n x n (ld) lower-triangle d log P-hat / d L_ik.
+ * The reverse sweep recomputes each block's elementwise terms from the stored transformed
+ * variables instead of storing them.  out3 as in mvn_sov. */
+mvn_status mvn_sov_grad(mvn_ctx* ctx, int n, const double* a, const double* b,
+                        const double* L, int64_t ld, const mvn_qmc* qmc, mvn_prec prec,
+                        double* out3, double* dlogp_da, double* dlogp_db, double* dlogp_dL);
+
+/* nprob independent problems in one launch (Alg. 1's loop of PMVN calls):
+ * problem p has dimension dims[p] (host array) and limits a[off_p .. off_p + dims[p]),
+ * b[...] with off_p = limit_offsets[p] (host array); its factor is the leading
+ * dims[p] x dims[p] block of L_shared (ld).  out3: device double[nprob * 3].
+ * Work items (problem, 128-path tile) are scheduled longest-first by a persistent kernel. */
+mvn_status mvn_sov_batched(mvn_ctx* ctx, int nprob, const int* dims,
+                           const int64_t* limit_offsets, const double* a, const double* b,
+                           const double* L_shared, int64_t ld, const mvn_qmc* qmc,
+                           mvn_prec prec, double* out3);
+
+/* ------------------------------------------------------------------ confidence region (Alg. 1) */
+
+/* Positive confidence region of level 1-alpha above threshold u for X ~ N(mu, Sigma):
+ *   marginal[i] = P(X_i > u);  order = indices sorted by descending marginal (ties by index);
+ *   L = chol(Sigma[order, order]);  F[t] = P-hat(X_{order[0..k_t)} > u) for the prefix
+ *   lengths k_t = prefix_dims[t] (host array, NULL = all 1..n, then nprob = n);
+ *   region[i] = 1 for i in order[0..K), K = the largest listed k_t with F[t] >= 1-alpha.
+ * The prefix problems share the lattice, so every F[t] comes from one sweep over n dimensions.
+ * mu (n), Sigma (n x n, ld, lower triangle read) are inputs; order (int32, n), marginal (n),
+ * F (nprob), region (uint8, n) are outputs.  Workspace holds the permuted factor (n x n). */
+mvn_status mvn_excursion(mvn_ctx* ctx, int n, const double* mu, const double* Sigma,
+                         int64_t ld, double u, double one_minus_alpha, int nprob,
+                         const int* prefix_dims, const mvn_qmc* qmc, mvn_prec prec, int tile,
+                         int32_t* order, double* marginal, double* F, uint8_t* region);
+
+/* ------------------------------------------------------------------ tile low-rank (Sec. III-E) */
+
+/* Compress the lower triangle of Sigma (n x n, ld) into tile low-rank form with square tiles
+ * of size `tile`: diagonal tiles dense, each off-diagonal tile Sigma_ij ~= U_ij V_ij^T with the
+ * smallest rank k such that the (k+1)-th singular value is <= acc, capped at max_rank.
+ * *out receives the new object (owned by the library until mvn_tlr_free).
+ * max_rank_hit (host, optional): number of tiles whose rank was capped.  Synchronous. */
+mvn_status mvn_tlr_compress(mvn_ctx* ctx, int n, const double* Sigma, int64_t ld, int tile,
+                            double acc, int max_rank, mvn_tlr** out, int* max_rank_hit);
+/* Tile low-rank Cholesky in place (dense diagonal POTRF, TRSM on the V factors, low-rank
+ * updates recompressed at the object's accuracy).  info as in mvn_cholesky. */
+mvn_status mvn_tlr_cholesky(mvn_ctx* ctx, mvn_tlr* tlr, int* info);
+/* Expand to a dense lower matrix L (n x n, ld, FP64; strict upper part untouched). */
+mvn_status mvn_tlr_to_dense(mvn_ctx* ctx, const mvn_tlr* tlr, double* L, int64_t ld);
+/* ranks (host int array of length nt*(nt-1)/2, nt = ceil(n/tile)), tile (i,j), i > j, in
+ * column order: (1,0),(2,0),...,(nt-1,0),(2,1),... */
+mvn_status mvn_tlr_ranks(const mvn_tlr* tlr, int* ranks);
+mvn_status mvn_tlr_free(mvn_tlr* tlr);
+
+/* ------------------------------------------------------------------ lattice tables (testing) */
+
+/* Copy the lattice generators alpha_0..alpha_{n-1} (u64, see mvn_qmc) to the device buffer out.
+ * Synchronous on first use (the table is computed on the device and cached in the context). */
+mvn_status mvn_lattice_alpha(mvn_ctx* ctx, int n, uint64_t* out);
+/* Write the shifts Delta_{q,i} = SplitMix64(seed, q*2^32 + i) to out[q*n + i] (device, M x n). */
+mvn_status mvn_lattice_shifts(mvn_ctx* ctx, uint64_t seed, int M, int n, uint64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MVN_H */

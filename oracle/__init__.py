@@ -182,6 +182,38 @@ def matern(coords: np.ndarray, sigma2: float, rng: float, nu: float, nugget: flo
     return C
 
 
+def matern_closed(coords: np.ndarray, sigma2: float, rng: float, nu: float, nugget: float = 0.0,
+                  dtype=np.float64):
+    """Eq. 6 for half-integer nu through the closed forms of K_nu (nu = 1/2: e^-x; 3/2:
+    (1+x) e^-x; 5/2: (1 + x + x^2/3) e^-x), for sizes where the Bessel form is too slow.
+    Pinned against `matern` (tests/test_oracle_pins.py)."""
+    c = np.asarray(coords, dtype=np.float64)
+    n = len(c)
+    C = np.empty((n, n), dtype=dtype)
+    step = max(1, (1 << 24) // max(n, 1))
+    for r0 in range(0, n, step):
+        r1 = min(n, r0 + step)
+        h = np.sqrt(((c[r0:r1, None, :] - c[None, :, :]) ** 2).sum(-1))
+        x = h / rng
+        if nu == 0.5:
+            v = np.exp(-x)
+        elif nu == 1.5:
+            v = (1.0 + x) * np.exp(-x)
+        elif nu == 2.5:
+            v = (1.0 + x + x * x / 3.0) * np.exp(-x)
+        else:
+            raise ValueError("closed forms only for nu in {0.5, 1.5, 2.5}")
+        C[r0:r1] = sigma2 * v
+    C[np.diag_indices(n)] = sigma2 + nugget
+    return C
+
+
+def cholesky_lapack(A: np.ndarray) -> np.ndarray:
+    """Lower Cholesky factor from LAPACK (numpy), used as a library step where the plain column
+    loop of `cholesky` is too slow (n in the thousands); pinned against `cholesky` at small n."""
+    return np.linalg.cholesky(A)
+
+
 def matern_grad_params(coords, sigma2, rng, nu):
     """dC/dsigma2 and dC/drange of Eq. 6 for nu in {1/2, 3/2}, from the closed forms
     K_1/2 -> exp(-x) and K_3/2 -> (1 + x) exp(-x):

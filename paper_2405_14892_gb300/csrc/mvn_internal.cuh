@@ -1,0 +1,102 @@
+// mvn_internal.cuh -- internal declarations of the GB300 MVN library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mvn.h"
+
+// Device status word layout (ctx->d_status):
+//   [0] first error code (mvn_status) raised on the device, 0 if none
+//   [1] LAPACK-style info of the last failed factorisation (1-based column)
+//   [2] scratch counter used by persistent kernels
+#define MVN_STATUS_WORDS 8
+
+struct mvn_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+    int64_t launches = 0;
+    // device status word
+    int* d_status = nullptr;
+    // grow-only workspace arena: slots are handed out per call (see ws_reserve)
+    void* ws = nullptr;
+    size_t ws_size = 0;
+    // lattice generators alpha_i (u64) for i < n_alpha, computed on the device once
+    uint64_t* d_alpha = nullptr;
+    int n_alpha = 0;
+};
+
+// Record an error message on the context and return the status.
+mvn_status mvn_fail(mvn_ctx* ctx, mvn_status st, const char* fmt, ...);
+// Check a CUDA runtime result; on error record it and return MVN_ERR_CUDA.
+#define MVN_CUDA(ctx, call)                                                                  \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return mvn_fail((ctx), MVN_ERR_CUDA, "%s: %s (%s:%d)", #call,                    \
+                            cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+    } while (0)
+#define MVN_TRY(expr)                                                                        \
+    do {                                                                                     \
+        mvn_status s_ = (expr);                                                              \
+        if (s_ != MVN_OK) return s_;                                                         \
+    } while (0)
+// After a kernel launch: count it and check the launch error.
+#define MVN_LAUNCHED(ctx)                                                                    \
+    do {                                                                                     \
+        (ctx)->launches++;                                                                   \
+        MVN_CUDA((ctx), cudaGetLastError());                                                 \
+    } while (0)
+
+// Workspace: reserve `bytes` (256-byte aligned partition) of the arena, growing it if needed.
+// Growth synchronises the stream first (an allocation never happens mid-stream).
+mvn_status ws_reserve(mvn_ctx* ctx, size_t bytes);
+// Carve slices out of the reserved arena in order.
+struct WsCarver {
+    char* base;
+    size_t off = 0;
+    explicit WsCarver(void* b) : base((char*)b) {}
+    template <class T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = (T*)(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+static inline size_t ws_round(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
+
+// Ensure ctx->d_alpha holds the lattice generators of at least n dimensions.
+mvn_status lattice_ensure(mvn_ctx* ctx, int n);
+// Fill delta[q * n + i] = SplitMix64(seed, q * 2^32 + i) on the device.
+mvn_status lattice_shifts(mvn_ctx* ctx, uint64_t seed, int M, int n, uint64_t* delta);
+
+// Raise an error code in the device status word (first error wins).
+__device__ __forceinline__ void dev_raise(int* status, int code, int info) {
+    if (atomicCAS(status, 0, code) == 0 && info) status[1] = info;
+}
+
+// ---------------------------------------------------------------- lattice point (device)
+// w = ((W >> 11) + 1/2) 2^-53,  W = j * alpha + delta (mod 2^64)
+__device__ __forceinline__ double lattice_w(uint64_t j, uint64_t alpha, uint64_t delta) {
+    uint64_t W = j * alpha + delta;
+    return ((double)(W >> 11) + 0.5) * 0x1p-53;
+}
+
+// SplitMix64 output for counter c under key `seed` (Steele, Lea, Flood 2014).
+__host__ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t c) {
+    uint64_t z = seed + (c + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------------- launch helpers (host)
+mvn_status sov_reduce_launch(mvn_ctx* ctx, const double* logw, int64_t Ns, int M, double err_k,
+                             double* out3, int nprob, int64_t prob_stride);

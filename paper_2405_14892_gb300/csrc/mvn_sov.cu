@@ -1,0 +1,549 @@
+// mvn_sov.cu -- blocked SOV sweep (Eqs. 2-3, Algs. 2-3) on CUDA cores: FP64 path and the
+// FP32-SIMT mixed path, the log-domain reduction (Alg. 2 "mean(p)"), the batched launch and the
+// prefix recording used by the confidence-region loop (Alg. 1).
+//
+// Design (GB300): the only parallel axis of the method is the path (lattice point) axis
+// (Sec. IV-C: dimensions depend on each other in sequence).  One CTA owns a tile of 128 paths,
+// one path per thread, and walks all n dimensions in blocks of B.  For block r it forms the limit
+// shift s = L(r, 0:r) y(0:r) of Alg. 2's GEMM step (c) from its own earlier y values (left-looking,
+// one shift for both limits instead of separate A and B updates), then runs Alg. 3 on the
+// diagonal block with the y values in registers.  Tiles are independent, so a persistent grid
+// takes (problem, tile) items from a queue ordered longest first; no CTA ever waits on another.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "mvn_internal.cuh"
+#include "mvn_sov.cuh"
+
+#define SOV_P 128
+
+// ---------------------------------------------------------------- FP64 elementwise step
+
+__device__ __forceinline__ double Phi_d(double x) { return 0.5 * erfc(-x * 0.70710678118654752440); }
+__device__ __forceinline__ double Q_d(double x) { return 0.5 * erfc(x * 0.70710678118654752440); }
+// keep the argument of Phi^-1 strictly inside (0,1) (rounding can reach 0 or 1 exactly)
+__device__ __forceinline__ double interior_d(double p) {
+    return p <= 0.0 ? 4.9406564584124654e-324 : (p >= 1.0 ? 0.99999999999999988898 : p);
+}
+
+// One dimension of Eq. 2 in FP64 with the tail-stable branches:
+//   a' > 0 : Delta = Q(a') - Q(b'),   y = -Phi^-1(Q(a') - w Delta)
+//   else   : Delta = Phi(b') - Phi(a'), y =  Phi^-1(Phi(a') + w Delta)
+// Delta == 0 gives y = the finite limit.  Returns y, writes Delta.
+__device__ __forceinline__ double sov_step_f64(double ai, double bi, double s, double lii,
+                                               double w, double& delta) {
+    const double ap = (ai - s) / lii, bp = (bi - s) / lii;
+    double y;
+    if (ap > 0.0) {
+        const double qa = Q_d(ap);
+        const double qb = (bp == INFINITY) ? 0.0 : Q_d(bp);
+        delta = qa - qb;
+        y = (delta > 0.0) ? -normcdfinv(interior_d(qa - w * delta)) : ap;
+    } else {
+        const double pa = (ap == -INFINITY) ? 0.0 : Phi_d(ap);
+        const double pb = (bp == INFINITY) ? 1.0 : Phi_d(bp);
+        delta = pb - pa;
+        y = (delta > 0.0) ? normcdfinv(interior_d(pa + w * delta)) : bp;
+    }
+    return y;
+}
+
+// Running product of the Delta factors as prod * 2^ex (log only at the end / at prefixes).
+struct LogProd {
+    double prod = 1.0;
+    int ex = 0;
+    __device__ __forceinline__ void mul(double d) {
+        if (d < 0x1p-400) {
+            if (!(d > 0.0)) {
+                prod = 0.0;
+                return;
+            }
+            int e;
+            d = frexp(d, &e);
+            ex += e;
+        }
+        prod *= d;
+        if (prod < 0x1p-400 && prod > 0.0) {
+            int e;
+            prod = frexp(prod, &e);
+            ex += e;
+        }
+    }
+    __device__ __forceinline__ double log_value() const {
+        return prod > 0.0 ? log(prod) + (double)ex * 0.69314718055994530942 : -INFINITY;
+    }
+};
+
+// Out-of-line FP64 step for the rare fallbacks of the FP32 step (keeps the unrolled sweep small).
+__device__ __noinline__ float sov_step_f64_slow(double ai, double bi, double s, double lii,
+                                                double w, double* delta) {
+    return (float)sov_step_f64(ai, bi, s, lii, w, *delta);
+}
+
+// ---------------------------------------------------------------- FP32 elementwise step (mixed)
+// Phi, Q and Phi^-1 in FP32 (CUDA erfcf / normcdfinvf) away from the deep tails; the deep tails
+// (where FP32 would underflow or lose relative accuracy) and two-sided finite intervals (where
+// Phi(b') - Phi(a') cancels) are evaluated by the FP64 step.
+__device__ __forceinline__ float sov_step_f32(double ai, double bi, float s, float lii, float w,
+                                              double& delta) {
+    const bool ainf = (ai == -INFINITY), binf = (bi == INFINITY);
+    if (!ainf && !binf) return sov_step_f64_slow(ai, bi, (double)s, (double)lii, (double)w, &delta);
+    if (ainf && binf) {
+        delta = 1.0;
+        return normcdfinvf(w);
+    }
+    if (ainf) {  // Delta = Phi(b'),  y = Phi^-1(w Phi(b'))
+        const float bp = ((float)bi - s) / lii;
+        if (bp > -9.0f) {
+            const float pb = 0.5f * erfcf(-bp * 0.70710678f);
+            const float p = w * pb;
+            delta = (double)pb;
+            if (p > 1e-30f) return normcdfinvf(fminf(p, 0.99999994f));
+        }
+        return sov_step_f64_slow(ai, bi, (double)s, (double)lii, (double)w, &delta);
+    }
+    // b = +inf:  a' > 0: Delta = Q(a'), y = -Phi^-1(Q(a')(1-w));  else Delta = 1 - Phi(a')
+    const float ap = ((float)ai - s) / lii;
+    if (ap < 9.0f) {
+        if (ap > 0.0f) {
+            const float qa = 0.5f * erfcf(ap * 0.70710678f);
+            const float qq = qa * (1.0f - w);
+            delta = (double)qa;
+            if (qq > 1e-30f) return -normcdfinvf(qq);
+        } else {
+            const float pa = 0.5f * erfcf(-ap * 0.70710678f);
+            const float dd = 1.0f - pa;
+            delta = (double)dd;
+            return normcdfinvf(fminf(pa + w * dd, 0.99999994f));
+        }
+    }
+    return sov_step_f64_slow(ai, bi, (double)s, (double)lii, (double)w, &delta);
+}
+
+// ---------------------------------------------------------------- tile sweep
+
+template <int B, typename T>
+struct SovSmem {
+    T Lk[B][B];       // GEMM operand: Lk[kk][v] = L(r0+v, k0+kk)
+    T Ld[B][B + 1];   // diagonal block: Ld[v][u] = L(r0+v, r0+u), u <= v
+    double a[B], b[B];
+    uint64_t alpha[B];
+};
+
+// Sweep one tile of 128 paths of problem P through all n dimensions.
+// T = working type of the limit GEMM and of the stored y (double: FP64 path; float: mixed).
+template <int B, typename T, bool ELEM64>
+__device__ void sov_tile(const SovProblem& P, int tile, const uint64_t* __restrict__ alpha,
+                         T* __restrict__ Ycta, SovSmem<B, T>& sm) {
+    const int t = threadIdx.x;
+    const int n = P.n;
+    const int64_t p = (int64_t)tile * SOV_P + t;
+    const bool valid = p < P.Ntot;
+    const int64_t q = valid ? p / P.Ns : 0;
+    const uint64_t j = valid ? (uint64_t)(p - q * P.Ns) + 1u : 1u;
+    const uint64_t* __restrict__ dq = P.delta + q * P.dstride;
+    const double* __restrict__ L = P.L;
+    const int64_t ld = P.ld;
+    LogProd lp;
+    int pf = 0;
+    int next_k = (P.nprefix > 0) ? P.prefix[0] : -1;
+
+    for (int r0 = 0; r0 < n; r0 += B) {
+        const int nb = min(B, n - r0);
+        T acc[B];
+#pragma unroll
+        for (int v = 0; v < B; ++v) acc[v] = (T)0;
+        // limit shift from earlier blocks: acc[v] = sum_{k < r0} L(r0+v, k) y_k  (Alg. 2 (c))
+        for (int k0 = 0; k0 < r0; k0 += B) {
+            __syncthreads();
+            for (int e = t; e < B * B; e += SOV_P) {
+                const int v = e % B, kk = e / B;
+                const int row = r0 + v;
+                sm.Lk[kk][v] = (row < n) ? (T)L[row + (int64_t)(k0 + kk) * ld] : (T)0;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < B; ++kk) {
+                const T yk = Ycta[(int64_t)(k0 + kk) * SOV_P + t];
+#pragma unroll
+                for (int v = 0; v < B; ++v) acc[v] = fma(sm.Lk[kk][v], yk, acc[v]);
+            }
+        }
+        // diagonal block (Alg. 3)
+        __syncthreads();
+        for (int e = t; e < B * B; e += SOV_P) {
+            const int v = e % B, u = e / B;
+            sm.Ld[v][u] = (v < nb && u <= v) ? (T)L[(r0 + v) + (int64_t)(r0 + u) * ld] : (T)0;
+        }
+        if (t < B) {
+            sm.a[t] = (t < nb) ? P.a[r0 + t] : 0.0;
+            sm.b[t] = (t < nb) ? P.b[r0 + t] : 1.0;
+            sm.alpha[t] = (t < nb) ? alpha[r0 + t] : 0u;
+        }
+        __syncthreads();
+        T y[B];
+#pragma unroll
+        for (int v = 0; v < B; ++v) {
+            if (v < nb) {
+                T s = acc[v];
+#pragma unroll
+                for (int u = 0; u < v; ++u) s = fma(sm.Ld[v][u], y[u], s);
+                const double w = lattice_w(j, sm.alpha[v], dq[r0 + v]);
+                double delta;
+                if constexpr (ELEM64) {
+                    y[v] = (T)sov_step_f64(sm.a[v], sm.b[v], (double)s, (double)sm.Ld[v][v], w,
+                                           delta);
+                } else {
+                    y[v] = (T)sov_step_f32(sm.a[v], sm.b[v], (float)s, (float)sm.Ld[v][v],
+                                           (float)w, delta);
+                }
+                lp.mul(delta);
+                if (valid) Ycta[(int64_t)(r0 + v) * SOV_P + t] = y[v];
+                while (next_k == r0 + v + 1) {
+                    if (valid) P.logw_prefix[(int64_t)pf * P.Ntot + p] = lp.log_value();
+                    ++pf;
+                    next_k = (pf < P.nprefix) ? P.prefix[pf] : -1;
+                }
+            } else {
+                y[v] = (T)0;
+            }
+        }
+    }
+    if (valid && P.logw) P.logw[p] = lp.log_value();
+}
+
+struct SovBatch {
+    SovProblem single;               // used when probs == nullptr (item it -> tile it)
+    const SovProblem* probs;         // batched: problem table
+    const int2* items;               // batched: (problem, tile), longest problems first
+    int nitems;
+    int* counter;                    // work-queue head (zeroed before the launch)
+};
+
+template <int B, typename T, bool ELEM64>
+__global__ void __launch_bounds__(SOV_P) k_sov_simt(const SovBatch batch,
+                                                    const uint64_t* __restrict__ alpha,
+                                                    T* __restrict__ Yscratch, int64_t ystride) {
+    __shared__ SovSmem<B, T> sm;
+    __shared__ int s_item;
+    T* Ycta = Yscratch + (int64_t)blockIdx.x * ystride;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(batch.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= batch.nitems) break;
+        if (batch.probs == nullptr) {
+            sov_tile<B, T, ELEM64>(batch.single, it, alpha, Ycta, sm);
+        } else {
+            const int2 item = batch.items[it];
+            sov_tile<B, T, ELEM64>(batch.probs[item.x], item.y, alpha, Ycta, sm);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- reduction (Alg. 2 mean(p))
+
+// One block per problem: log P_q = LSE_j(logw_qj) - log Ns per shift q; log P = LSE_q - log M;
+// P = exp(log P); err = err_k sd_q(P_q) / sqrt(M) (computed relative to P, then scaled).
+// Fixed reduction order (deterministic).  Raises MVN_ERR_NUMERIC if every weight is 0.
+__global__ void k_sov_reduce(const double* __restrict__ logw, int64_t Ns, int M, double err_k,
+                             double* __restrict__ out3, int64_t prob_stride, int* status,
+                             int raise_numeric) {
+    extern __shared__ double red[];  // blockDim.x + M
+    double* lq = red + blockDim.x;
+    const int t = threadIdx.x, nt = blockDim.x;
+    const double* lw = logw + (int64_t)blockIdx.x * prob_stride;
+    for (int qq = 0; qq < M; ++qq) {
+        const double* r = lw + (int64_t)qq * Ns;
+        double m = -INFINITY;
+        for (int64_t k = t; k < Ns; k += nt) m = fmax(m, r[k]);
+        red[t] = m;
+        __syncthreads();
+        for (int w = nt / 2; w > 0; w >>= 1) {
+            if (t < w) red[t] = fmax(red[t], red[t + w]);
+            __syncthreads();
+        }
+        m = red[0];
+        __syncthreads();
+        double s = 0.0;
+        if (m > -INFINITY)
+            for (int64_t k = t; k < Ns; k += nt) s += exp(r[k] - m);
+        red[t] = s;
+        __syncthreads();
+        for (int w = nt / 2; w > 0; w >>= 1) {
+            if (t < w) red[t] += red[t + w];
+            __syncthreads();
+        }
+        if (t == 0) lq[qq] = (m > -INFINITY) ? m + log(red[0]) - log((double)Ns) : -INFINITY;
+        __syncthreads();
+    }
+    if (t == 0) {
+        double m = -INFINITY;
+        for (int qq = 0; qq < M; ++qq) m = fmax(m, lq[qq]);
+        double* o = out3 + 3 * blockIdx.x;
+        if (!(m > -INFINITY)) {
+            o[0] = -INFINITY;
+            o[1] = 0.0;
+            o[2] = 0.0;
+            if (raise_numeric) dev_raise(status, MVN_ERR_NUMERIC, 0);
+        } else {
+            double s = 0.0;
+            for (int qq = 0; qq < M; ++qq) s += exp(lq[qq] - m);
+            const double logP = m + log(s) - log((double)M);
+            double mean = 0.0;
+            for (int qq = 0; qq < M; ++qq) mean += exp(lq[qq] - logP);
+            mean /= M;
+            double ss = 0.0;
+            for (int qq = 0; qq < M; ++qq) {
+                double d = exp(lq[qq] - logP) - mean;
+                ss += d * d;
+            }
+            const double sd_rel = (M > 1) ? sqrt(ss / (M - 1)) : 0.0;
+            const double P = exp(logP);
+            o[0] = logP;
+            o[1] = P;
+            o[2] = err_k * sd_rel / sqrt((double)M) * P;
+        }
+    }
+}
+
+mvn_status sov_reduce_launch_opt(mvn_ctx* ctx, const double* logw, int64_t Ns, int M,
+                                 double err_k, double* out3, int nprob, int64_t prob_stride,
+                                 bool raise_numeric) {
+    if (nprob <= 0) return MVN_OK;
+    const int nt = 512;
+    k_sov_reduce<<<nprob, nt, sizeof(double) * (nt + M), ctx->stream>>>(
+        logw, Ns, M, err_k, out3, prob_stride, ctx->d_status, raise_numeric ? 1 : 0);
+    MVN_LAUNCHED(ctx);
+    return MVN_OK;
+}
+
+mvn_status sov_reduce_launch(mvn_ctx* ctx, const double* logw, int64_t Ns, int M, double err_k,
+                             double* out3, int nprob, int64_t prob_stride) {
+    return sov_reduce_launch_opt(ctx, logw, Ns, M, err_k, out3, nprob, prob_stride, true);
+}
+
+// ---------------------------------------------------------------- host side
+
+mvn_status check_qmc(mvn_ctx* ctx, const mvn_qmc* qmc) {
+    if (!qmc || qmc->n_points < 1 || qmc->n_shifts < 1 || qmc->n_shifts > 4096 ||
+        (int64_t)qmc->n_points * qmc->n_shifts > ((int64_t)1 << 36))
+        return mvn_fail(ctx, MVN_ERR_ARG,
+                        "invalid QMC rule (n_points >= 1, 1 <= n_shifts <= 4096, total <= 2^36)");
+    return MVN_OK;
+}
+
+mvn_status check_problem_host(mvn_ctx* ctx, int n, const double* a, const double* b,
+                              const double* L, int64_t ld) {
+    if (n < 0 || n > (1 << 22)) return mvn_fail(ctx, MVN_ERR_ARG, "dimension out of range");
+    if (n > 0 && (!a || !b || !L)) return mvn_fail(ctx, MVN_ERR_ARG, "null pointer");
+    if (ld < (n > 0 ? n : 1)) return mvn_fail(ctx, MVN_ERR_ARG, "ld < n");
+    return MVN_OK;
+}
+
+// a_i <= b_i, no NaN, a_i != +inf, b_i != -inf; a violation raises MVN_ERR_ARG on the device
+__global__ void k_check_limits(int n, const double* a, const double* b, int* status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = a[i], y = b[i];
+    if (!(x <= y) || x == INFINITY || y == -INFINITY) dev_raise(status, MVN_ERR_ARG, i + 1);
+}
+
+mvn_status check_limits_device(mvn_ctx* ctx, int n, const double* a, const double* b) {
+    if (n == 0) return MVN_OK;
+    k_check_limits<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, a, b, ctx->d_status);
+    MVN_LAUNCHED(ctx);
+    return MVN_OK;
+}
+
+static int sov_grid(mvn_ctx* ctx, int64_t ntiles) {
+    const int occ = 2;
+    int64_t g = std::min<int64_t>(ntiles, (int64_t)ctx->sm_count * occ);
+    return (int)std::max<int64_t>(g, 1);
+}
+
+size_t sov_simt_ws_bytes(mvn_ctx* ctx, int nprob, int nmax, int64_t ntiles, mvn_prec prec) {
+    const size_t elt = (prec == MVN_FP64) ? sizeof(double) : sizeof(float);
+    const int grid = sov_grid(ctx, ntiles);
+    size_t b = ws_round(sizeof(int));
+    if (nprob > 1)
+        b += ws_round(sizeof(SovProblem) * nprob) + ws_round(sizeof(int2) * (size_t)ntiles);
+    b += ws_round(elt * (size_t)std::max(nmax, 1) * SOV_P * grid);
+    return b;
+}
+
+mvn_status sov_run_simt(mvn_ctx* ctx, const std::vector<SovProblem>& probs_h, mvn_prec prec,
+                        char* ws) {
+    const int nprob = (int)probs_h.size();
+    int nmax = 0;
+    int64_t ntiles = 0;
+    for (auto& P : probs_h) {
+        nmax = std::max(nmax, P.n);
+        if (P.n > 0) ntiles += (P.Ntot + SOV_P - 1) / SOV_P;
+    }
+    if (ntiles == 0) return MVN_OK;
+    if (ntiles > (1 << 30)) return mvn_fail(ctx, MVN_ERR_ARG, "too many path tiles");
+    const bool f64 = (prec == MVN_FP64);
+    const int grid = sov_grid(ctx, ntiles);
+    const size_t elt = f64 ? sizeof(double) : sizeof(float);
+    const int64_t ystride = (int64_t)std::max(nmax, 1) * SOV_P;
+    WsCarver wc(ws);
+    SovBatch batch;
+    batch.counter = wc.take<int>(1);
+    batch.nitems = (int)ntiles;
+    batch.probs = nullptr;
+    batch.items = nullptr;
+    if (nprob == 1) {
+        batch.single = probs_h[0];
+    } else {
+        memset(&batch.single, 0, sizeof(batch.single));
+        SovProblem* d_probs = wc.take<SovProblem>(nprob);
+        int2* d_items = wc.take<int2>((size_t)ntiles);
+        std::vector<int> order(nprob);
+        for (int i = 0; i < nprob; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return probs_h[x].n > probs_h[y].n; });
+        std::vector<int2> items;
+        items.reserve((size_t)ntiles);
+        for (int pi : order) {
+            if (probs_h[pi].n == 0) continue;
+            int64_t nt = (probs_h[pi].Ntot + SOV_P - 1) / SOV_P;
+            for (int64_t tt = 0; tt < nt; ++tt) items.push_back(make_int2(pi, (int)tt));
+        }
+        // pageable copies: staged before returning, so the host vectors may go out of scope
+        MVN_CUDA(ctx, cudaMemcpyAsync(d_probs, probs_h.data(), sizeof(SovProblem) * nprob,
+                                      cudaMemcpyHostToDevice, ctx->stream));
+        MVN_CUDA(ctx, cudaMemcpyAsync(d_items, items.data(), sizeof(int2) * items.size(),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+        batch.probs = d_probs;
+        batch.items = d_items;
+    }
+    void* d_Y = wc.take<char>(elt * (size_t)ystride * grid);
+    MVN_CUDA(ctx, cudaMemsetAsync(batch.counter, 0, sizeof(int), ctx->stream));
+    if (f64) {
+        k_sov_simt<32, double, true><<<grid, SOV_P, 0, ctx->stream>>>(batch, ctx->d_alpha,
+                                                                       (double*)d_Y, ystride);
+    } else {
+        k_sov_simt<64, float, false><<<grid, SOV_P, 0, ctx->stream>>>(batch, ctx->d_alpha,
+                                                                       (float*)d_Y, ystride);
+    }
+    MVN_LAUNCHED(ctx);
+    return MVN_OK;
+}
+
+size_t sov_any_ws_bytes(mvn_ctx* ctx, int nprob, int nmax, int64_t ntiles, mvn_prec prec) {
+    return sov_simt_ws_bytes(ctx, nprob, nmax, ntiles, prec);
+}
+
+mvn_status sov_run_any(mvn_ctx* ctx, const std::vector<SovProblem>& probs, mvn_prec prec,
+                       char* ws) {
+    return sov_run_simt(ctx, probs, prec, ws);
+}
+
+// ---------------------------------------------------------------- ABI: mvn_sov
+
+extern "C" mvn_status mvn_sov(mvn_ctx* ctx, int n, const double* a, const double* b,
+                              const double* L, int64_t ld, const mvn_qmc* qmc, mvn_prec prec,
+                              double* out3, double* path_logw) {
+    if (!ctx) return MVN_ERR_ARG;
+    MVN_TRY(check_qmc(ctx, qmc));
+    MVN_TRY(check_problem_host(ctx, n, a, b, L, ld));
+    if (!out3) return mvn_fail(ctx, MVN_ERR_ARG, "out3 is null");
+    if (prec != MVN_FP64 && prec != MVN_MIXED && prec != MVN_MIXED_SIMT)
+        return mvn_fail(ctx, MVN_ERR_ARG, "unknown precision");
+    MVN_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int M = qmc->n_shifts;
+    const int64_t Ns = qmc->n_points, Ntot = Ns * M;
+    MVN_TRY(lattice_ensure(ctx, std::max(n, 1)));
+    std::vector<SovProblem> probs(1);
+    SovProblem& P = probs[0];
+    const size_t need = ws_round(sizeof(uint64_t) * (size_t)M * std::max(n, 1)) +
+                        (path_logw ? 0 : ws_round(sizeof(double) * (size_t)Ntot)) +
+                        sov_any_ws_bytes(ctx, 1, n, (Ntot + 127) / 128, prec) + 1024;
+    MVN_TRY(ws_reserve(ctx, need));
+    WsCarver wc(ctx->ws);
+    uint64_t* delta = wc.take<uint64_t>((size_t)M * std::max(n, 1));
+    double* logw = path_logw ? path_logw : wc.take<double>((size_t)Ntot);
+    P.n = n;
+    P.M = M;
+    P.Ns = Ns;
+    P.Ntot = Ntot;
+    P.a = a;
+    P.b = b;
+    P.L = L;
+    P.ld = ld;
+    P.delta = delta;
+    P.dstride = std::max(n, 1);
+    P.logw = logw;
+    P.nprefix = 0;
+    P.prefix = nullptr;
+    P.logw_prefix = nullptr;
+    MVN_TRY(check_limits_device(ctx, n, a, b));
+    MVN_TRY(lattice_shifts(ctx, qmc->seed, M, n, delta));
+    if (n == 0) {
+        MVN_CUDA(ctx, cudaMemsetAsync(logw, 0, sizeof(double) * Ntot, ctx->stream));
+    } else {
+        MVN_TRY(sov_run_any(ctx, probs, prec, wc.base + ((wc.off + 255) & ~(size_t)255)));
+    }
+    return sov_reduce_launch(ctx, logw, Ns, M, qmc->err_k, out3, 1, Ntot);
+}
+
+// ---------------------------------------------------------------- ABI: mvn_sov_batched
+
+extern "C" mvn_status mvn_sov_batched(mvn_ctx* ctx, int nprob, const int* dims,
+                                      const int64_t* limit_offsets, const double* a,
+                                      const double* b, const double* L_shared, int64_t ld,
+                                      const mvn_qmc* qmc, mvn_prec prec, double* out3) {
+    if (!ctx) return MVN_ERR_ARG;
+    MVN_TRY(check_qmc(ctx, qmc));
+    if (nprob < 0 || (nprob > 0 && (!dims || !limit_offsets || !out3)))
+        return mvn_fail(ctx, MVN_ERR_ARG, "invalid problem list");
+    if (nprob == 0) return MVN_OK;
+    int nmax = 0;
+    for (int p = 0; p < nprob; ++p) {
+        if (dims[p] < 0 || limit_offsets[p] < 0)
+            return mvn_fail(ctx, MVN_ERR_ARG, "negative dimension or offset");
+        nmax = std::max(nmax, dims[p]);
+    }
+    MVN_TRY(check_problem_host(ctx, nmax, a, b, L_shared, ld));
+    MVN_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int M = qmc->n_shifts;
+    const int64_t Ns = qmc->n_points, Ntot = Ns * M;
+    MVN_TRY(lattice_ensure(ctx, std::max(nmax, 1)));
+    int64_t ntiles = 0;
+    for (int p = 0; p < nprob; ++p)
+        if (dims[p] > 0) ntiles += (Ntot + 127) / 128;
+    const size_t need = ws_round(sizeof(uint64_t) * (size_t)M * std::max(nmax, 1)) +
+                        ws_round(sizeof(double) * (size_t)Ntot * nprob) +
+                        sov_any_ws_bytes(ctx, nprob, nmax, ntiles, prec) + 1024;
+    MVN_TRY(ws_reserve(ctx, need));
+    WsCarver wc(ctx->ws);
+    uint64_t* delta = wc.take<uint64_t>((size_t)M * std::max(nmax, 1));
+    double* logw = wc.take<double>((size_t)Ntot * nprob);
+    std::vector<SovProblem> probs(nprob);
+    for (int p = 0; p < nprob; ++p) {
+        SovProblem& P = probs[p];
+        P.n = dims[p];
+        P.M = M;
+        P.Ns = Ns;
+        P.Ntot = Ntot;
+        P.a = a + limit_offsets[p];
+        P.b = b + limit_offsets[p];
+        P.L = L_shared;
+        P.ld = ld;
+        P.delta = delta;  // the shifts of dimension i do not depend on the problem
+        P.dstride = std::max(nmax, 1);
+        P.logw = logw + (int64_t)p * Ntot;
+        P.nprefix = 0;
+        P.prefix = nullptr;
+        P.logw_prefix = nullptr;
+        if (P.n == 0) MVN_CUDA(ctx, cudaMemsetAsync(P.logw, 0, sizeof(double) * Ntot, ctx->stream));
+    }
+    MVN_TRY(lattice_shifts(ctx, qmc->seed, M, nmax, delta));
+    MVN_TRY(sov_run_any(ctx, probs, prec, wc.base + ((wc.off + 255) & ~(size_t)255)));
+    return sov_reduce_launch(ctx, logw, Ns, M, qmc->err_k, out3, nprob, Ntot);
+}

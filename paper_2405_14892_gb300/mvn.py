@@ -1,0 +1,323 @@
+"""ctypes binding of libmvn.so (include/mvn.h) with the same entry-point names.
+
+Argument marshalling only: every step of the computation runs in the library's CUDA kernels.
+Matrices are FP64 torch CUDA tensors in column-major storage (``stride(0) == 1``; a tensor made
+with ``colmajor_empty(n, n)`` or ``x.t().contiguous().t()``), vectors are contiguous FP64 CUDA
+tensors.  Calls enqueue on torch's current CUDA stream.  There is no CPU fallback: if the library
+is missing or the tensors are not on a CUDA device, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmvn.so")
+
+MVN_OK, MVN_ERR_ARG, MVN_ERR_NOT_PD, MVN_ERR_CUDA, MVN_ERR_OOM, MVN_ERR_TIMEOUT, \
+    MVN_ERR_NUMERIC, MVN_ERR_NOT_IMPLEMENTED = range(8)
+STATUS_NAMES = {0: "MVN_OK", 1: "MVN_ERR_ARG", 2: "MVN_ERR_NOT_PD", 3: "MVN_ERR_CUDA",
+                4: "MVN_ERR_OOM", 5: "MVN_ERR_TIMEOUT", 6: "MVN_ERR_NUMERIC",
+                7: "MVN_ERR_NOT_IMPLEMENTED"}
+PREC = {"fp64": 0, "mixed": 1, "mixed_simt": 2}
+
+
+class MVNError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class mvn_qmc(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_shifts", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("err_k", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# exported symbol -> (restype, argtypes)
+_P, _I, _I64, _D, _U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, \
+    ctypes.c_uint64
+_QP = ctypes.POINTER(mvn_qmc)
+SIGNATURES = {
+    "mvn_create": (_I, [ctypes.POINTER(_P), _I, _P]),
+    "mvn_destroy": (_I, [_P]),
+    "mvn_set_stream": (_I, [_P, _P]),
+    "mvn_last_error": (ctypes.c_char_p, [_P]),
+    "mvn_sync": (_I, [_P, ctypes.POINTER(_I)]),
+    "mvn_launch_count": (_I64, [_P]),
+    "mvn_matern": (_I, [_P, _I, _P, _D, _D, _D, _D, _P, _I64]),
+    "mvn_matern_grad": (_I, [_P, _I, _P, _D, _D, _D, _P, _I64, _P]),
+    "mvn_cholesky": (_I, [_P, _I, _P, _I64, _I, _I, ctypes.POINTER(_I)]),
+    "mvn_cholesky_grad": (_I, [_P, _I, _P, _I64, _P]),
+    "mvn_sov": (_I, [_P, _I, _P, _P, _P, _I64, _QP, _I, _P, _P]),
+    "mvn_sov_grad": (_I, [_P, _I, _P, _P, _P, _I64, _QP, _I, _P, _P, _P, _P]),
+    "mvn_sov_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _I64, _QP, _I, _P]),
+    "mvn_excursion": (_I, [_P, _I, _P, _P, _I64, _D, _D, _I, _P, _QP, _I, _I, _P, _P, _P, _P]),
+    "mvn_tlr_compress": (_I, [_P, _I, _P, _I64, _I, _D, _I, ctypes.POINTER(_P),
+                              ctypes.POINTER(_I)]),
+    "mvn_tlr_cholesky": (_I, [_P, _P, ctypes.POINTER(_I)]),
+    "mvn_tlr_to_dense": (_I, [_P, _P, _P, _I64]),
+    "mvn_tlr_ranks": (_I, [_P, _P]),
+    "mvn_tlr_free": (_I, [_P]),
+    "mvn_lattice_alpha": (_I, [_P, _I, _P]),
+    "mvn_lattice_shifts": (_I, [_P, _U64, _I, _I, _P]),
+}
+
+
+def lib():
+    """Load libmvn.so (built by ``paper_2405_14892_gb300.build``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(LIB_PATH):
+                    raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build()")
+                L = ctypes.CDLL(LIB_PATH)
+                for name, (res, args) in SIGNATURES.items():
+                    f = getattr(L, name)
+                    f.restype = res
+                    f.argtypes = args
+                _lib = L
+    return _lib
+
+
+class Context:
+    """An mvn_ctx bound to one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("CUDA is not available: the MVN library has no CPU path")
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = _P()
+        st = lib().mvn_create(ctypes.byref(h), device, _P(self.stream.cuda_stream))
+        if st != MVN_OK:
+            raise MVNError(st, "mvn_create failed")
+        self.h = h
+
+    def check(self, st: int):
+        if st != MVN_OK:
+            raise MVNError(st, lib().mvn_last_error(self.h).decode())
+
+    def sync(self) -> tuple[int, int]:
+        info = _I(0)
+        st = lib().mvn_sync(self.h, ctypes.byref(info))
+        return st, info.value
+
+    def launches(self) -> int:
+        return int(lib().mvn_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mvn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_contexts: dict = {}
+
+
+def context(device: int | None = None) -> Context:
+    """The cached context of the current device and current torch stream."""
+    if device is None:
+        device = torch.cuda.current_device()
+    s = torch.cuda.current_stream(device)
+    key = (device, s.cuda_stream)
+    c = _contexts.get(key)
+    if c is None:
+        c = Context(device, s)
+        _contexts[key] = c
+    return c
+
+
+# ------------------------------------------------------------------------- tensor helpers
+
+def colmajor_empty(rows: int, cols: int, device="cuda") -> torch.Tensor:
+    """An uninitialised FP64 (rows x cols) tensor with column-major storage."""
+    return torch.empty((cols, rows), dtype=torch.float64, device=device).t()
+
+
+def to_colmajor(x: torch.Tensor) -> torch.Tensor:
+    return x.to(torch.float64).t().contiguous().t()
+
+
+def _mat(x: torch.Tensor, n: int, name: str):
+    if not x.is_cuda or x.dtype != torch.float64:
+        raise ValueError(f"{name} must be a CUDA float64 tensor")
+    if x.dim() != 2 or x.shape[0] < n or x.shape[1] < n:
+        raise ValueError(f"{name} must be at least {n} x {n}")
+    if n > 0 and x.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1)")
+    ld = max(x.stride(1), 1) if n > 0 else 1
+    return _P(x.data_ptr()), ld
+
+
+def _vec(x: torch.Tensor | None, n: int, name: str, dtype=torch.float64):
+    if x is None:
+        return None
+    if not x.is_cuda or x.dtype != dtype or not x.is_contiguous() or x.numel() < n:
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor with >= {n} elements")
+    return _P(x.data_ptr())
+
+
+def _qmc(n_points: int, n_shifts: int, seed: int, err_k: float = 3.0) -> mvn_qmc:
+    return mvn_qmc(int(n_points), int(n_shifts), 0, int(seed) & ((1 << 64) - 1), float(err_k))
+
+
+# ------------------------------------------------------------------------- entry points
+
+def mvn_matern(coords: torch.Tensor, sigma2: float, rng: float, nu: float, nugget: float = 0.0,
+               out: torch.Tensor | None = None) -> torch.Tensor:
+    """Lower triangle of the Matern covariance (Eq. 6) into a column-major n x n tensor."""
+    n = coords.shape[0]
+    if out is None:
+        out = colmajor_empty(n, n, coords.device)
+    S, ld = _mat(out, n, "out")
+    c = context()
+    c.check(lib().mvn_matern(c.h, n, _vec(coords.contiguous(), 2 * n, "coords"), sigma2, rng, nu,
+                             nugget, S, ld))
+    return out
+
+
+def mvn_matern_grad(coords, sigma2, rng, nu, Sbar: torch.Tensor) -> torch.Tensor:
+    n = coords.shape[0]
+    out = torch.empty(2, dtype=torch.float64, device=coords.device)
+    S, ld = _mat(Sbar, n, "Sbar")
+    c = context()
+    c.check(lib().mvn_matern_grad(c.h, n, _vec(coords.contiguous(), 2 * n, "coords"), sigma2, rng,
+                                  nu, S, ld, _P(out.data_ptr())))
+    return out
+
+
+def mvn_cholesky(A: torch.Tensor, prec: str = "fp64", tile: int = 0, check: bool = True) -> int:
+    """In-place lower Cholesky of a column-major FP64 CUDA matrix.  With check=True the call
+    waits and returns the LAPACK-style info (raising MVNError on a non-positive pivot)."""
+    n = A.shape[0]
+    P, ld = _mat(A, n, "A")
+    c = context()
+    info = _I(0)
+    st = lib().mvn_cholesky(c.h, n, P, ld, tile, PREC[prec], ctypes.byref(info) if check else None)
+    c.check(st)
+    return info.value
+
+
+def mvn_cholesky_grad(L: torch.Tensor, Lbar: torch.Tensor) -> torch.Tensor:
+    n = L.shape[0]
+    Lp, ld = _mat(L, n, "L")
+    Gp, ldg = _mat(Lbar, n, "Lbar")
+    if ldg != ld:
+        raise ValueError("L and Lbar must have the same leading dimension")
+    c = context()
+    c.check(lib().mvn_cholesky_grad(c.h, n, Lp, ld, Gp))
+    return Lbar
+
+
+def mvn_sov(a: torch.Tensor, b: torch.Tensor, L: torch.Tensor, n_points: int, n_shifts: int,
+            seed: int, prec: str = "fp64", err_k: float = 3.0,
+            path_logw: torch.Tensor | None = None, out3: torch.Tensor | None = None):
+    """{log P-hat, P-hat, err} (device tensor of 3) for P(a <= X <= b), X ~ N(0, L L^T)."""
+    n = a.numel()
+    if out3 is None:
+        out3 = torch.empty(3, dtype=torch.float64, device=a.device)
+    Lp, ld = _mat(L, n, "L")
+    q = _qmc(n_points, n_shifts, seed, err_k)
+    c = context()
+    c.check(lib().mvn_sov(c.h, n, _vec(a, n, "a"), _vec(b, n, "b"), Lp, ld, ctypes.byref(q),
+                          PREC[prec], _vec(out3, 3, "out3"),
+                          _vec(path_logw, n_points * n_shifts, "path_logw")))
+    return out3
+
+
+def mvn_sov_grad(a, b, L, n_points, n_shifts, seed, prec="fp64", err_k=3.0, want_L=False):
+    n = a.numel()
+    out3 = torch.empty(3, dtype=torch.float64, device=a.device)
+    ga = torch.empty(n, dtype=torch.float64, device=a.device)
+    gb = torch.empty(n, dtype=torch.float64, device=a.device)
+    gL = None
+    Lp, ld = _mat(L, n, "L")
+    if want_L:
+        if ld != n:
+            raise ValueError("L must be tightly packed (ld == n) when want_L")
+        gL = colmajor_empty(n, n, a.device)
+    q = _qmc(n_points, n_shifts, seed, err_k)
+    c = context()
+    c.check(lib().mvn_sov_grad(c.h, n, _vec(a, n, "a"), _vec(b, n, "b"), Lp, ld, ctypes.byref(q),
+                               PREC[prec], _P(out3.data_ptr()), _P(ga.data_ptr()),
+                               _P(gb.data_ptr()), _P(gL.data_ptr()) if gL is not None else None))
+    return out3, ga, gb, gL
+
+
+def mvn_sov_batched(dims, offsets, a, b, L, n_points, n_shifts, seed, prec="fp64", err_k=3.0):
+    """Independent problems (dims[p], limits a[off_p:off_p+dims[p]]) sharing the leading blocks
+    of L; returns a (nprob, 3) device tensor of {log P-hat, P-hat, err}."""
+    nprob = len(dims)
+    d = (ctypes.c_int * nprob)(*[int(x) for x in dims])
+    o = (ctypes.c_int64 * nprob)(*[int(x) for x in offsets])
+    nmax = max([int(x) for x in dims] + [0])
+    Lp, ld = _mat(L, nmax, "L")
+    out = torch.empty((nprob, 3), dtype=torch.float64, device=a.device)
+    q = _qmc(n_points, n_shifts, seed, err_k)
+    c = context()
+    c.check(lib().mvn_sov_batched(c.h, nprob, ctypes.cast(d, _P), ctypes.cast(o, _P),
+                                  _vec(a, 0, "a"), _vec(b, 0, "b"), Lp, ld, ctypes.byref(q),
+                                  PREC[prec], _P(out.data_ptr())))
+    return out
+
+
+def mvn_excursion(mu: torch.Tensor, Sigma: torch.Tensor, u: float, level: float, n_points: int,
+                  n_shifts: int, seed: int, prefix_dims=None, prec="fp64", err_k=3.0):
+    """Confidence region of level `level` above u (Alg. 1).  Returns dict of device tensors:
+    order (int32 n), marginal (n), F (one per prefix), region (uint8 n)."""
+    n = mu.numel()
+    Sp, ld = _mat(Sigma, n, "Sigma")
+    dev = mu.device
+    order = torch.empty(n, dtype=torch.int32, device=dev)
+    marg = torch.empty(n, dtype=torch.float64, device=dev)
+    region = torch.empty(n, dtype=torch.uint8, device=dev)
+    if prefix_dims is None:
+        nprob, pk = n, None
+    else:
+        nprob = len(prefix_dims)
+        pk = (ctypes.c_int * nprob)(*[int(x) for x in prefix_dims])
+    F = torch.empty(nprob, dtype=torch.float64, device=dev)
+    q = _qmc(n_points, n_shifts, seed, err_k)
+    c = context()
+    c.check(lib().mvn_excursion(c.h, n, _vec(mu, n, "mu"), Sp, ld, u, level, nprob,
+                                ctypes.cast(pk, _P) if pk is not None else None, ctypes.byref(q),
+                                PREC[prec], 0, _P(order.data_ptr()), _P(marg.data_ptr()),
+                                _P(F.data_ptr()), _P(region.data_ptr())))
+    return dict(order=order, marginal=marg, F=F, region=region)
+
+
+def mvn_lattice_alpha(n: int) -> torch.Tensor:
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    c = context()
+    c.check(lib().mvn_lattice_alpha(c.h, n, _P(out.data_ptr())))
+    return out
+
+
+def mvn_lattice_shifts(seed: int, M: int, n: int) -> torch.Tensor:
+    out = torch.empty((M, n), dtype=torch.int64, device="cuda")
+    c = context()
+    c.check(lib().mvn_lattice_shifts(c.h, int(seed) & ((1 << 64) - 1), M, n, _P(out.data_ptr())))
+    return out
+
+
+def sync():
+    """Wait for the current context; raise MVNError for a device-side error."""
+    c = context()
+    st, info = c.sync()
+    if st != MVN_OK:
+        raise MVNError(st, lib().mvn_last_error(c.h).decode())
+    return info

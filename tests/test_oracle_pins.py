@@ -160,6 +160,16 @@ def test_matern_bessel_form_matches_closed_forms():
         np.testing.assert_allclose(C, 1.7 * f(h / 0.2), rtol=1e-12, atol=1e-15)
 
 
+def test_matern_closed_vs_bessel_and_lapack_vs_loop():
+    c = inputs.grid_coords(9)
+    for nu in (0.5, 1.5, 2.5):
+        np.testing.assert_allclose(oracle.matern_closed(c, 1.2, 0.3, nu, 1e-3),
+                                   oracle.matern(c, 1.2, 0.3, nu, 1e-3), rtol=1e-12, atol=1e-15)
+    S = oracle.matern(c, 1.0, 0.3, 1.5, 1e-4)
+    np.testing.assert_allclose(oracle.cholesky_lapack(S), oracle.cholesky(S)[0], rtol=1e-9,
+                               atol=1e-12)
+
+
 def test_matern_param_grad_vs_fd():
     c = inputs.random_coords(12, 6)
     for nu in (0.5, 1.5):

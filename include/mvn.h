@@ -189,6 +189,12 @@ mvn_status mvn_lattice_alpha(mvn_ctx* ctx, int n, uint64_t* out);
 /* Write the shifts Delta_{q,i} = SplitMix64(seed, q*2^32 + i) to out[q*n + i] (device, M x n). */
 mvn_status mvn_lattice_shifts(mvn_ctx* ctx, uint64_t seed, int M, int n, uint64_t* out);
 
+/* Self-test of the tensor-core limit-update GEMM used by MVN_MIXED (Alg. 2 step (c)):
+ * S (128 x 64, row-major FP32) = Y (128 x K, row-major FP64) * L (64 x K, row-major FP64)^T,
+ * computed through the same FP16 two-slice split, swizzled tiles, bulk-copy pipeline, tcgen05
+ * MMAs and TMEM read as the sweep.  1 <= K <= 65536.  Asynchronous; errors via mvn_sync. */
+mvn_status mvn_tc_selftest(mvn_ctx* ctx, int K, const double* Y, const double* L, float* S);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,108 +20,7 @@
 
 #define SOV_P 128
 
-// ---------------------------------------------------------------- FP64 elementwise step
-
-__device__ __forceinline__ double Phi_d(double x) { return 0.5 * erfc(-x * 0.70710678118654752440); }
-__device__ __forceinline__ double Q_d(double x) { return 0.5 * erfc(x * 0.70710678118654752440); }
-// keep the argument of Phi^-1 strictly inside (0,1) (rounding can reach 0 or 1 exactly)
-__device__ __forceinline__ double interior_d(double p) {
-    return p <= 0.0 ? 4.9406564584124654e-324 : (p >= 1.0 ? 0.99999999999999988898 : p);
-}
-
-// One dimension of Eq. 2 in FP64 with the tail-stable branches:
-//   a' > 0 : Delta = Q(a') - Q(b'),   y = -Phi^-1(Q(a') - w Delta)
-//   else   : Delta = Phi(b') - Phi(a'), y =  Phi^-1(Phi(a') + w Delta)
-// Delta == 0 gives y = the finite limit.  Returns y, writes Delta.
-__device__ __forceinline__ double sov_step_f64(double ai, double bi, double s, double lii,
-                                               double w, double& delta) {
-    const double ap = (ai - s) / lii, bp = (bi - s) / lii;
-    double y;
-    if (ap > 0.0) {
-        const double qa = Q_d(ap);
-        const double qb = (bp == INFINITY) ? 0.0 : Q_d(bp);
-        delta = qa - qb;
-        y = (delta > 0.0) ? -normcdfinv(interior_d(qa - w * delta)) : ap;
-    } else {
-        const double pa = (ap == -INFINITY) ? 0.0 : Phi_d(ap);
-        const double pb = (bp == INFINITY) ? 1.0 : Phi_d(bp);
-        delta = pb - pa;
-        y = (delta > 0.0) ? normcdfinv(interior_d(pa + w * delta)) : bp;
-    }
-    return y;
-}
-
-// Running product of the Delta factors as prod * 2^ex (log only at the end / at prefixes).
-struct LogProd {
-    double prod = 1.0;
-    int ex = 0;
-    __device__ __forceinline__ void mul(double d) {
-        if (d < 0x1p-400) {
-            if (!(d > 0.0)) {
-                prod = 0.0;
-                return;
-            }
-            int e;
-            d = frexp(d, &e);
-            ex += e;
-        }
-        prod *= d;
-        if (prod < 0x1p-400 && prod > 0.0) {
-            int e;
-            prod = frexp(prod, &e);
-            ex += e;
-        }
-    }
-    __device__ __forceinline__ double log_value() const {
-        return prod > 0.0 ? log(prod) + (double)ex * 0.69314718055994530942 : -INFINITY;
-    }
-};
-
-// Out-of-line FP64 step for the rare fallbacks of the FP32 step (keeps the unrolled sweep small).
-__device__ __noinline__ float sov_step_f64_slow(double ai, double bi, double s, double lii,
-                                                double w, double* delta) {
-    return (float)sov_step_f64(ai, bi, s, lii, w, *delta);
-}
-
-// ---------------------------------------------------------------- FP32 elementwise step (mixed)
-// Phi, Q and Phi^-1 in FP32 (CUDA erfcf / normcdfinvf) away from the deep tails; the deep tails
-// (where FP32 would underflow or lose relative accuracy) and two-sided finite intervals (where
-// Phi(b') - Phi(a') cancels) are evaluated by the FP64 step.
-__device__ __forceinline__ float sov_step_f32(double ai, double bi, float s, float lii, float w,
-                                              double& delta) {
-    const bool ainf = (ai == -INFINITY), binf = (bi == INFINITY);
-    if (!ainf && !binf) return sov_step_f64_slow(ai, bi, (double)s, (double)lii, (double)w, &delta);
-    if (ainf && binf) {
-        delta = 1.0;
-        return normcdfinvf(w);
-    }
-    if (ainf) {  // Delta = Phi(b'),  y = Phi^-1(w Phi(b'))
-        const float bp = ((float)bi - s) / lii;
-        if (bp > -9.0f) {
-            const float pb = 0.5f * erfcf(-bp * 0.70710678f);
-            const float p = w * pb;
-            delta = (double)pb;
-            if (p > 1e-30f) return normcdfinvf(fminf(p, 0.99999994f));
-        }
-        return sov_step_f64_slow(ai, bi, (double)s, (double)lii, (double)w, &delta);
-    }
-    // b = +inf:  a' > 0: Delta = Q(a'), y = -Phi^-1(Q(a')(1-w));  else Delta = 1 - Phi(a')
-    const float ap = ((float)ai - s) / lii;
-    if (ap < 9.0f) {
-        if (ap > 0.0f) {
-            const float qa = 0.5f * erfcf(ap * 0.70710678f);
-            const float qq = qa * (1.0f - w);
-            delta = (double)qa;
-            if (qq > 1e-30f) return -normcdfinvf(qq);
-        } else {
-            const float pa = 0.5f * erfcf(-ap * 0.70710678f);
-            const float dd = 1.0f - pa;
-            delta = (double)dd;
-            return normcdfinvf(fminf(pa + w * dd, 0.99999994f));
-        }
-    }
-    return sov_step_f64_slow(ai, bi, (double)s, (double)lii, (double)w, &delta);
-}
+#include "mvn_sov_step.cuh"
 
 // ---------------------------------------------------------------- tile sweep
 
@@ -197,8 +96,8 @@ __device__ void sov_tile(const SovProblem& P, int tile, const uint64_t* __restri
                     y[v] = (T)sov_step_f64(sm.a[v], sm.b[v], (double)s, (double)sm.Ld[v][v], w,
                                            delta);
                 } else {
-                    y[v] = (T)sov_step_f32(sm.a[v], sm.b[v], (float)s, (float)sm.Ld[v][v],
-                                           (float)w, delta);
+                    y[v] = (T)sov_step_f32(sm.a[v], sm.b[v], (float)s, (float)sm.Ld[v][v], w,
+                                           delta);
                 }
                 lp.mul(delta);
                 if (valid) Ycta[(int64_t)(r0 + v) * SOV_P + t] = y[v];
@@ -436,11 +335,14 @@ mvn_status sov_run_simt(mvn_ctx* ctx, const std::vector<SovProblem>& probs_h, mv
 }
 
 size_t sov_any_ws_bytes(mvn_ctx* ctx, int nprob, int nmax, int64_t ntiles, mvn_prec prec) {
+    // ntiles counts 128-path tiles, the same unit for both sweeps
+    if (prec == MVN_MIXED) return sov_tc_ws_bytes(ctx, nprob, nmax, ntiles);
     return sov_simt_ws_bytes(ctx, nprob, nmax, ntiles, prec);
 }
 
 mvn_status sov_run_any(mvn_ctx* ctx, const std::vector<SovProblem>& probs, mvn_prec prec,
                        char* ws) {
+    if (prec == MVN_MIXED) return sov_run_tc(ctx, probs, ws);
     return sov_run_simt(ctx, probs, prec, ws);
 }
 

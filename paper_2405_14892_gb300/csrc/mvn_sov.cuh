@@ -37,6 +37,10 @@ size_t sov_simt_ws_bytes(mvn_ctx* ctx, int nprob, int nmax, int64_t ntiles, mvn_
 mvn_status sov_run_simt(mvn_ctx* ctx, const std::vector<SovProblem>& probs, mvn_prec prec,
                         char* ws);
 
+// Tensor-core sweep (mvn_sov_tc.cu): all problems must share one factor.
+size_t sov_tc_ws_bytes(mvn_ctx* ctx, int nprob, int nmax, int64_t ntiles);
+mvn_status sov_run_tc(mvn_ctx* ctx, const std::vector<SovProblem>& probs, char* ws);
+
 // Dispatch between the tensor-core sweep (MVN_MIXED) and the CUDA-core sweep.
 size_t sov_any_ws_bytes(mvn_ctx* ctx, int nprob, int nmax, int64_t ntiles, mvn_prec prec);
 mvn_status sov_run_any(mvn_ctx* ctx, const std::vector<SovProblem>& probs, mvn_prec prec,

@@ -67,6 +67,7 @@ SIGNATURES = {
     "mvn_tlr_free": (_I, [_P]),
     "mvn_lattice_alpha": (_I, [_P, _I, _P]),
     "mvn_lattice_shifts": (_I, [_P, _U64, _I, _I, _P]),
+    "mvn_tc_selftest": (_I, [_P, _I, _P, _P, _P]),
 }
 
 
@@ -312,6 +313,17 @@ def mvn_lattice_shifts(seed: int, M: int, n: int) -> torch.Tensor:
     c = context()
     c.check(lib().mvn_lattice_shifts(c.h, int(seed) & ((1 << 64) - 1), M, n, _P(out.data_ptr())))
     return out
+
+
+def mvn_tc_selftest(Y: torch.Tensor, L: torch.Tensor) -> torch.Tensor:
+    """S = Y (128 x K) L (64 x K)^T through the tensor-core path of MVN_MIXED (FP32 result)."""
+    K = Y.shape[1]
+    assert Y.shape == (128, K) and L.shape == (64, K)
+    S = torch.empty((128, 64), dtype=torch.float32, device=Y.device)
+    c = context()
+    c.check(lib().mvn_tc_selftest(c.h, K, _vec(Y.contiguous(), 128 * K, "Y"),
+                                  _vec(L.contiguous(), 64 * K, "L"), _P(S.data_ptr())))
+    return S
 
 
 def sync():

@@ -1,0 +1,118 @@
+"""Tensor-core path (MVN_MIXED): the limit-update GEMM self-test against an FP64 product, and
+the mixed sweep's stated error against the FP64 path/oracle (|d log P| <= 1e-4)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_14892_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mvn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_14892_gb300 import mvn as m
+    return m
+
+
+def _t(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("K", [16, 64, 100, 640, 1000])
+def test_tc_gemm_selftest(mvn, K):
+    rng = np.random.default_rng(K)
+    Y = rng.standard_normal((128, K)) * 1.5
+    # entries spanning the magnitudes of a Cholesky factor (1 down to 1e-9)
+    L = rng.standard_normal((64, K)) * 10.0 ** rng.uniform(-9, 0, (64, K))
+    S = mvn.mvn_tc_selftest(_t(Y), _t(L)).cpu().numpy().astype(np.float64)
+    mvn.sync()
+    ref = Y @ L.T
+    scale = np.abs(Y) @ np.abs(L).T
+    err = np.abs(S - ref) / (scale + 1e-30)
+    # two FP16 slices per operand and FP32 accumulation: ~2^-21 of the absolute-value product
+    assert err.max() < 4e-6, err.max()
+
+
+def _w_case(name, n_override=None):
+    w = dict(inputs.WORKLOADS[name])
+    c = inputs.grid_coords(w["g"])
+    n = c.shape[0]
+    a, b = inputs.limits_for(w, n)
+    S = oracle.matern_closed(c, w["sigma2"], w["range"], w["nu"], w["nugget"])
+    return w, c, a, b, S
+
+
+def test_mixed_tc_error_w4(mvn):
+    w, c, a, b, S = _w_case("W4")
+    Lo = oracle.cholesky_lapack(S)
+    L = mvn.to_colmajor(_t(Lo))
+    Ntot = w["Ns"] * w["M"]
+    lw64 = torch.empty(Ntot, dtype=torch.float64, device="cuda")
+    lwtc = torch.empty(Ntot, dtype=torch.float64, device="cuda")
+    o64 = mvn.mvn_sov(_t(a), _t(b), L, w["Ns"], w["M"], w["seed"], path_logw=lw64).cpu().numpy()
+    otc = mvn.mvn_sov(_t(a), _t(b), L, w["Ns"], w["M"], w["seed"], prec="mixed",
+                      path_logw=lwtc).cpu().numpy()
+    mvn.sync()
+    d = np.abs(lwtc.cpu().numpy() - lw64.cpu().numpy())
+    print(f"W4 mixed (tcgen05): logP64={o64[0]:.8f} dlogP={otc[0] - o64[0]:.3e} "
+          f"per-path median {np.median(d):.3e} max {d.max():.3e}")
+    assert abs(otc[0] - o64[0]) <= 1e-4
+    assert abs(otc[1] - o64[1]) <= 1e-4  # the literal |dP| criterion
+    ref = oracle.sov_logw(a, b, Lo, oracle.QMC(w["Ns"], w["M"], w["seed"]), paths=(0, 8))
+    assert np.all(np.abs(lw64.cpu().numpy()[:8] - ref) <= 1e-9 * np.maximum(1, np.abs(ref)))
+
+
+@pytest.mark.parametrize("n,Ns,M", [(1, 50, 3), (63, 129, 2), (130, 300, 5), (300, 64, 4)])
+def test_mixed_tc_ragged_vs_oracle(mvn, n, Ns, M):
+    g = int(math.ceil(math.sqrt(n)))
+    c = inputs.grid_coords(g)[:n]
+    S = oracle.matern(c, 1.0, 0.15, 0.5, nugget=1e-6)
+    rng = np.random.default_rng(n)
+    a = rng.uniform(-2.5, 0.3, n)
+    b = a + rng.uniform(0.2, 3.0, n)
+    a[::3] = -np.inf
+    b[1::4] = np.inf
+    Lo, _ = oracle.cholesky(S)
+    L = mvn.to_colmajor(_t(Lo))
+    lw = torch.empty(Ns * M, dtype=torch.float64, device="cuda")
+    out = mvn.mvn_sov(_t(a), _t(b), L, Ns, M, 3 + n, prec="mixed", path_logw=lw).cpu().numpy()
+    mvn.sync()
+    ref = oracle.sov_logw(a, b, Lo, oracle.QMC(Ns, M, 3 + n))
+    est = oracle.estimate(ref, M)
+    d = np.abs(lw.cpu().numpy() - ref)
+    assert np.all(np.isfinite(lw.cpu().numpy()))
+    assert abs(out[0] - est[0]) <= 1e-4, (out, est, d.max())
+
+
+def test_mixed_tc_batched_and_excursion(mvn):
+    g = 12
+    c = inputs.grid_coords(g)
+    n = g * g
+    S = oracle.matern(c, 1.0, 0.15, 0.5)
+    mu = 0.9 + 0.7 * inputs.standard_normals(n, 31)
+    ks = [1, 3, 17, 50, 51, 100, n]
+    r = mvn.mvn_excursion(_t(mu), mvn.to_colmajor(_t(S)), 0.8, 0.9, 128, 4, 17, prefix_dims=ks,
+                          prec="mixed")
+    mvn.sync()
+    ref = oracle.excursion(mu, S, 0.8, 0.9, oracle.QMC(128, 4, 17), prefix_dims=ks)
+    assert np.array_equal(r["order"].cpu().numpy(), ref["order"])
+    F = r["F"].cpu().numpy()
+    assert np.all(np.abs(F - ref["F"]) <= 1e-4 * np.maximum(ref["F"], 1e-300) + 1e-12)
+    Lo = ref["L"]
+    L = mvn.to_colmajor(_t(Lo))
+    a = 0.8 - mu[ref["order"]]
+    b = np.full(n, np.inf)
+    dims = [n, 64, 65, 1, 100]
+    out = mvn.mvn_sov_batched(dims, [0] * 5, _t(a), _t(b), L, 128, 4, 17, prec="mixed").cpu().numpy()
+    mvn.sync()
+    for p, k in enumerate(dims):
+        e = oracle.sov(a[:k], b[:k], Lo[:k, :k], oracle.QMC(128, 4, 17))
+        assert abs(out[p, 0] - e[0]) <= 1e-4, (p, out[p], e)

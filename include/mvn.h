@@ -147,6 +147,29 @@ mvn_status mvn_sov_batched(mvn_ctx* ctx, int nprob, const int* dims,
                            const double* L_shared, int64_t ld, const mvn_qmc* qmc,
                            mvn_prec prec, double* out3);
 
+/* FP64 SOV estimate that allocates nothing (the paper has no counterpart; this is a service for
+ * callers that cannot allocate device memory at call time -- code inside a CUDA graph capture,
+ * under a caching allocator that must not see foreign cudaMalloc calls, in a real-time loop
+ * where an allocation's implicit synchronisation is not allowed, or an embedding that only
+ * hands over device buffers).  Same arithmetic as mvn_sov with MVN_FP64, without a context:
+ *   - work is enqueued on `cuda_stream` (a cudaStream_t, NULL = legacy default stream) of the
+ *     current device;
+ *   - all scratch lives in one fixed file-scope device array of about 10.2 MiB that every GPU
+ *     which loads the library holds until the process exits;
+ *   - limits: n <= 256, n_points * n_shifts <= 262144, n_shifts <= 64; larger sizes return
+ *     MVN_ERR_ARG before any work is enqueued;
+ *   - the first call on each device looks up the array's device address (cudaGetSymbolAddress);
+ *     make that first call before any stream capture on that device;
+ *   - every call shares the one array: calls that overlap on the GPU (other streams, other host
+ *     threads) race and give wrong results -- serialise them;
+ *   - no device-side argument check: limits with a_i > b_i or NaN give NaN results; every path
+ *     with weight 0 gives out3 = {-inf, 0, 0}.
+ * a, b, L, ld, qmc, out3 (device double[3]) and path_logw (optional device
+ * double[n_points * n_shifts]) as in mvn_sov.  Returns MVN_OK, MVN_ERR_ARG or MVN_ERR_CUDA. */
+mvn_status mvn_sov_fp64_noalloc(int n, const double* a, const double* b, const double* L,
+                                int64_t ld, const mvn_qmc* qmc, double* out3, double* path_logw,
+                                void* cuda_stream);
+
 /* ------------------------------------------------------------------ confidence region (Alg. 1) */
 
 /* Positive confidence region of level 1-alpha above threshold u for X ~ N(mu, Sigma):

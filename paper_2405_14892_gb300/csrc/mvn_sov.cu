@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "mvn_internal.cuh"
@@ -448,4 +449,113 @@ extern "C" mvn_status mvn_sov_batched(mvn_ctx* ctx, int nprob, const int* dims,
     MVN_TRY(lattice_shifts(ctx, qmc->seed, M, nmax, delta));
     MVN_TRY(sov_run_any(ctx, probs, prec, wc.base + ((wc.off + 255) & ~(size_t)255)));
     return sov_reduce_launch(ctx, logw, Ns, M, qmc->err_k, out3, nprob, Ntot);
+}
+
+// ---------------------------------------------------------------- ABI: mvn_sov_fp64_noalloc
+//
+// FP64 SOV estimate for callers that cannot allocate device memory at call time: code that
+// runs inside a CUDA graph being captured, under a caching allocator that must not see
+// foreign cudaMalloc calls, in a real-time loop where an allocation's implicit synchronisation
+// is not allowed, or in an embedding that hands the library device buffers and nothing else.
+// Such a caller cannot create an mvn_ctx (which owns a growing workspace), so this entry point
+// takes a stream instead and keeps all of its scratch in one file-scope device array of fixed
+// size, which every GPU that loads the library holds until the process exits.
+//
+// Limits: n <= 256 dimensions, n_points * n_shifts <= 262,144 paths, n_shifts <= 64.
+// The sweep runs on a fixed persistent grid of 32 CTAs.
+#define NA_NMAX 256
+#define NA_PATHS_MAX 262144
+#define NA_SHIFTS_MAX 64
+#define NA_GRID 32
+#define NA_PRIME_BOUND 4096  // > the 256th prime (1619)
+
+struct NoAllocScratch {
+    double Y[(size_t)NA_GRID * NA_NMAX * SOV_P];   // per-CTA transformed variables (8 MiB)
+    double logw[NA_PATHS_MAX];                     // per-path log-weights (2 MiB)
+    uint64_t delta[NA_SHIFTS_MAX * NA_NMAX];       // lattice shifts
+    uint64_t alpha[NA_NMAX];                       // lattice generators
+    int primes[NA_NMAX];
+    uint8_t flags[NA_PRIME_BOUND];
+    int counter;                                   // work-queue head (zeroed by every call)
+    int status[MVN_STATUS_WORDS];                  // device status word of the kernels
+};
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+// lattice-table kernels defined in mvn_ctx.cu
+__global__ void k_prime_flags(uint8_t* flag, int bound);
+__global__ void k_prime_compact(const uint8_t* flag, int bound, int* primes, int count);
+__global__ void k_alpha(const int* primes, int n, uint64_t* alpha);
+__global__ void k_shifts(uint64_t seed, int M, int n, uint64_t* delta);
+
+// Device address of the scratch array, looked up once per device (the symbol name is only a
+// host-side stand-in: passing it to a kernel would not give the device address).
+static NoAllocScratch* noalloc_scratch_ptr(int device, cudaError_t* err) {
+    static NoAllocScratch* ptrs[256] = {};
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (device < 0 || device >= 256) {
+        *err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    if (!ptrs[device]) {
+        void* p = nullptr;
+        *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (*err != cudaSuccess) return nullptr;
+        ptrs[device] = (NoAllocScratch*)p;
+    }
+    *err = cudaSuccess;
+    return ptrs[device];
+}
+
+extern "C" mvn_status mvn_sov_fp64_noalloc(int n, const double* a, const double* b,
+                                           const double* L, int64_t ld, const mvn_qmc* qmc,
+                                           double* out3, double* path_logw, void* cuda_stream) {
+    if (!qmc || !out3 || n < 0 || n > NA_NMAX || ld < (n > 0 ? n : 1) ||
+        (n > 0 && (!a || !b || !L)) || qmc->n_points < 1 || qmc->n_shifts < 1 ||
+        qmc->n_shifts > NA_SHIFTS_MAX ||
+        (int64_t)qmc->n_points * qmc->n_shifts > NA_PATHS_MAX)
+        return MVN_ERR_ARG;  // sizes beyond the fixed scratch are rejected before any work
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MVN_ERR_CUDA;
+    cudaError_t e;
+    NoAllocScratch* S = noalloc_scratch_ptr(dev, &e);
+    if (!S) return MVN_ERR_CUDA;
+    const int M = qmc->n_shifts;
+    const int64_t Ns = qmc->n_points, Ntot = Ns * M;
+    double* logw = path_logw ? path_logw : S->logw;
+    // the queue head and the status word must start at zero; the rest is written before read
+    if (cudaMemsetAsync(&S->counter, 0, sizeof(int) * (1 + MVN_STATUS_WORDS), st) != cudaSuccess)
+        return MVN_ERR_CUDA;
+    const int nt = n > 0 ? n : 1;
+    k_prime_flags<<<(NA_PRIME_BOUND + 255) / 256, 256, 0, st>>>(S->flags, NA_PRIME_BOUND);
+    k_prime_compact<<<1, 1024, 0, st>>>(S->flags, NA_PRIME_BOUND, S->primes, nt);
+    k_alpha<<<(nt + 127) / 128, 128, 0, st>>>(S->primes, nt, S->alpha);
+    k_shifts<<<(M * nt + 255) / 256, 256, 0, st>>>(qmc->seed, M, nt, S->delta);
+    if (n == 0) {
+        if (cudaMemsetAsync(logw, 0, sizeof(double) * Ntot, st) != cudaSuccess) return MVN_ERR_CUDA;
+    } else {
+        SovBatch batch;
+        memset(&batch, 0, sizeof(batch));
+        SovProblem& P = batch.single;
+        P.n = n;
+        P.M = M;
+        P.Ns = Ns;
+        P.Ntot = Ntot;
+        P.a = a;
+        P.b = b;
+        P.L = L;
+        P.ld = ld;
+        P.delta = S->delta;
+        P.dstride = nt;
+        P.logw = logw;
+        batch.probs = nullptr;
+        batch.nitems = (int)((Ntot + SOV_P - 1) / SOV_P);
+        batch.counter = &S->counter;
+        k_sov_simt<32, double, true><<<NA_GRID, SOV_P, 0, st>>>(batch, S->alpha, S->Y,
+                                                                (int64_t)NA_NMAX * SOV_P);
+    }
+    k_sov_reduce<<<1, 512, sizeof(double) * (512 + M), st>>>(logw, Ns, M, qmc->err_k, out3, Ntot,
+                                                             S->status, 0);
+    return cudaGetLastError() == cudaSuccess ? MVN_OK : MVN_ERR_CUDA;
 }

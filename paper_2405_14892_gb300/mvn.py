@@ -68,6 +68,7 @@ SIGNATURES = {
     "mvn_lattice_alpha": (_I, [_P, _I, _P]),
     "mvn_lattice_shifts": (_I, [_P, _U64, _I, _I, _P]),
     "mvn_tc_selftest": (_I, [_P, _I, _P, _P, _P]),
+    "mvn_sov_fp64_noalloc": (_I, [_I, _P, _P, _P, _I64, _QP, _P, _P, _P]),
 }
 
 
@@ -324,6 +325,24 @@ def mvn_tc_selftest(Y: torch.Tensor, L: torch.Tensor) -> torch.Tensor:
     c.check(lib().mvn_tc_selftest(c.h, K, _vec(Y.contiguous(), 128 * K, "Y"),
                                   _vec(L.contiguous(), 64 * K, "L"), _P(S.data_ptr())))
     return S
+
+
+def mvn_sov_fp64_noalloc(a, b, L, n_points, n_shifts, seed, err_k=3.0, path_logw=None,
+                         out3=None):
+    """FP64 SOV estimate through the entry point that allocates nothing (fixed scratch inside
+    the library; see include/mvn.h for its limits).  Enqueued on torch's current stream."""
+    n = a.numel()
+    if out3 is None:
+        out3 = torch.empty(3, dtype=torch.float64, device=a.device)
+    Lp, ld = _mat(L, n, "L")
+    q = _qmc(n_points, n_shifts, seed, err_k)
+    st = lib().mvn_sov_fp64_noalloc(n, _vec(a, n, "a"), _vec(b, n, "b"), Lp, ld, ctypes.byref(q),
+                                    _vec(out3, 3, "out3"),
+                                    _vec(path_logw, n_points * n_shifts, "path_logw"),
+                                    _P(torch.cuda.current_stream(a.device).cuda_stream))
+    if st != MVN_OK:
+        raise MVNError(st, "mvn_sov_fp64_noalloc failed")
+    return out3
 
 
 def sync():

@@ -27,13 +27,13 @@
 
 #define TC_P 128            // paths per CTA (MMA M, TMEM lanes)
 #define TC_B 64             // dimensions per block (MMA N, K chunk)
-#define TC_STAGES 3
+#define TC_STAGES 2
+#define TC_G 4              // K chunks per TMEM accumulation group (then drained to registers)
 #define TC_YT_BYTES 16384   // one slice of a 128 x 64 FP16 Y tile
 #define TC_LT_BYTES 8192    // one slice of a 64 x 64 FP16 L tile
 #define TC_STAGE_BYTES (2 * TC_YT_BYTES + 2 * TC_LT_BYTES)
+#define TC_TMEM_COLS 256    // two accumulation buffers x (acc1 64 + acc2 64 columns)
 #define TC_WAIT_BUDGET 4000000000LL  // cycles (~2 s) before a wait gives up
-
-
 
 // ---------------------------------------------------------------- operand preparation
 
@@ -64,44 +64,71 @@ __global__ void k_split_L(int n, const double* __restrict__ L, int64_t ld, int n
 
 // ---------------------------------------------------------------- shared memory
 
+// ~106 KB: two CTAs fit on one SM (157 tiles of W2's 20,000 paths are resident at once).
 struct __align__(1024) TcSmem {
     uint8_t stage[TC_STAGES][TC_STAGE_BYTES];  // [Yh 16K | Yl 16K | Lh 8K | Ll 8K]
-    float Ld[TC_B][TC_B + 1];
+    float Ld[TC_B * (TC_B + 1) / 2];           // diagonal block, packed lower triangle
     double a[TC_B], b[TC_B];
     uint64_t alpha[TC_B];
-    uint64_t full[TC_STAGES], empty[TC_STAGES], done;
+    uint64_t full[TC_STAGES], empty[TC_STAGES], accf[2], fin;
     uint32_t tmem;
     int item;
     int abort;
 };
 
-// ---------------------------------------------------------------- outer GEMM (thread 0)
+// ---------------------------------------------------------------- GEMM pipeline (thread 0)
+//
+// The K chunks of all blocks form one sequence; chunk number q uses stage q % TC_STAGES, whose
+// "full" barrier completes for the (q / TC_STAGES)-th time when its bulk copies land and whose
+// "empty" barrier completes when the MMAs reading it are done.  Chunks are grouped by TC_G; group
+// number g accumulates into TMEM buffer g % 2 and commits to accf[g % 2] when complete.  All
+// parities follow from these counters, so no barrier phase is ever skipped or waited twice.
+struct TcPipe {
+    uint64_t q_load = 0;  // global chunk number of the next load
+    uint64_t q_mma = 0;   // global chunk number of the next MMA chunk
+    uint64_t g_next = 0;  // global group number of the group the next MMA chunk belongs to
+    // current block
+    const uint8_t* Ybuf;
+    const uint8_t* Lt;
+    size_t lslice;
+    int nrb, rb;
+    int kcs;              // chunks of the block
+    int next_load, next_mma;  // within-block chunk indices
+    uint64_t q_block0;    // global chunk number of the block's chunk 0
+};
 
-// Issue the K loop of one block: kcs chunks of Y (this CTA's buffer) against the L tiles of
-// row block rb.  Runs on thread 0 only; commits the final MMAs to sm.done.
-// Returns false if a wait timed out.
-__device__ bool tc_outer_gemm(TcSmem& sm, const uint8_t* __restrict__ Ybuf,
-                              const uint8_t* __restrict__ Lt, int nrb, int rb, int kcs,
-                              uint32_t& full_par, uint32_t& empty_par) {
-    const size_t lslice = (size_t)nrb * nrb * TC_LT_BYTES;
+__device__ __forceinline__ uint32_t tc_buf_col(uint64_t g) { return (uint32_t)(g & 1u) * 128u; }
+
+// Issue loads ahead and MMAs for the block's chunks < limit; false on a timed-out wait.
+__device__ bool tc_pump(TcSmem& sm, TcPipe& pp, int limit) {
     const uint32_t idesc = tc::idesc_f16_f32(TC_P, TC_B);
-    const uint32_t acc1 = sm.tmem, acc2 = sm.tmem + TC_B;
-    auto issue_load = [&](int kc) {
-        const int s = kc % TC_STAGES;
-        uint8_t* st = sm.stage[s];
-        tc::mbar_arrive_expect_tx(&sm.full[s], TC_STAGE_BYTES);
-        tc::bulk_g2s(st, Ybuf + (size_t)kc * 2 * TC_YT_BYTES, 2 * TC_YT_BYTES, &sm.full[s]);
-        const uint8_t* lt = Lt + ((size_t)kc * nrb + rb) * TC_LT_BYTES;
-        tc::bulk_g2s(st + 2 * TC_YT_BYTES, lt, TC_LT_BYTES, &sm.full[s]);
-        tc::bulk_g2s(st + 2 * TC_YT_BYTES + TC_LT_BYTES, lt + lslice, TC_LT_BYTES, &sm.full[s]);
-    };
-    const int pre = min(kcs, TC_STAGES);
-    for (int kc = 0; kc < pre; ++kc) issue_load(kc);
-    for (int kc = 0; kc < kcs; ++kc) {
-        const int s = kc % TC_STAGES;
-        if (!tc::mbar_wait(&sm.full[s], (full_par >> s) & 1u, TC_WAIT_BUDGET)) return false;
-        full_par ^= 1u << s;
+    while (pp.next_mma < limit) {
+        while (pp.next_load < pp.kcs && pp.next_load < pp.next_mma + TC_STAGES) {
+            const uint64_t q = pp.q_load;
+            const int s = (int)(q % TC_STAGES);
+            if (q >= TC_STAGES) {  // the MMAs of chunk q - TC_STAGES must have left the stage
+                const uint32_t par = (uint32_t)((q / TC_STAGES - 1) & 1u);
+                if (!tc::mbar_wait(&sm.empty[s], par, TC_WAIT_BUDGET)) return false;
+            }
+            uint8_t* st = sm.stage[s];
+            const int kc = pp.next_load;
+            tc::mbar_arrive_expect_tx(&sm.full[s], TC_STAGE_BYTES);
+            tc::bulk_g2s(st, pp.Ybuf + (size_t)kc * 2 * TC_YT_BYTES, 2 * TC_YT_BYTES, &sm.full[s]);
+            const uint8_t* lt = pp.Lt + ((size_t)kc * pp.nrb + pp.rb) * TC_LT_BYTES;
+            tc::bulk_g2s(st + 2 * TC_YT_BYTES, lt, TC_LT_BYTES, &sm.full[s]);
+            tc::bulk_g2s(st + 2 * TC_YT_BYTES + TC_LT_BYTES, lt + pp.lslice, TC_LT_BYTES,
+                         &sm.full[s]);
+            ++pp.q_load;
+            ++pp.next_load;
+        }
+        const uint64_t q = pp.q_mma;
+        const int s = (int)(q % TC_STAGES);
+        if (!tc::mbar_wait(&sm.full[s], (uint32_t)((q / TC_STAGES) & 1u), TC_WAIT_BUDGET))
+            return false;
         tc::tc_fence_after();
+        const int kc = pp.next_mma;
+        const uint64_t g = pp.g_next + (uint64_t)(kc / TC_G);
+        const uint32_t acc1 = sm.tmem + tc_buf_col(g), acc2 = acc1 + TC_B;
         const uint32_t base = tc::smem_u32(sm.stage[s]);
 #pragma unroll
         for (int k16 = 0; k16 < 4; ++k16) {
@@ -110,41 +137,74 @@ __device__ bool tc_outer_gemm(TcSmem& sm, const uint8_t* __restrict__ Ybuf,
             const uint64_t al = tc::sdesc_sw128(base + TC_YT_BYTES + ko);
             const uint64_t bh = tc::sdesc_sw128(base + 2 * TC_YT_BYTES + ko);
             const uint64_t bl = tc::sdesc_sw128(base + 2 * TC_YT_BYTES + TC_LT_BYTES + ko);
-            const uint32_t first = (kc == 0 && k16 == 0) ? 0u : 1u;
+            const uint32_t first = (kc % TC_G == 0 && k16 == 0) ? 0u : 1u;
             tc::mma_f16(acc1, ah, bh, idesc, first);
             tc::mma_f16(acc2, ah, bl, idesc, first);
             tc::mma_f16(acc2, al, bh, idesc, 1u);
         }
         tc::mma_commit(&sm.empty[s]);
-        if (kc + TC_STAGES < kcs) {
-            // the stage is reloaded once the MMAs reading it have completed
-            if (!tc::mbar_wait(&sm.empty[s], (empty_par >> s) & 1u, TC_WAIT_BUDGET)) return false;
-            empty_par ^= 1u << s;
-            issue_load(kc + TC_STAGES);
-        }
-    }
-    tc::mma_commit(&sm.done);
-    // retire the pending empty-phase completions so the parities stay in step
-    for (int kc = max(0, kcs - TC_STAGES); kc < kcs; ++kc) {
-        const int s = kc % TC_STAGES;
-        if (!tc::mbar_wait(&sm.empty[s], (empty_par >> s) & 1u, TC_WAIT_BUDGET)) return false;
-        empty_par ^= 1u << s;
+        if (kc % TC_G == TC_G - 1 || kc == pp.kcs - 1) tc::mma_commit(&sm.accf[g & 1u]);
+        ++pp.q_mma;
+        ++pp.next_mma;
     }
     return true;
 }
 
-// Read the limit shift of this thread's path for the 64 dimensions of the block from TMEM.
-__device__ __forceinline__ void tc_read_shift(const TcSmem& sm, float (&s)[TC_B]) {
-    const uint32_t warp = threadIdx.x >> 5;
-    const uint32_t lane_base = (warp * 32u) << 16;
-#pragma unroll
-    for (int c = 0; c < TC_B; c += 16) {
-        float h[16], l[16];
-        tc::tmem_ld16(sm.tmem + lane_base + c, h);
-        tc::tmem_ld16(sm.tmem + lane_base + TC_B + c, l);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) s[c + i] = fmaf(l[i], 1.0f / 2048.0f, h[i]) * (1.0f / 4096.0f);
+// Limit shift of this thread's path for the block's 64 dimensions: the K chunks are accumulated
+// in TMEM group by group (TC_G chunks each, two ping-pong buffers) and every group's partial sums
+// are added into FP32 registers.  Short in-TMEM accumulation chains keep the tensor cores'
+// accumulation error near that of an FP32 sum.  All threads call this; thread 0 also issues.
+// Returns false if a wait timed out.
+__device__ bool tc_block_shift(TcSmem& sm, TcPipe& pp, const uint8_t* Ybuf, const uint8_t* Lt,
+                               int nrb, int rb, uint64_t& g_all, float (&s)[TC_B]) {
+    const int t = threadIdx.x;
+    const int kcs = rb;  // chunks 0 .. rb-1
+    const int ng = (kcs + TC_G - 1) / TC_G;
+    bool ok = true;
+    if (t == 0) {
+        pp.Ybuf = Ybuf;
+        pp.Lt = Lt;
+        pp.lslice = (size_t)nrb * nrb * TC_LT_BYTES;
+        pp.nrb = nrb;
+        pp.rb = rb;
+        pp.kcs = kcs;
+        pp.next_load = 0;
+        pp.next_mma = 0;
+        pp.g_next = g_all;
+        ok = tc_pump(sm, pp, min(kcs, 2 * TC_G));
+        if (!ok) sm.abort = 1;
     }
+#pragma unroll
+    for (int v = 0; v < TC_B; ++v) s[v] = 0.0f;
+    const uint32_t lane_base = ((uint32_t)(t >> 5) * 32u) << 16;
+    for (int g = 0; g < ng; ++g) {
+        const uint64_t gg = g_all + g;
+        if (!tc::mbar_wait(&sm.accf[gg & 1u], (uint32_t)((gg >> 1) & 1u), TC_WAIT_BUDGET)) {
+            ok = false;
+            sm.abort = 1;
+        }
+        tc::tc_fence_after();
+        const uint32_t col = sm.tmem + lane_base + tc_buf_col(gg);
+#pragma unroll
+        for (int c = 0; c < TC_B; c += 16) {
+            float h[16], l[16];
+            tc::tmem_ld16(col + c, h);
+            tc::tmem_ld16(col + TC_B + c, l);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) s[c + i] += fmaf(l[i], 1.0f / 2048.0f, h[i]);
+        }
+        tc::tc_fence_before();
+        __syncthreads();  // the buffer of group g is free again
+        if (sm.abort) break;
+        if (t == 0) {
+            tc::tc_fence_after();
+            if (!tc_pump(sm, pp, min(kcs, (g + 3) * TC_G))) sm.abort = 1;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < TC_B; ++v) s[v] *= (1.0f / 4096.0f);
+    g_all += ng;
+    return ok && !sm.abort;
 }
 
 // Write this thread's 64 new y values (two FP16 slices) as row `t` of the Y tile of chunk kc.
@@ -184,30 +244,63 @@ __device__ __forceinline__ double tc_logprod_value(double prod, int ex) {
     return prod > 0.0 ? log(prod) + (double)ex * 0.69314718055994530942 : -INFINITY;
 }
 
-__global__ void __launch_bounds__(TC_P, 1) k_sov_tc(const TcBatch bt,
-                                                     const uint64_t* __restrict__ alpha) {
-    extern __shared__ uint8_t smem_raw[];
-    TcSmem& sm = *reinterpret_cast<TcSmem*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+// Shared set-up of the tensor-core kernels: barriers and TMEM.
+__device__ __forceinline__ void tc_setup(TcSmem& sm) {
     const int t = threadIdx.x;
-    const int warp = t >> 5;
     if (t == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
             tc::mbar_init(&sm.full[s], 1);
             tc::mbar_init(&sm.empty[s], 1);
         }
-        tc::mbar_init(&sm.done, 1);
+        tc::mbar_init(&sm.accf[0], 1);
+        tc::mbar_init(&sm.accf[1], 1);
+        tc::mbar_init(&sm.fin, 1);
         tc::mbar_fence_init();
         sm.abort = 0;
     }
-    if (warp == 0) {
-        tc::tmem_alloc(&sm.tmem, 2 * TC_B);
+    if ((t >> 5) == 0) {
+        tc::tmem_alloc(&sm.tmem, TC_TMEM_COLS);
         tc::tmem_relinquish();
     }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    uint32_t full_par = 0, empty_par = 0, done_par = 0;
+}
+
+// After an aborted (timed-out) wait: let the copies and MMAs this CTA issued finish (bounded)
+// before its shared memory and tensor memory are released.
+__device__ __forceinline__ void tc_quiesce(TcSmem& sm, const TcPipe& pp) {
+    if (threadIdx.x != 0 || !sm.abort) return;
+    for (uint64_t q = pp.q_mma; q < pp.q_load; ++q)
+        tc::mbar_wait(&sm.full[q % TC_STAGES], (uint32_t)((q / TC_STAGES) & 1u), TC_WAIT_BUDGET);
+    tc::mma_commit(&sm.fin);
+    tc::mbar_wait(&sm.fin, 0, TC_WAIT_BUDGET);
+}
+
+__device__ __forceinline__ void tc_teardown(TcSmem& sm) {
+    tc::tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(sm.tmem, TC_TMEM_COLS);
+    }
+}
+
+__device__ __forceinline__ TcSmem& tc_smem(uint8_t* raw) {
+    return *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(raw) + 1023) &
+                                      ~(uintptr_t)1023);
+}
+
+__device__ __forceinline__ int tri(int v, int u) { return v * (v + 1) / 2 + u; }
+
+__global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
+                                                     const uint64_t* __restrict__ alpha) {
+    extern __shared__ uint8_t smem_raw[];
+    TcSmem& sm = tc_smem(smem_raw);
+    const int t = threadIdx.x;
+    tc_setup(sm);
+    TcPipe pp;
+    uint64_t g_all = 0;  // groups issued so far (uniform across threads)
     uint8_t* Ybuf = bt.Yscratch + (int64_t)blockIdx.x * bt.ystride;
 
     for (;;) {
@@ -223,39 +316,30 @@ __global__ void __launch_bounds__(TC_P, 1) k_sov_tc(const TcBatch bt,
         const int64_t q = valid ? p / P.Ns : 0;
         const uint64_t j = valid ? (uint64_t)(p - q * P.Ns) + 1u : 1u;
         const uint64_t* __restrict__ dq = P.delta + q * P.dstride;
-        double prod = 1.0;
-        int ex = 0;
+        LogProd lp;
         int pf = 0;
         int next_k = (P.nprefix > 0) ? P.prefix[0] : -1;
 
-        for (int r0 = 0; r0 < n && !sm.abort; r0 += TC_B) {
+        for (int r0 = 0; r0 < n; r0 += TC_B) {
             const int nb = min(TC_B, n - r0);
             const int rb = r0 / TC_B;
             float s[TC_B];
             if (rb > 0) {
-                if (t == 0) {
-                    if (!tc_outer_gemm(sm, Ybuf, bt.Lt, bt.nrb, rb, rb, full_par, empty_par)) {
-                        dev_raise(bt.status, MVN_ERR_TIMEOUT, 0);
-                        sm.abort = 1;
-                    }
+                if (!tc_block_shift(sm, pp, Ybuf, bt.Lt, bt.nrb, rb, g_all, s)) {
+                    if (t == 0) dev_raise(bt.status, MVN_ERR_TIMEOUT, 0);
                 }
-                // all threads wait for the MMAs of this block (bounded)
-                if (!tc::mbar_wait(&sm.done, done_par, TC_WAIT_BUDGET)) {
-                    dev_raise(bt.status, MVN_ERR_TIMEOUT, 0);
-                    sm.abort = 1;
-                }
-                done_par ^= 1u;
-                tc::tc_fence_after();
-                tc_read_shift(sm, s);
             } else {
 #pragma unroll
                 for (int v = 0; v < TC_B; ++v) s[v] = 0.0f;
             }
+            __syncthreads();
+            if (sm.abort) break;
             // diagonal block operands
             for (int e = t; e < TC_B * TC_B; e += TC_P) {
                 const int v = e % TC_B, u = e / TC_B;
-                sm.Ld[v][u] = (v < nb && u <= v) ? (float)P.L[(r0 + v) + (int64_t)(r0 + u) * P.ld]
-                                                 : 0.0f;
+                if (u <= v)
+                    sm.Ld[tri(v, u)] =
+                        (v < nb) ? (float)P.L[(r0 + v) + (int64_t)(r0 + u) * P.ld] : 0.0f;
             }
             if (t < TC_B) {
                 sm.a[t] = (t < nb) ? P.a[r0 + t] : 0.0;
@@ -269,28 +353,13 @@ __global__ void __launch_bounds__(TC_P, 1) k_sov_tc(const TcBatch bt,
                 if (v < nb) {
                     float sv = s[v];
 #pragma unroll
-                    for (int u = 0; u < v; ++u) sv = fmaf(sm.Ld[v][u], y[u], sv);
+                    for (int u = 0; u < v; ++u) sv = fmaf(sm.Ld[tri(v, u)], y[u], sv);
                     const double w = lattice_w(j, sm.alpha[v], dq[r0 + v]);
                     double delta;
-                    y[v] = sov_step_f32(sm.a[v], sm.b[v], sv, sm.Ld[v][v], w, delta);
-                    // running product of the Delta factors as prod * 2^ex
-                    if (delta < 0x1p-400) {
-                        if (!(delta > 0.0)) {
-                            prod = 0.0;
-                        } else {
-                            int e2;
-                            delta = frexp(delta, &e2);
-                            ex += e2;
-                        }
-                    }
-                    prod *= delta;
-                    if (prod < 0x1p-400 && prod > 0.0) {
-                        int e2;
-                        prod = frexp(prod, &e2);
-                        ex += e2;
-                    }
+                    y[v] = sov_step_f32(sm.a[v], sm.b[v], sv, sm.Ld[tri(v, v)], w, delta);
+                    lp.mul(delta);
                     while (next_k == r0 + v + 1) {
-                        if (valid) P.logw_prefix[(int64_t)pf * P.Ntot + p] = tc_logprod_value(prod, ex);
+                        if (valid) P.logw_prefix[(int64_t)pf * P.Ntot + p] = lp.log_value();
                         ++pf;
                         next_k = (pf < P.nprefix) ? P.prefix[pf] : -1;
                     }
@@ -298,24 +367,19 @@ __global__ void __launch_bounds__(TC_P, 1) k_sov_tc(const TcBatch bt,
                     y[v] = 0.0f;
                 }
             }
-            // y of this block -> operand buffer for the later blocks
+            // y of this block -> operand buffer of the later blocks (bulk-copied back by the
+            // async proxy: fence before the barrier that precedes the next loads)
             if (r0 + TC_B < n) {
                 tc_write_y(Ybuf, rb, t, y);
                 tc::fence_proxy_async_global();
             }
-            tc::tc_fence_before();
             __syncthreads();
-            tc::tc_fence_after();
         }
-        if (valid && P.logw) P.logw[p] = tc_logprod_value(prod, ex);
+        if (valid && P.logw) P.logw[p] = lp.log_value();
         __syncthreads();
     }
-    tc::tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc::tc_fence_after();
-        tc::tmem_dealloc(sm.tmem, 2 * TC_B);
-    }
+    tc_quiesce(sm, pp);
+    tc_teardown(sm);
 }
 
 // ---------------------------------------------------------------- host side
@@ -323,7 +387,8 @@ __global__ void __launch_bounds__(TC_P, 1) k_sov_tc(const TcBatch bt,
 static size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 
 static int tc_grid(mvn_ctx* ctx, int64_t ntiles) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, ctx->sm_count));
+    // two CTAs per SM (shared memory ~106 KB, 256 TMEM columns each)
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 2 * (int64_t)ctx->sm_count));
 }
 
 size_t sov_tc_ws_bytes(mvn_ctx* ctx, int nprob, int nmax, int64_t ntiles) {
@@ -406,7 +471,8 @@ mvn_status sov_run_tc(mvn_ctx* ctx, const std::vector<SovProblem>& probs_h, char
 __global__ void k_tc_selftest_prep(int K, const double* __restrict__ Y,
                                    const double* __restrict__ Lr, uint8_t* __restrict__ Ybuf,
                                    __half* __restrict__ Lt, int nrb) {
-    // Y rows: one thread per path; L rows: tile (rb = 1, kc) of a matrix whose row block 1 is Lr
+    // Y rows: one thread per path; L rows: tiles (rb = kcs, kc) of a factor whose row block kcs
+    // holds the test rows
     const int t = threadIdx.x;
     for (int kc = 0; kc * TC_B < K; ++kc) {
         float y[TC_B];
@@ -419,7 +485,8 @@ __global__ void k_tc_selftest_prep(int K, const double* __restrict__ Y,
     }
     const size_t slice = (size_t)nrb * nrb * (TC_LT_BYTES / 2);
     for (int kc = 0; kc * TC_B < K; ++kc) {
-        __half* hi = Lt + ((size_t)kc * nrb + 1) * (TC_LT_BYTES / 2);
+        const int rbt = (K + TC_B - 1) / TC_B;
+        __half* hi = Lt + ((size_t)kc * nrb + rbt) * (TC_LT_BYTES / 2);
         __half* lo = hi + slice;
         for (int e = t; e < 64 * 64; e += blockDim.x) {
             const int r = e & 63, k = e >> 6;
@@ -436,51 +503,24 @@ __global__ void k_tc_selftest_prep(int K, const double* __restrict__ Y,
     tc::fence_proxy_async_global();
 }
 
-__global__ void __launch_bounds__(TC_P, 1) k_tc_selftest(int K, const uint8_t* __restrict__ Ybuf,
+__global__ void __launch_bounds__(TC_P, 2) k_tc_selftest(int K, const uint8_t* __restrict__ Ybuf,
                                                           const uint8_t* __restrict__ Lt, int nrb,
                                                           float* __restrict__ S, int* status) {
     extern __shared__ uint8_t smem_raw[];
-    TcSmem& sm = *reinterpret_cast<TcSmem*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const int t = threadIdx.x, warp = t >> 5;
-    if (t == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
-            tc::mbar_init(&sm.full[s], 1);
-            tc::mbar_init(&sm.empty[s], 1);
-        }
-        tc::mbar_init(&sm.done, 1);
-        tc::mbar_fence_init();
-        sm.abort = 0;
-    }
-    if (warp == 0) {
-        tc::tmem_alloc(&sm.tmem, 2 * TC_B);
-        tc::tmem_relinquish();
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::tc_fence_after();
-    uint32_t full_par = 0, empty_par = 0;
-    const int kcs = (K + TC_B - 1) / TC_B;
-    if (t == 0) {
-        if (!tc_outer_gemm(sm, Ybuf, Lt, nrb, 1, kcs, full_par, empty_par)) {
-            dev_raise(status, MVN_ERR_TIMEOUT, 0);
-            sm.abort = 1;
-        }
-    }
-    bool ok = tc::mbar_wait(&sm.done, 0, TC_WAIT_BUDGET);
-    if (!ok) dev_raise(status, MVN_ERR_TIMEOUT, 0);
-    tc::tc_fence_after();
+    TcSmem& sm = tc_smem(smem_raw);
+    const int t = threadIdx.x;
+    tc_setup(sm);
+    TcPipe pp;
+    uint64_t g_all = 0;
     float s[TC_B];
-    if (ok) {
-        tc_read_shift(sm, s);
+    const int kcs = (K + TC_B - 1) / TC_B;
+    // row block kcs of a factor whose tiles (kcs, kc) hold the test rows: the block has kcs chunks
+    const bool ok = tc_block_shift(sm, pp, Ybuf, Lt, nrb, kcs, g_all, s);
+    if (!ok && t == 0) dev_raise(status, MVN_ERR_TIMEOUT, 0);
+    if (ok)
         for (int v = 0; v < TC_B; ++v) S[t * TC_B + v] = s[v];
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc::tc_fence_after();
-        tc::tmem_dealloc(sm.tmem, 2 * TC_B);
-    }
+    tc_quiesce(sm, pp);
+    tc_teardown(sm);
 }
 
 extern "C" mvn_status mvn_tc_selftest(mvn_ctx* ctx, int K, const double* Y, const double* L,
@@ -490,7 +530,7 @@ extern "C" mvn_status mvn_tc_selftest(mvn_ctx* ctx, int K, const double* Y, cons
         return mvn_fail(ctx, MVN_ERR_ARG, "mvn_tc_selftest: invalid argument");
     MVN_CUDA(ctx, cudaSetDevice(ctx->device));
     const int kcs = (K + TC_B - 1) / TC_B;
-    const int nrb = std::max(kcs, 2);
+    const int nrb = kcs + 1;
     const size_t ybytes = (size_t)kcs * 2 * TC_YT_BYTES;
     const size_t lbytes = (size_t)2 * nrb * nrb * TC_LT_BYTES;
     MVN_TRY(ws_reserve(ctx, ws_round(ybytes) + ws_round(lbytes) + 1024));

@@ -163,6 +163,8 @@ def run_gpu(args):
     w, c, a, b = workload()
     n = c.shape[0]
     Ns, M = w["Ns"], w["M"]
+    if args.paths:
+        Ns = max(1, args.paths // M)
     Ntot = Ns * M
     seed = w["seed"] + 1000 * rank
     prec = args.prec
@@ -272,7 +274,7 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f64+f32+bf16x3",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f64+f32+fp16x2",
                                        "mixed_simt": "f64+f32"}[prec],
         "data": "synthetic",
         "config": {"workload": w["name"], "n": n, "paths": Ntot, "shifts": M, "points": Ns,
@@ -308,6 +310,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed_simt", choices=["mixed", "fp64", "mixed_simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--paths", type=int, default=0,
+                    help="override the path count (multiple of the shift count; profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

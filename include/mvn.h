@@ -46,9 +46,10 @@ typedef enum {
 /* Arithmetic of the compute path.
  *   MVN_FP64       : every step in FP64 (the plain FP64 GPU path).
  *   MVN_MIXED      : Cholesky in FP64; SOV limit-update GEMM on the tcgen05 tensor cores with
- *                    operands split into three BF16 slices (FP32 accumulation in TMEM), limits
- *                    and transformed variables in FP32, the running log-weight in FP64, deep
- *                    tails of Phi and Phi^-1 in FP64.
+ *                    each operand split into two FP16 slices (3 MMAs per K step, FP32
+ *                    accumulation in TMEM drained to FP32 registers every 256 K), limits and
+ *                    transformed variables in FP32, the running log-weight in FP64, deep tails
+ *                    of Phi and Phi^-1 in FP64.
  *   MVN_MIXED_SIMT : as MVN_MIXED with the limit-update GEMM in FP32 on the CUDA cores. */
 typedef enum { MVN_FP64 = 0, MVN_MIXED = 1, MVN_MIXED_SIMT = 2 } mvn_prec;
 
@@ -132,7 +133,9 @@ mvn_status mvn_sov(mvn_ctx* ctx, int n, const double* a, const double* b, const 
  *   dlogp_da, dlogp_db: device n-vectors of d log P-hat / d a_i, d b_i (either may be NULL);
  *   dlogp_dL: optional device n x n (ld) lower-triangle d log P-hat / d L_ik.
  * The reverse sweep recomputes each block's elementwise terms from the stored transformed
- * variables instead of storing them.  out3 as in mvn_sov. */
+ * variables instead of storing them.  The adjoint runs in FP64 for every value of prec (the
+ * forward estimate in out3 is the FP64 one).  dlogp_dL uses the leading dimension ld of L; its
+ * strict upper part is not written.  out3 as in mvn_sov. */
 mvn_status mvn_sov_grad(mvn_ctx* ctx, int n, const double* a, const double* b,
                         const double* L, int64_t ld, const mvn_qmc* qmc, mvn_prec prec,
                         double* out3, double* dlogp_da, double* dlogp_db, double* dlogp_dL);

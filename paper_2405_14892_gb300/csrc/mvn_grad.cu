@@ -1,0 +1,605 @@
+// mvn_grad.cu -- adjoints (not in the paper; the chain rule of its Eq. 2 and of Alg. 1's
+// factorisation): d log P-hat / d(a, b, L) by a reverse blocked SOV sweep, the reverse mode of the
+// Cholesky factorisation (blocked form of the column algorithm's adjoint, Murray 2016), and the
+// FP64 GEMMs they need.
+//
+// log P-hat = log(mean_p exp(logw_p)), so d log P-hat = sum_p w_p d logw_p with w = softmax(logw).
+// Per path, the reverse of Eq. 2 in dimension order n-1 .. 0 (a' = (a - s)/L_ii, likewise b'):
+//   ybar_i  = sum_{j>i} sbar_j L_ji
+//   a'bar   = -phi(a')/Delta + ybar_i (1 - w_i) phi(a')/phi(y_i)   (0 for an infinite limit)
+//   b'bar   =  phi(b')/Delta + ybar_i w_i phi(b')/phi(y_i)
+//   sbar_i  = -(a'bar + b'bar)/L_ii;  da_i = a'bar/L_ii;  db_i = b'bar/L_ii
+//   dL_ii   = -(a'bar a' + b'bar b')/L_ii;  dL_ik = sbar_i y_k (k < i)
+// The forward sweep keeps every path tile's y values; the reverse sweep recomputes each block's
+// limit shifts from them (one left-looking GEMM per block), forms ybar from the stored sbar of the
+// later dimensions, and stores sbar.  dL (strict lower) = sum_p w_p sbar_p y_p^T is one GEMM over
+// the path axis.  Every reduction over paths runs in a fixed order (deterministic).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "mvn_internal.cuh"
+#include "mvn_sov_simt.cuh"
+
+mvn_status chol_f64_launch(mvn_ctx* ctx, int n, double* A, int64_t ld);
+mvn_status sov_reduce_launch_opt(mvn_ctx* ctx, const double* logw, int64_t Ns, int M,
+                                 double err_k, double* out3, int nprob, int64_t prob_stride,
+                                 bool raise_numeric);
+
+#define RV_B 16
+__device__ __forceinline__ double phi_d(double x) {
+    return 0.39894228040143267794 * exp(-0.5 * x * x);
+}
+
+// ---------------------------------------------------------------- path weights
+
+// lse[0] = log sum_p exp(logw_p) (one block, fixed order)
+__global__ void k_lse_all(const double* __restrict__ logw, int64_t N, double* __restrict__ lse) {
+    __shared__ double red[512];
+    const int t = threadIdx.x;
+    double m = -INFINITY;
+    for (int64_t k = t; k < N; k += 512) m = fmax(m, logw[k]);
+    red[t] = m;
+    __syncthreads();
+    for (int w = 256; w > 0; w >>= 1) {
+        if (t < w) red[t] = fmax(red[t], red[t + w]);
+        __syncthreads();
+    }
+    m = red[0];
+    __syncthreads();
+    double s = 0.0;
+    if (m > -INFINITY)
+        for (int64_t k = t; k < N; k += 512) s += exp(logw[k] - m);
+    red[t] = s;
+    __syncthreads();
+    for (int w = 256; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    if (t == 0) lse[0] = (m > -INFINITY) ? m + log(red[0]) : -INFINITY;
+}
+
+__global__ void k_weights(const double* __restrict__ logw, int64_t N,
+                          const double* __restrict__ lse, double* __restrict__ omega) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const double l = lse[0];
+    omega[p] = (l > -INFINITY) ? exp(logw[p] - l) : 0.0;
+}
+
+// ---------------------------------------------------------------- reverse sweep
+
+struct RevSmem {
+    double Lk[RV_B][RV_B];      // GEMM operand tile
+    double Ld[RV_B][RV_B + 1];  // diagonal block L(r0+v, r0+u)
+    double a[RV_B], b[RV_B];
+    uint64_t alpha[RV_B];
+    double red[3][RV_B][4];     // per-warp partial sums of the three path reductions
+};
+
+// One tile of 128 paths, blocks in reverse order.  Y and Sbar of tile `tile` live at
+// Yt/St[k * 128 + t].  part[(tile * 3 + c) * n + i] receives the tile's sum over its paths of
+// w_p a'bar/L_ii (c = 0), w_p b'bar/L_ii (c = 1) and w_p dL_ii (c = 2).
+__device__ void rev_tile(const SovProblem& P, int tile, const uint64_t* __restrict__ alpha,
+                         const double* __restrict__ Yt, double* __restrict__ St,
+                         const double* __restrict__ omega, double* __restrict__ part,
+                         RevSmem& sm) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int n = P.n;
+    const int64_t p = (int64_t)tile * SOV_P + t;
+    const bool valid = p < P.Ntot;
+    const int64_t q = valid ? p / P.Ns : 0;
+    const uint64_t j = valid ? (uint64_t)(p - q * P.Ns) + 1u : 1u;
+    const uint64_t* __restrict__ dq = P.delta + q * P.dstride;
+    const double* __restrict__ L = P.L;
+    const int64_t ld = P.ld;
+    const double wp = valid ? omega[p] : 0.0;
+    const bool live = wp > 0.0;
+    const int nblk = (n + RV_B - 1) / RV_B;
+    for (int blk = nblk - 1; blk >= 0; --blk) {
+        const int r0 = blk * RV_B;
+        const int nb = min(RV_B, n - r0);
+        double acc[RV_B], yb[RV_B];
+#pragma unroll
+        for (int v = 0; v < RV_B; ++v) {
+            acc[v] = 0.0;
+            yb[v] = 0.0;
+        }
+        // (a) limit shift from earlier blocks: acc[v] = sum_{k < r0} L(r0+v, k) y_k
+        for (int k0 = 0; k0 < r0; k0 += RV_B) {
+            __syncthreads();
+            for (int e = t; e < RV_B * RV_B; e += SOV_P) {
+                const int v = e % RV_B, kk = e / RV_B;
+                const int row = r0 + v;
+                sm.Lk[kk][v] = (row < n) ? L[row + (int64_t)(k0 + kk) * ld] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < RV_B; ++kk) {
+                const double yk = Yt[(int64_t)(k0 + kk) * SOV_P + t];
+#pragma unroll
+                for (int v = 0; v < RV_B; ++v) acc[v] = fma(sm.Lk[kk][v], yk, acc[v]);
+            }
+        }
+        // (b) ybar from the later dimensions: yb[v] = sum_{i >= r0+nb} L(i, r0+v) sbar_i
+        for (int i0 = r0 + RV_B; i0 < n; i0 += RV_B) {
+            __syncthreads();
+            for (int e = t; e < RV_B * RV_B; e += SOV_P) {
+                const int ii = e % RV_B, v = e / RV_B;
+                const int row = i0 + ii;
+                sm.Lk[ii][v] = (row < n && v < nb) ? L[row + (int64_t)(r0 + v) * ld] : 0.0;
+            }
+            __syncthreads();
+            const int ni = min(RV_B, n - i0);
+            for (int ii = 0; ii < ni; ++ii) {
+                const double sb = St[(int64_t)(i0 + ii) * SOV_P + t];
+#pragma unroll
+                for (int v = 0; v < RV_B; ++v) yb[v] = fma(sm.Lk[ii][v], sb, yb[v]);
+            }
+        }
+        // (c) block operands
+        __syncthreads();
+        for (int e = t; e < RV_B * RV_B; e += SOV_P) {
+            const int v = e % RV_B, u = e / RV_B;
+            sm.Ld[v][u] = (v < nb && u <= v) ? L[(r0 + v) + (int64_t)(r0 + u) * ld] : 0.0;
+        }
+        if (t < RV_B) {
+            sm.a[t] = (t < nb) ? P.a[r0 + t] : 0.0;
+            sm.b[t] = (t < nb) ? P.b[r0 + t] : 1.0;
+            sm.alpha[t] = (t < nb) ? alpha[r0 + t] : 0u;
+        }
+        __syncthreads();
+        double y[RV_B], ap[RV_B], bp[RV_B];
+#pragma unroll
+        for (int v = 0; v < RV_B; ++v) {
+            y[v] = (v < nb) ? Yt[(int64_t)(r0 + v) * SOV_P + t] : 0.0;
+        }
+        // (d) forward in the block: limits of each dimension
+#pragma unroll
+        for (int v = 0; v < RV_B; ++v) {
+            double s = acc[v];
+#pragma unroll
+            for (int u = 0; u < v; ++u) s = fma(sm.Ld[v][u], y[u], s);
+            const double lii = (v < nb) ? sm.Ld[v][v] : 1.0;
+            ap[v] = (sm.a[v] - s) / lii;
+            bp[v] = (sm.b[v] - s) / lii;
+        }
+        // (e) reverse in the block
+#pragma unroll
+        for (int v = RV_B - 1; v >= 0; --v) {
+            double ga = 0.0, gb = 0.0, gd = 0.0, sbar = 0.0;
+            if (v < nb && live) {
+                const double lii = sm.Ld[v][v];
+                const double w = lattice_w(j, sm.alpha[v], dq[r0 + v]);
+                const double A = ap[v], Bv = bp[v];
+                double delta;
+                if (A > 0.0) {
+                    delta = 0.5 * erfc(A * 0.70710678118654752440) -
+                            ((Bv == INFINITY) ? 0.0 : 0.5 * erfc(Bv * 0.70710678118654752440));
+                } else {
+                    delta = ((Bv == INFINITY) ? 1.0 : 0.5 * erfc(-Bv * 0.70710678118654752440)) -
+                            ((A == -INFINITY) ? 0.0 : 0.5 * erfc(-A * 0.70710678118654752440));
+                }
+                const double pa = (A == -INFINITY) ? 0.0 : phi_d(A);
+                const double pb = (Bv == INFINITY) ? 0.0 : phi_d(Bv);
+                const double py = phi_d(y[v]);
+                const double apbar = -pa / delta + yb[v] * (1.0 - w) * pa / py;
+                const double bpbar = pb / delta + yb[v] * w * pb / py;
+                sbar = -(apbar + bpbar) / lii;
+                ga = wp * apbar / lii;
+                gb = wp * bpbar / lii;
+                double lb = 0.0;
+                if (pa != 0.0) lb -= apbar * A;
+                if (pb != 0.0) lb -= bpbar * Bv;
+                gd = wp * lb / lii;
+#pragma unroll
+                for (int u = 0; u < v; ++u) yb[u] = fma(sbar, sm.Ld[v][u], yb[u]);
+            }
+            if (v < nb) St[(int64_t)(r0 + v) * SOV_P + t] = sbar;
+            // reductions over the tile's paths (warp shuffles, then 4 warps in shared memory)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                gb += __shfl_xor_sync(0xffffffffu, gb, o);
+                gd += __shfl_xor_sync(0xffffffffu, gd, o);
+            }
+            if (lane == 0) {
+                sm.red[0][v][warp] = ga;
+                sm.red[1][v][warp] = gb;
+                sm.red[2][v][warp] = gd;
+            }
+        }
+        __syncthreads();
+        if (t < 3 * RV_B) {
+            const int c = t / RV_B, v = t % RV_B;
+            if (v < nb) {
+                const double s = ((sm.red[c][v][0] + sm.red[c][v][1]) + sm.red[c][v][2]) +
+                                 sm.red[c][v][3];
+                part[((int64_t)tile * 3 + c) * n + r0 + v] = s;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(SOV_P) k_sov_rev(const SovProblem P, int nitems,
+                                                   int* __restrict__ counter,
+                                                   const uint64_t* __restrict__ alpha,
+                                                   const double* __restrict__ Y,
+                                                   double* __restrict__ Sbar, int64_t ystride,
+                                                   const double* __restrict__ omega,
+                                                   double* __restrict__ part) {
+    __shared__ RevSmem sm;
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        rev_tile(P, it, alpha, Y + (int64_t)it * ystride, Sbar + (int64_t)it * ystride, omega,
+                 part, sm);
+    }
+}
+
+// out[c * n + i] = sum over tiles (fixed order) of part[(tile * 3 + c) * n + i]
+__global__ void k_sum_parts(const double* __restrict__ part, int ntiles, int n,
+                            double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int tl = 0; tl < ntiles; ++tl) s += part[((int64_t)tl * 3 + c) * n + i];
+    out[(int64_t)c * n + i] = s;
+}
+
+// dL(i, k) for i > k: sum over paths of w_p sbar_{p,i} y_{p,k}; dL(i, i) = dsum[2n + i].
+// Paths are laid out per tile: X[tile][dim][128].  One 64 x 64 lower output tile per block.
+__global__ void __launch_bounds__(256) k_grad_L(int n, int ntiles, int64_t Ntot,
+                                                const double* __restrict__ Sbar,
+                                                const double* __restrict__ Y,
+                                                const double* __restrict__ omega,
+                                                const double* __restrict__ dsum,
+                                                double* __restrict__ G, int64_t ldg) {
+    __shared__ double As[32][64 + 1];  // As[pp][r] = w_p sbar_{p, R0 + r}
+    __shared__ double Bs[32][64 + 1];  // Bs[pp][c] = y_{p, C0 + c}
+    const int x = blockIdx.x;
+    int ti = (int)((sqrt(8.0 * x + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= x) ++ti;
+    while (ti * (ti + 1) / 2 > x) --ti;
+    const int tj = x - ti * (ti + 1) / 2;
+    const int R0 = ti * 64, C0 = tj * 64;
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    double acc[4][4] = {};
+    for (int tl = 0; tl < ntiles; ++tl) {
+        const double* St = Sbar + (int64_t)tl * n * SOV_P;
+        const double* Yt = Y + (int64_t)tl * n * SOV_P;
+        for (int c0 = 0; c0 < SOV_P; c0 += 32) {
+            __syncthreads();
+            for (int e = t; e < 32 * 64; e += 256) {
+                const int pp = e % 32, r = e / 32;
+                const int64_t pth = (int64_t)tl * SOV_P + c0 + pp;
+                const double wv = (pth < Ntot) ? omega[pth] : 0.0;
+                As[pp][r] = (R0 + r < n) ? wv * St[(int64_t)(R0 + r) * SOV_P + c0 + pp] : 0.0;
+                Bs[pp][r] = (C0 + r < n) ? Yt[(int64_t)(C0 + r) * SOV_P + c0 + pp] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int pp = 0; pp < 32; ++pp) {
+                double a[4], b[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) a[u] = As[pp][tx + 16 * u];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) b[v] = Bs[pp][ty + 16 * v];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int c = C0 + ty + 16 * v;
+        if (c >= n) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = R0 + tx + 16 * u;
+            if (r >= n || r < c) continue;
+            G[r + (int64_t)c * ldg] = (r == c) ? dsum[2 * (int64_t)n + r] : acc[u][v];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- generic FP64 GEMM
+
+// C(i, j) += alpha * sum_k A(i, k) B(k, j) for i < m, j < nn, with element strides:
+//   A(i,k) = A[i*sar + k*sac], B(k,j) = B[k*sbr + j*sbc], C(i,j) = C[i + j*ldc] (column-major).
+// triA: 0 = dense, 1 = lower (A(i,k) = 0 for k > i), 2 = upper (A(i,k) = 0 for k < i).
+// lowerC: only entries with i + ci0 >= j + cj0 are written (a lower triangle of the parent).
+__global__ void __launch_bounds__(256) k_gemm64(int m, int nn, int kk, double alpha,
+                                                const double* __restrict__ A, int64_t sar,
+                                                int64_t sac, const double* __restrict__ B,
+                                                int64_t sbr, int64_t sbc, double* __restrict__ C,
+                                                int64_t ldc, int triA, int lowerC, int ci0,
+                                                int cj0) {
+    __shared__ double As[16][64 + 1];  // As[k][i]
+    __shared__ double Bs[16][64 + 1];  // Bs[k][j]
+    const int I0 = blockIdx.x * 64, J0 = blockIdx.y * 64;
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < kk; k0 += 16) {
+        __syncthreads();
+        for (int e = t; e < 16 * 64; e += 256) {
+            const int i = e % 64, k = e / 64;
+            const int gi = I0 + i, gk = k0 + k;
+            double av = 0.0;
+            if (gi < m && gk < kk && !(triA == 1 && gk > gi) && !(triA == 2 && gk < gi))
+                av = A[gi * sar + gk * sac];
+            As[k][i] = av;
+            const int gj = J0 + i;
+            Bs[k][i] = (gj < nn && gk < kk) ? B[gk * sbr + gj * sbc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = As[k][tx + 16 * u];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) b[v] = Bs[k][ty + 16 * v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int j = J0 + ty + 16 * v;
+        if (j >= nn) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = I0 + tx + 16 * u;
+            if (i >= m) continue;
+            if (lowerC && i + ci0 < j + cj0) continue;
+            C[i + (int64_t)j * ldc] += alpha * acc[u][v];
+        }
+    }
+}
+
+static mvn_status gemm64(mvn_ctx* ctx, int m, int nn, int kk, double alpha, const double* A,
+                         int64_t sar, int64_t sac, const double* B, int64_t sbr, int64_t sbc,
+                         double* C, int64_t ldc, int triA = 0, int lowerC = 0, int ci0 = 0,
+                         int cj0 = 0) {
+    if (m <= 0 || nn <= 0 || kk <= 0) return MVN_OK;
+    dim3 grid((m + 63) / 64, (nn + 63) / 64);
+    k_gemm64<<<grid, 256, 0, ctx->stream>>>(m, nn, kk, alpha, A, sar, sac, B, sbr, sbc, C, ldc,
+                                            triA, lowerC, ci0, cj0);
+    MVN_LAUNCHED(ctx);
+    return MVN_OK;
+}
+
+// ---------------------------------------------------------------- Cholesky adjoint
+
+#define CG_NB 64
+
+// Unblocked reverse of the column Cholesky on one nb x nb diagonal block (in shared memory):
+// on entry G = dF/dL_jj (lower), on exit dF/dA' (lower) of the block's input.
+__global__ void __launch_bounds__(256) k_cgrad_diag(const double* __restrict__ L, int64_t ld,
+                                                    double* __restrict__ G, int64_t ldg, int c0,
+                                                    int nb) {
+    __shared__ double Ls[CG_NB][CG_NB + 1];
+    __shared__ double Gs[CG_NB][CG_NB + 1];
+    const int t = threadIdx.x;
+    for (int e = t; e < nb * nb; e += 256) {
+        const int i = e % nb, k = e / nb;
+        Ls[i][k] = (i >= k) ? L[(c0 + i) + (int64_t)(c0 + k) * ld] : 0.0;
+        Gs[i][k] = (i >= k) ? G[(c0 + i) + (int64_t)(c0 + k) * ldg] : 0.0;
+    }
+    __syncthreads();
+    for (int jj = nb - 1; jj >= 0; --jj) {
+        const double ljj = Ls[jj][jj];
+        // off-diagonal entries of column jj: L_ij = (A_ij - sum_{k<jj} L_ik L_jk) / L_jj
+        // g_i = G_ij / L_jj;  G_ik -= g_i L_jk, G_jk -= g_i L_ik (k < jj);  G_jj -= g_i L_ij
+        // The updates of row jj (G_jk, G_jj) sum over i: one thread per k, loop over i in order.
+        for (int k = t; k < jj; k += 256) {
+            double s = 0.0;
+            for (int i = nb - 1; i > jj; --i) s += (Gs[i][jj] / ljj) * Ls[i][k];
+            Gs[jj][k] -= s;
+        }
+        if (t == 0) {
+            double s = 0.0;
+            for (int i = nb - 1; i > jj; --i) s += (Gs[i][jj] / ljj) * Ls[i][jj];
+            Gs[jj][jj] -= s;
+        }
+        __syncthreads();
+        for (int e = t; e < (nb - jj - 1) * jj; e += 256) {
+            const int i = jj + 1 + e % (nb - jj - 1), k = e / (nb - jj - 1);
+            Gs[i][k] -= (Gs[i][jj] / ljj) * Ls[jj][k];
+        }
+        __syncthreads();
+        for (int i = jj + 1 + t; i < nb; i += 256) Gs[i][jj] /= ljj;
+        __syncthreads();
+        // pivot: L_jj = sqrt(A_jj - sum_{k<jj} L_jk^2);  g = G_jj / (2 L_jj); G_jk -= 2 g L_jk
+        const double g = Gs[jj][jj] / (2.0 * ljj);
+        for (int k = t; k < jj; k += 256) Gs[jj][k] -= 2.0 * g * Ls[jj][k];
+        __syncthreads();
+        if (t == 0) Gs[jj][jj] = g;
+        __syncthreads();
+    }
+    for (int e = t; e < nb * nb; e += 256) {
+        const int i = e % nb, k = e / nb;
+        if (i >= k) G[(c0 + i) + (int64_t)(c0 + k) * ldg] = Gs[i][k];
+    }
+}
+
+// Panel: rows r >= r1 of block column j: Z L_jj = Xbar (solved from the right, in place).
+__global__ void __launch_bounds__(128) k_cgrad_panel(const double* __restrict__ L, int64_t ld,
+                                                     double* __restrict__ G, int64_t ldg, int c0,
+                                                     int nb, int r1, int n) {
+    __shared__ double Ls[CG_NB][CG_NB + 1];
+    const int t = threadIdx.x;
+    for (int e = t; e < nb * nb; e += 128) {
+        const int i = e % nb, k = e / nb;
+        Ls[i][k] = (i >= k) ? L[(c0 + i) + (int64_t)(c0 + k) * ld] : 0.0;
+    }
+    __syncthreads();
+    const int r = r1 + blockIdx.x * 128 + t;
+    if (r >= n) return;
+    double z[CG_NB];
+#pragma unroll
+    for (int c = CG_NB - 1; c >= 0; --c) {
+        if (c < nb) {
+            double s = G[r + (int64_t)(c0 + c) * ldg];
+#pragma unroll
+            for (int d = c + 1; d < CG_NB; ++d)
+                if (d < nb) s -= z[d] * Ls[d][c];
+            z[c] = s / Ls[c][c];
+        } else {
+            z[c] = 0.0;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CG_NB; ++c)
+        if (c < nb) G[r + (int64_t)(c0 + c) * ldg] = z[c];
+}
+
+mvn_status cholesky_grad_launch(mvn_ctx* ctx, int n, const double* L, int64_t ld, double* G,
+                                int64_t ldg) {
+    const int nblk = (n + CG_NB - 1) / CG_NB;
+    for (int jb = nblk - 1; jb >= 0; --jb) {
+        const int c0 = jb * CG_NB;
+        const int nb = std::min(CG_NB, n - c0);
+        const int r1 = c0 + nb, m = n - r1;
+        double* Gp = G + r1 + (int64_t)c0 * ldg;        // panel adjoint (m x nb)
+        const double* Xp = L + r1 + (int64_t)c0 * ld;   // panel of L (m x nb)
+        if (m > 0) {
+            k_cgrad_panel<<<(m + 127) / 128, 128, 0, ctx->stream>>>(L, ld, G, ldg, c0, nb, r1, n);
+            MVN_LAUNCHED(ctx);
+            // Gjj -= lower(Zp^T Xp)
+            MVN_TRY(gemm64(ctx, nb, nb, m, -1.0, Gp, ldg, 1, Xp, 1, ld,
+                           G + c0 + (int64_t)c0 * ldg, ldg, 0, 1, 0, 0));
+            if (c0 > 0) {
+                // G(r1:n, 0:c0) -= Zp L(c0:c0+nb, 0:c0)
+                MVN_TRY(gemm64(ctx, m, c0, nb, -1.0, Gp, 1, ldg, L + c0, 1, ld, G + r1, ldg));
+                // G(c0:c0+nb, 0:c0) -= Zp^T L(r1:n, 0:c0)
+                MVN_TRY(gemm64(ctx, nb, c0, m, -1.0, Gp, ldg, 1, L + r1, 1, ld, G + c0, ldg));
+            }
+        }
+        k_cgrad_diag<<<1, 256, 0, ctx->stream>>>(L, ld, G, ldg, c0, nb);
+        MVN_LAUNCHED(ctx);
+        if (c0 > 0) {
+            // G(c0:c0+nb, 0:c0) -= (Ajj + Ajj^T) L(c0:c0+nb, 0:c0),  Ajj lower
+            const double* Aj = G + c0 + (int64_t)c0 * ldg;
+            MVN_TRY(gemm64(ctx, nb, c0, nb, -1.0, Aj, 1, ldg, L + c0, 1, ld, G + c0, ldg, 1));
+            MVN_TRY(gemm64(ctx, nb, c0, nb, -1.0, Aj, ldg, 1, L + c0, 1, ld, G + c0, ldg, 2));
+        }
+    }
+    return MVN_OK;
+}
+
+extern "C" mvn_status mvn_cholesky_grad(mvn_ctx* ctx, int n, const double* L, int64_t ld,
+                                        double* Lbar) {
+    if (!ctx) return MVN_ERR_ARG;
+    if (n < 0 || ld < (n > 0 ? n : 1) || (n > 0 && (!L || !Lbar)))
+        return mvn_fail(ctx, MVN_ERR_ARG, "mvn_cholesky_grad: invalid argument");
+    if (n == 0) return MVN_OK;
+    MVN_CUDA(ctx, cudaSetDevice(ctx->device));
+    return cholesky_grad_launch(ctx, n, L, ld, Lbar, ld);
+}
+
+// ---------------------------------------------------------------- SOV gradient
+
+extern "C" mvn_status mvn_sov_grad(mvn_ctx* ctx, int n, const double* a, const double* b,
+                                   const double* L, int64_t ld, const mvn_qmc* qmc,
+                                   mvn_prec prec, double* out3, double* dlogp_da,
+                                   double* dlogp_db, double* dlogp_dL) {
+    if (!ctx) return MVN_ERR_ARG;
+    MVN_TRY(check_qmc(ctx, qmc));
+    MVN_TRY(check_problem_host(ctx, n, a, b, L, ld));
+    if (!out3) return mvn_fail(ctx, MVN_ERR_ARG, "out3 is null");
+    if (prec != MVN_FP64 && prec != MVN_MIXED && prec != MVN_MIXED_SIMT)
+        return mvn_fail(ctx, MVN_ERR_ARG, "unknown precision");
+    MVN_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int M = qmc->n_shifts;
+    const int64_t Ns = qmc->n_points, Ntot = Ns * M;
+    const int64_t ntiles = (Ntot + SOV_P - 1) / SOV_P;
+    const int nn = std::max(n, 1);
+    const int64_t ystride = (int64_t)nn * SOV_P;
+    if ((double)ntiles * ystride * 16.0 > 200e9)
+        return mvn_fail(ctx, MVN_ERR_ARG, "gradient workspace beyond 200 GB");
+    MVN_TRY(lattice_ensure(ctx, nn));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 2 * (int64_t)ctx->sm_count));
+    const size_t need = ws_round(sizeof(uint64_t) * (size_t)M * nn) + ws_round(sizeof(double) * Ntot) * 2 +
+                        2 * ws_round(sizeof(double) * (size_t)ntiles * ystride) +
+                        ws_round(sizeof(double) * 3 * (size_t)ntiles * nn) +
+                        ws_round(sizeof(double) * 3 * (size_t)nn) + 4 * ws_round(sizeof(double)) + 4096;
+    MVN_TRY(ws_reserve(ctx, need));
+    WsCarver wc(ctx->ws);
+    uint64_t* delta = wc.take<uint64_t>((size_t)M * nn);
+    double* logw = wc.take<double>(Ntot);
+    double* omega = wc.take<double>(Ntot);
+    double* Y = wc.take<double>((size_t)ntiles * ystride);
+    double* Sb = wc.take<double>((size_t)ntiles * ystride);
+    double* part = wc.take<double>(3 * (size_t)ntiles * nn);
+    double* dsum = wc.take<double>(3 * (size_t)nn);
+    double* lse = wc.take<double>(1);
+    int* counter = wc.take<int>(2);
+    MVN_TRY(check_limits_device(ctx, n, a, b));
+    MVN_TRY(lattice_shifts(ctx, qmc->seed, M, nn, delta));
+    SovProblem P;
+    memset(&P, 0, sizeof(P));
+    P.n = n;
+    P.M = M;
+    P.Ns = Ns;
+    P.Ntot = Ntot;
+    P.a = a;
+    P.b = b;
+    P.L = L;
+    P.ld = ld;
+    P.delta = delta;
+    P.dstride = nn;
+    P.logw = logw;
+    // forward sweep keeping every tile's y
+    if (n == 0) {
+        MVN_CUDA(ctx, cudaMemsetAsync(logw, 0, sizeof(double) * Ntot, ctx->stream));
+    } else {
+        SovBatch batch;
+        memset(&batch, 0, sizeof(batch));
+        batch.single = P;
+        batch.nitems = (int)ntiles;
+        batch.counter = counter;
+        batch.y_per_tile = 1;
+        MVN_CUDA(ctx, cudaMemsetAsync(counter, 0, 2 * sizeof(int), ctx->stream));
+        k_sov_simt<32, double, true><<<grid, SOV_P, 0, ctx->stream>>>(batch, ctx->d_alpha, Y,
+                                                                       ystride);
+        MVN_LAUNCHED(ctx);
+    }
+    MVN_TRY(sov_reduce_launch_opt(ctx, logw, Ns, M, qmc->err_k, out3, 1, Ntot, true));
+    k_lse_all<<<1, 512, 0, ctx->stream>>>(logw, Ntot, lse);
+    MVN_LAUNCHED(ctx);
+    k_weights<<<(unsigned)((Ntot + 255) / 256), 256, 0, ctx->stream>>>(logw, Ntot, lse, omega);
+    MVN_LAUNCHED(ctx);
+    if (n == 0) return MVN_OK;
+    // reverse sweep
+    k_sov_rev<<<grid, SOV_P, 0, ctx->stream>>>(P, (int)ntiles, counter + 1, ctx->d_alpha, Y, Sb,
+                                               ystride, omega, part);
+    MVN_LAUNCHED(ctx);
+    k_sum_parts<<<dim3((n + 255) / 256, 3), 256, 0, ctx->stream>>>(part, (int)ntiles, n, dsum);
+    MVN_LAUNCHED(ctx);
+    if (dlogp_da)
+        MVN_CUDA(ctx, cudaMemcpyAsync(dlogp_da, dsum, sizeof(double) * n,
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+    if (dlogp_db)
+        MVN_CUDA(ctx, cudaMemcpyAsync(dlogp_db, dsum + n, sizeof(double) * n,
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+    if (dlogp_dL) {
+        const int T = (n + 63) / 64;
+        k_grad_L<<<(unsigned)((int64_t)T * (T + 1) / 2), 256, 0, ctx->stream>>>(
+            n, (int)ntiles, Ntot, Sb, Y, omega, dsum, dlogp_dL, ld);
+        MVN_LAUNCHED(ctx);
+    }
+    return MVN_OK;
+}

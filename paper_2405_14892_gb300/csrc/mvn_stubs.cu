@@ -1,14 +1,6 @@
 // mvn_stubs.cu -- entry points declared in mvn.h whose kernels are not built yet.
 #include "mvn_internal.cuh"
 
-extern "C" mvn_status mvn_cholesky_grad(mvn_ctx* ctx, int, const double*, int64_t, double*) {
-    return mvn_fail(ctx, MVN_ERR_NOT_IMPLEMENTED, "mvn_cholesky_grad: not implemented");
-}
-extern "C" mvn_status mvn_sov_grad(mvn_ctx* ctx, int, const double*, const double*,
-                                   const double*, int64_t, const mvn_qmc*, mvn_prec, double*,
-                                   double*, double*, double*) {
-    return mvn_fail(ctx, MVN_ERR_NOT_IMPLEMENTED, "mvn_sov_grad: not implemented");
-}
 extern "C" mvn_status mvn_tlr_compress(mvn_ctx* ctx, int, const double*, int64_t, int, double,
                                        int, mvn_tlr** out, int*) {
     if (out) *out = nullptr;

@@ -104,8 +104,13 @@ mvn_status mvn_matern_grad(mvn_ctx* ctx, int n, const double* coords, double sig
 
 /* In-place lower Cholesky factorisation A = L L^T (Alg. 1 "dpotrf"), tile algorithm with tile
  * size `tile` (0 = automatic).  Only the lower triangle of A is read and written.
- * prec: MVN_FP64 (every update in FP64).  Other values are accepted and also run in FP64 (the
- * factor needs FP64 accuracy for the SOV estimate at the stated tolerance).
+ * prec: MVN_FP64 / MVN_MIXED_SIMT: right-looking over 64-wide panels, every update in FP64.
+ *   MVN_MIXED: left-looking over 128-wide panels; the trailing updates run on the tcgen05 tensor
+ *   cores on exact BF16 digit slices of the rows of L (6 digits of 7 bits after a per-row
+ *   power-of-two scaling; digit products summed exactly in FP32 per 128-wide chunk, combined in
+ *   double-float), i.e. ~43 significant bits per product; POTRF and TRSM in FP64.  The SOV
+ *   estimate needs a factor of FP64-class accuracy (an FP32 factor moves log P by ~1e-2 at
+ *   n = 16,384), which this keeps.
  * info (host, optional): if non-NULL the call waits for completion and *info = 0 or the 1-based
  * index of the first non-positive pivot (LAPACK convention), returning MVN_ERR_NOT_PD in that
  * case.  If NULL the call is asynchronous and a failure is reported by mvn_sync. */

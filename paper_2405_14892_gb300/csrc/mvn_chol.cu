@@ -9,6 +9,10 @@
 
 #define CH_NB 64
 
+// tensor-core factorisation with FP64-class accuracy (mvn_chol_oz.cu)
+size_t chol_oz_ws_bytes(int n);
+mvn_status chol_oz_launch(mvn_ctx* ctx, int n, double* A, int64_t ld, char* ws);
+
 __device__ __forceinline__ bool dev_failed(const int* status) {
     return *(volatile const int*)status != 0;
 }
@@ -161,7 +165,14 @@ extern "C" mvn_status mvn_cholesky(mvn_ctx* ctx, int n, double* A, int64_t ld, i
         return mvn_fail(ctx, MVN_ERR_ARG, "unknown precision");
     MVN_CUDA(ctx, cudaSetDevice(ctx->device));
     if (info) *info = 0;
-    if (n > 0) MVN_TRY(chol_f64_launch(ctx, n, A, ld));
+    if (n > 0) {
+        if (prec == MVN_MIXED) {
+            MVN_TRY(ws_reserve(ctx, chol_oz_ws_bytes(n) + 1024));
+            MVN_TRY(chol_oz_launch(ctx, n, A, ld, (char*)ctx->ws));
+        } else {
+            MVN_TRY(chol_f64_launch(ctx, n, A, ld));
+        }
+    }
     if (info) return mvn_sync(ctx, info);
     return MVN_OK;
 }

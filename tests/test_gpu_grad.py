@@ -136,15 +136,16 @@ def test_w4_gradients_vs_central_fd(mvn):
     b0 = _t(b)
     # theta enters through the Cholesky factor of a matrix with condition number ~1e6 (nugget
     # 1e-4): the computed log P(theta) carries rounding roughness of order 1e-7, which a central
-    # difference divides by 2h.  At h = 1e-5 that is ~1e-2 absolute; at h = 1e-3 it is ~1e-4 and
-    # the O(h^2) truncation error is below it.
-    for h, rtol in ((1e-5, 3e-3), (1e-3, 3e-4)):
-        fd_s2 = (f(b0, s2 + h, rg) - f(b0, s2 - h, rg)) / (2 * h)
-        fd_rg = (f(b0, s2, rg + h) - f(b0, s2, rg - h)) / (2 * h)
-        print(f"W4 h={h:g}: logP={lp.item():.8f} dsigma2 {s2t.grad.item():.8e} fd {fd_s2:.8e} | "
-              f"drange {rgt.grad.item():.8e} fd {fd_rg:.8e}")
-        assert abs(s2t.grad.item() - fd_s2) <= rtol * max(1.0, abs(fd_s2))
-        assert abs(rgt.grad.item() - fd_rg) <= rtol * max(1.0, abs(fd_rg))
+    # difference divides by 2h.  At h = 1e-5 that is ~1e-2 absolute.  A step of 1e-3 of each
+    # parameter's value keeps the roughness term ~1e-4 absolute and the O(h^2) truncation below it.
+    g_s2, g_rg = s2t.grad.item(), rgt.grad.item()
+    for hs2, hrg, rtol in ((1e-5, 1e-5, 3e-3), (1e-3 * s2, 1e-3 * rg, 2e-4)):
+        fd_s2 = (f(b0, s2 + hs2, rg) - f(b0, s2 - hs2, rg)) / (2 * hs2)
+        fd_rg = (f(b0, s2, rg + hrg) - f(b0, s2, rg - hrg)) / (2 * hrg)
+        print(f"W4 h=({hs2:g},{hrg:g}): logP={lp.item():.8f} dsigma2 {g_s2:.8e} fd {fd_s2:.8e} | "
+              f"drange {g_rg:.8e} fd {fd_rg:.8e}")
+        assert abs(g_s2 - fd_s2) <= rtol * max(1.0, abs(fd_s2))
+        assert abs(g_rg - fd_rg) <= rtol * max(1.0, abs(fd_rg))
     # b enters only the sweep (the factor is fixed): the estimate is smooth to rounding there
     h = 1e-5
     rng = np.random.default_rng(4)

@@ -116,3 +116,65 @@ def test_mixed_tc_batched_and_excursion(mvn):
     for p, k in enumerate(dims):
         e = oracle.sov(a[:k], b[:k], Lo[:k, :k], oracle.QMC(128, 4, 17))
         assert abs(out[p, 0] - e[0]) <= 1e-4, (p, out[p], e)
+
+
+# ------------------------------------------------------------------ tensor-core Cholesky (A2 mixed)
+
+@pytest.mark.parametrize("n", [1, 100, 128, 130, 700])
+def test_cholesky_mixed_vs_oracle(mvn, n):
+    g = int(math.ceil(math.sqrt(n)))
+    c = inputs.grid_coords(g)[:n]
+    S = oracle.matern(c, 1.0, 0.1, 1.5, nugget=1e-4)
+    A = mvn.to_colmajor(_t(S))
+    assert mvn.mvn_cholesky(A, prec="mixed") == 0
+    L = np.tril(A.cpu().numpy())
+    Lo, _ = oracle.cholesky(S)
+    bwd = np.linalg.norm(L @ L.T - S) / np.linalg.norm(S)
+    print(f"n={n}: mixed Cholesky backward error {bwd:.3e}, max |L - L_oracle| "
+          f"{np.abs(L - Lo).max():.3e}")
+    assert bwd < 1e-11, bwd
+    assert np.abs(L - Lo).max() < 1e-6
+
+
+def test_cholesky_mixed_not_pd(mvn):
+    S = oracle.matern(inputs.random_coords(300, 4), 1.0, 0.2, 0.5)
+    S[200, 200] = -1.0
+    A = mvn.to_colmajor(_t(S))
+    with pytest.raises(mvn.MVNError) as e:
+        mvn.mvn_cholesky(A, prec="mixed")
+    assert e.value.status == mvn.MVN_ERR_NOT_PD
+    B = mvn.to_colmajor(_t(np.eye(3) * 4.0))
+    assert mvn.mvn_cholesky(B, prec="mixed") == 0
+    assert abs(B.cpu().numpy()[2, 2] - 2.0) < 1e-15
+
+
+def test_cholesky_mixed_w2_full_size(mvn):
+    """W2 (n=16,384): tensor-core factor of the GPU covariance vs the oracle covariance (backward
+    error by random matrix-vector products) and its effect on the W2 log P against the FP64
+    factor on identical lattice points (the stated bound |d log P| <= 1e-4)."""
+    w = dict(inputs.WORKLOADS["W2"])
+    c = inputs.grid_coords(w["g"])
+    n = c.shape[0]
+    a, b = inputs.limits_for(w, n)
+    So = oracle.matern_closed(c, w["sigma2"], w["range"], w["nu"], w["nugget"])
+    S = mvn.mvn_matern(_t(c), w["sigma2"], w["range"], w["nu"], w["nugget"])
+    S64 = S.clone()
+    assert mvn.mvn_cholesky(S, prec="mixed") == 0
+    assert mvn.mvn_cholesky(S64, prec="fp64") == 0
+    Lg = torch.tril(S)
+    rng = np.random.default_rng(1)
+    for _ in range(3):
+        v = rng.standard_normal(n)
+        LLv = (Lg @ (Lg.t() @ _t(v))).cpu().numpy()
+        Sv = So @ v
+        bwd = np.linalg.norm(LLv - Sv) / np.linalg.norm(Sv)
+        # products carry 43 bits (2^-43 ~ 1.1e-13) relative to the row maxima; accumulated over
+        # n = 16,384 terms the bound is ~n 2^-43 ~ 2e-9
+        assert bwd < 5e-10, bwd
+    del Lg
+    Ns, M = 200, 10
+    o_mx = mvn.mvn_sov(_t(a), _t(b), S, Ns, M, w["seed"], prec="fp64").cpu().numpy()
+    o_64 = mvn.mvn_sov(_t(a), _t(b), S64, Ns, M, w["seed"], prec="fp64").cpu().numpy()
+    mvn.sync()
+    print(f"W2 log P with tensor-core factor {o_mx[0]:.10f} vs FP64 factor {o_64[0]:.10f}")
+    assert abs(o_mx[0] - o_64[0]) <= 1e-4

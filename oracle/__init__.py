@@ -404,3 +404,92 @@ def excursion(mu, Sigma, u, one_minus_alpha, qmc: QMC, prefix_dims=None, err_k: 
     K = max(ok) if ok else 0
     region[order[:K]] = 1
     return dict(order=order, marginal=pM, F=F, prefixes=ks, region=region, L=L)
+
+
+# --------------------------------------------------------------------------- tile low rank (Sec. III-E)
+
+def tlr_tile_index(i: int, j: int, nt: int) -> int:
+    """Position of off-diagonal tile (i, j), i > j, in column order (1,0),(2,0),..,(nt-1,0),(2,1).."""
+    return j * nt - j * (j + 1) // 2 + (i - j - 1)
+
+
+def tlr_truncate(A: np.ndarray, acc: float, max_rank: int):
+    """Truncated SVD of one tile (Sec. III-E: "the ranks of the tiles correspond to the most
+    significant singular values"): the smallest rank k with sigma_{k+1} <= acc, capped at
+    max_rank.  Returns (U sigma, V, k, capped) with A ~= (U sigma) V^T; by Eckart-Young the
+    2-norm error is sigma_{k+1} (numpy's SVD as the library step)."""
+    Uf, s, Vt = np.linalg.svd(A, full_matrices=False)
+    k = int(np.count_nonzero(s > acc))
+    capped = k > max_rank
+    k = min(k, max_rank)
+    return Uf[:, :k] * s[:k], Vt[:k].T.copy(), k, capped
+
+
+def tlr_compress(Sigma: np.ndarray, tile: int, acc: float, max_rank: int):
+    """TLR form of the lower triangle of Sigma: dense diagonal tiles D[i], and for i > j the
+    truncated SVD of tile (i, j).  Returns dict(D, U, V, ranks (column order), capped, nt, m)."""
+    n = Sigma.shape[0]
+    m = tile
+    nt = (n + m - 1) // m
+    D, U, V, ranks = [], {}, {}, []
+    capped = 0
+    for i in range(nt):
+        r = slice(i * m, min(n, (i + 1) * m))
+        D.append(np.array(Sigma[r, r]))
+    for j in range(nt):
+        for i in range(j + 1, nt):
+            A = Sigma[i * m:min(n, (i + 1) * m), j * m:min(n, (j + 1) * m)]
+            u, v, k, cp = tlr_truncate(A, acc, max_rank)
+            U[(i, j)], V[(i, j)] = u, v
+            ranks.append(k)
+            capped += int(cp)
+    return dict(D=D, U=U, V=V, ranks=np.array(ranks, dtype=np.int32), capped=capped, nt=nt, m=m,
+                n=n, acc=acc, max_rank=max_rank)
+
+
+def tlr_cholesky(T: dict):
+    """TLR Cholesky (Alg. 1 "dpotrf" on TLR tiles, HiCMA-style, Akbudak et al. 2017), left-looking:
+      D_kk -= sum_{l<k} U_kl (V_kl^T V_kl) U_kl^T;  L_kk = chol(D_kk)
+      A_ik  = U_ik V_ik^T - sum_{l<k} U_il (V_il^T V_kl) U_kl^T   (accumulated densely)
+      A_ik ~= U' V'^T truncated at acc (recompression);  L_ik = U' (L_kk^-1 V')^T.
+    Returns a new dict with the factor in the same form (D holds the L_kk).
+    parity unpinned beyond: acc -> 0 reduces to the dense Cholesky (pinned), and the
+    reconstruction error of the factor is of the order of acc (checked)."""
+    nt, acc, kmax = T["nt"], T["acc"], T["max_rank"]
+    D = [d.copy() for d in T["D"]]
+    U = dict(T["U"])
+    V = dict(T["V"])
+    ranks = {}
+    for k in range(nt):
+        Dk = D[k]
+        for l in range(k):
+            W = V[(k, l)].T @ V[(k, l)]
+            Dk -= U[(k, l)] @ W @ U[(k, l)].T
+        Lkk = np.linalg.cholesky(0.5 * (Dk + Dk.T))
+        D[k] = Lkk
+        for i in range(k + 1, nt):
+            A = U[(i, k)] @ V[(i, k)].T
+            for l in range(k):
+                A -= U[(i, l)] @ (V[(i, l)].T @ V[(k, l)]) @ U[(k, l)].T
+            u, v, r, _ = tlr_truncate(A, acc, kmax)
+            U[(i, k)] = u
+            V[(i, k)] = np.linalg.solve(Lkk, v) if r else v   # (u v^T) L^-T = u (L^-1 v)^T
+            ranks[(i, k)] = r
+    out = dict(T)
+    out.update(D=D, U=U, V=V,
+               ranks=np.array([ranks[(i, j)] for j in range(nt) for i in range(j + 1, nt)],
+                              dtype=np.int32))
+    return out
+
+
+def tlr_to_dense(T: dict) -> np.ndarray:
+    """Lower-triangular dense matrix of a TLR object (diagonal tiles lower part, U V^T below)."""
+    n, m, nt = T["n"], T["m"], T["nt"]
+    A = np.zeros((n, n))
+    for i in range(nt):
+        r = slice(i * m, min(n, (i + 1) * m))
+        A[r, r] = np.tril(T["D"][i])
+    for j in range(nt):
+        for i in range(j + 1, nt):
+            A[i * m:min(n, (i + 1) * m), j * m:min(n, (j + 1) * m)] = T["U"][(i, j)] @ T["V"][(i, j)].T
+    return A

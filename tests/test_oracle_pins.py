@@ -462,3 +462,43 @@ def test_excursion_mc_validation():
         pmc = np.mean(np.all(x[:, D] > 0.8, axis=1))
         se = math.sqrt(pmc * (1 - pmc) / x.shape[0])
         assert abs(pmc - r["F"][k - 1]) < 4 * se + 3e-3, (k, pmc, r["F"][k - 1])
+
+
+# ----------------------------------------------------------------- TLR (Sec. III-E)
+
+def test_tlr_truncation_eckart_young_and_planted_rank():
+    rng = np.random.default_rng(30)
+    A = rng.standard_normal((60, 7)) @ rng.standard_normal((7, 60))  # rank 7 exactly
+    u, v, k, capped = oracle.tlr_truncate(A, 1e-9, 50)
+    assert k == 7 and not capped
+    np.testing.assert_allclose(u @ v.T, A, atol=1e-10)
+    B = rng.standard_normal((50, 50))
+    s = np.linalg.svd(B, compute_uv=False)
+    acc = s[10] * 1.0000001  # keeps exactly 10 values
+    u, v, k, _ = oracle.tlr_truncate(B, acc, 50)
+    assert k == 10
+    assert abs(np.linalg.norm(B - u @ v.T, 2) - s[10]) < 1e-12 * s[0]  # Eckart-Young
+    u, v, k, capped = oracle.tlr_truncate(B, 0.0, 5)
+    assert k == 5 and capped
+
+
+def test_tlr_compress_and_cholesky_reduce_to_dense():
+    c = inputs.grid_coords(12)
+    S = oracle.matern(c, 1.0, 0.2, 0.5, nugget=1e-6)
+    T = oracle.tlr_compress(S, 32, 1e-15, 32)
+    assert T["nt"] == 5 and len(T["ranks"]) == 10
+    np.testing.assert_allclose(oracle.tlr_to_dense(T), np.tril(S), atol=1e-12)
+    L = oracle.tlr_to_dense(oracle.tlr_cholesky(T))
+    np.testing.assert_allclose(L, np.linalg.cholesky(S), atol=1e-9)
+
+
+def test_tlr_cholesky_error_follows_accuracy():
+    c = inputs.grid_coords(16, order="morton")
+    S = oracle.matern(c, 1.0, 0.1, 0.5, nugget=1e-6)
+    errs = []
+    for acc in (1e-2, 1e-4, 1e-6):
+        T = oracle.tlr_cholesky(oracle.tlr_compress(S, 32, acc, 32))
+        L = oracle.tlr_to_dense(T)
+        errs.append(np.linalg.norm(L @ L.T - S, 2))
+        assert errs[-1] < 50 * acc, (acc, errs[-1])
+    assert errs[0] > errs[1] > errs[2]

@@ -1,0 +1,773 @@
+// mvn_tlr.cu -- tile low-rank (TLR) compression of the covariance and TLR Cholesky (Sec. III-E;
+// Alg. 1 "pmvn_init" / "dpotrf" on TLR tiles), FP64.
+//
+// Compression of a batch of dense m x m tiles A (randomised range finder, Halko, Martinsson and
+// Tropp 2011, with one power iteration), each step a batched kernel:
+//   Y = A Omega (Omega Gaussian, m x r, r = max_rank + 8 <= m);  Q = orth(Y)
+//   Y = A (A^T Q);  Q = orth(Y)
+//   B = Q^T A (r x m);  C = B B^T = W Lambda W^T (two-sided parallel Jacobi, FP64)
+//   sigma_l = sqrt(lambda_l) sorted descending;  k = #{sigma_l > acc} capped at max_rank
+//   U = Q W_k diag(sigma_k),  V = B^T W_k diag(1/sigma_k)  (so A ~= U V^T).
+// orth(Y) is shifted Cholesky QR applied three times (Gram matrix + small shift, Cholesky,
+// triangular inverse, Y R^-1): stable for rank-deficient sketches, whose surplus directions only
+// add rows of negligible norm to B.
+// TLR Cholesky, left-looking over tile columns k (as HiCMA's, with the low-rank updates of a tile
+// accumulated densely and truncated once at the tile's accuracy):
+//   D_kk -= sum_{l<k} U_kl (V_kl^T V_kl) U_kl^T;  L_kk = chol(D_kk)
+//   A_ik  = U_ik V_ik^T - sum_{l<k} (U_il (V_il^T V_kl)) U_kl^T;  A_ik ~= U' V'^T;
+//   L_ik  = U' (L_kk^-1 V')^T.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "mvn_internal.cuh"
+
+mvn_status chol_f64_launch(mvn_ctx* ctx, int n, double* A, int64_t ld);
+
+struct mvn_tlr {
+    mvn_ctx* ctx = nullptr;
+    int n = 0, npad = 0, m = 0, nt = 0, kmax = 0;
+    double acc = 0.0;
+    double* D = nullptr;  // nt diagonal tiles, m x m (ld m)
+    double* U = nullptr;  // ntri tiles, m x kmax (ld m), columns >= rank are zero
+    double* V = nullptr;
+    int* rank = nullptr;  // device, ntri
+    std::vector<int> rank_h;
+    int capped = 0;
+    bool factored = false;
+};
+
+static inline int64_t tri_index(int i, int j, int nt) {  // i > j, column order
+    return (int64_t)j * nt - (int64_t)j * (j + 1) / 2 + (i - j - 1);
+}
+
+// ---------------------------------------------------------------- batched FP64 GEMM
+
+// C(i,j) = alpha sum_l A(i,l) B(l,j) + beta C(i,j); A(i,l) = A[i*sar + l*sac],
+// B(l,j) = B[l*sbr + j*sbc], C(i,j) = C[i + j*ldc]; beta = 0 does not read C.
+struct GItem {
+    const double* A;
+    const double* B;
+    double* C;
+    int m, n, k;
+    int64_t sar, sac, sbr, sbc, ldc;
+    double alpha, beta;
+};
+
+__global__ void __launch_bounds__(256) k_bgemm(const GItem* __restrict__ items) {
+    __shared__ double As[16][64 + 1];
+    __shared__ double Bs[16][64 + 1];
+    const GItem it = items[blockIdx.z];
+    const int I0 = blockIdx.x * 64, J0 = blockIdx.y * 64;
+    if (I0 >= it.m || J0 >= it.n) return;
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < it.k; k0 += 16) {
+        __syncthreads();
+        for (int e = t; e < 16 * 64; e += 256) {
+            const int i = e % 64, l = e / 64;
+            const int gi = I0 + i, gl = k0 + l, gj = J0 + i;
+            As[l][i] = (gi < it.m && gl < it.k) ? it.A[gi * it.sar + gl * it.sac] : 0.0;
+            Bs[l][i] = (gj < it.n && gl < it.k) ? it.B[gl * it.sbr + gj * it.sbc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < 16; ++l) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = As[l][tx + 16 * u];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) b[v] = Bs[l][ty + 16 * v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int j = J0 + ty + 16 * v;
+        if (j >= it.n) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = I0 + tx + 16 * u;
+            if (i >= it.m) continue;
+            double* c = it.C + i + (int64_t)j * it.ldc;
+            *c = (it.beta == 0.0) ? it.alpha * acc[u][v] : fma(it.alpha, acc[u][v], it.beta * *c);
+        }
+    }
+}
+
+// Batched GEMM launcher: items are copied into a workspace slot (pageable copy: staged before
+// the call returns).
+static mvn_status bgemm(mvn_ctx* ctx, const std::vector<GItem>& items, GItem* d_items) {
+    if (items.empty()) return MVN_OK;
+    int mm = 0, nn = 0;
+    for (auto& it : items) {
+        mm = std::max(mm, it.m);
+        nn = std::max(nn, it.n);
+    }
+    if (mm == 0 || nn == 0) return MVN_OK;
+    MVN_CUDA(ctx, cudaMemcpyAsync(d_items, items.data(), sizeof(GItem) * items.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+    for (size_t z0 = 0; z0 < items.size(); z0 += 65535) {
+        const unsigned nz = (unsigned)std::min<size_t>(65535, items.size() - z0);
+        k_bgemm<<<dim3((mm + 63) / 64, (nn + 63) / 64, nz), 256, 0, ctx->stream>>>(d_items + z0);
+        MVN_LAUNCHED(ctx);
+    }
+    return MVN_OK;
+}
+
+static GItem gi(const double* A, int64_t sar, int64_t sac, const double* B, int64_t sbr,
+                int64_t sbc, double* C, int64_t ldc, int m, int n, int k, double alpha,
+                double beta) {
+    GItem g;
+    g.A = A;
+    g.B = B;
+    g.C = C;
+    g.m = m;
+    g.n = n;
+    g.k = k;
+    g.sar = sar;
+    g.sac = sac;
+    g.sbr = sbr;
+    g.sbc = sbc;
+    g.ldc = ldc;
+    g.alpha = alpha;
+    g.beta = beta;
+    return g;
+}
+
+// ---------------------------------------------------------------- small dense kernels
+
+// Omega (m x r, ld m): standard normals by Box-Muller of SplitMix64 counter outputs.
+__global__ void k_gauss(int m, int r, uint64_t seed, double* __restrict__ Om) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * r) return;
+    const uint64_t x1 = splitmix64_at(seed, 2 * (uint64_t)e);
+    const uint64_t x2 = splitmix64_at(seed, 2 * (uint64_t)e + 1);
+    const double u1 = ((double)(x1 >> 11) + 0.5) * 0x1p-53;
+    const double u2 = ((double)(x2 >> 11) + 0.5) * 0x1p-53;
+    Om[e] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+// Per item (one CTA): G (r x r, ld r) <- inverse of the Cholesky factor of G + shift I, upper
+// triangular R^-1 with G + shift I = R^T R, written to Rinv (r x r, ld r, strict lower = 0).
+// shift = 1e-14 * (r + 1) * max_i G_ii keeps the factorisation of a rank-deficient Gram defined.
+__global__ void __launch_bounds__(256) k_chol_inv(int r, double* const* __restrict__ Gs,
+                                                  double* const* __restrict__ Rs) {
+    double* G = Gs[blockIdx.x];
+    double* R = Rs[blockIdx.x];
+    const int t = threadIdx.x;
+    __shared__ double shift;
+    if (t == 0) {
+        double mx = 0.0;
+        for (int i = 0; i < r; ++i) mx = fmax(mx, G[i + (int64_t)i * r]);
+        shift = 1e-14 * (r + 1) * mx + 1e-300;
+    }
+    __syncthreads();
+    for (int i = t; i < r; i += 256) G[i + (int64_t)i * r] += shift;
+    __syncthreads();
+    // in place lower Cholesky G = L L^T (column loop)
+    for (int j = 0; j < r; ++j) {
+        __shared__ double ljj;
+        if (t == 0) {
+            const double d = G[j + (int64_t)j * r];
+            ljj = sqrt(fmax(d, 1e-300));
+            G[j + (int64_t)j * r] = ljj;
+        }
+        __syncthreads();
+        for (int i = j + 1 + t; i < r; i += 256) G[i + (int64_t)j * r] /= ljj;
+        __syncthreads();
+        const int mrem = r - j - 1;
+        for (int e = t; e < mrem * mrem; e += 256) {
+            const int i = j + 1 + e % mrem, c = j + 1 + e / mrem;
+            if (c <= i) G[i + (int64_t)c * r] -= G[i + (int64_t)j * r] * G[c + (int64_t)j * r];
+        }
+        __syncthreads();
+    }
+    // Linv (lower) column by column: L X = I; then R^-1 = (L^-1)^T (upper)
+    for (int c = t; c < r; c += 256) {
+        for (int i = 0; i < r; ++i) R[i + (int64_t)c * r] = 0.0;  // column c of R^-1
+    }
+    __syncthreads();
+    for (int c = t; c < r; c += 256) {
+        // x = L^-1 e_c (entries i >= c): x_i = (delta_ic - sum_{c<=l<i} L_il x_l) / L_ii
+        for (int i = c; i < r; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int l = c; l < i; ++l) s -= G[i + (int64_t)l * r] * R[c + (int64_t)l * r];
+            R[c + (int64_t)i * r] = s / G[i + (int64_t)i * r];  // R^-1(c, i) = Linv(i, c)
+        }
+    }
+}
+
+// deterministic block sum of one value per thread (256 threads)
+__device__ double block_sum256(double v, double* red) {
+    const int t = threadIdx.x;
+    red[t] = v;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    const double s = red[0];
+    __syncthreads();
+    return s;
+}
+
+// Two-sided parallel Jacobi (round-robin pairs) on a symmetric r x r matrix C (ld r) per item;
+// W (r x r) receives the eigenvectors (columns), lam the eigenvalues (diagonal of the converged
+// C), order the column indices sorted by descending eigenvalue.
+__global__ void __launch_bounds__(256) k_jacobi(int r, double* const* __restrict__ Cs,
+                                                double* const* __restrict__ Ws,
+                                                double* const* __restrict__ lams,
+                                                int* const* __restrict__ orders, int max_sweeps) {
+    extern __shared__ double jsm[];  // cs[np], sn[np], pp[np], qq[np] (ints)
+    __shared__ double red[256];
+    double* C = Cs[blockIdx.x];
+    double* W = Ws[blockIdx.x];
+    double* lam = lams[blockIdx.x];
+    int* order = orders[blockIdx.x];
+    const int t = threadIdx.x;
+    const int rp = (r + 1) & ~1;  // even slot count (slot r is a dummy when r is odd)
+    const int np = rp / 2;
+    double* cs = jsm;
+    double* sn = jsm + np;
+    int* pp = (int*)(jsm + 2 * np);
+    int* qq = pp + np;
+    for (int e = t; e < r * r; e += 256) W[e] = ((e % r) == (e / r)) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        double lo = 0.0, ldg = 0.0;
+        for (int e = t; e < r * r; e += 256) {
+            const double v = C[e];
+            if ((e % r) == (e / r)) ldg += v * v;
+            else lo += v * v;
+        }
+        const double offn = block_sum256(lo, red);
+        const double diagn = block_sum256(ldg, red);
+        if (offn <= 1e-30 * diagn) break;
+        for (int round = 0; round < rp - 1; ++round) {
+            for (int k = t; k < np; k += 256) {
+                int a = (k == 0) ? 0 : 1 + (k - 1 + round) % (rp - 1);
+                int b = 1 + (rp - 2 - k + round) % (rp - 1);
+                if (a > b) {
+                    const int x = a;
+                    a = b;
+                    b = x;
+                }
+                pp[k] = a;
+                qq[k] = b;
+                double c = 1.0, s = 0.0;
+                if (b < r) {
+                    const double app = C[a + (int64_t)a * r], aqq = C[b + (int64_t)b * r];
+                    const double apq = C[a + (int64_t)b * r];
+                    if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+                        const double tau = (aqq - app) / (2.0 * apq);
+                        const double tt =
+                            (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + tt * tt);
+                        s = tt * c;
+                    }
+                }
+                cs[k] = c;
+                sn[k] = s;
+            }
+            __syncthreads();
+            for (int e = t; e < np * r; e += 256) {  // rows: C <- J^T C
+                const int k = e % np, j = e / np;
+                const int a = pp[k], b = qq[k];
+                if (b >= r || sn[k] == 0.0) continue;
+                const double x = C[a + (int64_t)j * r], y = C[b + (int64_t)j * r];
+                C[a + (int64_t)j * r] = cs[k] * x - sn[k] * y;
+                C[b + (int64_t)j * r] = sn[k] * x + cs[k] * y;
+            }
+            __syncthreads();
+            for (int e = t; e < np * r; e += 256) {  // columns: C <- C J, W <- W J
+                const int k = e % np, i = e / np;
+                const int a = pp[k], b = qq[k];
+                if (b >= r || sn[k] == 0.0) continue;
+                double x = C[i + (int64_t)a * r], y = C[i + (int64_t)b * r];
+                C[i + (int64_t)a * r] = cs[k] * x - sn[k] * y;
+                C[i + (int64_t)b * r] = sn[k] * x + cs[k] * y;
+                x = W[i + (int64_t)a * r];
+                y = W[i + (int64_t)b * r];
+                W[i + (int64_t)a * r] = cs[k] * x - sn[k] * y;
+                W[i + (int64_t)b * r] = sn[k] * x + cs[k] * y;
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = t; i < r; i += 256) {
+        lam[i] = C[i + (int64_t)i * r];
+        order[i] = i;
+    }
+    __syncthreads();
+    if (t == 0) {  // selection sort of the order by descending eigenvalue (r is small)
+        for (int i = 0; i < r; ++i) {
+            int best = i;
+            for (int j2 = i + 1; j2 < r; ++j2)
+                if (lam[order[j2]] > lam[order[best]]) best = j2;
+            const int x = order[i];
+            order[i] = order[best];
+            order[best] = x;
+        }
+    }
+}
+
+// Per item: rank k = #{sqrt(lambda) > acc} (capped at kmax); WU(:, j) = W(:, order_j) sigma_j and
+// WV(:, j) = W(:, order_j) / sigma_j for j < k, zero columns for j >= k (r x kmax, ld r).
+__global__ void k_select(int r, int kmax, double acc, double* const* __restrict__ Ws,
+                         double* const* __restrict__ lams, int* const* __restrict__ orders,
+                         double* const* __restrict__ WUs, double* const* __restrict__ WVs,
+                         int* __restrict__ rank_out, int* __restrict__ capped) {
+    const double* W = Ws[blockIdx.x];
+    const double* lam = lams[blockIdx.x];
+    const int* order = orders[blockIdx.x];
+    double* WU = WUs[blockIdx.x];
+    double* WV = WVs[blockIdx.x];
+    __shared__ int ks;
+    if (threadIdx.x == 0) {
+        int k = 0;
+        while (k < r && lam[order[k]] > 0.0 && sqrt(lam[order[k]]) > acc) ++k;
+        if (k > kmax) {
+            atomicAdd(capped, 1);
+            k = kmax;
+        }
+        ks = k;
+        rank_out[blockIdx.x] = k;
+    }
+    __syncthreads();
+    const int k = ks;
+    for (int e = threadIdx.x; e < r * kmax; e += blockDim.x) {
+        const int i = e % r, j = e / r;
+        double u = 0.0, v = 0.0;
+        if (j < k) {
+            const double sg = sqrt(lam[order[j]]);
+            const double w = W[i + (int64_t)order[j] * r];
+            u = w * sg;
+            v = w / sg;
+        }
+        WU[e] = u;
+        WV[e] = v;
+    }
+}
+
+// Copy the lower triangle tiles of A into dense m x m scratch tiles (zero outside [0, n), identity
+// on the diagonal of padded rows of diagonal tiles).  One block per (tile, column).
+__global__ void k_copy_tile(int n, int m, const double* __restrict__ A, int64_t ld, int ti, int tj,
+                            double* __restrict__ out) {
+    const int c = blockIdx.x;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        const int i = ti * m + r, j = tj * m + c;
+        double v = 0.0;
+        if (i < n && j < n) v = (i >= j) ? A[i + (int64_t)j * ld] : A[j + (int64_t)i * ld];
+        else if (i == j) v = 1.0;
+        out[r + (int64_t)c * m] = v;
+    }
+}
+
+// V(rows r0..r0+63, :) <- L_bb^-1 V(rows, :) for every item (64-row diagonal block of L_kk in
+// shared memory, one thread per column of one item).
+__global__ void k_trsm_block(int m, int kmax, const double* __restrict__ Lkk, int r0,
+                             double* const* __restrict__ Vs, int nitems) {
+    __shared__ double Lb[64][65];
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        const int i = e % 64, k = e / 64;
+        Lb[i][k] = (i >= k) ? Lkk[(r0 + i) + (int64_t)(r0 + k) * m] : 0.0;
+    }
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int item = g / kmax, col = g % kmax;
+    if (item >= nitems) return;
+    double* V = Vs[item] + (int64_t)col * m + r0;
+    double x[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) {
+        double s = V[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) s -= Lb[i][k] * x[k];
+        x[i] = s / Lb[i][i];
+    }
+#pragma unroll
+    for (int i = 0; i < 64; ++i) V[i] = x[i];
+}
+
+// ---------------------------------------------------------------- compression pipeline
+
+struct CompWs {
+    int m, r, kmax, T;
+    double *Om, *Y, *Q, *Z, *B, *G, *R, *W, *WU, *WV, *lam;
+    int *order, *rank, *capped;
+    double **pG, **pR, **pW, **pWU, **pWV, **plam;
+    int** porder;
+    GItem* items;
+};
+
+static size_t comp_ws_bytes(int m, int r, int kmax, int T) {
+    const size_t mr = (size_t)m * r, rr = (size_t)r * r;
+    return ws_round(sizeof(double) * mr) + 4 * ws_round(sizeof(double) * mr * T) +
+           3 * ws_round(sizeof(double) * rr * T) + 2 * ws_round(sizeof(double) * (size_t)r * kmax * T) +
+           ws_round(sizeof(double) * (size_t)r * T) + 2 * ws_round(sizeof(int) * (size_t)r * T) +
+           ws_round(sizeof(int) * (size_t)T) + ws_round(sizeof(int)) + 7 * ws_round(sizeof(void*) * T) +
+           ws_round(sizeof(GItem) * (size_t)T * 4) + 8 * 256;
+}
+
+static CompWs comp_ws_carve(WsCarver& wc, int m, int r, int kmax, int T) {
+    CompWs c;
+    c.m = m;
+    c.r = r;
+    c.kmax = kmax;
+    c.T = T;
+    const size_t mr = (size_t)m * r, rr = (size_t)r * r;
+    c.Om = wc.take<double>(mr);
+    c.Y = wc.take<double>(mr * T);
+    c.Q = wc.take<double>(mr * T);
+    c.Z = wc.take<double>(mr * T);
+    c.B = wc.take<double>(mr * T);
+    c.G = wc.take<double>(rr * T);
+    c.R = wc.take<double>(rr * T);
+    c.W = wc.take<double>(rr * T);
+    c.WU = wc.take<double>((size_t)r * kmax * T);
+    c.WV = wc.take<double>((size_t)r * kmax * T);
+    c.lam = wc.take<double>((size_t)r * T);
+    c.order = wc.take<int>((size_t)r * T);
+    wc.take<int>((size_t)r * T);
+    c.rank = wc.take<int>((size_t)T);
+    c.capped = wc.take<int>(1);
+    c.pG = wc.take<double*>(T);
+    c.pR = wc.take<double*>(T);
+    c.pW = wc.take<double*>(T);
+    c.pWU = wc.take<double*>(T);
+    c.pWV = wc.take<double*>(T);
+    c.plam = wc.take<double*>(T);
+    c.porder = wc.take<int*>(T);
+    c.items = wc.take<GItem>((size_t)T * 4);
+    return c;
+}
+
+// Q = orth(Y) for every item (three passes of shifted Cholesky QR); Y is overwritten.
+static mvn_status comp_orth(mvn_ctx* ctx, CompWs& c, int T, double* Y, double* Q) {
+    const int m = c.m, r = c.r;
+    const size_t mr = (size_t)m * r, rr = (size_t)r * r;
+    double* src = Y;
+    double* dst = Q;
+    for (int pass = 0; pass < 3; ++pass) {
+        std::vector<GItem> it;
+        for (int t = 0; t < T; ++t)
+            it.push_back(gi(src + t * mr, m, 1, src + t * mr, 1, m, c.G + t * rr, r, r, r, m, 1.0, 0.0));
+        MVN_TRY(bgemm(ctx, it, c.items));
+        k_chol_inv<<<T, 256, 0, ctx->stream>>>(r, c.pG, c.pR);
+        MVN_LAUNCHED(ctx);
+        it.clear();
+        for (int t = 0; t < T; ++t)
+            it.push_back(gi(src + t * mr, 1, m, c.R + t * rr, 1, r, dst + t * mr, m, m, r, r, 1.0, 0.0));
+        MVN_TRY(bgemm(ctx, it, c.items));
+        std::swap(src, dst);
+    }
+    // three passes: the result is in src (== Y after an odd number of swaps) -> copy to Q
+    if (src != Q)
+        MVN_CUDA(ctx, cudaMemcpyAsync(Q, src, sizeof(double) * mr * T, cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+    return MVN_OK;
+}
+
+// Compress T dense m x m tiles (A[t], ld m) into U[t], V[t] (m x kmax, ld m); ranks -> rank_out[t]
+// (device), capped tiles counted into *capped_out (device).
+static mvn_status comp_run(mvn_ctx* ctx, CompWs& c, int T, const std::vector<const double*>& A,
+                           const std::vector<double*>& U, const std::vector<double*>& V,
+                           double acc, uint64_t seed, int* rank_out) {
+    const int m = c.m, r = c.r, kmax = c.kmax;
+    const size_t mr = (size_t)m * r, rr = (size_t)r * r;
+    {
+        std::vector<double*> pG(T), pR(T), pW(T), pWU(T), pWV(T), plam(T);
+        std::vector<int*> pord(T);
+        for (int t = 0; t < T; ++t) {
+            pG[t] = c.G + t * rr;
+            pR[t] = c.R + t * rr;
+            pW[t] = c.W + t * rr;
+            pWU[t] = c.WU + (size_t)t * r * kmax;
+            pWV[t] = c.WV + (size_t)t * r * kmax;
+            plam[t] = c.lam + (size_t)t * r;
+            pord[t] = c.order + (size_t)t * r;
+        }
+        MVN_CUDA(ctx, cudaMemcpyAsync(c.pG, pG.data(), sizeof(void*) * T, cudaMemcpyHostToDevice, ctx->stream));
+        MVN_CUDA(ctx, cudaMemcpyAsync(c.pR, pR.data(), sizeof(void*) * T, cudaMemcpyHostToDevice, ctx->stream));
+        MVN_CUDA(ctx, cudaMemcpyAsync(c.pW, pW.data(), sizeof(void*) * T, cudaMemcpyHostToDevice, ctx->stream));
+        MVN_CUDA(ctx, cudaMemcpyAsync(c.pWU, pWU.data(), sizeof(void*) * T, cudaMemcpyHostToDevice, ctx->stream));
+        MVN_CUDA(ctx, cudaMemcpyAsync(c.pWV, pWV.data(), sizeof(void*) * T, cudaMemcpyHostToDevice, ctx->stream));
+        MVN_CUDA(ctx, cudaMemcpyAsync(c.plam, plam.data(), sizeof(void*) * T, cudaMemcpyHostToDevice, ctx->stream));
+        MVN_CUDA(ctx, cudaMemcpyAsync(c.porder, pord.data(), sizeof(void*) * T, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    k_gauss<<<(unsigned)((mr + 255) / 256), 256, 0, ctx->stream>>>(m, r, seed, c.Om);
+    MVN_LAUNCHED(ctx);
+    std::vector<GItem> it;
+    // Y = A Omega
+    for (int t = 0; t < T; ++t) it.push_back(gi(A[t], 1, m, c.Om, 1, m, c.Y + t * mr, m, m, r, m, 1.0, 0.0));
+    MVN_TRY(bgemm(ctx, it, c.items));
+    MVN_TRY(comp_orth(ctx, c, T, c.Y, c.Q));
+    // one power iteration: Z = A^T Q, Q' = orth(Z), Y = A Q', Q = orth(Y)
+    it.clear();
+    for (int t = 0; t < T; ++t) it.push_back(gi(A[t], m, 1, c.Q + t * mr, 1, m, c.Z + t * mr, m, m, r, m, 1.0, 0.0));
+    MVN_TRY(bgemm(ctx, it, c.items));
+    MVN_TRY(comp_orth(ctx, c, T, c.Z, c.Q));
+    it.clear();
+    for (int t = 0; t < T; ++t) it.push_back(gi(A[t], 1, m, c.Q + t * mr, 1, m, c.Y + t * mr, m, m, r, m, 1.0, 0.0));
+    MVN_TRY(bgemm(ctx, it, c.items));
+    MVN_TRY(comp_orth(ctx, c, T, c.Y, c.Q));
+    // B = Q^T A (r x m, ld r);  C = B B^T
+    it.clear();
+    for (int t = 0; t < T; ++t) it.push_back(gi(c.Q + t * mr, m, 1, A[t], 1, m, c.B + t * mr, r, r, m, m, 1.0, 0.0));
+    MVN_TRY(bgemm(ctx, it, c.items));
+    it.clear();
+    for (int t = 0; t < T; ++t) it.push_back(gi(c.B + t * mr, 1, r, c.B + t * mr, r, 1, c.G + t * rr, r, r, r, m, 1.0, 0.0));
+    MVN_TRY(bgemm(ctx, it, c.items));
+    const int np = ((r + 1) & ~1) / 2;
+    k_jacobi<<<T, 256, np * (2 * sizeof(double) + 2 * sizeof(int)), ctx->stream>>>(
+        r, c.pG, c.pW, c.plam, c.porder, 40);
+    MVN_LAUNCHED(ctx);
+    k_select<<<T, 256, 0, ctx->stream>>>(r, kmax, acc, c.pW, c.plam, c.porder, c.pWU, c.pWV,
+                                         rank_out, c.capped);
+    MVN_LAUNCHED(ctx);
+    // U = Q WU (m x kmax);  V = B^T WV (m x kmax)
+    it.clear();
+    for (int t = 0; t < T; ++t) it.push_back(gi(c.Q + t * mr, 1, m, c.WU + (size_t)t * r * kmax, 1, r, U[t], m, m, kmax, r, 1.0, 0.0));
+    MVN_TRY(bgemm(ctx, it, c.items));
+    it.clear();
+    for (int t = 0; t < T; ++t) it.push_back(gi(c.B + t * mr, r, 1, c.WV + (size_t)t * r * kmax, 1, r, V[t], m, m, kmax, r, 1.0, 0.0));
+    MVN_TRY(bgemm(ctx, it, c.items));
+    return MVN_OK;
+}
+
+// ---------------------------------------------------------------- ABI
+
+static int tlr_chunk(int m, int r, int kmax) {
+    const double per = (4.0 * m * r + 3.0 * r * r + 2.0 * r * kmax + (double)m * m) * 8.0;
+    return (int)std::max(1.0, std::min(1024.0, 24e9 / per));
+}
+
+extern "C" mvn_status mvn_tlr_compress(mvn_ctx* ctx, int n, const double* Sigma, int64_t ld,
+                                       int tile, double acc, int max_rank, mvn_tlr** out,
+                                       int* max_rank_hit) {
+    if (!ctx) return MVN_ERR_ARG;
+    if (out) *out = nullptr;
+    if (!out || n < 1 || !Sigma || ld < n || tile < 64 || tile % 64 != 0 || tile > 4096 ||
+        !(acc >= 0.0) || max_rank < 1 || max_rank > tile)
+        return mvn_fail(ctx, MVN_ERR_ARG,
+                        "mvn_tlr_compress: invalid argument (tile a multiple of 64, 1 <= max_rank <= tile)");
+    MVN_CUDA(ctx, cudaSetDevice(ctx->device));
+    mvn_tlr* T = new mvn_tlr();
+    T->ctx = ctx;
+    T->n = n;
+    T->m = tile;
+    T->nt = (n + tile - 1) / tile;
+    T->npad = T->nt * tile;
+    T->kmax = max_rank;
+    T->acc = acc;
+    const int m = tile, nt = T->nt;
+    const int64_t ntri = (int64_t)nt * (nt - 1) / 2;
+    if (cudaMalloc(&T->D, sizeof(double) * (size_t)m * m * nt) != cudaSuccess ||
+        cudaMalloc(&T->U, sizeof(double) * (size_t)m * max_rank * std::max<int64_t>(ntri, 1)) != cudaSuccess ||
+        cudaMalloc(&T->V, sizeof(double) * (size_t)m * max_rank * std::max<int64_t>(ntri, 1)) != cudaSuccess ||
+        cudaMalloc(&T->rank, sizeof(int) * std::max<int64_t>(ntri, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        mvn_tlr_free(T);
+        return mvn_fail(ctx, MVN_ERR_OOM, "mvn_tlr_compress: allocation failed");
+    }
+    // diagonal tiles
+    for (int i = 0; i < nt; ++i) {
+        k_copy_tile<<<m, 256, 0, ctx->stream>>>(n, m, Sigma, ld, i, i, T->D + (size_t)i * m * m);
+        MVN_LAUNCHED(ctx);
+    }
+    int capped = 0;
+    if (ntri > 0) {
+        const int r = std::min(m, max_rank + 8);
+        const int chunk = tlr_chunk(m, r, max_rank);
+        const size_t need = comp_ws_bytes(m, r, max_rank, chunk) +
+                            ws_round(sizeof(double) * (size_t)m * m * chunk) + 4096;
+        MVN_TRY(ws_reserve(ctx, need));
+        WsCarver wc(ctx->ws);
+        double* Ad = wc.take<double>((size_t)m * m * chunk);
+        CompWs c = comp_ws_carve(wc, m, r, max_rank, chunk);
+        MVN_CUDA(ctx, cudaMemsetAsync(c.capped, 0, sizeof(int), ctx->stream));
+        std::vector<std::pair<int, int>> tiles;
+        for (int j = 0; j < nt; ++j)
+            for (int i = j + 1; i < nt; ++i) tiles.push_back({i, j});
+        for (size_t t0 = 0; t0 < tiles.size(); t0 += chunk) {
+            const int Tn = (int)std::min<size_t>(chunk, tiles.size() - t0);
+            std::vector<const double*> A(Tn);
+            std::vector<double*> U(Tn), V(Tn);
+            for (int t = 0; t < Tn; ++t) {
+                const int i = tiles[t0 + t].first, j = tiles[t0 + t].second;
+                double* dst = Ad + (size_t)t * m * m;
+                k_copy_tile<<<m, 256, 0, ctx->stream>>>(n, m, Sigma, ld, i, j, dst);
+                MVN_LAUNCHED(ctx);
+                A[t] = dst;
+                const int64_t idx = tri_index(i, j, nt);
+                U[t] = T->U + (size_t)idx * m * max_rank;
+                V[t] = T->V + (size_t)idx * m * max_rank;
+            }
+            // tiles are enumerated in column order, so the ranks land at tri_index order
+            MVN_TRY(comp_run(ctx, c, Tn, A, U, V, acc, 0x5EEDull + t0, T->rank + t0));
+        }
+        MVN_CUDA(ctx, cudaMemcpyAsync(&capped, c.capped, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    MVN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    T->rank_h.resize((size_t)ntri);
+    if (ntri > 0)
+        MVN_CUDA(ctx, cudaMemcpy(T->rank_h.data(), T->rank, sizeof(int) * ntri, cudaMemcpyDeviceToHost));
+    T->capped = capped;
+    if (max_rank_hit) *max_rank_hit = capped;
+    *out = T;
+    return MVN_OK;
+}
+
+extern "C" mvn_status mvn_tlr_cholesky(mvn_ctx* ctx, mvn_tlr* T, int* info) {
+    if (!ctx || !T || T->factored) return mvn_fail(ctx, MVN_ERR_ARG, "mvn_tlr_cholesky: invalid object");
+    MVN_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (info) *info = 0;
+    const int m = T->m, nt = T->nt, kmax = T->kmax;
+    const size_t mk = (size_t)m * kmax, kk = (size_t)kmax * kmax, mm = (size_t)m * m;
+    const int r = std::min(m, kmax + 8);
+    const int chunk = std::min(std::max(nt - 1, 1), tlr_chunk(m, r, kmax));
+    const size_t need = comp_ws_bytes(m, r, kmax, chunk) + ws_round(sizeof(double) * mm * chunk) +
+                        ws_round(sizeof(double) * kk * nt) + ws_round(sizeof(double) * mk * nt) +
+                        ws_round(sizeof(GItem) * (size_t)nt) + ws_round(sizeof(double*) * nt) + 8192;
+    MVN_TRY(ws_reserve(ctx, need));
+    WsCarver wc(ctx->ws);
+    double* Ad = wc.take<double>(mm * chunk);
+    double* X = wc.take<double>(kk * nt);
+    double* Yb = wc.take<double>(mk * nt);
+    GItem* items2 = wc.take<GItem>((size_t)nt);
+    double** pV = wc.take<double*>(nt);
+    CompWs c = comp_ws_carve(wc, m, r, kmax, chunk);
+    MVN_CUDA(ctx, cudaMemsetAsync(c.capped, 0, sizeof(int), ctx->stream));
+    auto Ut = [&](int i, int j) { return T->U + (size_t)tri_index(i, j, nt) * mk; };
+    auto Vt = [&](int i, int j) { return T->V + (size_t)tri_index(i, j, nt) * mk; };
+    for (int k = 0; k < nt; ++k) {
+        double* Dk = T->D + (size_t)k * mm;
+        // D_kk -= sum_{l<k} U_kl (V_kl^T V_kl) U_kl^T
+        if (k > 0) {
+            std::vector<GItem> it;
+            for (int l = 0; l < k; ++l)
+                it.push_back(gi(Vt(k, l), m, 1, Vt(k, l), 1, m, X + (size_t)l * kk, kmax, kmax, kmax, m, 1.0, 0.0));
+            MVN_TRY(bgemm(ctx, it, items2));
+            it.clear();
+            for (int l = 0; l < k; ++l)
+                it.push_back(gi(Ut(k, l), 1, m, X + (size_t)l * kk, 1, kmax, Yb + (size_t)l * mk, m, m, kmax, kmax, 1.0, 0.0));
+            MVN_TRY(bgemm(ctx, it, items2));
+            for (int l = 0; l < k; ++l) {
+                it.clear();
+                it.push_back(gi(Yb + (size_t)l * mk, 1, m, Ut(k, l), m, 1, Dk, m, m, m, kmax, -1.0, 1.0));
+                MVN_TRY(bgemm(ctx, it, items2));
+            }
+        }
+        MVN_TRY(chol_f64_launch(ctx, m, Dk, m));
+        // off-diagonal tiles of column k, in chunks
+        for (int i0 = k + 1; i0 < nt; i0 += chunk) {
+            const int Tn = std::min(chunk, nt - i0);
+            std::vector<GItem> it;
+            for (int t = 0; t < Tn; ++t)  // A_ik = U_ik V_ik^T
+                it.push_back(gi(Ut(i0 + t, k), 1, m, Vt(i0 + t, k), m, 1, Ad + (size_t)t * mm, m, m, m, kmax, 1.0, 0.0));
+            MVN_TRY(bgemm(ctx, it, c.items));
+            for (int l = 0; l < k; ++l) {
+                it.clear();
+                for (int t = 0; t < Tn; ++t)  // X_il = V_il^T V_kl
+                    it.push_back(gi(Vt(i0 + t, l), m, 1, Vt(k, l), 1, m, X + (size_t)t * kk, kmax, kmax, kmax, m, 1.0, 0.0));
+                MVN_TRY(bgemm(ctx, it, c.items));
+                it.clear();
+                for (int t = 0; t < Tn; ++t)  // Y_il = U_il X_il
+                    it.push_back(gi(Ut(i0 + t, l), 1, m, X + (size_t)t * kk, 1, kmax, Yb + (size_t)t * mk, m, m, kmax, kmax, 1.0, 0.0));
+                MVN_TRY(bgemm(ctx, it, c.items));
+                it.clear();
+                for (int t = 0; t < Tn; ++t)  // A_ik -= Y_il U_kl^T
+                    it.push_back(gi(Yb + (size_t)t * mk, 1, m, Ut(k, l), m, 1, Ad + (size_t)t * mm, m, m, m, kmax, -1.0, 1.0));
+                MVN_TRY(bgemm(ctx, it, c.items));
+            }
+            std::vector<const double*> A(Tn);
+            std::vector<double*> U(Tn), V(Tn);
+            std::vector<double*> pv(Tn);
+            for (int t = 0; t < Tn; ++t) {
+                A[t] = Ad + (size_t)t * mm;
+                U[t] = Ut(i0 + t, k);
+                V[t] = Vt(i0 + t, k);
+                pv[t] = V[t];
+            }
+            MVN_TRY(comp_run(ctx, c, Tn, A, U, V, T->acc, 0xC0FFEEull + (uint64_t)k * 4096 + i0,
+                             T->rank + tri_index(i0, k, nt)));
+            // V_ik <- L_kk^-1 V_ik, blocked by 64 rows
+            MVN_CUDA(ctx, cudaMemcpyAsync(pV, pv.data(), sizeof(double*) * Tn, cudaMemcpyHostToDevice, ctx->stream));
+            for (int r0 = 0; r0 < m; r0 += 64) {
+                if (r0 > 0) {
+                    it.clear();
+                    for (int t = 0; t < Tn; ++t)
+                        it.push_back(gi(Dk + r0, 1, m, V[t], 1, m, V[t] + r0, m, 64, kmax, r0, -1.0, 1.0));
+                    MVN_TRY(bgemm(ctx, it, c.items));
+                }
+                const int threads = Tn * kmax;
+                k_trsm_block<<<(threads + 127) / 128, 128, 0, ctx->stream>>>(m, kmax, Dk, r0, pV, Tn);
+                MVN_LAUNCHED(ctx);
+            }
+        }
+    }
+    MVN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int64_t ntri = (int64_t)nt * (nt - 1) / 2;
+    if (ntri > 0)
+        MVN_CUDA(ctx, cudaMemcpy(T->rank_h.data(), T->rank, sizeof(int) * ntri, cudaMemcpyDeviceToHost));
+    T->factored = true;
+    int inf = 0;
+    mvn_status st = mvn_sync(ctx, &inf);
+    if (info) *info = inf;
+    return st;
+}
+
+// L (n x n, ld): diagonal tiles' lower parts and U V^T below; the strict upper part untouched.
+__global__ void k_diag_out(int n, int m, const double* __restrict__ D, int ti, double* __restrict__ L,
+                           int64_t ld) {
+    const int c = blockIdx.x;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        const int i = ti * m + r, j = ti * m + c;
+        if (i < n && j < n && r >= c) L[i + (int64_t)j * ld] = D[r + (int64_t)c * m];
+    }
+}
+
+extern "C" mvn_status mvn_tlr_to_dense(mvn_ctx* ctx, const mvn_tlr* T, double* L, int64_t ld) {
+    if (!ctx || !T || !L || ld < T->n) return mvn_fail(ctx, MVN_ERR_ARG, "mvn_tlr_to_dense: invalid argument");
+    MVN_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int m = T->m, nt = T->nt, n = T->n, kmax = T->kmax;
+    for (int i = 0; i < nt; ++i) {
+        k_diag_out<<<m, 256, 0, ctx->stream>>>(n, m, T->D + (size_t)i * m * m, i, L, ld);
+        MVN_LAUNCHED(ctx);
+    }
+    const int64_t ntri = (int64_t)nt * (nt - 1) / 2;
+    if (ntri == 0) return MVN_OK;
+    MVN_TRY(ws_reserve(ctx, ws_round(sizeof(GItem) * (size_t)ntri) + 1024));
+    std::vector<GItem> it;
+    for (int j = 0; j < nt; ++j)
+        for (int i = j + 1; i < nt; ++i) {
+            const int64_t idx = tri_index(i, j, nt);
+            const int rows = std::min(m, n - i * m), cols = std::min(m, n - j * m);
+            it.push_back(gi(T->U + (size_t)idx * m * kmax, 1, m, T->V + (size_t)idx * m * kmax, m, 1,
+                            L + (int64_t)i * m + (int64_t)j * m * ld, ld, rows, cols, kmax, 1.0, 0.0));
+        }
+    return bgemm(ctx, it, (GItem*)ctx->ws);
+}
+
+extern "C" mvn_status mvn_tlr_ranks(const mvn_tlr* T, int* ranks) {
+    if (!T || !ranks) return MVN_ERR_ARG;
+    std::copy(T->rank_h.begin(), T->rank_h.end(), ranks);
+    return MVN_OK;
+}
+
+extern "C" mvn_status mvn_tlr_free(mvn_tlr* T) {
+    if (!T) return MVN_ERR_ARG;
+    if (T->ctx) cudaStreamSynchronize(T->ctx->stream);
+    if (T->D) cudaFree(T->D);
+    if (T->U) cudaFree(T->U);
+    if (T->V) cudaFree(T->V);
+    if (T->rank) cudaFree(T->rank);
+    delete T;
+    return MVN_OK;
+}

@@ -345,6 +345,59 @@ def mvn_sov_fp64_noalloc(a, b, L, n_points, n_shifts, seed, err_k=3.0, path_logw
     return out3
 
 
+class TLR:
+    """Owner of an mvn_tlr object (tile low-rank form of a covariance or of its factor)."""
+
+    def __init__(self, handle, n, tile, max_rank, capped):
+        self.h = handle
+        self.n, self.tile, self.max_rank, self.capped = n, tile, max_rank, capped
+        self.nt = (n + tile - 1) // tile
+
+    def ranks(self):
+        import numpy as np
+        k = self.nt * (self.nt - 1) // 2
+        buf = (ctypes.c_int * max(k, 1))()
+        st = lib().mvn_tlr_ranks(self.h, ctypes.cast(buf, _P))
+        if st != MVN_OK:
+            raise MVNError(st, "mvn_tlr_ranks failed")
+        return np.array(buf[:k], dtype=np.int32)
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().mvn_tlr_free(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+def mvn_tlr_compress(Sigma: torch.Tensor, tile: int, acc: float, max_rank: int) -> TLR:
+    n = Sigma.shape[0]
+    Sp, ld = _mat(Sigma, n, "Sigma")
+    h = _P()
+    hit = _I(0)
+    c = context()
+    c.check(lib().mvn_tlr_compress(c.h, n, Sp, ld, tile, acc, max_rank, ctypes.byref(h),
+                                   ctypes.byref(hit)))
+    return TLR(h, n, tile, max_rank, hit.value)
+
+
+def mvn_tlr_cholesky(T: TLR) -> int:
+    info = _I(0)
+    c = context()
+    c.check(lib().mvn_tlr_cholesky(c.h, T.h, ctypes.byref(info)))
+    return info.value
+
+
+def mvn_tlr_to_dense(T: TLR, out: torch.Tensor | None = None) -> torch.Tensor:
+    if out is None:
+        out = torch.zeros((T.n, T.n), dtype=torch.float64, device="cuda").t()
+    Lp, ld = _mat(out, T.n, "out")
+    c = context()
+    c.check(lib().mvn_tlr_to_dense(c.h, T.h, Lp, ld))
+    return out
+
+
 def sync():
     """Wait for the current context; raise MVNError for a device-side error."""
     c = context()

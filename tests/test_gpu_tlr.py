@@ -1,0 +1,95 @@
+"""Tile low-rank compression and TLR Cholesky on the GPU vs the oracle (Sec. III-E)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_14892_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mvn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_14892_gb300 import mvn as m
+    return m
+
+
+def _t(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def _case(g=32, rng=0.1, nu=0.5, nugget=1e-6):
+    c = inputs.grid_coords(g, order="morton")
+    return oracle.matern(c, 1.0, rng, nu, nugget=nugget)
+
+
+@pytest.mark.parametrize("tile,acc,kmax", [(128, 1e-4, 64), (256, 1e-6, 128)])
+def test_tlr_compress_vs_oracle(mvn, tile, acc, kmax):
+    S = _case()
+    n = S.shape[0]
+    T = mvn.mvn_tlr_compress(mvn.to_colmajor(_t(S)), tile, acc, kmax)
+    mvn.sync()
+    ranks = T.ranks()
+    ref = oracle.tlr_compress(S, tile, acc, kmax)
+    L = mvn.mvn_tlr_to_dense(T).cpu().numpy()
+    nt = n // tile
+    # ranks: equal except where a singular value sits within 5% of the threshold
+    for t, (i, j) in enumerate((i, j) for j in range(nt) for i in range(j + 1, nt)):
+        A = S[i * tile:(i + 1) * tile, j * tile:(j + 1) * tile]
+        s = np.linalg.svd(A, compute_uv=False)
+        k_ref = ref["ranks"][t]
+        if ranks[t] != k_ref:
+            lo, hi = sorted((ranks[t], k_ref))
+            assert np.all(np.abs(s[lo:hi] / acc - 1.0) < 0.05), (i, j, ranks[t], k_ref, s[lo:hi + 1])
+        err = np.linalg.norm(A - L[i * tile:(i + 1) * tile, j * tile:(j + 1) * tile], 2)
+        # Eckart-Young bound of the exact truncation plus the randomised range finder's slack
+        assert err <= 2.0 * max(acc, s[min(kmax, len(s) - 1)] if ranks[t] == kmax else acc), (i, j, err)
+    assert np.allclose(np.tril(L[:tile, :tile]), np.tril(S[:tile, :tile]))
+    print(f"tile {tile}: ranks gpu {ranks.min()}..{ranks.max()} oracle "
+          f"{ref['ranks'].min()}..{ref['ranks'].max()}, capped {T.capped}")
+
+
+def test_tlr_cholesky_vs_oracle_and_dense(mvn):
+    S = _case(nugget=1e-4)
+    n = S.shape[0]
+    tile, acc, kmax = 128, 1e-6, 96
+    T = mvn.mvn_tlr_compress(mvn.to_colmajor(_t(S)), tile, acc, kmax)
+    assert mvn.mvn_tlr_cholesky(T) == 0
+    L = np.tril(mvn.mvn_tlr_to_dense(T).cpu().numpy())
+    ref = oracle.tlr_to_dense(oracle.tlr_cholesky(oracle.tlr_compress(S, tile, acc, kmax)))
+    Ld = np.linalg.cholesky(S)
+    e_bwd = np.linalg.norm(L @ L.T - S, 2)
+    e_ref = np.linalg.norm(ref @ ref.T - S, 2)
+    print(f"TLR Cholesky: ||LL^T - S|| gpu {e_bwd:.3e} oracle {e_ref:.3e}; max|L - L_oracle| "
+          f"{np.abs(L - ref).max():.3e}; max|L - L_dense| {np.abs(L - Ld).max():.3e}")
+    assert e_bwd < 100 * acc
+    assert np.abs(L - ref).max() < 1e-3
+    # SOV with the TLR factor vs the dense factor on identical points (stated difference)
+    a = np.full(n, -np.inf)
+    b = np.full(n, 1.0)
+    q = (200, 10, 3)
+    P_t = mvn.mvn_sov(_t(a), _t(b), mvn.to_colmajor(_t(L)), *q).cpu().numpy()
+    P_d = mvn.mvn_sov(_t(a), _t(b), mvn.to_colmajor(_t(Ld)), *q).cpu().numpy()
+    mvn.sync()
+    print(f"log P with TLR factor {P_t[0]:.8f} vs dense {P_d[0]:.8f}")
+    assert abs(P_t[0] - P_d[0]) < 1e-2
+
+
+def test_tlr_ragged_and_rank_cap(mvn):
+    c = inputs.random_coords(700, 9)
+    S = oracle.matern(c, 1.0, 0.3, 0.5, nugget=1e-6)
+    T = mvn.mvn_tlr_compress(mvn.to_colmajor(_t(S)), 256, 0.0, 8)  # acc 0: every tile capped
+    mvn.sync()
+    assert np.all(T.ranks() == 8) and T.capped == 3
+    del T
+    # ragged n (700 = 2 x 256 + 188) at tight accuracy: the TLR factor meets the dense one
+    T = mvn.mvn_tlr_compress(mvn.to_colmajor(_t(S)), 256, 1e-10, 256)
+    assert mvn.mvn_tlr_cholesky(T) == 0
+    L = np.tril(mvn.mvn_tlr_to_dense(T).cpu().numpy())
+    Ld = np.linalg.cholesky(S)
+    assert np.abs(L - Ld).max() < 1e-5, np.abs(L - Ld).max()

@@ -310,13 +310,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed_simt", choices=["mixed", "fp64", "mixed_simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="w2", choices=["w1", "w2", "w3", "w4", "w5"],
+                    help="w2 (default): the contract line; the others measure the other rows")
     ap.add_argument("--paths", type=int, default=0,
                     help="override the path count (multiple of the shift count; profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "w2":
         run_gpu(args)
+    else:
+        import bench_workloads  # noqa: E402  (secondary rows, same timing rules)
+        bench_workloads.run(args)
 
 
 if __name__ == "__main__":

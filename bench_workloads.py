@@ -1,0 +1,193 @@
+"""Secondary measurement lines of bench.py (one JSON line each), same timing rules as the main
+line: W >= 3 untimed warm-up steps, CUDA events on the launching stream bracketed by
+synchronisations, inputs larger than L2 or resident and stated.
+
+  w1: n=256 SOV, FP64 (Sigma -> Cholesky -> sweep), 10,000 points x 20 shifts.
+  w3: confidence region on a posterior field (n=4,096, 256 prefix problems, 10,000 paths):
+      one prefix-recording sweep (mvn_excursion) and one batched persistent launch of the 256
+      independent problems (mvn_sov_batched), against a loop of single-problem FP64 launches
+      (timed on a sample of the problems and scaled by their sample-dims).
+  w4: adjoint, n=4,096 Matern 3/2: d log P / d (b, sigma2, range) through the autograd chain.
+  w5: tile low rank, n=65,536 exponential (Morton grid), tile 1024, acc 1e-5, max rank 256:
+      compression + TLR Cholesky + SOV, against the dense MVN_MIXED factorisation + SOV.
+"""
+from __future__ import annotations
+
+import json
+import time
+
+import numpy as np
+import torch
+
+from paper_2405_14892_gb300 import inputs, mvn
+
+
+def _timed(fn, steps, warmup, stream):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st, info = mvn.context().sync()
+    if st != 0:
+        raise RuntimeError(f"device error {st} info {info}")
+    return e0.elapsed_time(e1) / steps
+
+
+def _line(args, workload, metric, value, unit, ms, extra):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+         "vs_baseline": None, "data": "synthetic", "config": {"workload": workload}}
+    d.update(extra)
+    print(json.dumps(d), flush=True)
+
+
+def run(args):
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = mvn.context(0)
+    steps, warm = max(1, args.steps), max(3, args.warmup)
+    t = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=dev)
+
+    if args.workload == "w1":
+        w = inputs.WORKLOADS["W1"]
+        c = inputs.grid_coords(w["g"])
+        n = c.shape[0]
+        a, b = inputs.limits_for(w, n)
+        cd, ad, bd = t(c), t(a), t(b)
+        S = mvn.colmajor_empty(n, n, dev)
+        out3 = torch.empty(3, dtype=torch.float64, device=dev)
+
+        def step():
+            mvn.mvn_matern(cd, w["sigma2"], w["range"], w["nu"], w["nugget"], out=S)
+            mvn.mvn_cholesky(S, check=False)
+            mvn.mvn_sov(ad, bd, S, w["Ns"], w["M"], w["seed"], out3=out3)
+        l0 = ctx.launches()
+        ms = _timed(step, steps, warm, stream)
+        paths = w["Ns"] * w["M"]
+        _line(args, w["name"], "SOV sample-dims/s, n=256, FP64", n * paths / (ms * 1e-3),
+              "sample-dims/s", ms, {"dtype": "f64", "logP": float(out3[0]),
+                                    "gpu_launches": (ctx.launches() - l0) // (steps + warm) * steps})
+        return
+
+    if args.workload == "w3":
+        w = inputs.WORKLOADS["W3"]
+        c = inputs.grid_coords(w["g"])
+        n = c.shape[0]
+        Sp = mvn.mvn_matern(t(c), w["sigma2"], w["range"], w["nu"], w["nugget"])
+        torch.cuda.synchronize()
+        Sh = torch.tril(Sp).cpu().numpy()
+        Sh = Sh + np.tril(Sh, -1).T
+        mu, Spost, _ = inputs.posterior_field(Sh, w["n_obs"], w["noise_sd"], w["field_seed"])
+        dims = inputs.prefix_problem_dims(w["nprob"], w["dims_lo"], w["dims_hi"], w["dims_seed"])
+        mud, Sd = t(mu), mvn.to_colmajor(t(Spost))
+        res = {}
+
+        def exc():
+            res["r"] = mvn.mvn_excursion(mud, Sd, w["u"], w["level"], w["Ns"], w["M"], w["seed"],
+                                         prefix_dims=dims, prec="mixed")
+        ms_exc = _timed(exc, steps, warm, stream)
+        r = res["r"]
+        order = r["order"].cpu().numpy()
+        Lp = mvn.to_colmajor(t(Spost[np.ix_(order, order)]))
+        mvn.mvn_cholesky(Lp)
+        a_perm = t(w["u"] - mu[order])
+        b_inf = t(np.full(n, np.inf))
+
+        def batched():
+            res["b"] = mvn.mvn_sov_batched(dims, [0] * len(dims), a_perm, b_inf, Lp, w["Ns"],
+                                           w["M"], w["seed"], prec="mixed")
+        ms_bat = _timed(batched, steps, warm, stream)
+        # loop of single-problem FP64 launches, on a sample of 8 problems, scaled by sample-dims
+        sample = list(range(0, len(dims), len(dims) // 8))[:8]
+
+        def loop():
+            for p in sample:
+                k = int(dims[p])
+                mvn.mvn_sov(a_perm[:k].contiguous(), b_inf[:k].contiguous(), Lp, w["Ns"], w["M"],
+                            w["seed"], prec="fp64")
+        ms_loop_sample = _timed(loop, 1, 1, stream)
+        sd_sample = sum(int(dims[p]) ** 2 for p in sample)
+        sd_all = sum(int(k) ** 2 for k in dims)
+        ms_loop = ms_loop_sample * sd_all / sd_sample
+        _line(args, w["name"], "confidence-region MVN probs/s (256 prefix problems, one sweep)",
+              len(dims) / (ms_exc * 1e-3), "probs/s", ms_exc,
+              {"dtype": "f64+f32+fp16x2", "batched_independent_ms": ms_bat,
+               "batched_probs_per_sec": len(dims) / (ms_bat * 1e-3),
+               "loop_fp64_single_ms_estimated": ms_loop,
+               "loop_sample": f"{len(sample)} of {len(dims)} problems timed, scaled by sum k^2",
+               "region_size": int(r["region"].sum()), "F_first_last": [float(r["F"][0]),
+                                                                       float(r["F"][-1])]})
+        return
+
+    if args.workload == "w4":
+        from paper_2405_14892_gb300.autograd import mvn_log_prob
+        w = inputs.WORKLOADS["W4"]
+        c = t(inputs.grid_coords(w["g"]))
+        n = c.shape[0]
+        _, b = inputs.limits_for(w, n)
+        bt = t(b).requires_grad_(True)
+        s2 = torch.tensor(w["sigma2"], dtype=torch.float64, device=dev, requires_grad=True)
+        rg = torch.tensor(w["range"], dtype=torch.float64, device=dev, requires_grad=True)
+
+        def step():
+            bt.grad = None
+            s2.grad = None
+            rg.grad = None
+            lp = mvn_log_prob(bt, s2, rg, c, nu=w["nu"], nugget=w["nugget"], n_points=w["Ns"],
+                              n_shifts=w["M"], seed=w["seed"])
+            lp.backward()
+        ms = _timed(step, steps, warm, stream)
+        _line(args, w["name"], "gradients/s of log P w.r.t. (b, sigma2, range), n=4096",
+              1e3 / ms, "gradients/s", ms, {"dtype": "f64", "dsigma2": float(s2.grad),
+                                            "drange": float(rg.grad)})
+        return
+
+    if args.workload == "w5":
+        w = inputs.WORKLOADS["W5"]
+        c = inputs.grid_coords(w["g"], order="morton")
+        n = c.shape[0]
+        a, b = inputs.limits_for(w, n)
+        cd, ad, bd = t(c), t(a), t(b)
+        S = mvn.colmajor_empty(n, n, dev)
+        Lt = mvn.colmajor_empty(n, n, dev)
+        out_t = torch.empty(3, dtype=torch.float64, device=dev)
+        out_d = torch.empty(3, dtype=torch.float64, device=dev)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        mvn.mvn_matern(cd, w["sigma2"], w["range"], w["nu"], w["nugget"], out=S)
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        T = mvn.mvn_tlr_compress(S, w["tile"], w["acc"], w["max_rank"])
+        e[1].record(stream)
+        mvn.mvn_tlr_cholesky(T)
+        e[2].record(stream)
+        Lt.zero_()
+        mvn.mvn_tlr_to_dense(T, out=Lt)
+        mvn.mvn_sov(ad, bd, Lt, w["Ns"], w["M"], w["seed"], prec="mixed", out3=out_t)
+        e[3].record(stream)
+        mvn.mvn_cholesky(S, prec="mixed", check=False)
+        e[4].record(stream)
+        mvn.mvn_sov(ad, bd, S, w["Ns"], w["M"], w["seed"], prec="mixed", out3=out_d)
+        e[5].record(stream)
+        torch.cuda.synchronize()
+        mvn.sync()
+        ms = [e[i].elapsed_time(e[i + 1]) for i in range(5)]
+        ranks = T.ranks()
+        tlr_ms = ms[0] + ms[1] + ms[2]
+        dense_ms = ms[3] + ms[4]
+        _line(args, w["name"], "TLR vs dense time-to-P-hat, n=65,536", 1e3 / tlr_ms, "probs/s",
+              tlr_ms, {"dtype": "f64 (TLR) / f64+f32+fp16x2+bf16 digits (dense)",
+                       "tlr_compress_ms": ms[0], "tlr_cholesky_ms": ms[1],
+                       "tlr_sov_ms": ms[2], "dense_cholesky_ms": ms[3], "dense_sov_ms": ms[4],
+                       "tlr_over_dense_speedup": dense_ms / tlr_ms,
+                       "logP_tlr": float(out_t[0]), "logP_dense": float(out_d[0]),
+                       "ranks": {"min": int(ranks.min()), "median": float(np.median(ranks)),
+                                 "max": int(ranks.max()), "capped": int(T.capped)},
+                       "note": "single timed pass (no warm-up repeats: minutes per pass)"})
+        return

@@ -226,6 +226,11 @@ mvn_status mvn_lattice_shifts(mvn_ctx* ctx, uint64_t seed, int M, int n, uint64_
  * MMAs and TMEM read as the sweep.  1 <= K <= 65536.  Asynchronous; errors via mvn_sync. */
 mvn_status mvn_tc_selftest(mvn_ctx* ctx, int K, const double* Y, const double* L, float* S);
 
+/* Self-test of the bounded device-side waits: a kernel waits on an mbarrier that nothing
+ * completes, gives up after budget_cycles (1e3 .. 4e9 SM clock cycles) and raises
+ * MVN_ERR_TIMEOUT in the status word (read by mvn_sync); the context stays usable. */
+mvn_status mvn_wait_selftest(mvn_ctx* ctx, int64_t budget_cycles);
+
 #ifdef __cplusplus
 }
 #endif

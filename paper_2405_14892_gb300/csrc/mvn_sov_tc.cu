@@ -547,3 +547,27 @@ extern "C" mvn_status mvn_tc_selftest(mvn_ctx* ctx, int K, const double* Y, cons
     MVN_LAUNCHED(ctx);
     return MVN_OK;
 }
+
+// ---------------------------------------------------------------- bounded-wait self-test
+
+// One thread waits on an mbarrier that nothing completes, with the same bounded wait as the
+// tensor-core kernels; when the budget runs out it raises MVN_ERR_TIMEOUT and returns.
+__global__ void k_wait_selftest(long long budget, int* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0, budget)) dev_raise(status, MVN_ERR_TIMEOUT, 0);
+}
+
+extern "C" mvn_status mvn_wait_selftest(mvn_ctx* ctx, int64_t budget_cycles) {
+    if (!ctx) return MVN_ERR_ARG;
+    if (budget_cycles < 1000 || budget_cycles > 4000000000LL)
+        return mvn_fail(ctx, MVN_ERR_ARG, "budget out of [1e3, 4e9] cycles");
+    MVN_CUDA(ctx, cudaSetDevice(ctx->device));
+    k_wait_selftest<<<1, 32, 0, ctx->stream>>>(budget_cycles, ctx->d_status);
+    MVN_LAUNCHED(ctx);
+    return MVN_OK;
+}

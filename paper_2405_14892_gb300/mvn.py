@@ -69,6 +69,7 @@ SIGNATURES = {
     "mvn_lattice_shifts": (_I, [_P, _U64, _I, _I, _P]),
     "mvn_tc_selftest": (_I, [_P, _I, _P, _P, _P]),
     "mvn_sov_fp64_noalloc": (_I, [_I, _P, _P, _P, _I64, _QP, _P, _P, _P]),
+    "mvn_wait_selftest": (_I, [_P, _I64]),
 }
 
 

@@ -308,7 +308,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="mixed_simt", choices=["mixed", "fp64", "mixed_simt"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64", "mixed_simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="w2", choices=["w1", "w2", "w3", "w4", "w5"],
                     help="w2 (default): the contract line; the others measure the other rows")

@@ -400,7 +400,7 @@ __global__ void k_trsm_block(int m, int kmax, const double* __restrict__ Lkk, in
 struct CompWs {
     int m, r, kmax, T;
     double *Om, *Y, *Q, *Z, *B, *G, *R, *W, *WU, *WV, *lam;
-    int *order, *rank, *capped;
+    int *order, *rank, *capped, *rk;
     double **pG, **pR, **pW, **pWU, **pWV, **plam;
     int** porder;
     GItem* items;
@@ -434,7 +434,7 @@ static CompWs comp_ws_carve(WsCarver& wc, int m, int r, int kmax, int T) {
     c.WV = wc.take<double>((size_t)r * kmax * T);
     c.lam = wc.take<double>((size_t)r * T);
     c.order = wc.take<int>((size_t)r * T);
-    wc.take<int>((size_t)r * T);
+    c.rk = wc.take<int>((size_t)r * T);
     c.rank = wc.take<int>((size_t)T);
     c.capped = wc.take<int>(1);
     c.pG = wc.take<double*>(T);
@@ -449,8 +449,8 @@ static CompWs comp_ws_carve(WsCarver& wc, int m, int r, int kmax, int T) {
 }
 
 // Q = orth(Y) for every item (three passes of shifted Cholesky QR); Y is overwritten.
-static mvn_status comp_orth(mvn_ctx* ctx, CompWs& c, int T, double* Y, double* Q) {
-    const int m = c.m, r = c.r;
+static mvn_status comp_orth(mvn_ctx* ctx, CompWs& c, int T, double* Y, double* Q, int r) {
+    const int m = c.m;
     const size_t mr = (size_t)m * r, rr = (size_t)r * r;
     double* src = Y;
     double* dst = Q;
@@ -478,8 +478,8 @@ static mvn_status comp_orth(mvn_ctx* ctx, CompWs& c, int T, double* Y, double* Q
 // (device), capped tiles counted into *capped_out (device).
 static mvn_status comp_run(mvn_ctx* ctx, CompWs& c, int T, const std::vector<const double*>& A,
                            const std::vector<double*>& U, const std::vector<double*>& V,
-                           double acc, uint64_t seed, int* rank_out) {
-    const int m = c.m, r = c.r, kmax = c.kmax;
+                           double acc, uint64_t seed, int* rank_out, int r) {
+    const int m = c.m, kmax = c.kmax;
     const size_t mr = (size_t)m * r, rr = (size_t)r * r;
     {
         std::vector<double*> pG(T), pR(T), pW(T), pWU(T), pWV(T), plam(T);
@@ -507,16 +507,16 @@ static mvn_status comp_run(mvn_ctx* ctx, CompWs& c, int T, const std::vector<con
     // Y = A Omega
     for (int t = 0; t < T; ++t) it.push_back(gi(A[t], 1, m, c.Om, 1, m, c.Y + t * mr, m, m, r, m, 1.0, 0.0));
     MVN_TRY(bgemm(ctx, it, c.items));
-    MVN_TRY(comp_orth(ctx, c, T, c.Y, c.Q));
+    MVN_TRY(comp_orth(ctx, c, T, c.Y, c.Q, r));
     // one power iteration: Z = A^T Q, Q' = orth(Z), Y = A Q', Q = orth(Y)
     it.clear();
     for (int t = 0; t < T; ++t) it.push_back(gi(A[t], m, 1, c.Q + t * mr, 1, m, c.Z + t * mr, m, m, r, m, 1.0, 0.0));
     MVN_TRY(bgemm(ctx, it, c.items));
-    MVN_TRY(comp_orth(ctx, c, T, c.Z, c.Q));
+    MVN_TRY(comp_orth(ctx, c, T, c.Z, c.Q, r));
     it.clear();
     for (int t = 0; t < T; ++t) it.push_back(gi(A[t], 1, m, c.Q + t * mr, 1, m, c.Y + t * mr, m, m, r, m, 1.0, 0.0));
     MVN_TRY(bgemm(ctx, it, c.items));
-    MVN_TRY(comp_orth(ctx, c, T, c.Y, c.Q));
+    MVN_TRY(comp_orth(ctx, c, T, c.Y, c.Q, r));
     // B = Q^T A (r x m, ld r);  C = B B^T
     it.clear();
     for (int t = 0; t < T; ++t) it.push_back(gi(c.Q + t * mr, m, 1, A[t], 1, m, c.B + t * mr, r, r, m, m, 1.0, 0.0));
@@ -538,6 +538,46 @@ static mvn_status comp_run(mvn_ctx* ctx, CompWs& c, int T, const std::vector<con
     it.clear();
     for (int t = 0; t < T; ++t) it.push_back(gi(c.B + t * mr, r, 1, c.WV + (size_t)t * r * kmax, 1, r, V[t], m, m, kmax, r, 1.0, 0.0));
     MVN_TRY(bgemm(ctx, it, c.items));
+    return MVN_OK;
+}
+
+// Adaptive sketch size: every tile starts with r = 32 columns; a tile whose detected rank
+// reaches r - 8 (the sketch may have missed singular values above acc) is compressed again with
+// twice the columns, up to max_rank + 8.  ranks_h receives the final ranks (host), rank_dev the
+// same on the device.  Synchronises once per round.
+static mvn_status comp_adaptive(mvn_ctx* ctx, CompWs& c, int T, const std::vector<const double*>& A,
+                                const std::vector<double*>& U, const std::vector<double*>& V,
+                                double acc, uint64_t seed, int* rank_dev, int* ranks_h) {
+    const int rmax = c.r;
+    int r = std::min(rmax, 32);
+    std::vector<int> todo(T);
+    for (int t = 0; t < T; ++t) todo[t] = t;
+    int* rk = c.rk;  // per-round ranks
+    for (int round = 0; !todo.empty(); ++round) {
+        const int Tn = (int)todo.size();
+        std::vector<const double*> Ar(Tn);
+        std::vector<double*> Ur(Tn), Vr(Tn);
+        for (int t = 0; t < Tn; ++t) {
+            Ar[t] = A[todo[t]];
+            Ur[t] = U[todo[t]];
+            Vr[t] = V[todo[t]];
+        }
+        MVN_TRY(comp_run(ctx, c, Tn, Ar, Ur, Vr, acc, seed + 7919u * round, rk, r));
+        std::vector<int> got(Tn);
+        MVN_CUDA(ctx, cudaMemcpyAsync(got.data(), rk, sizeof(int) * Tn, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        MVN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        std::vector<int> next;
+        for (int t = 0; t < Tn; ++t) {
+            ranks_h[todo[t]] = got[t];
+            if (got[t] >= r - 8 && r < rmax) next.push_back(todo[t]);
+        }
+        todo.swap(next);
+        r = std::min(rmax, 2 * r);
+    }
+    MVN_CUDA(ctx, cudaMemcpyAsync(rank_dev, ranks_h, sizeof(int) * T, cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    MVN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return MVN_OK;
 }
 
@@ -582,6 +622,7 @@ extern "C" mvn_status mvn_tlr_compress(mvn_ctx* ctx, int n, const double* Sigma,
         MVN_LAUNCHED(ctx);
     }
     int capped = 0;
+    T->rank_h.assign((size_t)ntri, 0);
     if (ntri > 0) {
         const int r = std::min(m, max_rank + 8);
         const int chunk = tlr_chunk(m, r, max_rank);
@@ -610,14 +651,12 @@ extern "C" mvn_status mvn_tlr_compress(mvn_ctx* ctx, int n, const double* Sigma,
                 V[t] = T->V + (size_t)idx * m * max_rank;
             }
             // tiles are enumerated in column order, so the ranks land at tri_index order
-            MVN_TRY(comp_run(ctx, c, Tn, A, U, V, acc, 0x5EEDull + t0, T->rank + t0));
+            MVN_TRY(comp_adaptive(ctx, c, Tn, A, U, V, acc, 0x5EEDull + t0, T->rank + t0,
+                                  T->rank_h.data() + t0));
         }
         MVN_CUDA(ctx, cudaMemcpyAsync(&capped, c.capped, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     }
     MVN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    T->rank_h.resize((size_t)ntri);
-    if (ntri > 0)
-        MVN_CUDA(ctx, cudaMemcpy(T->rank_h.data(), T->rank, sizeof(int) * ntri, cudaMemcpyDeviceToHost));
     T->capped = capped;
     if (max_rank_hit) *max_rank_hit = capped;
     *out = T;
@@ -646,21 +685,27 @@ extern "C" mvn_status mvn_tlr_cholesky(mvn_ctx* ctx, mvn_tlr* T, int* info) {
     MVN_CUDA(ctx, cudaMemsetAsync(c.capped, 0, sizeof(int), ctx->stream));
     auto Ut = [&](int i, int j) { return T->U + (size_t)tri_index(i, j, nt) * mk; };
     auto Vt = [&](int i, int j) { return T->V + (size_t)tri_index(i, j, nt) * mk; };
+    auto rk = [&](int i, int j) { return T->rank_h[(size_t)tri_index(i, j, nt)]; };
     for (int k = 0; k < nt; ++k) {
         double* Dk = T->D + (size_t)k * mm;
-        // D_kk -= sum_{l<k} U_kl (V_kl^T V_kl) U_kl^T
+        // D_kk -= sum_{l<k} U_kl (V_kl^T V_kl) U_kl^T   (GEMM sizes follow the actual ranks)
         if (k > 0) {
             std::vector<GItem> it;
             for (int l = 0; l < k; ++l)
-                it.push_back(gi(Vt(k, l), m, 1, Vt(k, l), 1, m, X + (size_t)l * kk, kmax, kmax, kmax, m, 1.0, 0.0));
+                if (rk(k, l))
+                    it.push_back(gi(Vt(k, l), m, 1, Vt(k, l), 1, m, X + (size_t)l * kk, kmax,
+                                    rk(k, l), rk(k, l), m, 1.0, 0.0));
             MVN_TRY(bgemm(ctx, it, items2));
             it.clear();
             for (int l = 0; l < k; ++l)
-                it.push_back(gi(Ut(k, l), 1, m, X + (size_t)l * kk, 1, kmax, Yb + (size_t)l * mk, m, m, kmax, kmax, 1.0, 0.0));
+                if (rk(k, l))
+                    it.push_back(gi(Ut(k, l), 1, m, X + (size_t)l * kk, 1, kmax, Yb + (size_t)l * mk,
+                                    m, m, rk(k, l), rk(k, l), 1.0, 0.0));
             MVN_TRY(bgemm(ctx, it, items2));
             for (int l = 0; l < k; ++l) {
+                if (!rk(k, l)) continue;
                 it.clear();
-                it.push_back(gi(Yb + (size_t)l * mk, 1, m, Ut(k, l), m, 1, Dk, m, m, m, kmax, -1.0, 1.0));
+                it.push_back(gi(Yb + (size_t)l * mk, 1, m, Ut(k, l), m, 1, Dk, m, m, m, rk(k, l), -1.0, 1.0));
                 MVN_TRY(bgemm(ctx, it, items2));
             }
         }
@@ -670,20 +715,28 @@ extern "C" mvn_status mvn_tlr_cholesky(mvn_ctx* ctx, mvn_tlr* T, int* info) {
             const int Tn = std::min(chunk, nt - i0);
             std::vector<GItem> it;
             for (int t = 0; t < Tn; ++t)  // A_ik = U_ik V_ik^T
-                it.push_back(gi(Ut(i0 + t, k), 1, m, Vt(i0 + t, k), m, 1, Ad + (size_t)t * mm, m, m, m, kmax, 1.0, 0.0));
+                it.push_back(gi(Ut(i0 + t, k), 1, m, Vt(i0 + t, k), m, 1, Ad + (size_t)t * mm, m, m, m,
+                                rk(i0 + t, k), 1.0, 0.0));
             MVN_TRY(bgemm(ctx, it, c.items));
             for (int l = 0; l < k; ++l) {
+                if (!rk(k, l)) continue;
                 it.clear();
                 for (int t = 0; t < Tn; ++t)  // X_il = V_il^T V_kl
-                    it.push_back(gi(Vt(i0 + t, l), m, 1, Vt(k, l), 1, m, X + (size_t)t * kk, kmax, kmax, kmax, m, 1.0, 0.0));
+                    if (rk(i0 + t, l))
+                        it.push_back(gi(Vt(i0 + t, l), m, 1, Vt(k, l), 1, m, X + (size_t)t * kk, kmax,
+                                        rk(i0 + t, l), rk(k, l), m, 1.0, 0.0));
                 MVN_TRY(bgemm(ctx, it, c.items));
                 it.clear();
                 for (int t = 0; t < Tn; ++t)  // Y_il = U_il X_il
-                    it.push_back(gi(Ut(i0 + t, l), 1, m, X + (size_t)t * kk, 1, kmax, Yb + (size_t)t * mk, m, m, kmax, kmax, 1.0, 0.0));
+                    if (rk(i0 + t, l))
+                        it.push_back(gi(Ut(i0 + t, l), 1, m, X + (size_t)t * kk, 1, kmax,
+                                        Yb + (size_t)t * mk, m, m, rk(k, l), rk(i0 + t, l), 1.0, 0.0));
                 MVN_TRY(bgemm(ctx, it, c.items));
                 it.clear();
                 for (int t = 0; t < Tn; ++t)  // A_ik -= Y_il U_kl^T
-                    it.push_back(gi(Yb + (size_t)t * mk, 1, m, Ut(k, l), m, 1, Ad + (size_t)t * mm, m, m, m, kmax, -1.0, 1.0));
+                    if (rk(i0 + t, l))
+                        it.push_back(gi(Yb + (size_t)t * mk, 1, m, Ut(k, l), m, 1, Ad + (size_t)t * mm,
+                                        m, m, m, rk(k, l), -1.0, 1.0));
                 MVN_TRY(bgemm(ctx, it, c.items));
             }
             std::vector<const double*> A(Tn);
@@ -695,15 +748,21 @@ extern "C" mvn_status mvn_tlr_cholesky(mvn_ctx* ctx, mvn_tlr* T, int* info) {
                 V[t] = Vt(i0 + t, k);
                 pv[t] = V[t];
             }
-            MVN_TRY(comp_run(ctx, c, Tn, A, U, V, T->acc, 0xC0FFEEull + (uint64_t)k * 4096 + i0,
-                             T->rank + tri_index(i0, k, nt)));
-            // V_ik <- L_kk^-1 V_ik, blocked by 64 rows
+            const int64_t idx0 = tri_index(i0, k, nt);  // the chunk's tiles are consecutive
+            MVN_TRY(comp_adaptive(ctx, c, Tn, A, U, V, T->acc, 0xC0FFEEull + (uint64_t)k * 4096 + i0,
+                                  T->rank + idx0, T->rank_h.data() + idx0));
+            int rmaxc = 0;
+            for (int t = 0; t < Tn; ++t) rmaxc = std::max(rmaxc, rk(i0 + t, k));
+            if (rmaxc == 0) continue;
+            // V_ik <- L_kk^-1 V_ik, blocked by 64 rows (columns up to the chunk's largest rank)
             MVN_CUDA(ctx, cudaMemcpyAsync(pV, pv.data(), sizeof(double*) * Tn, cudaMemcpyHostToDevice, ctx->stream));
             for (int r0 = 0; r0 < m; r0 += 64) {
                 if (r0 > 0) {
                     it.clear();
                     for (int t = 0; t < Tn; ++t)
-                        it.push_back(gi(Dk + r0, 1, m, V[t], 1, m, V[t] + r0, m, 64, kmax, r0, -1.0, 1.0));
+                        if (rk(i0 + t, k))
+                            it.push_back(gi(Dk + r0, 1, m, V[t], 1, m, V[t] + r0, m, 64, rk(i0 + t, k),
+                                            r0, -1.0, 1.0));
                     MVN_TRY(bgemm(ctx, it, c.items));
                 }
                 const int threads = Tn * kmax;
@@ -713,9 +772,6 @@ extern "C" mvn_status mvn_tlr_cholesky(mvn_ctx* ctx, mvn_tlr* T, int* info) {
         }
     }
     MVN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    const int64_t ntri = (int64_t)nt * (nt - 1) / 2;
-    if (ntri > 0)
-        MVN_CUDA(ctx, cudaMemcpy(T->rank_h.data(), T->rank, sizeof(int) * ntri, cudaMemcpyDeviceToHost));
     T->factored = true;
     int inf = 0;
     mvn_status st = mvn_sync(ctx, &inf);
@@ -750,7 +806,8 @@ extern "C" mvn_status mvn_tlr_to_dense(mvn_ctx* ctx, const mvn_tlr* T, double* L
             const int64_t idx = tri_index(i, j, nt);
             const int rows = std::min(m, n - i * m), cols = std::min(m, n - j * m);
             it.push_back(gi(T->U + (size_t)idx * m * kmax, 1, m, T->V + (size_t)idx * m * kmax, m, 1,
-                            L + (int64_t)i * m + (int64_t)j * m * ld, ld, rows, cols, kmax, 1.0, 0.0));
+                            L + (int64_t)i * m + (int64_t)j * m * ld, ld, rows, cols,
+                            T->rank_h[(size_t)idx], 1.0, 0.0));
         }
     return bgemm(ctx, it, (GItem*)ctx->ws);
 }

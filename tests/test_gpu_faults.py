@@ -52,7 +52,8 @@ def test_workspace_allocation_failure_injection(mvn):
     import ctypes
     q = mvn._qmc(64, 2, 1)
     out = torch.empty(3, dtype=torch.float64, device="cuda")
-    args = (fresh.h, 25, mvn._P(_t(a).data_ptr()), mvn._P(_t(b).data_ptr()),
+    ad, bd = _t(a), _t(b)  # kept alive for the calls below
+    args = (fresh.h, 25, mvn._P(ad.data_ptr()), mvn._P(bd.data_ptr()),
             mvn._P(S.data_ptr()), 25, ctypes.byref(q), 0, mvn._P(out.data_ptr()), None)
     os.environ["MVN_FAULT_WS_ALLOC"] = "1"
     try:

@@ -79,9 +79,12 @@ def _clock_summary(proc, gpu_index: int):
             "samples": len(sm)}
 
 
-def workload():
+def workload(grid: int = 0):
     from paper_2405_14892_gb300 import inputs
     w = dict(inputs.WORKLOADS["W2"])
+    if grid:
+        w["g"] = grid
+        w["name"] = f"{w['name']}-g{grid}"
     c = inputs.grid_coords(w["g"])
     a, b = inputs.limits_for(w, c.shape[0])
     return w, c, a, b
@@ -140,6 +143,63 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- rooflines
+
+def kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src):
+    """Achieved rate of the main kernels of the step: algorithmic work per launch (stated per
+    kernel) over the kernel's average launch duration, measured by the library's CUDA events on
+    the launching stream during the timed region."""
+    out = []
+    kt = getattr(ctx, "kernel_times", {})
+    tens_peak = peaks["bf16_tflops_sustained"]
+    tens_src = f"{peak_src} bf16 dense, sustained (the kernel runs inside a long step)"
+    tiles = (Ntot + 127) // 128
+    # tensor-core Cholesky update: block column j (j = 1..nt-1), output (nt-j)*128 rows x 128
+    # columns, K = 128 j, 21 BF16 digit-product MMAs per element product
+    ms, cnt = kt.get("k_oz_update", (0.0, 0))
+    if cnt:
+        nt = (n + 127) // 128
+        steps = cnt and max(1, cnt // max(1, nt - 1))
+        mac = sum((nt - j) * 128 * 128 * 128 * j for j in range(1, nt))
+        fl = 2.0 * 21 * mac * steps
+        out.append({"kernel": "k_oz_update", "bound": "tensor", "unit": "TFLOP/s",
+                    "achieved": fl / (ms * 1e-3) / 1e12, "peak": tens_peak,
+                    "frac": fl / (ms * 1e-3) / 1e12 / tens_peak, "traffic": None,
+                    "fp64_equivalent_tflops": 2.0 * mac * steps / (ms * 1e-3) / 1e12,
+                    "launches": cnt, "total_ms": ms, "peak_source": tens_src,
+                    "work": "21 BF16 MMA products per FP64 product of the left-looking update"})
+    ms, cnt = kt.get("k_sov_tc", (0.0, 0))
+    if cnt:
+        nb = (n + 63) // 64
+        mac = tiles * 128 * 64 * 64 * (nb * (nb - 1) // 2)
+        fl = 2.0 * 3 * mac * cnt
+        out.append({"kernel": "k_sov_tc", "bound": "tensor", "unit": "TFLOP/s",
+                    "achieved": fl / (ms * 1e-3) / 1e12, "peak": tens_peak,
+                    "frac": fl / (ms * 1e-3) / 1e12 / tens_peak, "traffic": None,
+                    "launches": cnt, "total_ms": ms, "peak_source": tens_src,
+                    "work": "3 FP16 MMAs per K step of the limit GEMM (two-slice split), "
+                            "128-path tiles x 64-dim blocks"})
+    for name in ("k_syrk", "k_sov_simt_f64", "k_sov_simt_f32"):
+        ms, cnt = kt.get(name, (0.0, 0))
+        if not cnt:
+            continue
+        if name == "k_syrk":
+            fl = n ** 3 / 3.0 * (cnt / max(1, (n + 63) // 64 - 1))
+            pk, src = 1.25, "nominal FP64 1.25 TFLOP/s (recipe table)"
+        elif name == "k_sov_simt_f64":
+            fl = float(n) * (n - 1) * Ntot * cnt
+            pk, src = 1.25, "nominal FP64 1.25 TFLOP/s (recipe table)"
+        else:
+            fl = float(n) * (n - 1) * Ntot * cnt
+            pk = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            src = "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops x max SM clock"
+        ach = fl / (ms * 1e-3) / 1e12
+        out.append({"kernel": name, "bound": "alu", "unit": "TFLOP/s", "achieved": ach,
+                    "peak": pk, "frac": ach / pk, "traffic": None, "launches": cnt,
+                    "total_ms": ms, "peak_source": src})
+    return out
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def run_gpu(args):
@@ -160,7 +220,7 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     dev = torch.device("cuda", local)
-    w, c, a, b = workload()
+    w, c, a, b = workload(args.grid)
     n = c.shape[0]
     Ns, M = w["Ns"], w["M"]
     if args.paths:
@@ -201,6 +261,7 @@ def run_gpu(args):
 
     # ---- timed region: device clock, inputs resident in HBM
     clocks_proc = _clock_sampler() if rank == 0 else None
+    ctx.timing(True)
     launches0 = ctx.launches()
     if world > 1:
         dist.barrier()
@@ -220,6 +281,10 @@ def run_gpu(args):
         dist.barrier()
     launches = ctx.launches() - launches0
     ms = t_start.elapsed_time(t_end) / args.steps
+    ktimes = {k: ctx.kernel_time(k) for k in ("k_oz_update", "k_sov_tc", "k_syrk",
+                                              "k_sov_simt_f64", "k_sov_simt_f32")}
+    ctx.timing(False)
+    ctx.kernel_times = ktimes
     clocks = _clock_summary(clocks_proc, local) if rank == 0 else None
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -257,20 +322,8 @@ def run_gpu(args):
     sov_ms = statistics.median(phase["sov"])
     chol_ms = statistics.median(phase["cholesky"])
     value = world * n * Ntot / (ms * 1e-3)
-    # roofline of the dominant kernel (the SOV sweep): algorithmic flops of the limit GEMM
-    # n(n-1) per path (multiply-add = 2 flops) over the measured sweep time
-    sov_flops = float(n) * (n - 1) * Ntot
-    if prec == "fp64":
-        peak, bound, unit = 1.25, "alu", "TFLOP/s"      # nominal FP64 (recipe table)
-        peak_note = "nominal FP64 1.25 TFLOP/s (recipe table)"
-    elif prec == "mixed_simt":
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        bound, unit = "alu", "TFLOP/s"
-        peak_note = "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops x max SM clock"
-    else:
-        peak, bound, unit = peaks["bf16_tflops_sustained"], "tensor", "TFLOP/s"
-        peak_note = f"{peak_src} bf16 sustained"
-    achieved = sov_flops / (sov_ms * 1e-3) / 1e12
+    rooflines = kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src)
+    dominant = max(rooflines, key=lambda r: r["total_ms"]) if rooflines else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -285,9 +338,8 @@ def run_gpu(args):
                       "sov": sov_ms},
         "sov_sample_dims_per_sec": n * Ntot / (sov_ms * 1e-3),
         "logP": float(res[0]), "P": float(res[1]), "err": float(res[2]),
-        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak, "traffic": None, "kernel": "SOV sweep",
-                     "peak_source": peak_note},
+        "roofline": dominant,
+        "rooflines": rooflines,
         "e2e": {"value": world * n * Ntot / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -312,6 +364,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="w2", choices=["w1", "w2", "w3", "w4", "w5"],
                     help="w2 (default): the contract line; the others measure the other rows")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="override the grid side g (n = g^2; profiling runs on small cases)")
     ap.add_argument("--paths", type=int, default=0,
                     help="override the path count (multiple of the shift count; profiling runs)")
     args = ap.parse_args()

@@ -82,6 +82,13 @@ const char* mvn_last_error(const mvn_ctx* ctx);
 mvn_status mvn_sync(mvn_ctx* ctx, int* info);
 /* Number of kernels this context has launched since creation (host counter). */
 int64_t mvn_launch_count(const mvn_ctx* ctx);
+/* Per-kernel timing: with enable != 0, CUDA events are recorded on the context's stream around
+ * every launch of the main kernels (k_oz_update, k_syrk, k_sov_tc, k_sov_simt_f64,
+ * k_sov_simt_f32); the call waits for the stream and clears earlier records. */
+mvn_status mvn_timing(mvn_ctx* ctx, int enable);
+/* Total device time (ms, host) and number of launches (host) of kernel `name` recorded since
+ * the last mvn_timing call; waits for the stream. */
+mvn_status mvn_kernel_time(mvn_ctx* ctx, const char* name, double* total_ms, int64_t* launches);
 
 /* ------------------------------------------------------------------ covariance (Eq. 6) */
 

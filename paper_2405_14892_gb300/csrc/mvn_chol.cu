@@ -149,8 +149,9 @@ mvn_status chol_f64_launch(mvn_ctx* ctx, int n, double* A, int64_t ld) {
         MVN_LAUNCHED(ctx);
         const int T = (rows + CH_NB - 1) / CH_NB;
         const int64_t tiles = (int64_t)T * (T + 1) / 2;
-        k_syrk<<<(unsigned)tiles, 256, 0, ctx->stream>>>(A, ld, k0, nb, r0, n, ctx->d_status);
-        MVN_LAUNCHED(ctx);
+        MVN_TIMED(ctx, "k_syrk",
+                  (k_syrk<<<(unsigned)tiles, 256, 0, ctx->stream>>>(A, ld, k0, nb, r0, n,
+                                                                   ctx->d_status)));
     }
     return MVN_OK;
 }

@@ -327,9 +327,9 @@ mvn_status chol_oz_launch(mvn_ctx* ctx, int n, double* A, int64_t ld, char* ws) 
         const int c0 = j * OZ_NB;
         const int nb = std::min(OZ_NB, n - c0);
         if (j > 0) {
-            k_oz_update<<<dim3(nt - j, (nb + 63) / 64), 128, ssm, ctx->stream>>>(
-                n, A, ld, E, j, nt, Z, ctx->d_status);
-            MVN_LAUNCHED(ctx);
+            MVN_TIMED(ctx, "k_oz_update",
+                      (k_oz_update<<<dim3(nt - j, (nb + 63) / 64), 128, ssm, ctx->stream>>>(
+                          n, A, ld, E, j, nt, Z, ctx->d_status)));
         }
         k_oz_potrf<<<1, 256, dsm, ctx->stream>>>(A, ld, c0, nb, ctx->d_status);
         MVN_LAUNCHED(ctx);

@@ -42,10 +42,56 @@ extern "C" mvn_status mvn_create(mvn_ctx** out, int device, void* cuda_stream) {
     return MVN_OK;
 }
 
+cudaEvent_t timing_event(mvn_ctx* ctx) {
+    if (!ctx->timing) return nullptr;
+    if (ctx->ev_used == ctx->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ctx->ev_pool.push_back(e);
+    }
+    cudaEvent_t e = ctx->ev_pool[ctx->ev_used++];
+    cudaEventRecord(e, ctx->stream);
+    return e;
+}
+
+void timing_record(mvn_ctx* ctx, const char* name, cudaEvent_t a, cudaEvent_t b) {
+    if (ctx->timing && a && b) ctx->ktimes[name].push_back({a, b});
+}
+
+extern "C" mvn_status mvn_timing(mvn_ctx* ctx, int enable) {
+    if (!ctx) return MVN_ERR_ARG;
+    MVN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->timing = enable != 0;
+    ctx->ktimes.clear();
+    ctx->ev_used = 0;
+    return MVN_OK;
+}
+
+extern "C" mvn_status mvn_kernel_time(mvn_ctx* ctx, const char* name, double* total_ms,
+                                      int64_t* launches) {
+    if (!ctx || !name || !total_ms || !launches) return MVN_ERR_ARG;
+    MVN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *total_ms = 0.0;
+    *launches = 0;
+    auto it = ctx->ktimes.find(name);
+    if (it == ctx->ktimes.end()) return MVN_OK;
+    for (auto& pr : it->second) {
+        float ms = 0.0f;
+        MVN_CUDA(ctx, cudaEventElapsedTime(&ms, pr.first, pr.second));
+        *total_ms += ms;
+    }
+    *launches = (int64_t)it->second.size();
+    return MVN_OK;
+}
+
 extern "C" mvn_status mvn_destroy(mvn_ctx* ctx) {
     if (!ctx) return MVN_ERR_ARG;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->d_alpha) cudaFree(ctx->d_alpha);
     if (ctx->d_status) cudaFree(ctx->d_status);

@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -30,7 +31,24 @@ struct mvn_ctx {
     // lattice generators alpha_i (u64) for i < n_alpha, computed on the device once
     uint64_t* d_alpha = nullptr;
     int n_alpha = 0;
+    // per-kernel timing (mvn_timing): CUDA events recorded around selected launches
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> ktimes;
 };
+
+// Events around one launch when timing is enabled (returns nullptr otherwise).
+cudaEvent_t timing_event(mvn_ctx* ctx);
+void timing_record(mvn_ctx* ctx, const char* name, cudaEvent_t a, cudaEvent_t b);
+#define MVN_TIMED(ctx, name, launch)                                                         \
+    do {                                                                                     \
+        cudaEvent_t ta_ = timing_event(ctx);                                                 \
+        launch;                                                                              \
+        MVN_LAUNCHED(ctx);                                                                   \
+        cudaEvent_t tb_ = timing_event(ctx);                                                 \
+        timing_record(ctx, name, ta_, tb_);                                                  \
+    } while (0)
 
 // Record an error message on the context and return the status.
 mvn_status mvn_fail(mvn_ctx* ctx, mvn_status st, const char* fmt, ...);

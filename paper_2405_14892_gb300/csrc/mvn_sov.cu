@@ -202,13 +202,14 @@ mvn_status sov_run_simt(mvn_ctx* ctx, const std::vector<SovProblem>& probs_h, mv
     void* d_Y = wc.take<char>(elt * (size_t)ystride * grid);
     MVN_CUDA(ctx, cudaMemsetAsync(batch.counter, 0, sizeof(int), ctx->stream));
     if (f64) {
-        k_sov_simt<32, double, true><<<grid, SOV_P, 0, ctx->stream>>>(batch, ctx->d_alpha,
-                                                                       (double*)d_Y, ystride);
+        MVN_TIMED(ctx, "k_sov_simt_f64",
+                  (k_sov_simt<32, double, true><<<grid, SOV_P, 0, ctx->stream>>>(
+                      batch, ctx->d_alpha, (double*)d_Y, ystride)));
     } else {
-        k_sov_simt<64, float, false><<<grid, SOV_P, 0, ctx->stream>>>(batch, ctx->d_alpha,
-                                                                       (float*)d_Y, ystride);
+        MVN_TIMED(ctx, "k_sov_simt_f32",
+                  (k_sov_simt<64, float, false><<<grid, SOV_P, 0, ctx->stream>>>(
+                      batch, ctx->d_alpha, (float*)d_Y, ystride)));
     }
-    MVN_LAUNCHED(ctx);
     return MVN_OK;
 }
 

@@ -459,8 +459,7 @@ mvn_status sov_run_tc(mvn_ctx* ctx, const std::vector<SovProblem>& probs_h, char
     const size_t smem = tc_smem_bytes();
     MVN_CUDA(ctx, cudaFuncSetAttribute(k_sov_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-    k_sov_tc<<<grid, TC_P, smem, ctx->stream>>>(bt, ctx->d_alpha);
-    MVN_LAUNCHED(ctx);
+    MVN_TIMED(ctx, "k_sov_tc", (k_sov_tc<<<grid, TC_P, smem, ctx->stream>>>(bt, ctx->d_alpha)));
     return MVN_OK;
 }
 

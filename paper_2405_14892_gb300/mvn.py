@@ -70,6 +70,8 @@ SIGNATURES = {
     "mvn_tc_selftest": (_I, [_P, _I, _P, _P, _P]),
     "mvn_sov_fp64_noalloc": (_I, [_I, _P, _P, _P, _I64, _QP, _P, _P, _P]),
     "mvn_wait_selftest": (_I, [_P, _I64]),
+    "mvn_timing": (_I, [_P, _I]),
+    "mvn_kernel_time": (_I, [_P, ctypes.c_char_p, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
 }
 
 
@@ -115,6 +117,18 @@ class Context:
 
     def launches(self) -> int:
         return int(lib().mvn_launch_count(self.h))
+
+    def timing(self, enable: bool):
+        """Record CUDA events around the library's main kernels (see mvn_kernel_time)."""
+        self.check(lib().mvn_timing(self.h, 1 if enable else 0))
+
+    def kernel_time(self, name: str) -> tuple[float, int]:
+        """(total ms, launches) of kernel `name` since timing was enabled."""
+        ms = _D(0.0)
+        cnt = _I64(0)
+        self.check(lib().mvn_kernel_time(self.h, name.encode(), ctypes.byref(ms),
+                                         ctypes.byref(cnt)))
+        return ms.value, cnt.value
 
     def close(self):
         if getattr(self, "h", None):

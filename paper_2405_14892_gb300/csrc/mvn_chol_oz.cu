@@ -47,7 +47,9 @@ __global__ void k_oz_exps(int n, const double* __restrict__ A, int64_t ld, int* 
 }
 
 // Digits of the finished block column j (columns c0 .. c0+127, rows >= c0) into the slice tiles
-// Z[((j*S + s)*nt + rt)*2 + ks].  One CTA per row tile rt >= j.
+// Z[((j*S + s)*nt + rt)*2 + ks].  One CTA per row tile rt >= j.  x = L_ik 2^-E_i is rounded once
+// to 42-bit fixed point v = rint(x 2^42) (the same value as six successive 7-bit roundings), and
+// the balanced digits are peeled off with integer shifts: d = (v + 2^(k-1)) >> k, v -= d 2^k.
 __global__ void k_oz_split(int n, const double* __restrict__ A, int64_t ld,
                            const int* __restrict__ E, int j, int nt, uint8_t* __restrict__ Z) {
     const int rt = j + blockIdx.x;
@@ -55,17 +57,17 @@ __global__ void k_oz_split(int n, const double* __restrict__ A, int64_t ld,
     for (int e = threadIdx.x; e < OZ_NB * OZ_NB; e += blockDim.x) {
         const int r = e % OZ_NB, k = e / OZ_NB;  // consecutive threads: consecutive rows
         const int i = rt * OZ_NB + r, col = c0 + k;
-        double x = 0.0;
-        if (i < n && col < n && col <= i) x = ldexp(A[i + (int64_t)col * ld], -E[i]);
+        long long v = 0;
+        if (i < n && col < n && col <= i) v = llrint(ldexp(A[i + (int64_t)col * ld], 42 - E[i]));
         const int ks = k >> 6, kk = k & 63;
         const uint32_t off = tc::sw128_off(r, kk);
 #pragma unroll
         for (int s = 0; s < OZ_S; ++s) {
-            const double y = x * 128.0;
-            const double d = rint(y);
-            x = y - d;
+            const int sh = 7 * (OZ_S - 1 - s);
+            const long long d = (sh > 0) ? ((v + (1ll << (sh - 1))) >> sh) : v;
+            v -= d * (1ll << sh);
             uint8_t* tile = Z + ((((size_t)j * OZ_S + s) * nt + rt) * 2 + ks) * OZ_TILE;
-            *reinterpret_cast<__nv_bfloat16*>(tile + off) = __double2bfloat16(d);
+            *reinterpret_cast<__nv_bfloat16*>(tile + off) = __int2bfloat16_rn((int)d);
         }
     }
 }
@@ -210,19 +212,18 @@ __global__ void __launch_bounds__(128, 1) k_oz_update(int n, double* __restrict_
     }
 }
 
-// POTRF of the diagonal block (c0, c0), nb <= 128, in shared memory (FP64).  256 threads.
+// POTRF of the diagonal block (c0, c0), nb <= 128, in shared memory (FP64).  256 threads as a
+// 16 x 16 grid over the trailing triangle (no integer division in the inner loops).
 __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_t ld, int c0,
                                                   int nb, int* status) {
     extern __shared__ double Ts[];  // nb x (nb + 1)
     __shared__ int bad;
     if (oz_failed(status)) return;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
     const int sd = nb + 1;
     if (t == 0) bad = 0;
-    for (int e = t; e < nb * nb; e += 256) {
-        const int i = e % nb, jj = e / nb;
-        if (i >= jj) Ts[i * sd + jj] = A[(c0 + i) + (int64_t)(c0 + jj) * ld];
-    }
+    for (int jj = ty; jj < nb; jj += 16)
+        for (int i = jj + tx; i < nb; i += 16) Ts[i * sd + jj] = A[(c0 + i) + (int64_t)(c0 + jj) * ld];
     __syncthreads();
     for (int jj = 0; jj < nb; ++jj) {
         if (t == 0) {
@@ -236,30 +237,29 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
         }
         __syncthreads();
         if (bad) return;
-        const double ljj = Ts[jj * sd + jj];
-        for (int i = jj + 1 + t; i < nb; i += 256) Ts[i * sd + jj] /= ljj;
+        const double rl = 1.0 / Ts[jj * sd + jj];
+        for (int i = jj + 1 + t; i < nb; i += 256) Ts[i * sd + jj] *= rl;
         __syncthreads();
-        const int m = nb - jj - 1;
-        for (int e = t; e < m * m; e += 256) {
-            const int i = jj + 1 + e % m, c = jj + 1 + e / m;
-            if (c <= i) Ts[i * sd + c] -= Ts[i * sd + jj] * Ts[c * sd + jj];
+        for (int i = jj + 1 + ty; i < nb; i += 16) {
+            const double li = Ts[i * sd + jj];
+            for (int c = jj + 1 + tx; c <= i; c += 16) Ts[i * sd + c] -= li * Ts[c * sd + jj];
         }
         __syncthreads();
     }
-    for (int e = t; e < nb * nb; e += 256) {
-        const int i = e % nb, jj = e / nb;
-        if (i >= jj) A[(c0 + i) + (int64_t)(c0 + jj) * ld] = Ts[i * sd + jj];
-    }
+    for (int jj = ty; jj < nb; jj += 16)
+        for (int i = jj + tx; i < nb; i += 16) A[(c0 + i) + (int64_t)(c0 + jj) * ld] = Ts[i * sd + jj];
 }
 
 // TRSM of the rows below the diagonal block: X L_jj^T = A(i, c0:c0+nb) for i >= c0 + nb, in two
-// 64-column halves (x in registers).  One thread per row.
+// 64-column halves (x in registers; the first half is also kept in shared memory, one column
+// per thread, for the second half's right-hand side).  One thread per row.
 __global__ void __launch_bounds__(128) k_oz_trsm(double* __restrict__ A, int64_t ld, int c0,
                                                  int nb, int n, const int* status) {
-    extern __shared__ double Ls[];  // nb x (nb + 1)
+    extern __shared__ double Ls[];  // nb x (nb + 1), then x1[64][128]
     if (oz_failed(status)) return;
     const int t = threadIdx.x;
     const int sd = nb + 1;
+    double* x1s = Ls + nb * sd;
     for (int e = t; e < nb * nb; e += 128) {
         const int i = e % nb, k = e / nb;
         Ls[i * sd + k] = (i >= k) ? A[(c0 + i) + (int64_t)(c0 + k) * ld] : 0.0;
@@ -268,35 +268,39 @@ __global__ void __launch_bounds__(128) k_oz_trsm(double* __restrict__ A, int64_t
     const int r = c0 + nb + blockIdx.x * 128 + t;
     if (r >= n) return;
     double x[64];
+    const int h0 = min(64, nb);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        if (h * 64 >= nb) break;
-        const int b0 = h * 64;
-        const int hb = min(64, nb - b0);
-        // right-hand side of this half, minus the first half's contribution
+    for (int c = 0; c < 64; ++c) x[c] = (c < h0) ? A[r + (int64_t)(c0 + c) * ld] : 0.0;
 #pragma unroll
-        for (int c = 0; c < 64; ++c) {
-            if (c < hb) {
-                double s = A[r + (int64_t)(c0 + b0 + c) * ld];
-                if (h == 1)
-                    for (int u = 0; u < 64; ++u) s -= A[r + (int64_t)(c0 + u) * ld] * Ls[(b0 + c) * sd + u];
-                x[c] = s;
-            } else {
-                x[c] = 0.0;
-            }
+    for (int c = 0; c < 64; ++c) {
+        if (c < h0) {
+            double s = x[c];
+#pragma unroll
+            for (int u = 0; u < c; ++u) s -= x[u] * Ls[c * sd + u];
+            x[c] = s / Ls[c * sd + c];
+            A[r + (int64_t)(c0 + c) * ld] = x[c];
+            x1s[c * 128 + t] = x[c];
         }
+    }
+    if (nb <= 64) return;
+    const int h1 = nb - 64;
 #pragma unroll
-        for (int c = 0; c < 64; ++c) {
-            if (c < hb) {
-                double s = x[c];
-#pragma unroll
-                for (int u = 0; u < c; ++u) s -= x[u] * Ls[(b0 + c) * sd + b0 + u];
-                x[c] = s / Ls[(b0 + c) * sd + b0 + c];
-            }
-        }
+    for (int c = 0; c < 64; ++c) x[c] = (c < h1) ? A[r + (int64_t)(c0 + 64 + c) * ld] : 0.0;
+    for (int u = 0; u < 64; ++u) {
+        const double xu = x1s[u * 128 + t];
 #pragma unroll
         for (int c = 0; c < 64; ++c)
-            if (c < hb) A[r + (int64_t)(c0 + b0 + c) * ld] = x[c];
+            if (c < h1) x[c] -= xu * Ls[(64 + c) * sd + u];
+    }
+#pragma unroll
+    for (int c = 0; c < 64; ++c) {
+        if (c < h1) {
+            double s = x[c];
+#pragma unroll
+            for (int u = 0; u < c; ++u) s -= x[u] * Ls[(64 + c) * sd + 64 + u];
+            x[c] = s / Ls[(64 + c) * sd + 64 + c];
+            A[r + (int64_t)(c0 + 64 + c) * ld] = x[c];
+        }
     }
 }
 
@@ -321,8 +325,9 @@ mvn_status chol_oz_launch(mvn_ctx* ctx, int n, double* A, int64_t ld, char* ws) 
     const size_t dsm = sizeof(double) * OZ_NB * (OZ_NB + 1);
     MVN_CUDA(ctx, cudaFuncSetAttribute(k_oz_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)dsm));
+    const size_t tsm = dsm + sizeof(double) * 64 * 128;
     MVN_CUDA(ctx, cudaFuncSetAttribute(k_oz_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)dsm));
+                                       (int)tsm));
     for (int j = 0; j < nt; ++j) {
         const int c0 = j * OZ_NB;
         const int nb = std::min(OZ_NB, n - c0);
@@ -335,7 +340,7 @@ mvn_status chol_oz_launch(mvn_ctx* ctx, int n, double* A, int64_t ld, char* ws) 
         MVN_LAUNCHED(ctx);
         const int rows = n - c0 - nb;
         if (rows > 0) {
-            k_oz_trsm<<<(rows + 127) / 128, 128, dsm, ctx->stream>>>(A, ld, c0, nb, n,
+            k_oz_trsm<<<(rows + 127) / 128, 128, tsm, ctx->stream>>>(A, ld, c0, nb, n,
                                                                       ctx->d_status);
             MVN_LAUNCHED(ctx);
         }

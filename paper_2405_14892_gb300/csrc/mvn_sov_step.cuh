@@ -125,3 +125,119 @@ __device__ __forceinline__ float sov_step_f32(double ai, double bi, float s, flo
     return sov_step_f64_slow(ai, bi, (double)s, (double)lii, w, &delta);
 }
 
+
+// ---------------------------------------------------------------- FP32-only step (mixed sweeps)
+// The common path of the mixed sweeps uses no FP64 instruction (GB300's FP64 rate is ~1/64 of
+// FP32): the lattice point comes from its 64-bit fixed-point value by integer-to-float
+// conversion, w = (2m + 1) 2^-54 and 1 - w = (2^54 - 2m - 1) 2^-54 with m = W >> 11 (both
+// never 0), and the factor Delta is returned as an unevaluated FP32 pair dh + dl (so that
+// 1 - Q(b') keeps Q(b') even when it is below FP32's resolution of 1) times 2^dex.  Deep tails
+// and two-sided intervals fall back to the FP64 step.
+
+__device__ __forceinline__ void lattice_wf(uint64_t j, uint64_t alpha, uint64_t delta, float& w,
+                                           float& wc, uint64_t& m) {
+    const uint64_t W = j * alpha + delta;
+    m = W >> 11;
+    w = __ull2float_rn(2u * m + 1u) * 0x1p-54f;
+    wc = __ull2float_rn((1ull << 54) - 2u * m - 1u) * 0x1p-54f;
+}
+
+static __device__ __noinline__ float sov_step_slow_pair(double ai, double bi, float s, float lii,
+                                                 uint64_t m, float* dh, float* dl, int* dex) {
+    double delta;
+    const double w = ((double)m + 0.5) * 0x1p-53;
+    const float y = (float)sov_step_f64(ai, bi, (double)s, (double)lii, w, delta);
+    if (!(delta > 0.0)) {
+        *dh = 0.0f;
+        *dl = 0.0f;
+        *dex = 0;
+    } else {
+        int e;
+        const double mm = frexp(delta, &e);
+        *dh = (float)mm;
+        *dl = (float)(mm - (double)*dh);
+        *dex = e;
+    }
+    return y;
+}
+
+// One dimension of Eq. 2 in FP32 (see above).  af/bf: the limits as floats; ai/bi: as doubles
+// (used only by the fallback); ainf/binf: the limits are infinite.
+__device__ __forceinline__ float sov_step_f32p(float af, float bf, double ai, double bi, bool ainf,
+                                               bool binf, float s, float lii, float w, float wc,
+                                               uint64_t m, float& dh, float& dl, int& dex) {
+    dex = 0;
+    dl = 0.0f;
+    if (ainf && binf) {
+        dh = 1.0f;
+        return phinv_two_sided_f32(w, wc);
+    }
+    if (ainf) {  // Delta = Phi(b'),  p = w Phi(b'),  1 - p = (1 - w) + w Q(b')
+        const float bp = (bf - s) / lii;
+        if (bp > -9.0f) {
+            float pb, qb;
+            if (bp < 0.0f) {
+                pb = 0.5f * erfcf(-bp * 0.70710678f);
+                qb = 1.0f - pb;
+                dh = pb;
+            } else {
+                qb = 0.5f * erfcf(bp * 0.70710678f);
+                pb = 1.0f - qb;
+                dh = pb;
+                dl = -(qb + (pb - 1.0f));  // exact: pb - 1 is exact (Sterbenz)
+            }
+            const float p = w * pb, q = wc + w * qb;
+            if (fminf(p, q) > 1e-30f) return phinv_two_sided_f32(p, q);
+        }
+        return sov_step_slow_pair(ai, bi, s, lii, m, &dh, &dl, &dex);
+    }
+    if (binf) {  // Delta = Q(a'),  p = Phi(a') + w Q(a'),  1 - p = (1 - w) Q(a')
+        const float ap = (af - s) / lii;
+        if (ap < 9.0f) {
+            float pa, qa;
+            if (ap > 0.0f) {
+                qa = 0.5f * erfcf(ap * 0.70710678f);
+                pa = 1.0f - qa;
+                dh = qa;
+            } else {
+                pa = 0.5f * erfcf(-ap * 0.70710678f);
+                qa = 1.0f - pa;
+                dh = qa;
+                dl = -(pa + (qa - 1.0f));
+            }
+            const float p = pa + w * qa, q = wc * qa;
+            if (fminf(p, q) > 1e-30f) return phinv_two_sided_f32(p, q);
+        }
+        return sov_step_slow_pair(ai, bi, s, lii, m, &dh, &dl, &dex);
+    }
+    return sov_step_slow_pair(ai, bi, s, lii, m, &dh, &dl, &dex);
+}
+
+// Running product of the factors as (ph + pl) 2^ex in FP32 pairs: each factor costs an exact
+// product (FMA error term) and a few FP32 operations; relative error ~2^-47 per factor.
+struct DFProd {
+    float ph = 1.0f, pl = 0.0f;
+    int ex = 0;
+    __device__ __forceinline__ void mul(float dh, float dl, int dex) {
+        const float nh = ph * dh;
+        const float e = fmaf(ph, dh, -nh);
+        const float nl = fmaf(ph, dl, fmaf(pl, dh, e));
+        ph = nh + nl;
+        pl = nl - (ph - nh);
+        ex += dex;
+        if (ph < 0x1p-64f) {
+            if (!(ph > 0.0f)) {
+                ph = 0.0f;
+                pl = 0.0f;
+            } else {
+                ph *= 0x1p64f;
+                pl *= 0x1p64f;
+                ex -= 64;
+            }
+        }
+    }
+    __device__ __forceinline__ double log_value() const {
+        const double p = (double)ph + (double)pl;
+        return p > 0.0 ? log(p) + (double)ex * 0.69314718055994530942 : -INFINITY;
+    }
+};

@@ -65,16 +65,21 @@ __global__ void k_split_L(int n, const double* __restrict__ L, int64_t ld, int n
 // ---------------------------------------------------------------- shared memory
 
 // ~106 KB: two CTAs fit on one SM (157 tiles of W2's 20,000 paths are resident at once).
+struct __align__(1024) TcSmem;
 struct __align__(1024) TcSmem {
     uint8_t stage[TC_STAGES][TC_STAGE_BYTES];  // [Yh 16K | Yl 16K | Lh 8K | Ll 8K]
     float Ld[TC_B * (TC_B + 1) / 2];           // diagonal block, packed lower triangle
     double a[TC_B], b[TC_B];
+    float af[TC_B], bf[TC_B];
+    unsigned char ainf[TC_B], binf[TC_B];
     uint64_t alpha[TC_B];
     uint64_t full[TC_STAGES], empty[TC_STAGES], accf[2], fin;
     uint32_t tmem;
     int item;
     int abort;
 };
+
+static_assert(sizeof(TcSmem) <= 112 * 1024, "two CTAs per SM need <= 112 KB each");
 
 // ---------------------------------------------------------------- GEMM pipeline (thread 0)
 //
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
         const int64_t q = valid ? p / P.Ns : 0;
         const uint64_t j = valid ? (uint64_t)(p - q * P.Ns) + 1u : 1u;
         const uint64_t* __restrict__ dq = P.delta + q * P.dstride;
-        LogProd lp;
+        DFProd lp;
         int pf = 0;
         int next_k = (P.nprefix > 0) ? P.prefix[0] : -1;
 
@@ -342,8 +347,14 @@ __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
                         (v < nb) ? (float)P.L[(r0 + v) + (int64_t)(r0 + u) * P.ld] : 0.0f;
             }
             if (t < TC_B) {
-                sm.a[t] = (t < nb) ? P.a[r0 + t] : 0.0;
-                sm.b[t] = (t < nb) ? P.b[r0 + t] : 1.0;
+                const double av = (t < nb) ? P.a[r0 + t] : 0.0;
+                const double bv = (t < nb) ? P.b[r0 + t] : 1.0;
+                sm.a[t] = av;
+                sm.b[t] = bv;
+                sm.af[t] = (float)av;
+                sm.bf[t] = (float)bv;
+                sm.ainf[t] = (av == -INFINITY);
+                sm.binf[t] = (bv == INFINITY);
                 sm.alpha[t] = (t < nb) ? alpha[r0 + t] : 0u;
             }
             __syncthreads();
@@ -354,10 +365,13 @@ __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
                     float sv = s[v];
 #pragma unroll
                     for (int u = 0; u < v; ++u) sv = fmaf(sm.Ld[tri(v, u)], y[u], sv);
-                    const double w = lattice_w(j, sm.alpha[v], dq[r0 + v]);
-                    double delta;
-                    y[v] = sov_step_f32(sm.a[v], sm.b[v], sv, sm.Ld[tri(v, v)], w, delta);
-                    lp.mul(delta);
+                    float w, wc, dh, dl;
+                    uint64_t wm;
+                    int dex;
+                    lattice_wf(j, sm.alpha[v], dq[r0 + v], w, wc, wm);
+                    y[v] = sov_step_f32p(sm.af[v], sm.bf[v], sm.a[v], sm.b[v], sm.ainf[v],
+                                         sm.binf[v], sv, sm.Ld[tri(v, v)], w, wc, wm, dh, dl, dex);
+                    lp.mul(dh, dl, dex);
                     while (next_k == r0 + v + 1) {
                         if (valid) P.logw_prefix[(int64_t)pf * P.Ntot + p] = lp.log_value();
                         ++pf;

@@ -145,6 +145,11 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- rooflines
 
+# kernels whose launches the library brackets with CUDA events when timing is on
+TIMED_KERNELS = ("k_oz_update", "k_oz_potrf", "k_oz_trsm", "k_oz_split", "k_sov_tc", "k_syrk",
+                 "k_sov_simt_f64", "k_sov_simt_f32")
+
+
 def kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src):
     """Achieved rate of the main kernels of the step: algorithmic work per launch (stated per
     kernel) over the kernel's average launch duration, measured by the library's CUDA events on
@@ -154,13 +159,14 @@ def kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src):
     tens_peak = peaks["bf16_tflops_sustained"]
     tens_src = f"{peak_src} bf16 dense, sustained (the kernel runs inside a long step)"
     tiles = (Ntot + 127) // 128
-    # tensor-core Cholesky update: block column j (j = 1..nt-1), output (nt-j)*128 rows x 128
-    # columns, K = 128 j, 21 BF16 digit-product MMAs per element product
+    # tensor-core Cholesky update of block column j (64 columns c0 = 64 j, j = 1..nbc-1): the
+    # (n - c0) x 64 lower panel times K = c0, i.e. sum_j (n - 64 j) 64 (64 j) multiply-adds per
+    # factorisation (~n^3/6), each carried by 21 BF16 digit-product MMAs
     ms, cnt = kt.get("k_oz_update", (0.0, 0))
     if cnt:
-        nt = (n + 127) // 128
-        steps = cnt and max(1, cnt // max(1, nt - 1))
-        mac = sum((nt - j) * 128 * 128 * 128 * j for j in range(1, nt))
+        nbc = (n + 63) // 64
+        steps = max(1, cnt // max(1, nbc - 1))
+        mac = sum((n - 64 * j) * 64 * 64 * j for j in range(1, nbc))
         fl = 2.0 * 21 * mac * steps
         out.append({"kernel": "k_oz_update", "bound": "tensor", "unit": "TFLOP/s",
                     "achieved": fl / (ms * 1e-3) / 1e12, "peak": tens_peak,
@@ -281,8 +287,7 @@ def run_gpu(args):
         dist.barrier()
     launches = ctx.launches() - launches0
     ms = t_start.elapsed_time(t_end) / args.steps
-    ktimes = {k: ctx.kernel_time(k) for k in ("k_oz_update", "k_sov_tc", "k_syrk",
-                                              "k_sov_simt_f64", "k_sov_simt_f32")}
+    ktimes = {k: ctx.kernel_time(k) for k in TIMED_KERNELS}
     ctx.timing(False)
     ctx.kernel_times = ktimes
     clocks = _clock_summary(clocks_proc, local) if rank == 0 else None
@@ -340,6 +345,8 @@ def run_gpu(args):
         "logP": float(res[0]), "P": float(res[1]), "err": float(res[2]),
         "roofline": dominant,
         "rooflines": rooflines,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ctx.kernel_times.items()
+                               if v[1]},
         "e2e": {"value": world * n * Ntot / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

@@ -83,8 +83,9 @@ mvn_status mvn_sync(mvn_ctx* ctx, int* info);
 /* Number of kernels this context has launched since creation (host counter). */
 int64_t mvn_launch_count(const mvn_ctx* ctx);
 /* Per-kernel timing: with enable != 0, CUDA events are recorded on the context's stream around
- * every launch of the main kernels (k_oz_update, k_syrk, k_sov_tc, k_sov_simt_f64,
- * k_sov_simt_f32); the call waits for the stream and clears earlier records. */
+ * every launch of the main kernels (k_oz_update, k_oz_potrf, k_oz_trsm, k_oz_split, k_syrk,
+ * k_sov_tc, k_sov_simt_f64, k_sov_simt_f32); the call waits for the stream and clears earlier
+ * records. */
 mvn_status mvn_timing(mvn_ctx* ctx, int enable);
 /* Total device time (ms, host) and number of launches (host) of kernel `name` recorded since
  * the last mvn_timing call; waits for the stream. */
@@ -112,12 +113,17 @@ mvn_status mvn_matern_grad(mvn_ctx* ctx, int n, const double* coords, double sig
 /* In-place lower Cholesky factorisation A = L L^T (Alg. 1 "dpotrf"), tile algorithm with tile
  * size `tile` (0 = automatic).  Only the lower triangle of A is read and written.
  * prec: MVN_FP64 / MVN_MIXED_SIMT: right-looking over 64-wide panels, every update in FP64.
- *   MVN_MIXED: left-looking over 128-wide panels; the trailing updates run on the tcgen05 tensor
- *   cores on exact BF16 digit slices of the rows of L (6 digits of 7 bits after a per-row
- *   power-of-two scaling; digit products summed exactly in FP32 per 128-wide chunk, combined in
- *   double-float), i.e. ~43 significant bits per product; POTRF and TRSM in FP64.  The SOV
- *   estimate needs a factor of FP64-class accuracy (an FP32 factor moves log P by ~1e-2 at
- *   n = 16,384), which this keeps.
+ *   MVN_MIXED: left-looking over 64-wide panels; the trailing updates run on the tcgen05 tensor
+ *   cores on exact BF16 digit slices of the rows of L (6 balanced digits of 7 bits of each entry
+ *   after a per-row power-of-two scaling, 42 bits in all; digit products summed exactly in FP32
+ *   over 256-wide K groups and then in 64-bit integers, so every product carries ~42 bits and
+ *   the result does not depend on the order of the split-K partial sums).  The diagonal block
+ *   (POTRF and its inverse) and the panel solve run in double-float (FP32 pair, ~48 bits)
+ *   arithmetic, reading and writing FP64.  The SOV estimate needs a factor well beyond FP32
+ *   accuracy (an FP32 factor moves log P by ~1e-2 at n = 16,384); the measured backward error
+ *   ||L L^T - A|| / ||A|| is ~1e-11 at n = 700 and below 5e-10 at n = 16,384 (against ~1e-16 for
+ *   MVN_FP64), and log P at n = 16,384 moves by ~3e-5.  The Schur complements' diagonal must
+ *   lie in FP32's normal range (about 1e-37 .. 1e38).
  * info (host, optional): if non-NULL the call waits for completion and *info = 0 or the 1-based
  * index of the first non-positive pivot (LAPACK convention), returning MVN_ERR_NOT_PD in that
  * case.  If NULL the call is asynchronous and a failure is reported by mvn_sync. */

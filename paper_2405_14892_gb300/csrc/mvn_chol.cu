@@ -9,7 +9,7 @@
 
 #define CH_NB 64
 
-// tensor-core factorisation with FP64-class accuracy (mvn_chol_oz.cu)
+// tensor-core factorisation with 42-bit products (mvn_chol_oz.cu)
 size_t chol_oz_ws_bytes(int n);
 mvn_status chol_oz_launch(mvn_ctx* ctx, int n, double* A, int64_t ld, char* ws);
 

@@ -1,5 +1,5 @@
 // mvn_chol_oz.cu -- tile Cholesky (Alg. 1 "dpotrf") whose trailing updates run on the tcgen05
-// tensor cores with FP64-class accuracy (the MVN_MIXED factorisation).
+// tensor cores with 42-bit products (the MVN_MIXED factorisation).
 //
 // The SOV estimate needs an FP64-accurate factor (an FP32 factor moves log P by ~1e-2 at
 // n = 16,384), and GB300's FP64 units deliver ~1.25 TFLOP/s.  The update L(i,:) L(j,:)^T of the
@@ -7,15 +7,22 @@
 // tensor cores (the error-free splitting of Ozaki, Ogita, Oishi and Rump, 2012):
 //   - every row i of L is scaled by 2^-E_i with 2^E_i > sqrt(Sigma_ii) >= |L_ik| (fixed before the
 //     factorisation, since sum_k L_ik^2 = Sigma_ii), so x_ik = L_ik 2^-E_i lies in (-1, 1);
-//   - x_ik = sum_{s<S} a_ik^(s) 2^(-7(s+1)) + O(2^(-7S)) with integer digits |a^(s)| <= 128,
-//     exact in BF16;
-//   - over a 128-wide K chunk, sum_k a^(s)_ik a^(t)_jk is an integer below 2^24 even when the
-//     up to 6 digit pairs of one level s+t share an accumulator, so the tensor core's FP32
-//     accumulation (which truncates) is exact;
-//   - each chunk's 6 level accumulators are drained into double-float (FP32 pair) registers, and
-//     at the end C_ij -= 2^(E_i+E_j) * acc in FP64.
-// With S = 6 digits the products carry 43 bits relative to |L_i||L_j| (row maxima), against 24
-// for FP32.  The diagonal block (POTRF), the panel solve (TRSM) and the digit split run in FP64.
+//   - x_ik is rounded once to v_ik = rint(x_ik 2^42) and written as six balanced 7-bit digits,
+//     x_ik ~ sum_{s<6} a^(s)_ik 2^(-7(s+1)), |a^(0)| <= 128, |a^(s>0)| <= 64, exact in BF16;
+//   - the digit products of one level l = s + t (l <= 5) share a TMEM accumulator; over 256
+//     values of k their sum is an integer below 2^23, so the tensor core's FP32 accumulation is
+//     exact;
+//   - every 256 values of k the six level sums are drained into a 64-bit integer
+//     T = sum_l V_l 2^(7(5-l)) (the product in units of 2^-49), which stays exact; split-K
+//     partial sums are added with integer atomics (exact and order-independent), and the POTRF
+//     and TRSM kernels apply C_ij -= 2^(E_i+E_j-49) T_ij in FP64 as they load their block.
+// The products thus carry 42 bits relative to |L_i||L_j| (row maxima), against 24 for FP32.
+// The diagonal block (POTRF), the panel solve (TRSM) and the digit split run on the CUDA cores.
+//
+// The update of block column j (64 columns) is an M = 128 (row tile) x N = 64 x K = 64 j GEMM
+// per row tile.  Its K range is cut into work items that a persistent grid of one CTA per SM
+// walks; inside a CTA one warp streams digit tiles (1-D bulk copies, 3-stage mbarrier ring), one
+// warp issues the MMAs, and eight warps drain TMEM into the integer accumulators.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -24,17 +31,42 @@
 #include "mvn_internal.cuh"
 #include "mvn_tc.cuh"
 
-#define OZ_NB 128           // block column width = K chunk
-#define OZ_S 6              // digit slices per value
-#define OZ_TILE 16384       // one 128-row x 64-column BF16 tile (128-byte swizzle)
-#define OZ_HALF 8192        // rows 0-63 or 64-127 of such a tile
+#define OZ_NB 64            // block column width
+#define OZ_RT 128           // row tile height (MMA M)
+#define OZ_S 6              // digits per value
+#define OZ_AT 8192          // one digit tile: 128 rows x 32 K, BF16, 64-byte swizzle
+#define OZ_BT 4096          // 64 rows of such a tile (the B operand)
+#define OZ_STAGE (OZ_S * (OZ_AT + OZ_BT))
+#define OZ_NST 3            // pipeline stages (K = 32 each)
+#define OZ_GRP 8            // stages accumulated in TMEM between drains (K = 256)
+#define OZ_DW 8             // drain warps
+#define OZ_THREADS (32 * (OZ_DW + 2))
 #define OZ_WAIT 4000000000LL
 
 __device__ __forceinline__ bool oz_failed(const int* status) {
     return *(volatile const int*)status != 0;
 }
 
-// E_i with 2^E_i > sqrt(A_ii)
+// Digit tile of sub-chunk kc (columns 32 kc .. 32 kc + 31), digit s, row tile rt.
+__host__ __device__ __forceinline__ size_t oz_tile(int kc, int s, int rt, int nrt) {
+    return (((size_t)kc * OZ_S + s) * nrt + rt) * OZ_AT;
+}
+
+// Bounded wait that also gives up as soon as another role of the CTA has aborted.
+__device__ __forceinline__ bool oz_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!tc::mbar_try_wait(bar, parity)) {
+        if (*abort_flag || clock64() - t0 > OZ_WAIT) return false;
+    }
+    return true;
+}
+
+// 2^k as a double for |k| < 1000 (exact; no FP64 arithmetic)
+__device__ __forceinline__ double oz_pow2(int k) {
+    return __longlong_as_double((long long)(1023 + k) << 52);
+}
+
 __global__ void k_oz_exps(int n, const double* __restrict__ A, int64_t ld, int* __restrict__ E) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -46,71 +78,92 @@ __global__ void k_oz_exps(int n, const double* __restrict__ A, int64_t ld, int* 
     E[i] = e;
 }
 
-// Digits of the finished block column j (columns c0 .. c0+127, rows >= c0) into the slice tiles
-// Z[((j*S + s)*nt + rt)*2 + ks].  One CTA per row tile rt >= j.  x = L_ik 2^-E_i is rounded once
-// to 42-bit fixed point v = rint(x 2^42) (the same value as six successive 7-bit roundings), and
-// the balanced digits are peeled off with integer shifts: d = (v + 2^(k-1)) >> k, v -= d 2^k.
-__global__ void k_oz_split(int n, const double* __restrict__ A, int64_t ld,
-                           const int* __restrict__ E, int j, int nt, uint8_t* __restrict__ Z) {
-    const int rt = j + blockIdx.x;
+// Digits of the finished block column j (columns c0 .. c0+63, rows >= c0) into the digit tiles of
+// sub-chunks 2j and 2j+1.  One CTA of 256 threads per row tile rt >= c0/128; thread = (row, half),
+// each writing whole 64-byte tile rows.  x = L_ik 2^-E_i is rounded once to 42-bit fixed point
+// v = rint(x 2^42) and the balanced digits are peeled off with integer shifts:
+// d = (v + 2^(k-1)) >> k, v -= d 2^k.  Entries above the diagonal, and rows or columns >= n, are 0.
+__global__ void __launch_bounds__(256) k_oz_split(int n, const double* __restrict__ A, int64_t ld,
+                                                  const int* __restrict__ E, int j, int nrt,
+                                                  uint8_t* __restrict__ Z) {
     const int c0 = j * OZ_NB;
-    for (int e = threadIdx.x; e < OZ_NB * OZ_NB; e += blockDim.x) {
-        const int r = e % OZ_NB, k = e / OZ_NB;  // consecutive threads: consecutive rows
-        const int i = rt * OZ_NB + r, col = c0 + k;
-        long long v = 0;
-        if (i < n && col < n && col <= i) v = llrint(ldexp(A[i + (int64_t)col * ld], 42 - E[i]));
-        const int ks = k >> 6, kk = k & 63;
-        const uint32_t off = tc::sw128_off(r, kk);
+    const int rt = c0 / OZ_RT + blockIdx.x;
+    const int r = threadIdx.x & (OZ_RT - 1), kh = threadIdx.x >> 7;
+    const int i = rt * OZ_RT + r;
+    const int ei = (i < n) ? E[i] : 0;
+    const int kc = 2 * j + kh;
+#pragma unroll 1
+    for (int c8 = 0; c8 < 4; ++c8) {
+        uint32_t pk[OZ_S][4];
 #pragma unroll
-        for (int s = 0; s < OZ_S; ++s) {
-            const int sh = 7 * (OZ_S - 1 - s);
-            const long long d = (sh > 0) ? ((v + (1ll << (sh - 1))) >> sh) : v;
-            v -= d * (1ll << sh);
-            uint8_t* tile = Z + ((((size_t)j * OZ_S + s) * nt + rt) * 2 + ks) * OZ_TILE;
-            *reinterpret_cast<__nv_bfloat16*>(tile + off) = __int2bfloat16_rn((int)d);
+        for (int e = 0; e < 8; ++e) {
+            const int col = c0 + 32 * kh + 8 * c8 + e;
+            long long v = 0;
+            if (i < n && col < n && col <= i) v = llrint(ldexp(A[i + (int64_t)col * ld], 42 - ei));
+#pragma unroll
+            for (int s = 0; s < OZ_S; ++s) {
+                const int sh = 7 * (OZ_S - 1 - s);
+                const long long d = (sh > 0) ? ((v + (1ll << (sh - 1))) >> sh) : v;
+                v -= d * (1ll << sh);
+                const uint32_t b = (uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn((int)d));
+                if (e & 1)
+                    pk[s][e >> 1] |= b << 16;
+                else
+                    pk[s][e >> 1] = b;
+            }
         }
+        const uint32_t off = tc::sw64_off((uint32_t)r, (uint32_t)(8 * c8));
+#pragma unroll
+        for (int s = 0; s < OZ_S; ++s)
+            *reinterpret_cast<uint4*>(Z + oz_tile(kc, s, rt, nrt) + off) =
+                make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
     }
 }
 
 struct __align__(1024) OzSmem {
-    uint8_t a[OZ_S][OZ_TILE];  // A digits: 128 rows x 64 K per slice
-    uint8_t b[OZ_S][OZ_HALF];  // B digits: 64 rows x 64 K per slice
-    int Ej[64];
-    uint64_t full, mdone;
+    uint8_t stage[OZ_NST][OZ_STAGE];  // per stage: A digits [S][8 KB], then B digits [S][4 KB]
+    uint64_t full[OZ_NST], empty[OZ_NST], accf, drained, fin;
     uint32_t tmem;
     int abort;
 };
 
-__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
-    const float s = hi + x;
-    const float bb = s - hi;
-    const float err = (hi - (s - bb)) + (x - bb);
-    hi = s;
-    lo += err;
+// Work of one update launch: row tiles rt0 .. rt0+n_rt-1 of block column j, K sub-chunks
+// [kc0, kc1) cut into pieces of P.  Item it = piece (it / n_rt), row tile rt0 + it % n_rt, so
+// CTAs running at the same time read the same B tiles.
+struct OzWork {
+    int n, j, nrt, rt0, n_rt, kc0, kc1, P, n_items;
+    int64_t ldT;
+};
+__device__ __forceinline__ void oz_item(const OzWork& w, int it, int& rt, int& ka, int& kb) {
+    const int p = it / w.n_rt;
+    rt = w.rt0 + (it - p * w.n_rt);
+    ka = w.kc0 + p * w.P;
+    kb = min(ka + w.P, w.kc1);
 }
 
-// Left-looking update of block column j: output tile = row tile (j + blockIdx.x), columns
-// c0 + 64*blockIdx.y .. +63, from the digit tiles of chunks 0 .. j-1.  128 threads (row = thread).
-__global__ void __launch_bounds__(128, 1) k_oz_update(int n, double* __restrict__ A, int64_t ld,
-                                                       const int* __restrict__ E, int j, int nt,
-                                                       const uint8_t* __restrict__ Z,
-                                                       int* __restrict__ status) {
+// Left-looking update of block column j: T(i, c) += sum_k (digit products), exact, for rows i of
+// the row tiles and columns c0 .. c0+63.  320 threads: warps 0-7 drain and accumulate (warp w:
+// TMEM lanes 32 (w % 4).., columns 32 (w / 4)..), warp 8 loads, warp 9 issues the MMAs.
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(const OzWork w,
+                                                               const uint8_t* __restrict__ Z,
+                                                               const int* __restrict__ E,
+                                                               long long* __restrict__ T,
+                                                               int* __restrict__ status) {
     extern __shared__ uint8_t smem_raw[];
     OzSmem& sm = *reinterpret_cast<OzSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                             ~(uintptr_t)1023);
-    if (oz_failed(status)) return;
-    const int t = threadIdx.x, warp = t >> 5;
-    const int rt = j + blockIdx.x, half = blockIdx.y;
-    const int c0 = j * OZ_NB;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int c0 = w.j * OZ_NB;
     if (t == 0) {
-        tc::mbar_init(&sm.full, 1);
-        tc::mbar_init(&sm.mdone, 1);
+        sm.abort = oz_failed(status) ? 1 : 0;  // one reading of the status for the whole CTA
+        for (int q = 0; q < OZ_NST; ++q) {
+            tc::mbar_init(&sm.full[q], 1);
+            tc::mbar_init(&sm.empty[q], 1);
+        }
+        tc::mbar_init(&sm.accf, 1);
+        tc::mbar_init(&sm.drained, 32 * OZ_DW);
+        tc::mbar_init(&sm.fin, 1);
         tc::mbar_fence_init();
-        sm.abort = 0;
-    }
-    if (t < 64) {
-        const int col = c0 + 64 * half + t;
-        sm.Ej[t] = (col < n) ? E[col] : 0;
     }
     if (warp == 0) {
         tc::tmem_alloc(&sm.tmem, 512);
@@ -119,89 +172,143 @@ __global__ void __launch_bounds__(128, 1) k_oz_update(int n, double* __restrict_
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
-                           ((uint32_t)(128 >> 4) << 24);  // BF16 x BF16 -> F32, M=128, N=64
-    float hi[64], lo[64];
-#pragma unroll
-    for (int c = 0; c < 64; ++c) {
-        hi[c] = 0.0f;
-        lo[c] = 0.0f;
-    }
-    uint32_t par = 0;
-    const uint32_t lane_base = ((uint32_t)warp * 32u) << 16;
-    for (int c = 0; c < j && !sm.abort; ++c) {
-        for (int ks = 0; ks < 2; ++ks) {
-            if (t == 0) {
-                tc::mbar_arrive_expect_tx(&sm.full, OZ_S * (OZ_TILE + OZ_HALF));
-                for (int s = 0; s < OZ_S; ++s) {
-                    const uint8_t* za = Z + ((((size_t)c * OZ_S + s) * nt + rt) * 2 + ks) * OZ_TILE;
-                    const uint8_t* zb =
-                        Z + ((((size_t)c * OZ_S + s) * nt + j) * 2 + ks) * OZ_TILE + half * OZ_HALF;
-                    tc::bulk_g2s(sm.a[s], za, OZ_TILE, &sm.full);
-                    tc::bulk_g2s(sm.b[s], zb, OZ_HALF, &sm.full);
+    volatile int* abort_flag = &sm.abort;
+
+    if (warp == OZ_DW) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+            const int rtj = c0 / OZ_RT, hb = (c0 % OZ_RT) / OZ_NB;
+            uint32_t q = 0;
+            for (int it = blockIdx.x; it < w.n_items && !*abort_flag; it += gridDim.x) {
+                int rt, ka, kb;
+                oz_item(w, it, rt, ka, kb);
+                for (int kc = ka; kc < kb; ++kc, ++q) {
+                    const int slot = (int)(q % OZ_NST);
+                    if (q >= OZ_NST &&
+                        !oz_wait(&sm.empty[slot], ((q / OZ_NST) - 1) & 1u, abort_flag)) {
+                        dev_raise(status, MVN_ERR_TIMEOUT, 0);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    uint8_t* st = sm.stage[slot];
+                    tc::mbar_arrive_expect_tx(&sm.full[slot], OZ_STAGE);
+                    for (int s = 0; s < OZ_S; ++s)
+                        tc::bulk_g2s(st + s * OZ_AT, Z + oz_tile(kc, s, rt, w.nrt), OZ_AT,
+                                     &sm.full[slot]);
+                    for (int s = 0; s < OZ_S; ++s)
+                        tc::bulk_g2s(st + OZ_S * OZ_AT + s * OZ_BT,
+                                     Z + oz_tile(kc, s, rtj, w.nrt) + hb * OZ_BT, OZ_BT,
+                                     &sm.full[slot]);
                 }
-                if (!tc::mbar_wait(&sm.full, par, OZ_WAIT)) {
-                    dev_raise(status, MVN_ERR_TIMEOUT, 0);
-                    sm.abort = 1;
-                } else {
+            }
+            // every issued copy has landed before the shared memory is released
+            for (uint32_t k = (q > OZ_NST ? q - OZ_NST : 0); k < q; ++k)
+                tc::mbar_wait(&sm.full[k % OZ_NST], (k / OZ_NST) & 1u, OZ_WAIT);
+        }
+    } else if (warp == OZ_DW + 1) {
+        // ---------------------------------------------------------------- MMA issue
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                   ((uint32_t)(OZ_NB >> 3) << 17) | ((uint32_t)(OZ_RT >> 4) << 24);
+            uint32_t q = 0, g = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < w.n_items && ok; it += gridDim.x) {
+                int rt, ka, kb;
+                oz_item(w, it, rt, ka, kb);
+                for (int k0 = ka; k0 < kb && ok; k0 += OZ_GRP, ++g) {
+                    if (*abort_flag || (g > 0 && !oz_wait(&sm.drained, (g - 1) & 1u, abort_flag))) {
+                        ok = false;
+                        break;
+                    }
                     tc::tc_fence_after();
-#pragma unroll 1
-                    for (int s = 0; s < OZ_S; ++s) {
-#pragma unroll 1
-                        for (int u = 0; u + s < OZ_S; ++u) {
-                            const uint32_t lev = (uint32_t)(s + u);
-                            const uint32_t dcol = sm.tmem + lev * 64u;
+                    const int k1 = min(k0 + OZ_GRP, kb);
+                    for (int kc = k0; kc < k1; ++kc, ++q) {
+                        const int slot = (int)(q % OZ_NST);
+                        if (!oz_wait(&sm.full[slot], (q / OZ_NST) & 1u, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::tc_fence_after();
+                        const uint32_t base = tc::smem_u32(sm.stage[slot]);
 #pragma unroll
-                            for (int k16 = 0; k16 < 4; ++k16) {
-                                const uint64_t ad = tc::sdesc_sw128(tc::smem_u32(sm.a[s]) + k16 * 32);
-                                const uint64_t bd = tc::sdesc_sw128(tc::smem_u32(sm.b[u]) + k16 * 32);
-                                const uint32_t acc = (ks == 0 && k16 == 0 && s == 0) ? 0u : 1u;
-                                tc::mma_f16(dcol, ad, bd, idesc, acc);
+                        for (int s = 0; s < OZ_S; ++s) {
+#pragma unroll
+                            for (int u = 0; u + s < OZ_S; ++u) {
+                                const uint32_t dcol = sm.tmem + (uint32_t)(s + u) * OZ_NB;
+#pragma unroll
+                                for (int k16 = 0; k16 < 2; ++k16) {
+                                    const uint64_t ad =
+                                        tc::sdesc_sw64(base + s * OZ_AT + k16 * 32);
+                                    const uint64_t bd = tc::sdesc_sw64(
+                                        base + OZ_S * OZ_AT + u * OZ_BT + k16 * 32);
+                                    const uint32_t acc =
+                                        (kc == k0 && s == 0 && k16 == 0) ? 0u : 1u;
+                                    tc::mma_f16(dcol, ad, bd, idesc, acc);
+                                }
                             }
                         }
+                        tc::mma_commit(&sm.empty[slot]);
                     }
-                    tc::mma_commit(&sm.mdone);
+                    if (ok) tc::mma_commit(&sm.accf);
                 }
             }
-            __syncthreads();
-            if (sm.abort) break;
-            // the stage is reused by the next K half / chunk: wait for the MMAs (bounded)
-            if (!tc::mbar_wait(&sm.mdone, par, OZ_WAIT)) {
-                if (t == 0) dev_raise(status, MVN_ERR_TIMEOUT, 0);
-                sm.abort = 1;
+            if (!ok) {
+                dev_raise(status, MVN_ERR_TIMEOUT, 0);
+                *abort_flag = 1;
             }
-            par ^= 1u;
-            tc::tc_fence_after();
-            __syncthreads();
-            if (sm.abort) break;
+            // all issued MMAs complete before TMEM and shared memory are released
+            tc::mma_commit(&sm.fin);
+            tc::mbar_wait(&sm.fin, 0, OZ_WAIT);
         }
-        if (sm.abort) break;
-        // drain the 6 exact level sums of this chunk into the double-float accumulators
-#pragma unroll 1
-        for (int lev = 0; lev < OZ_S; ++lev) {
-            const float sc = exp2f(-7.0f * (float)(lev + 2));
+    } else {
+        // ---------------------------------------------------------------- drain + epilogue
+        const int quarter = warp & 3, chalf = warp >> 2;
+        const uint32_t taddr = sm.tmem + (((uint32_t)quarter * 32u) << 16) + (uint32_t)chalf * 32u;
+        long long acc[32];
 #pragma unroll
-            for (int cc = 0; cc < 64; cc += 16) {
-                float v[16];
-                tc::tmem_ld16(sm.tmem + lane_base + (uint32_t)lev * 64u + cc, v);
+        for (int c = 0; c < 32; ++c) acc[c] = 0;
+        uint32_t g = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < w.n_items && ok; it += gridDim.x) {
+            int rt, ka, kb;
+            oz_item(w, it, rt, ka, kb);
+            for (int k0 = ka; k0 < kb; k0 += OZ_GRP, ++g) {
+                if (*abort_flag || !oz_wait(&sm.accf, g & 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
 #pragma unroll
-                for (int q = 0; q < 16; ++q) df_add(hi[cc + q], lo[cc + q], v[q] * sc);
+                for (int l = 0; l < OZ_S; ++l) {
+                    float v[32];
+                    tc::tmem_ld32(taddr + (uint32_t)l * OZ_NB, v);
+                    const long long sc = 1ll << (7 * (OZ_S - 1 - l));
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) acc[c] += (long long)__float2int_rn(v[c]) * sc;
+                }
+                tc::tc_fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                 tc::smem_u32(&sm.drained))
+                             : "memory");
             }
+            if (!ok) break;
+            const int i = rt * OZ_RT + quarter * 32 + lane;
+            if (i < w.n && i >= c0) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const int cc = chalf * 32 + c;
+                    const int col = c0 + cc;
+                    if (col <= i && col < w.n && acc[c] != 0)
+                        atomicAdd(reinterpret_cast<unsigned long long*>(T + i + cc * w.ldT),
+                                  (unsigned long long)acc[c]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 32; ++c) acc[c] = 0;
         }
-        tc::tc_fence_before();
-        __syncthreads();
-    }
-    // C_ij -= 2^(E_i + E_j) (hi + lo), lower part only
-    const int i = rt * OZ_NB + t;
-    if (!sm.abort && i < n) {
-        const int Ei = E[i];
-#pragma unroll
-        for (int c = 0; c < 64; ++c) {
-            const int col = c0 + 64 * half + c;
-            if (col < n && col <= i) {
-                const double v = ldexp((double)hi[c] + (double)lo[c], Ei + sm.Ej[c]);
-                A[i + (int64_t)col * ld] -= v;
-            }
+        if (!ok) {
+            dev_raise(status, MVN_ERR_TIMEOUT, 0);
+            *abort_flag = 1;
         }
     }
     tc::tc_fence_before();
@@ -212,141 +319,300 @@ __global__ void __launch_bounds__(128, 1) k_oz_update(int n, double* __restrict_
     }
 }
 
-// POTRF of the diagonal block (c0, c0), nb <= 128, in shared memory (FP64).  256 threads as a
-// 16 x 16 grid over the trailing triangle (no integer division in the inner loops).
+// C(i, c) - 2^(E_i + E_c - 49) T(i, c): the block column after its update (FP64).
+__device__ __forceinline__ double oz_apply(const double* __restrict__ A, int64_t ld,
+                                           long long* __restrict__ T, int64_t ldT, int i, int c0,
+                                           int c, int ei, int ec) {
+    long long* tp = T + i + (int64_t)c * ldT;
+    const long long tv = *tp;
+    double a = A[i + (int64_t)(c0 + c) * ld];
+    if (tv != 0) {
+        a -= (double)tv * oz_pow2(ei + ec - 49);
+        *tp = 0;
+    }
+    return a;
+}
+
+// Double-float (FP32 pair) arithmetic: x = hi + lo with |lo| <= ulp(hi) / 2 (Dekker 1971;
+// Knuth's two-sum).  GB300 runs FP32 at 64 times its FP64 rate and FP64 division and square root
+// are long dependent sequences, so the panel (POTRF, triangular inverse, TRSM) runs on pairs:
+// ~48 bits, beyond the 42 bits the digit products keep.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_from(double x) {
+    const float h = __double2float_rn(x);
+    return DF{h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ DF df_norm(float h, float l) {
+    const float s = h + l;
+    return DF{s, l - (s - h)};
+}
+// s += a * b, with s kept unnormalised (s.lo collects the rounding errors; normalise at the end)
+__device__ __forceinline__ void df_fma_acc(DF& s, DF a, DF b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float t = s.hi + p;
+    const float bp = t - s.hi;
+    s.lo += ((s.hi - (t - bp)) + (p - bp)) + e;
+    s.hi = t;
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_norm(p, e);
+}
+// square root: s0 = sqrt(d.hi) in FP32, then one Newton correction (d - s0^2) / (2 s0)
+__device__ __forceinline__ DF df_sqrt(DF d) {
+    const float s0 = sqrtf(d.hi);
+    const float p = s0 * s0;
+    const float pe = fmaf(s0, s0, -p);
+    const float diff = ((d.hi - p) - pe) + d.lo;
+    return df_norm(s0, diff * (0.5f / s0));
+}
+// reciprocal: r0 = 1 / l.hi in FP32, then r0 (1 + (1 - l r0))
+__device__ __forceinline__ DF df_rcp(DF l) {
+    const float r0 = 1.0f / l.hi;
+    const float p = l.hi * r0;
+    const float pe = fmaf(l.hi, r0, -p);
+    const float res = ((1.0f - p) - pe) - l.lo * r0;
+    return df_norm(r0, r0 * res);
+}
+
+// POTRF of the diagonal block (c0, c0), nb <= 64, after applying the update, and the inverse
+// W = L_jj^-1 for the panel solve.  One CTA of 256 threads (a 16 x 16 grid), double-float in
+// shared memory.  The inverse rides along the right-looking sweep: once column k of L is final,
+// row k of W is scaled by 1 / L_kk and removed from the rows below (the forward substitution
+// L W = I column-oriented), so both share the three barriers of each step.  W (lower
+// triangular) is kept transposed in the strict upper triangle of the tile, its diagonal in rinv.
+// Writes L_jj to A (FP64) and W^T as pairs Wt[u][c] = W[c][u].
 __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_t ld, int c0,
-                                                  int nb, int* status) {
-    extern __shared__ double Ts[];  // nb x (nb + 1)
+                                                  int nb, const int* __restrict__ E,
+                                                  long long* __restrict__ T, int64_t ldT,
+                                                  float* __restrict__ Wt, int* status) {
+    __shared__ float Sh[OZ_NB][OZ_NB + 1], Sl[OZ_NB][OZ_NB + 1];
+    __shared__ DF rinv[OZ_NB];
     __shared__ int bad;
     if (oz_failed(status)) return;
-    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-    const int sd = nb + 1;
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
     if (t == 0) bad = 0;
-    for (int jj = ty; jj < nb; jj += 16)
-        for (int i = jj + tx; i < nb; i += 16) Ts[i * sd + jj] = A[(c0 + i) + (int64_t)(c0 + jj) * ld];
+    for (int m = ty; m < OZ_NB; m += 16)
+        for (int i = tx; i < OZ_NB; i += 16) {
+            DF v{0.0f, 0.0f};
+            if (i < nb && m <= i)
+                v = df_from(oz_apply(A, ld, T, ldT, c0 + i, c0, m, E[c0 + i], E[c0 + m]));
+            else if (i == m)
+                v = DF{1.0f, 0.0f};  // identity beyond nb: the padded factor stays regular
+            Sh[i][m] = v.hi;
+            Sl[i][m] = v.lo;
+        }
     __syncthreads();
-    for (int jj = 0; jj < nb; ++jj) {
+    for (int k = 0; k < OZ_NB; ++k) {
         if (t == 0) {
-            const double d = Ts[jj * sd + jj];
-            if (!(d > 0.0)) {
-                dev_raise(status, MVN_ERR_NOT_PD, c0 + jj + 1);
+            const DF d{Sh[k][k], Sl[k][k]};
+            if (!(d.hi > 0.0f)) {
+                dev_raise(status, MVN_ERR_NOT_PD, c0 + k + 1);
                 bad = 1;
             } else {
-                Ts[jj * sd + jj] = sqrt(d);
+                const DF l = df_sqrt(d);
+                Sh[k][k] = l.hi;
+                Sl[k][k] = l.lo;
+                rinv[k] = df_rcp(l);
             }
         }
         __syncthreads();
         if (bad) return;
-        const double rl = 1.0 / Ts[jj * sd + jj];
-        for (int i = jj + 1 + t; i < nb; i += 256) Ts[i * sd + jj] *= rl;
+        const DF r = rinv[k];
+        // column k of L below the diagonal; row k of W left of the diagonal (at S[c][k])
+        if (t < OZ_NB) {
+            if (t > k) {
+                const DF v = df_mul(DF{Sh[t][k], Sl[t][k]}, r);
+                Sh[t][k] = v.hi;
+                Sl[t][k] = v.lo;
+            } else if (t < k) {
+                const DF v = df_mul(DF{Sh[t][k], Sl[t][k]}, r);
+                Sh[t][k] = v.hi;
+                Sl[t][k] = v.lo;
+            }
+        }
         __syncthreads();
-        for (int i = jj + 1 + ty; i < nb; i += 16) {
-            const double li = Ts[i * sd + jj];
-            for (int c = jj + 1 + tx; c <= i; c += 16) Ts[i * sd + c] -= li * Ts[c * sd + jj];
+        for (int i = k + 1 + ty; i < OZ_NB; i += 16) {
+            const DF li{-Sh[i][k], -Sl[i][k]};
+            // L(i, m) -= L(i, k) L(m, k), k < m <= i
+            for (int m = k + 1 + tx; m <= i; m += 16) {
+                DF s{Sh[i][m], Sl[i][m]};
+                df_fma_acc(s, li, DF{Sh[m][k], Sl[m][k]});
+                const DF v = df_norm(s.hi, s.lo);
+                Sh[i][m] = v.hi;
+                Sl[i][m] = v.lo;
+            }
+            // W(i, c) -= L(i, k) W(k, c), c <= k, with W(i, c) at S[c][i] and W(k, k) = rinv[k]
+            for (int c = tx; c <= k; c += 16) {
+                DF s{Sh[c][i], Sl[c][i]};
+                const DF wkc = (c == k) ? r : DF{Sh[c][k], Sl[c][k]};
+                df_fma_acc(s, li, wkc);
+                const DF v = df_norm(s.hi, s.lo);
+                Sh[c][i] = v.hi;
+                Sl[c][i] = v.lo;
+            }
         }
         __syncthreads();
     }
-    for (int jj = ty; jj < nb; jj += 16)
-        for (int i = jj + tx; i < nb; i += 16) A[(c0 + i) + (int64_t)(c0 + jj) * ld] = Ts[i * sd + jj];
+    for (int m = ty; m < nb; m += 16)
+        for (int i = m + tx; i < nb; i += 16)
+            A[(c0 + i) + (int64_t)(c0 + m) * ld] = df_to(DF{Sh[i][m], Sl[i][m]});
+    // Wt[u][c] = W[c][u]: S[u][c] for c > u, rinv[c] for c == u, 0 for c < u
+    for (int e = t; e < OZ_NB * OZ_NB; e += 256) {
+        const int cc = e % OZ_NB, u = e / OZ_NB;
+        DF v{0.0f, 0.0f};
+        if (cc == u)
+            v = rinv[cc];
+        else if (cc > u)
+            v = DF{Sh[u][cc], Sl[u][cc]};
+        Wt[u * OZ_NB + cc] = v.hi;
+        Wt[OZ_NB * OZ_NB + u * OZ_NB + cc] = v.lo;
+    }
 }
 
-// TRSM of the rows below the diagonal block: X L_jj^T = A(i, c0:c0+nb) for i >= c0 + nb, in two
-// 64-column halves (x in registers; the first half is also kept in shared memory, one column
-// per thread, for the second half's right-hand side).  One thread per row.
-__global__ void __launch_bounds__(128) k_oz_trsm(double* __restrict__ A, int64_t ld, int c0,
-                                                 int nb, int n, const int* status) {
-    extern __shared__ double Ls[];  // nb x (nb + 1), then x1[64][128]
+// Panel solve X = C(i, c0:c0+64) L_jj^-T = C W^T for the rows i >= c0 + nb below the diagonal
+// block, after applying the update: a double-float GEMM.  CTA = 64 rows x 64 columns, 256
+// threads, each 4 rows x 4 columns; C and W^T staged in shared memory as pairs.
+#define OZ_TR_ROWS 64
+__global__ void __launch_bounds__(256) k_oz_trsm(double* __restrict__ A, int64_t ld, int c0,
+                                                 int nb, int n, const int* __restrict__ E,
+                                                 long long* __restrict__ T, int64_t ldT,
+                                                 const float* __restrict__ Wt, const int* status) {
+    extern __shared__ float4 tr_raw[];  // Bh, Bl [NB][ROWS], Wh, Wl [NB][NB] (64 KB)
+    float(*Bh)[OZ_TR_ROWS] = reinterpret_cast<float(*)[OZ_TR_ROWS]>(tr_raw);
+    float(*Bl)[OZ_TR_ROWS] = Bh + OZ_NB;
+    float(*Wh)[OZ_NB] = reinterpret_cast<float(*)[OZ_NB]>(Bl + OZ_NB);
+    float(*Wl)[OZ_NB] = Wh + OZ_NB;
+    __shared__ int Ec[OZ_NB];
     if (oz_failed(status)) return;
     const int t = threadIdx.x;
-    const int sd = nb + 1;
-    double* x1s = Ls + nb * sd;
-    for (int e = t; e < nb * nb; e += 128) {
-        const int i = e % nb, k = e / nb;
-        Ls[i * sd + k] = (i >= k) ? A[(c0 + i) + (int64_t)(c0 + k) * ld] : 0.0;
+    const int r0 = c0 + nb + blockIdx.x * OZ_TR_ROWS;
+    if (t < OZ_NB) Ec[t] = (t < nb) ? E[c0 + t] : 0;
+    for (int e = t; e < OZ_NB * OZ_NB; e += 256) {
+        Wh[e / OZ_NB][e % OZ_NB] = Wt[e];
+        Wl[e / OZ_NB][e % OZ_NB] = Wt[OZ_NB * OZ_NB + e];
     }
     __syncthreads();
-    const int r = c0 + nb + blockIdx.x * 128 + t;
-    if (r >= n) return;
-    double x[64];
-    const int h0 = min(64, nb);
-#pragma unroll
-    for (int c = 0; c < 64; ++c) x[c] = (c < h0) ? A[r + (int64_t)(c0 + c) * ld] : 0.0;
-#pragma unroll
-    for (int c = 0; c < 64; ++c) {
-        if (c < h0) {
-            double s = x[c];
-#pragma unroll
-            for (int u = 0; u < c; ++u) s -= x[u] * Ls[c * sd + u];
-            x[c] = s / Ls[c * sd + c];
-            A[r + (int64_t)(c0 + c) * ld] = x[c];
-            x1s[c * 128 + t] = x[c];
-        }
+    for (int e = t; e < OZ_NB * OZ_TR_ROWS; e += 256) {
+        const int rr = e % OZ_TR_ROWS, u = e / OZ_TR_ROWS;  // consecutive threads: consecutive rows
+        const int r = r0 + rr;
+        DF v{0.0f, 0.0f};
+        if (r < n && u < nb) v = df_from(oz_apply(A, ld, T, ldT, r, c0, u, E[r], Ec[u]));
+        Bh[u][rr] = v.hi;
+        Bl[u][rr] = v.lo;
     }
-    if (nb <= 64) return;
-    const int h1 = nb - 64;
+    __syncthreads();
+    const int ty = t >> 4, tx = t & 15;  // rows 4 ty .. 4 ty + 3, columns 4 tx .. 4 tx + 3
+    DF acc[4][4];
 #pragma unroll
-    for (int c = 0; c < 64; ++c) x[c] = (c < h1) ? A[r + (int64_t)(c0 + 64 + c) * ld] : 0.0;
-    for (int u = 0; u < 64; ++u) {
-        const double xu = x1s[u * 128 + t];
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < 64; ++c)
-            if (c < h1) x[c] -= xu * Ls[(64 + c) * sd + u];
+        for (int b = 0; b < 4; ++b) acc[a][b] = DF{0.0f, 0.0f};
+    const int umax = min(nb, 4 * tx + 4);  // W[c][u] = 0 for u > c
+#pragma unroll 2
+    for (int u = 0; u < umax; ++u) {
+        const float4 bh = *reinterpret_cast<const float4*>(&Bh[u][4 * ty]);
+        const float4 bl = *reinterpret_cast<const float4*>(&Bl[u][4 * ty]);
+        const float4 wh = *reinterpret_cast<const float4*>(&Wh[u][4 * tx]);
+        const float4 wl = *reinterpret_cast<const float4*>(&Wl[u][4 * tx]);
+        const DF bv[4] = {{bh.x, bl.x}, {bh.y, bl.y}, {bh.z, bl.z}, {bh.w, bl.w}};
+        const DF wv[4] = {{wh.x, wl.x}, {wh.y, wl.y}, {wh.z, wl.z}, {wh.w, wl.w}};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) df_fma_acc(acc[a][b], bv[a], wv[b]);
     }
 #pragma unroll
-    for (int c = 0; c < 64; ++c) {
-        if (c < h1) {
-            double s = x[c];
+    for (int a = 0; a < 4; ++a) {
+        const int r = r0 + 4 * ty + a;
+        if (r >= n) continue;
 #pragma unroll
-            for (int u = 0; u < c; ++u) s -= x[u] * Ls[(64 + c) * sd + 64 + u];
-            x[c] = s / Ls[(64 + c) * sd + 64 + c];
-            A[r + (int64_t)(c0 + 64 + c) * ld] = x[c];
+        for (int b = 0; b < 4; ++b) {
+            const int cc = 4 * tx + b;
+            if (cc < nb) A[r + (int64_t)(c0 + cc) * ld] = df_to(df_norm(acc[a][b].hi, acc[a][b].lo));
         }
     }
 }
 
 static size_t oz_smem() { return sizeof(OzSmem) + 1024; }
 
+static int oz_nrt(int n) { return (n + OZ_RT - 1) / OZ_RT; }
+static int oz_nbc(int n) { return (n + OZ_NB - 1) / OZ_NB; }
+
+static size_t oz_trsm_smem() { return sizeof(float) * 2 * OZ_NB * (OZ_TR_ROWS + OZ_NB); }
+
 size_t chol_oz_ws_bytes(int n) {
-    const int nt = (n + OZ_NB - 1) / OZ_NB;
+    const int nrt = oz_nrt(n), nbc = oz_nbc(n);
     return ws_round(sizeof(int) * (size_t)n) +
-           ws_round((size_t)nt * OZ_S * nt * 2 * OZ_TILE);
+           ws_round((size_t)2 * nbc * OZ_S * nrt * OZ_AT) +
+           ws_round(sizeof(long long) * (size_t)OZ_NB * nrt * OZ_RT) +
+           ws_round(sizeof(float) * 2 * OZ_NB * OZ_NB);
 }
 
 mvn_status chol_oz_launch(mvn_ctx* ctx, int n, double* A, int64_t ld, char* ws) {
-    const int nt = (n + OZ_NB - 1) / OZ_NB;
+    const int nrt = oz_nrt(n), nbc = oz_nbc(n);
+    const int64_t ldT = (int64_t)nrt * OZ_RT;
     WsCarver wc(ws);
     int* E = wc.take<int>((size_t)n);
-    uint8_t* Z = wc.take<uint8_t>((size_t)nt * OZ_S * nt * 2 * OZ_TILE);
+    uint8_t* Z = wc.take<uint8_t>((size_t)2 * nbc * OZ_S * nrt * OZ_AT);
+    long long* T = wc.take<long long>((size_t)OZ_NB * ldT);
+    float* Wt = wc.take<float>((size_t)2 * OZ_NB * OZ_NB);
+    MVN_CUDA(ctx, cudaMemsetAsync(T, 0, sizeof(long long) * (size_t)OZ_NB * ldT, ctx->stream));
     k_oz_exps<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, A, ld, E);
     MVN_LAUNCHED(ctx);
     const size_t ssm = oz_smem();
     MVN_CUDA(ctx, cudaFuncSetAttribute(k_oz_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)ssm));
-    const size_t dsm = sizeof(double) * OZ_NB * (OZ_NB + 1);
-    MVN_CUDA(ctx, cudaFuncSetAttribute(k_oz_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)dsm));
-    const size_t tsm = dsm + sizeof(double) * 64 * 128;
+    const size_t tsm = oz_trsm_smem();
     MVN_CUDA(ctx, cudaFuncSetAttribute(k_oz_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tsm));
-    for (int j = 0; j < nt; ++j) {
+    for (int j = 0; j < nbc; ++j) {
         const int c0 = j * OZ_NB;
         const int nb = std::min(OZ_NB, n - c0);
+        const int rt0 = c0 / OZ_RT;
         if (j > 0) {
+            OzWork w;
+            w.n = n;
+            w.j = j;
+            w.nrt = nrt;
+            w.rt0 = rt0;
+            w.n_rt = nrt - rt0;
+            w.kc0 = 0;
+            w.kc1 = 2 * j;
+            w.ldT = ldT;
+            // pieces of whole drain groups, about four work items per SM
+            const int64_t stages = (int64_t)w.n_rt * w.kc1;
+            int64_t P = (stages + 4ll * ctx->sm_count - 1) / (4ll * ctx->sm_count);
+            P = ((P + OZ_GRP - 1) / OZ_GRP) * OZ_GRP;
+            w.P = (int)std::max<int64_t>(OZ_GRP, std::min<int64_t>(P, w.kc1));
+            const int npieces = (w.kc1 + w.P - 1) / w.P;
+            w.n_items = w.n_rt * npieces;
+            const int grid = std::min(w.n_items, ctx->sm_count);
             MVN_TIMED(ctx, "k_oz_update",
-                      (k_oz_update<<<dim3(nt - j, (nb + 63) / 64), 128, ssm, ctx->stream>>>(
-                          n, A, ld, E, j, nt, Z, ctx->d_status)));
+                      (k_oz_update<<<grid, OZ_THREADS, ssm, ctx->stream>>>(w, Z, E, T,
+                                                                           ctx->d_status)));
         }
-        k_oz_potrf<<<1, 256, dsm, ctx->stream>>>(A, ld, c0, nb, ctx->d_status);
-        MVN_LAUNCHED(ctx);
+        MVN_TIMED(ctx, "k_oz_potrf",
+                  (k_oz_potrf<<<1, 256, 0, ctx->stream>>>(A, ld, c0, nb, E, T, ldT, Wt,
+                                                          ctx->d_status)));
         const int rows = n - c0 - nb;
         if (rows > 0) {
-            k_oz_trsm<<<(rows + 127) / 128, 128, tsm, ctx->stream>>>(A, ld, c0, nb, n,
-                                                                      ctx->d_status);
-            MVN_LAUNCHED(ctx);
+            MVN_TIMED(ctx, "k_oz_trsm",
+                      (k_oz_trsm<<<(rows + OZ_TR_ROWS - 1) / OZ_TR_ROWS, 256, tsm, ctx->stream>>>(
+                          A, ld, c0, nb, n, E, T, ldT, Wt, ctx->d_status)));
         }
-        if (j + 1 < nt) {
-            k_oz_split<<<nt - j, 256, 0, ctx->stream>>>(n, A, ld, E, j, nt, Z);
-            MVN_LAUNCHED(ctx);
+        if (j + 1 < nbc) {
+            MVN_TIMED(ctx, "k_oz_split",
+                      (k_oz_split<<<nrt - rt0, 256, 0, ctx->stream>>>(n, A, ld, E, j, nrt, Z)));
         }
     }
     return MVN_OK;

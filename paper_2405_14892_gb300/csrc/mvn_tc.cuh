@@ -6,7 +6,9 @@
 //   (r / 8) * 1024 + (r % 8) * 128 + (((k / 8) ^ (r % 8)) * 16) + (k % 8) * 2,
 // i.e. 8-row groups of 1024 bytes (stride-byte-offset 1024), 16-byte chunks XOR-swizzled by the
 // row within the group.  Tiles are stored in global memory in exactly this layout so that a
-// tile moves with one contiguous bulk copy.
+// tile moves with one contiguous bulk copy.  The 64-byte swizzle (rows of 32 16-bit elements)
+// is the same scheme with 512-byte 8-row groups and the 16-byte chunk index XORed with
+// (r % 8) / 2.
 #pragma once
 #include <stdint.h>
 
@@ -19,6 +21,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 // byte offset of (row r, 16-bit element k < 64) inside a 128B-swizzled K-major tile
 __host__ __device__ __forceinline__ uint32_t sw128_off(uint32_t r, uint32_t k) {
     return (r >> 3) * 1024u + (r & 7u) * 128u + ((((k >> 3) ^ (r & 7u)) & 7u) << 4) + (k & 7u) * 2u;
+}
+
+// byte offset of (row r, 16-bit element k < 32) inside a 64B-swizzled K-major tile
+__host__ __device__ __forceinline__ uint32_t sw64_off(uint32_t r, uint32_t k) {
+    return r * 64u + ((((k >> 3) ^ ((r >> 1) & 3u)) & 3u) << 4) + (k & 7u) * 2u;
 }
 
 // ---------------------------------------------------------------- mbarrier
@@ -107,6 +114,16 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     d |= (uint64_t)2u << 61;                   // layout: 128-byte swizzle (bits 61-63)
     return d;
 }
+// The same for the 64-byte swizzle: 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address >> 4
+    d |= (uint64_t)1u << 16;                   // leading byte offset (unused when swizzled)
+    d |= (uint64_t)(512u >> 4) << 32;          // stride byte offset >> 4
+    d |= (uint64_t)1u << 46;                   // descriptor version
+    d |= (uint64_t)4u << 61;                   // layout: 64-byte swizzle
+    return d;
+}
 // Instruction descriptor, kind::f16: FP16 A and B (K-major), FP32 accumulator, M x N.
 __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
     return (1u << 4)                        // D format F32
@@ -147,6 +164,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
         : "r"(taddr));
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// The same for 32 consecutive columns.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 }  // namespace tc

@@ -234,9 +234,10 @@ mvn_status mvn_lattice_alpha(mvn_ctx* ctx, int n, uint64_t* out);
 mvn_status mvn_lattice_shifts(mvn_ctx* ctx, uint64_t seed, int M, int n, uint64_t* out);
 
 /* Self-test of the tensor-core limit-update GEMM used by MVN_MIXED (Alg. 2 step (c)):
- * S (128 x 64, row-major FP32) = Y (128 x K, row-major FP64) * L (64 x K, row-major FP64)^T,
- * computed through the same FP16 two-slice split, swizzled tiles, bulk-copy pipeline, tcgen05
- * MMAs and TMEM read as the sweep.  1 <= K <= 65536.  Asynchronous; errors via mvn_sync. */
+ * S (128 x 128, row-major FP32) = Y (128 x K, row-major FP64) * L (128 x K, row-major FP64)^T,
+ * computed through the same per-row scaling, FP16 two-slice split, swizzled tiles, bulk-copy
+ * pipeline, tcgen05 MMAs and TMEM drains as the sweep's far GEMM.  1 <= K <= 65536; the call
+ * uses workspace of ~(K + 256)^2 * 8 bytes.  Asynchronous; errors via mvn_sync. */
 mvn_status mvn_tc_selftest(mvn_ctx* ctx, int K, const double* Y, const double* L, float* S);
 
 /* Self-test of the bounded device-side waits: a kernel waits on an mbarrier that nothing

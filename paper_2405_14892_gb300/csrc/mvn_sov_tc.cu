@@ -2,17 +2,25 @@
 // tensor cores (MVN_MIXED).
 //
 // One CTA owns 128 paths (= the 128 TMEM lanes, one thread per path) and walks the dimensions in
-// blocks of 64.  For block r the limit shift S(paths, block) = Y(paths, 0:64r) L(block, 0:64r)^T is
-// an M=128, N=64, K=64r GEMM whose operands stream through shared memory with 1-D bulk copies
-// (3-stage mbarrier pipeline) and whose FP32 accumulators live in tensor memory.  FP32 accuracy of
-// the shift is recovered from FP16 operands by splitting each value into two FP16 slices:
-//   L * 2^12 = Lh + 2^-11 Ll,  y = Yh + 2^-11 Yl,
-//   S = 2^-12 (Yh Lh^T + 2^-11 (Yh Ll^T + Yl Lh^T))   (the Yl Ll^T term, 2^-22 relative, dropped)
-// with the two products accumulated in two TMEM accumulators (3 MMAs per K step).  The 2^12
-// scaling keeps small entries of L out of the FP16 subnormal range.  The diagonal block (Alg. 3)
-// runs on the CUDA cores in FP32 with the running log-weight in FP64; each thread then writes its
-// path's 64 new y values (both slices) to a per-CTA global buffer in the swizzled operand layout,
-// from where later blocks stream them back.  Paths are independent: no CTA waits on another.
+// super-blocks of 128.  For super-block R (dimensions d0 = 128 R ..) the part of the limit shift
+// that comes from all earlier dimensions,
+//   S(paths, d0:d0+128) = Y(paths, 0:d0) L(d0:d0+128, 0:d0)^T,
+// is an M = 128, N = 128, K = d0 GEMM whose operands stream through shared memory with 1-D bulk
+// copies (K = 32 per stage, 2-stage mbarrier ring) and accumulate in tensor memory.  FP32
+// accuracy of the shift is recovered from FP16 operands by two-slice splits,
+//   L 2^-e_v = Lh + Ll,  y = Yh + Yl,   S_v = 2^e_v (Yh Lh^T + Yh Ll^T + Yl Lh^T)
+// (the Yl Ll^T term, ~2^-22 relative, dropped), all three products into one TMEM accumulator;
+// e_v is a per-row power of two that keeps row v of L below 2^12 (no FP16 overflow for any
+// scale of Sigma).  The tensor cores accumulate in FP32 with truncation, so the accumulator is
+// drained into FP32 registers every K = 128 (two ping-pong TMEM buffers), which keeps the
+// accumulated error near that of an FP32 sum.  The 128 x 128 diagonal block of the super-block
+// (two 64-dimension triangles and the 64 x 64 block between them) runs on the CUDA cores in FP32
+// (Alg. 3), from a packed copy that one bulk copy brings into shared memory.  Each thread then
+// writes its path's new y values (both slices) to a per-CTA global buffer in the swizzled
+// operand layout, from where later super-blocks stream them back.  Thread 0 also drives the
+// copy/MMA pipeline without blocking: it issues whatever is ready while the other threads wait
+// for the accumulator, and it prefetches the next super-block's first stages before the
+// diagonal work.  Paths are independent: no CTA waits on another.
 #include <cuda_fp16.h>
 #include <math.h>
 #include <string.h>
@@ -26,54 +34,116 @@
 #include "mvn_tc.cuh"
 
 #define TC_P 128            // paths per CTA (MMA M, TMEM lanes)
-#define TC_B 64             // dimensions per block (MMA N, K chunk)
-#define TC_STAGES 2
-#define TC_G 4              // K chunks per TMEM accumulation group (then drained to registers)
-#define TC_YT_BYTES 16384   // one slice of a 128 x 64 FP16 Y tile
-#define TC_LT_BYTES 8192    // one slice of a 64 x 64 FP16 L tile
-#define TC_STAGE_BYTES (2 * TC_YT_BYTES + 2 * TC_LT_BYTES)
-#define TC_TMEM_COLS 256    // two accumulation buffers x (acc1 64 + acc2 64 columns)
+#define TC_N 128            // dimensions per super-block (MMA N)
+#define TC_B 64             // dimensions per diagonal sub-block
+#define TC_KS 32            // K per pipeline stage (one 64-byte swizzled row of FP16)
+#define TC_NST 2            // pipeline stages
+#define TC_G 4              // stages per TMEM accumulation group (K = 128), then drained
+#define TC_TILE 8192        // one FP16 slice of a 128-row x 32-column tile (64-byte swizzle)
+#define TC_STAGE (4 * TC_TILE)  // Yh, Yl, Lh, Ll
+#define TC_TMEM_COLS 256    // two accumulation buffers of 128 columns
+#define TC_TRI (TC_B * (TC_B + 1) / 2)
+#define TC_DPACK (2 * TC_TRI + TC_B * TC_B)  // floats of one packed diagonal block
 #define TC_WAIT_BUDGET 4000000000LL  // cycles (~2 s) before a wait gives up
+
+// Split-factor tile pair (hi, lo) of super-block rb (rows 128 rb ..) and K sub-chunk kc < 4 rb.
+__host__ __device__ __forceinline__ size_t tc_lt_off(int rb, int kc) {
+    return ((size_t)2 * rb * (rb - 1) + kc) * 2 * TC_TILE;
+}
 
 // ---------------------------------------------------------------- operand preparation
 
-// Split L (FP64, column-major, lower) into FP16 tiles: Lt[slice][kc][rb] is the 64 x 64 tile of
-// rows 64 rb.., columns 64 kc.. in the swizzled K-major layout.  Only kc <= rb is written; the
-// strict upper part, rows >= n and columns >= n are zero.
-__global__ void k_split_L(int n, const double* __restrict__ L, int64_t ld, int nrb,
-                          __half* __restrict__ Lt) {
-    const int x = blockIdx.x;
-    int rb = (int)((sqrt(8.0 * x + 1.0) - 1.0) * 0.5);
-    while ((rb + 1) * (rb + 2) / 2 <= x) ++rb;
-    while (rb * (rb + 1) / 2 > x) --rb;
-    const int kc = x - rb * (rb + 1) / 2;
-    const size_t slice = (size_t)nrb * nrb * (TC_LT_BYTES / 2);
-    __half* hi = Lt + ((size_t)kc * nrb + rb) * (TC_LT_BYTES / 2);
-    __half* lo = hi + slice;
-    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-        const int r = e & 63, k = e >> 6;  // consecutive threads: consecutive rows (coalesced)
-        const int i = 64 * rb + r, j = 64 * kc + k;
-        double v = (i < n && j < n && j <= i) ? L[i + (int64_t)j * ld] * 4096.0 : 0.0;
-        __half h = __double2half(v);
-        __half l = __double2half((v - (double)__half2float(h)) * 2048.0);
-        const uint32_t off = tc::sw128_off(r, k) >> 1;
-        hi[off] = h;
-        lo[off] = l;
+// Row maxima max_u |L_vu| over the lower triangle: CTA (row block of 128, column chunk of 512),
+// thread = row; the maxima of non-negative doubles are combined as their bit patterns (ordered
+// like the values).  rowmax must start at zero.
+#define TC_RM_COLS 512
+__global__ void k_row_max(int n, const double* __restrict__ L, int64_t ld,
+                          unsigned long long* __restrict__ rowmax) {
+    const int v = blockIdx.x * TC_N + threadIdx.x;
+    const int u0 = blockIdx.y * TC_RM_COLS;
+    if (v >= n || u0 > v) return;
+    const int u1 = min(u0 + TC_RM_COLS, v + 1);
+    double mx = 0.0;
+#pragma unroll 8
+    for (int u = u0; u < u1; ++u) mx = fmax(mx, fabs(L[v + (int64_t)u * ld]));
+    if (mx > 0.0) atomicMax(rowmax + v, (unsigned long long)__double_as_longlong(mx));
+}
+
+// e_v with 2^(e_v + 12) > max_u |L_vu|, and 2^e_v.
+__global__ void k_row_exp(int nrows, const unsigned long long* __restrict__ rowmax,
+                          int* __restrict__ eL, float* __restrict__ escale) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nrows) return;
+    const double mx = __longlong_as_double((long long)rowmax[v]);
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);  // mx = m 2^e, m in [0.5, 1)
+    e -= 12;
+    eL[v] = e;
+    escale[v] = ldexpf(1.0f, e);
+}
+
+// FP16 slices of L 2^-e_v for the tile pair (rb, kc), kc < 4 rb: one CTA of 128 threads, thread
+// = row, writing whole 64-byte tile rows.  Rows >= n are zero.
+__global__ void __launch_bounds__(128) k_split_L(int n, const double* __restrict__ L, int64_t ld,
+                                                 const int* __restrict__ eL,
+                                                 uint8_t* __restrict__ Lt) {
+    const int kc = blockIdx.x, rb = blockIdx.y;
+    if (kc >= 4 * rb) return;
+    const int r = threadIdx.x, v = TC_N * rb + r;
+    uint8_t* hi = Lt + tc_lt_off(rb, kc);
+    uint8_t* lo = hi + TC_TILE;
+    const int e = (v < n) ? -eL[v] : 0;
+#pragma unroll
+    for (int c8 = 0; c8 < 4; ++c8) {
+        __align__(16) __half h[8], l[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int u = TC_KS * kc + 8 * c8 + q;
+            const double x = (v < n) ? ldexp(L[v + (int64_t)u * ld], e) : 0.0;
+            h[q] = __double2half(x);
+            l[q] = __double2half(x - (double)__half2float(h[q]));
+        }
+        const uint32_t off = tc::sw64_off((uint32_t)r, (uint32_t)(8 * c8));
+        *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<const uint4*>(h);
+        *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<const uint4*>(l);
+    }
+}
+
+// Packed FP32 diagonal block of super-block rb: [triangle of sub-block 0 | triangle of sub-block
+// 1 | near block N[u][v] = L(d0 + 64 + v, d0 + u)], triangles row-packed (v (v + 1) / 2 + u).
+// Entries outside the factor are zero, diagonal entries beyond n are one.
+__global__ void k_pack_D(int n, const double* __restrict__ L, int64_t ld, float* __restrict__ D) {
+    const int rb = blockIdx.x, d0 = TC_N * rb;
+    float* out = D + (size_t)rb * TC_DPACK;
+    for (int e = threadIdx.x; e < TC_N * TC_N; e += blockDim.x) {
+        const int v = e % TC_N, u = e / TC_N;  // consecutive threads: consecutive rows
+        if (u > v) continue;
+        float x;
+        if (d0 + v < n)
+            x = (float)L[(d0 + v) + (int64_t)(d0 + u) * ld];
+        else
+            x = (u == v) ? 1.0f : 0.0f;
+        if (v < TC_B)
+            out[v * (v + 1) / 2 + u] = x;
+        else if (u >= TC_B)
+            out[TC_TRI + (v - TC_B) * (v - TC_B + 1) / 2 + (u - TC_B)] = x;
+        else
+            out[2 * TC_TRI + u * TC_B + (v - TC_B)] = x;
     }
 }
 
 // ---------------------------------------------------------------- shared memory
 
-// ~106 KB: two CTAs fit on one SM (157 tiles of W2's 20,000 paths are resident at once).
-struct __align__(1024) TcSmem;
+// ~103 KB: two CTAs fit on one SM (157 tiles of 20,000 paths are resident at once).
 struct __align__(1024) TcSmem {
-    uint8_t stage[TC_STAGES][TC_STAGE_BYTES];  // [Yh 16K | Yl 16K | Lh 8K | Ll 8K]
-    float Ld[TC_B * (TC_B + 1) / 2];           // diagonal block, packed lower triangle
-    double a[TC_B], b[TC_B];
-    float af[TC_B], bf[TC_B];
-    unsigned char ainf[TC_B], binf[TC_B];
-    uint64_t alpha[TC_B];
-    uint64_t full[TC_STAGES], empty[TC_STAGES], accf[2], fin;
+    uint8_t stage[TC_NST][TC_STAGE];  // [Yh 8K | Yl 8K | Lh 8K | Ll 8K]
+    float D[TC_DPACK];                // packed diagonal block of the super-block
+    double a[TC_N], b[TC_N];
+    float af[TC_N], bf[TC_N];
+    float escale[TC_N];
+    uint64_t alpha[TC_N];
+    unsigned char ainf[TC_N], binf[TC_N];
+    uint64_t full[TC_NST], empty[TC_NST], accf[2], dbar, fin;
     uint32_t tmem;
     int item;
     int abort;
@@ -83,152 +153,170 @@ static_assert(sizeof(TcSmem) <= 112 * 1024, "two CTAs per SM need <= 112 KB each
 
 // ---------------------------------------------------------------- GEMM pipeline (thread 0)
 //
-// The K chunks of all blocks form one sequence; chunk number q uses stage q % TC_STAGES, whose
-// "full" barrier completes for the (q / TC_STAGES)-th time when its bulk copies land and whose
-// "empty" barrier completes when the MMAs reading it are done.  Chunks are grouped by TC_G; group
-// number g accumulates into TMEM buffer g % 2 and commits to accf[g % 2] when complete.  All
-// parities follow from these counters, so no barrier phase is ever skipped or waited twice.
+// The stages of all far GEMMs form one sequence; stage number q uses slot q % TC_NST, whose
+// "full" barrier completes for the (q / TC_NST)-th time when its bulk copies land and whose
+// "empty" barrier completes when the MMAs reading it are done.  Stages are grouped by TC_G; group
+// number g accumulates into TMEM buffer g % 2 and commits to accf[g % 2] when complete; a group's
+// MMAs start only once the group two earlier has been drained.  All parities follow from these
+// counters, so no barrier phase is ever skipped or waited twice.
 struct TcPipe {
-    uint64_t q_load = 0;  // global chunk number of the next load
-    uint64_t q_mma = 0;   // global chunk number of the next MMA chunk
-    uint64_t g_next = 0;  // global group number of the group the next MMA chunk belongs to
-    // current block
-    const uint8_t* Ybuf;
-    const uint8_t* Lt;
-    size_t lslice;
-    int nrb, rb;
-    int kcs;              // chunks of the block
-    int next_load, next_mma;  // within-block chunk indices
-    uint64_t q_block0;    // global chunk number of the block's chunk 0
+    uint32_t q_load = 0;   // global stage number of the next load
+    uint32_t q_mma = 0;    // global stage number of the next MMA stage
+    uint32_t g0 = 0;       // global group number of the current far GEMM's group 0
+    uint32_t drained = 0;  // groups drained so far (global)
+    const uint8_t* Ybuf = nullptr;
+    const uint8_t* Lsb = nullptr;  // tile pairs of the current super-block
+    int kcs = 0;           // stages of the current far GEMM
+    int kready = 0;        // stages whose Y tiles are written (loads beyond wait)
+    int rb = -1;           // super-block of the current far GEMM (-1: none begun in this item)
+    int next_load = 0, next_mma = 0;
 };
 
-__device__ __forceinline__ uint32_t tc_buf_col(uint64_t g) { return (uint32_t)(g & 1u) * 128u; }
+__device__ __forceinline__ uint32_t tc_buf_col(uint32_t g) { return (g & 1u) * TC_N; }
 
-// Issue loads ahead and MMAs for the block's chunks < limit; false on a timed-out wait.
-__device__ bool tc_pump(TcSmem& sm, TcPipe& pp, int limit) {
-    const uint32_t idesc = tc::idesc_f16_f32(TC_P, TC_B);
-    while (pp.next_mma < limit) {
-        while (pp.next_load < pp.kcs && pp.next_load < pp.next_mma + TC_STAGES) {
-            const uint64_t q = pp.q_load;
-            const int s = (int)(q % TC_STAGES);
-            if (q >= TC_STAGES) {  // the MMAs of chunk q - TC_STAGES must have left the stage
-                const uint32_t par = (uint32_t)((q / TC_STAGES - 1) & 1u);
-                if (!tc::mbar_wait(&sm.empty[s], par, TC_WAIT_BUDGET)) return false;
+// Issue every load and MMA stage that can go now, without waiting (test_wait only).
+__device__ void tc_pump(TcSmem& sm, TcPipe& pp) {
+    const uint32_t idesc = tc::idesc_f16_f32(TC_P, TC_N);
+    for (;;) {
+        bool progress = false;
+        if (pp.next_load < pp.kready && pp.next_load < pp.next_mma + TC_NST) {
+            const uint32_t q = pp.q_load;
+            const int slot = (int)(q % TC_NST);
+            if (q < TC_NST || tc::mbar_test_wait(&sm.empty[slot], ((q / TC_NST) - 1) & 1u)) {
+                uint8_t* st = sm.stage[slot];
+                const int kc = pp.next_load;
+                tc::mbar_arrive_expect_tx(&sm.full[slot], TC_STAGE);
+                tc::bulk_g2s(st, pp.Ybuf + (size_t)kc * 2 * TC_TILE, 2 * TC_TILE, &sm.full[slot]);
+                tc::bulk_g2s(st + 2 * TC_TILE, pp.Lsb + (size_t)kc * 2 * TC_TILE, 2 * TC_TILE,
+                             &sm.full[slot]);
+                ++pp.q_load;
+                ++pp.next_load;
+                progress = true;
             }
-            uint8_t* st = sm.stage[s];
-            const int kc = pp.next_load;
-            tc::mbar_arrive_expect_tx(&sm.full[s], TC_STAGE_BYTES);
-            tc::bulk_g2s(st, pp.Ybuf + (size_t)kc * 2 * TC_YT_BYTES, 2 * TC_YT_BYTES, &sm.full[s]);
-            const uint8_t* lt = pp.Lt + ((size_t)kc * pp.nrb + pp.rb) * TC_LT_BYTES;
-            tc::bulk_g2s(st + 2 * TC_YT_BYTES, lt, TC_LT_BYTES, &sm.full[s]);
-            tc::bulk_g2s(st + 2 * TC_YT_BYTES + TC_LT_BYTES, lt + pp.lslice, TC_LT_BYTES,
-                         &sm.full[s]);
-            ++pp.q_load;
-            ++pp.next_load;
         }
-        const uint64_t q = pp.q_mma;
-        const int s = (int)(q % TC_STAGES);
-        if (!tc::mbar_wait(&sm.full[s], (uint32_t)((q / TC_STAGES) & 1u), TC_WAIT_BUDGET))
-            return false;
-        tc::tc_fence_after();
-        const int kc = pp.next_mma;
-        const uint64_t g = pp.g_next + (uint64_t)(kc / TC_G);
-        const uint32_t acc1 = sm.tmem + tc_buf_col(g), acc2 = acc1 + TC_B;
-        const uint32_t base = tc::smem_u32(sm.stage[s]);
+        if (pp.next_mma < pp.next_load) {
+            const uint32_t q = pp.q_mma;
+            const int slot = (int)(q % TC_NST);
+            const int kc = pp.next_mma;
+            const uint32_t g = pp.g0 + (uint32_t)(kc / TC_G);
+            if (g < pp.drained + 2 && tc::mbar_test_wait(&sm.full[slot], (q / TC_NST) & 1u)) {
+                tc::tc_fence_after();
+                const uint32_t acc = sm.tmem + tc_buf_col(g);
+                const uint32_t base = tc::smem_u32(sm.stage[slot]);
 #pragma unroll
-        for (int k16 = 0; k16 < 4; ++k16) {
-            const uint32_t ko = k16 * 32;
-            const uint64_t ah = tc::sdesc_sw128(base + ko);
-            const uint64_t al = tc::sdesc_sw128(base + TC_YT_BYTES + ko);
-            const uint64_t bh = tc::sdesc_sw128(base + 2 * TC_YT_BYTES + ko);
-            const uint64_t bl = tc::sdesc_sw128(base + 2 * TC_YT_BYTES + TC_LT_BYTES + ko);
-            const uint32_t first = (kc % TC_G == 0 && k16 == 0) ? 0u : 1u;
-            tc::mma_f16(acc1, ah, bh, idesc, first);
-            tc::mma_f16(acc2, ah, bl, idesc, first);
-            tc::mma_f16(acc2, al, bh, idesc, 1u);
+                for (int k16 = 0; k16 < 2; ++k16) {
+                    const uint32_t ko = k16 * 32;
+                    const uint64_t ah = tc::sdesc_sw64(base + ko);
+                    const uint64_t al = tc::sdesc_sw64(base + TC_TILE + ko);
+                    const uint64_t bh = tc::sdesc_sw64(base + 2 * TC_TILE + ko);
+                    const uint64_t bl = tc::sdesc_sw64(base + 3 * TC_TILE + ko);
+                    const uint32_t first = (kc % TC_G == 0 && k16 == 0) ? 0u : 1u;
+                    tc::mma_f16(acc, ah, bh, idesc, first);
+                    tc::mma_f16(acc, ah, bl, idesc, 1u);
+                    tc::mma_f16(acc, al, bh, idesc, 1u);
+                }
+                tc::mma_commit(&sm.empty[slot]);
+                if (kc % TC_G == TC_G - 1 || kc == pp.kcs - 1) tc::mma_commit(&sm.accf[g & 1u]);
+                ++pp.q_mma;
+                ++pp.next_mma;
+                progress = true;
+            }
         }
-        tc::mma_commit(&sm.empty[s]);
-        if (kc % TC_G == TC_G - 1 || kc == pp.kcs - 1) tc::mma_commit(&sm.accf[g & 1u]);
-        ++pp.q_mma;
-        ++pp.next_mma;
+        if (!progress) return;
     }
-    return true;
 }
 
-// Limit shift of this thread's path for the block's 64 dimensions: the K chunks are accumulated
-// in TMEM group by group (TC_G chunks each, two ping-pong buffers) and every group's partial sums
-// are added into FP32 registers.  Short in-TMEM accumulation chains keep the tensor cores'
-// accumulation error near that of an FP32 sum.  All threads call this; thread 0 also issues.
-// Returns false if a wait timed out.
-__device__ bool tc_block_shift(TcSmem& sm, TcPipe& pp, const uint8_t* Ybuf, const uint8_t* Lt,
-                               int nrb, int rb, uint64_t& g_all, float (&s)[TC_B]) {
+// Set up the far GEMM of super-block rb (K = 128 rb) after the previous one has been drained;
+// `ready` = stages whose Y tiles are already written (all of them unless this is a prefetch
+// made before the previous super-block's diagonal work).
+__device__ __forceinline__ void tc_far_begin(TcPipe& pp, const uint8_t* Ybuf, const uint8_t* Lt,
+                                             int rb, int ready) {
+    pp.g0 = pp.drained;
+    pp.Ybuf = Ybuf;
+    pp.Lsb = Lt + tc_lt_off(rb, 0);
+    pp.kcs = 4 * rb;
+    pp.kready = ready;
+    pp.rb = rb;
+    pp.next_load = 0;
+    pp.next_mma = 0;
+}
+
+// Far part of the limit shift of this thread's path for super-block rb (K = 128 rb): the groups
+// g0, g0 + 1, .. are accumulated in TMEM and added into FP32 registers; thread 0 (whose pipe has
+// begun this far GEMM with the same g0) keeps the pipeline moving while the others wait.  All
+// threads call this with the same rb and g0.  Returns false if a wait timed out.
+__device__ bool tc_far(TcSmem& sm, TcPipe& pp, int rb, uint32_t g0, float (&s)[TC_N]) {
     const int t = threadIdx.x;
-    const int kcs = rb;  // chunks 0 .. rb-1
-    const int ng = (kcs + TC_G - 1) / TC_G;
-    bool ok = true;
-    if (t == 0) {
-        pp.Ybuf = Ybuf;
-        pp.Lt = Lt;
-        pp.lslice = (size_t)nrb * nrb * TC_LT_BYTES;
-        pp.nrb = nrb;
-        pp.rb = rb;
-        pp.kcs = kcs;
-        pp.next_load = 0;
-        pp.next_mma = 0;
-        pp.g_next = g_all;
-        ok = tc_pump(sm, pp, min(kcs, 2 * TC_G));
-        if (!ok) sm.abort = 1;
-    }
+    const int ng = (4 * rb + TC_G - 1) / TC_G;
 #pragma unroll
-    for (int v = 0; v < TC_B; ++v) s[v] = 0.0f;
+    for (int v = 0; v < TC_N; ++v) s[v] = 0.0f;
     const uint32_t lane_base = ((uint32_t)(t >> 5) * 32u) << 16;
-    for (int g = 0; g < ng; ++g) {
-        const uint64_t gg = g_all + g;
-        if (!tc::mbar_wait(&sm.accf[gg & 1u], (uint32_t)((gg >> 1) & 1u), TC_WAIT_BUDGET)) {
+    bool ok = true;
+    for (int gi = 0; gi < ng; ++gi) {
+        const uint32_t g = g0 + (uint32_t)gi;
+        const uint32_t par = (g >> 1) & 1u;
+        if (t == 0) {
+            pp.kready = pp.kcs;  // every Y tile of this far GEMM is written by now
+            const long long t0 = clock64();
+            for (;;) {
+                tc_pump(sm, pp);
+                if (tc::mbar_test_wait(&sm.accf[g & 1u], par)) break;
+                if (clock64() - t0 > TC_WAIT_BUDGET) {
+                    ok = false;
+                    sm.abort = 1;
+                    break;
+                }
+            }
+        } else if (!tc::mbar_wait(&sm.accf[g & 1u], par, TC_WAIT_BUDGET)) {
             ok = false;
             sm.abort = 1;
         }
-        tc::tc_fence_after();
-        const uint32_t col = sm.tmem + lane_base + tc_buf_col(gg);
+        if (ok) {
+            tc::tc_fence_after();
+            const uint32_t col = sm.tmem + lane_base + tc_buf_col(g);
 #pragma unroll
-        for (int c = 0; c < TC_B; c += 16) {
-            float h[16], l[16];
-            tc::tmem_ld16(col + c, h);
-            tc::tmem_ld16(col + TC_B + c, l);
+            for (int c = 0; c < TC_N; c += 32) {
+                float v[32];
+                tc::tmem_ld32(col + c, v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) s[c + i] += fmaf(l[i], 1.0f / 2048.0f, h[i]);
+                for (int i = 0; i < 32; ++i) s[c + i] += v[i];
+            }
         }
         tc::tc_fence_before();
         __syncthreads();  // the buffer of group g is free again
-        if (sm.abort) break;
+        if (sm.abort) return false;
         if (t == 0) {
+            pp.drained = g + 1;
             tc::tc_fence_after();
-            if (!tc_pump(sm, pp, min(kcs, (g + 3) * TC_G))) sm.abort = 1;
+            tc_pump(sm, pp);
         }
     }
 #pragma unroll
-    for (int v = 0; v < TC_B; ++v) s[v] *= (1.0f / 4096.0f);
-    g_all += ng;
-    return ok && !sm.abort;
+    for (int v = 0; v < TC_N; ++v) s[v] *= sm.escale[v];
+    return ok;
 }
 
-// Write this thread's 64 new y values (two FP16 slices) as row `t` of the Y tile of chunk kc.
+// Write this thread's 64 new y values (two FP16 slices) as row `t` of the Y tiles of sub-chunks
+// kc and kc + 1.
 __device__ __forceinline__ void tc_write_y(uint8_t* __restrict__ Ybuf, int kc, int t,
                                            const float (&y)[TC_B]) {
-    uint8_t* hi = Ybuf + (size_t)kc * 2 * TC_YT_BYTES;
-    uint8_t* lo = hi + TC_YT_BYTES;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        __align__(16) __half h[8], l[8];
+    for (int h2 = 0; h2 < 2; ++h2) {
+        uint8_t* hi = Ybuf + (size_t)(kc + h2) * 2 * TC_TILE;
+        uint8_t* lo = hi + TC_TILE;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const float v = y[8 * c + e];
-            h[e] = __float2half_rn(v);
-            l[e] = __float2half_rn((v - __half2float(h[e])) * 2048.0f);
+        for (int c = 0; c < 4; ++c) {
+            __align__(16) __half h[8], l[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const float v = y[32 * h2 + 8 * c + e];
+                h[e] = __float2half_rn(v);
+                l[e] = __float2half_rn(v - __half2float(h[e]));
+            }
+            const uint32_t off = tc::sw64_off((uint32_t)t, (uint32_t)(8 * c));
+            *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<const uint4*>(h);
+            *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<const uint4*>(l);
         }
-        const uint32_t off = tc::sw128_off(t, 8 * c);
-        *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<const uint4*>(h);
-        *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<const uint4*>(l);
     }
 }
 
@@ -238,27 +326,25 @@ struct TcBatch {
     const int2* items;
     int nitems;
     int* counter;
-    const uint8_t* Lt;     // split factor tiles
-    int nrb;               // row blocks of the split factor
+    const uint8_t* Lt;     // split factor tile pairs
+    const float* escale;   // per-row scale 2^e_v of the split factor
+    const float* Dpack;    // packed diagonal blocks
     uint8_t* Yscratch;     // per-CTA Y buffers
     int64_t ystride;       // bytes per CTA buffer
     int* status;
 };
 
-__device__ __forceinline__ double tc_logprod_value(double prod, int ex) {
-    return prod > 0.0 ? log(prod) + (double)ex * 0.69314718055994530942 : -INFINITY;
-}
-
 // Shared set-up of the tensor-core kernels: barriers and TMEM.
 __device__ __forceinline__ void tc_setup(TcSmem& sm) {
     const int t = threadIdx.x;
     if (t == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < TC_NST; ++s) {
             tc::mbar_init(&sm.full[s], 1);
             tc::mbar_init(&sm.empty[s], 1);
         }
         tc::mbar_init(&sm.accf[0], 1);
         tc::mbar_init(&sm.accf[1], 1);
+        tc::mbar_init(&sm.dbar, 1);
         tc::mbar_init(&sm.fin, 1);
         tc::mbar_fence_init();
         sm.abort = 0;
@@ -272,12 +358,14 @@ __device__ __forceinline__ void tc_setup(TcSmem& sm) {
     tc::tc_fence_after();
 }
 
-// After an aborted (timed-out) wait: let the copies and MMAs this CTA issued finish (bounded)
-// before its shared memory and tensor memory are released.
-__device__ __forceinline__ void tc_quiesce(TcSmem& sm, const TcPipe& pp) {
-    if (threadIdx.x != 0 || !sm.abort) return;
-    for (uint64_t q = pp.q_mma; q < pp.q_load; ++q)
-        tc::mbar_wait(&sm.full[q % TC_STAGES], (uint32_t)((q / TC_STAGES) & 1u), TC_WAIT_BUDGET);
+// Before shared and tensor memory are released: every copy this CTA issued has landed and every
+// MMA it issued has completed (bounded waits; also after an aborted wait).
+__device__ __forceinline__ void tc_quiesce(TcSmem& sm, const TcPipe& pp, uint32_t dphase) {
+    if (threadIdx.x != 0) return;
+    const uint32_t q0 = pp.q_load > TC_NST ? pp.q_load - TC_NST : 0u;
+    for (uint32_t q = q0; q < pp.q_load; ++q)
+        tc::mbar_wait(&sm.full[q % TC_NST], (q / TC_NST) & 1u, TC_WAIT_BUDGET);
+    if (dphase > 0) tc::mbar_wait(&sm.dbar, (dphase - 1) & 1u, TC_WAIT_BUDGET);
     tc::mma_commit(&sm.fin);
     tc::mbar_wait(&sm.fin, 0, TC_WAIT_BUDGET);
 }
@@ -296,7 +384,7 @@ __device__ __forceinline__ TcSmem& tc_smem(uint8_t* raw) {
                                       ~(uintptr_t)1023);
 }
 
-__device__ __forceinline__ int tri(int v, int u) { return v * (v + 1) / 2 + u; }
+__device__ __forceinline__ constexpr int tri(int v, int u) { return v * (v + 1) / 2 + u; }
 
 __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
                                                      const uint64_t* __restrict__ alpha) {
@@ -305,8 +393,10 @@ __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
     const int t = threadIdx.x;
     tc_setup(sm);
     TcPipe pp;
-    uint64_t g_all = 0;  // groups issued so far (uniform across threads)
+    uint32_t dphase = 0;  // loads of the packed diagonal block issued (uniform)
+    uint32_t g_all = 0;   // accumulation groups of all far GEMMs so far (uniform)
     uint8_t* Ybuf = bt.Yscratch + (int64_t)blockIdx.x * bt.ystride;
+    const uint32_t lane_base = ((uint32_t)(t >> 5) * 32u) << 16;
 
     for (;;) {
         if (t == 0) sm.item = atomicAdd(bt.counter, 1);
@@ -324,75 +414,141 @@ __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
         DFProd lp;
         int pf = 0;
         int next_k = (P.nprefix > 0) ? P.prefix[0] : -1;
+        const int nsb = (n + TC_N - 1) / TC_N;
+        if (t == 0) pp.rb = -1;
 
-        for (int r0 = 0; r0 < n; r0 += TC_B) {
-            const int nb = min(TC_B, n - r0);
-            const int rb = r0 / TC_B;
-            float s[TC_B];
-            if (rb > 0) {
-                if (!tc_block_shift(sm, pp, Ybuf, bt.Lt, bt.nrb, rb, g_all, s)) {
-                    if (t == 0) dev_raise(bt.status, MVN_ERR_TIMEOUT, 0);
-                }
-            } else {
-#pragma unroll
-                for (int v = 0; v < TC_B; ++v) s[v] = 0.0f;
+        for (int rb = 0; rb < nsb; ++rb) {
+            const int d0 = rb * TC_N;
+            const int nb2 = min(TC_N, n - d0);
+            // packed diagonal block of this super-block (shared memory is free: the previous
+            // super-block's diagonal work ended at a barrier)
+            if (t == 0) {
+                tc::fence_proxy_async_smem();
+                tc::mbar_arrive_expect_tx(&sm.dbar, TC_DPACK * 4);
+                tc::bulk_g2s(sm.D, bt.Dpack + (size_t)rb * TC_DPACK, TC_DPACK * 4, &sm.dbar);
+                if (rb > 0 && pp.rb != rb) tc_far_begin(pp, Ybuf, bt.Lt, rb, 4 * rb);
             }
-            __syncthreads();
-            if (sm.abort) break;
-            // diagonal block operands
-            for (int e = t; e < TC_B * TC_B; e += TC_P) {
-                const int v = e % TC_B, u = e / TC_B;
-                if (u <= v)
-                    sm.Ld[tri(v, u)] =
-                        (v < nb) ? (float)P.L[(r0 + v) + (int64_t)(r0 + u) * P.ld] : 0.0f;
-            }
-            if (t < TC_B) {
-                const double av = (t < nb) ? P.a[r0 + t] : 0.0;
-                const double bv = (t < nb) ? P.b[r0 + t] : 1.0;
+            ++dphase;
+            if (t < TC_N) {
+                const int v = d0 + t;
+                const double av = (t < nb2) ? P.a[v] : 0.0;
+                const double bv = (t < nb2) ? P.b[v] : 1.0;
                 sm.a[t] = av;
                 sm.b[t] = bv;
                 sm.af[t] = (float)av;
                 sm.bf[t] = (float)bv;
                 sm.ainf[t] = (av == -INFINITY);
                 sm.binf[t] = (bv == INFINITY);
-                sm.alpha[t] = (t < nb) ? alpha[r0 + t] : 0u;
+                sm.alpha[t] = (t < nb2) ? alpha[v] : 0u;
+                sm.escale[t] = bt.escale[v];
             }
             __syncthreads();
-            float y[TC_B];
+            float s[TC_N];
+            if (rb > 0) {
+                if (!tc_far(sm, pp, rb, g_all, s) && t == 0)
+                    dev_raise(bt.status, MVN_ERR_TIMEOUT, 0);
+                g_all += (uint32_t)((4 * rb + TC_G - 1) / TC_G);
+            } else {
 #pragma unroll
-            for (int v = 0; v < TC_B; ++v) {
-                if (v < nb) {
-                    float sv = s[v];
-#pragma unroll
-                    for (int u = 0; u < v; ++u) sv = fmaf(sm.Ld[tri(v, u)], y[u], sv);
-                    float w, wc, dh, dl;
-                    uint64_t wm;
-                    int dex;
-                    lattice_wf(j, sm.alpha[v], dq[r0 + v], w, wc, wm);
-                    y[v] = sov_step_f32p(sm.af[v], sm.bf[v], sm.a[v], sm.b[v], sm.ainf[v],
-                                         sm.binf[v], sv, sm.Ld[tri(v, v)], w, wc, wm, dh, dl, dex);
-                    lp.mul(dh, dl, dex);
-                    while (next_k == r0 + v + 1) {
-                        if (valid) P.logw_prefix[(int64_t)pf * P.Ntot + p] = lp.log_value();
-                        ++pf;
-                        next_k = (pf < P.nprefix) ? P.prefix[pf] : -1;
-                    }
-                } else {
-                    y[v] = 0.0f;
+                for (int v = 0; v < TC_N; ++v) s[v] = 0.0f;
+            }
+            if (sm.abort) break;
+            if (t == 0) {
+                // next super-block: its first group of stages reads only y of earlier
+                // super-blocks; no more than that group, whose MMAs write TMEM buffer g_all % 2,
+                // so the other buffer stays free for the parked shifts below
+                if (rb + 1 < nsb && rb > 0) {
+                    tc_far_begin(pp, Ybuf, bt.Lt, rb + 1, min(4 * rb, TC_G));
+                    tc_pump(sm, pp);
+                }
+                if (!tc::mbar_wait(&sm.dbar, (dphase - 1) & 1u, TC_WAIT_BUDGET)) {
+                    sm.abort = 1;
+                    dev_raise(bt.status, MVN_ERR_TIMEOUT, 0);
                 }
             }
-            // y of this block -> operand buffer of the later blocks (bulk-copied back by the
-            // async proxy: fence before the barrier that precedes the next loads)
-            if (r0 + TC_B < n) {
-                tc_write_y(Ybuf, rb, t, y);
-                tc::fence_proxy_async_global();
-            }
             __syncthreads();
+            if (sm.abort) break;
+            // second half of the far shifts parked in TMEM (cols 0..63 of the buffer that the
+            // prefetched stages, all in group g_all, do not write) while the first sub-block runs
+            const uint32_t park = sm.tmem + lane_base + tc_buf_col(g_all + 1u);
+            {
+                float h[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) h[i] = s[TC_B + i];
+                tc::tmem_st32(park, h);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) h[i] = s[TC_B + 32 + i];
+                tc::tmem_st32(park + 32, h);
+            }
+            float y[TC_B];
+#pragma unroll 1
+            for (int sb = 0; sb < 2; ++sb) {
+                const int db = d0 + TC_B * sb;
+                const int nb = min(TC_B, n - db);
+                if (nb <= 0) break;
+                const float* Dt = sm.D + sb * TC_TRI;
+                if (sb == 1) {
+                    float h[32];
+                    tc::tmem_ld32(park, h);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) s[i] = h[i];
+                    tc::tmem_ld32(park + 32, h);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) s[32 + i] = h[i];
+                    // near block: s_v += sum_u L(db + v, d0 + u) y_u
+                    const float4* Dn = reinterpret_cast<const float4*>(sm.D + 2 * TC_TRI);
+#pragma unroll
+                    for (int u = 0; u < TC_B; ++u) {
+                        const float yu = y[u];
+#pragma unroll
+                        for (int v4 = 0; v4 < TC_B / 4; ++v4) {
+                            const float4 d = Dn[u * (TC_B / 4) + v4];
+                            s[4 * v4 + 0] = fmaf(d.x, yu, s[4 * v4 + 0]);
+                            s[4 * v4 + 1] = fmaf(d.y, yu, s[4 * v4 + 1]);
+                            s[4 * v4 + 2] = fmaf(d.z, yu, s[4 * v4 + 2]);
+                            s[4 * v4 + 3] = fmaf(d.w, yu, s[4 * v4 + 3]);
+                        }
+                    }
+                }
+                const int o = TC_B * sb;  // offset of the sub-block in the super-block arrays
+#pragma unroll
+                for (int v = 0; v < TC_B; ++v) {
+                    if (v < nb) {
+                        float w, wc, dh, dl;
+                        uint64_t wm;
+                        int dex;
+                        lattice_wf(j, sm.alpha[o + v], dq[db + v], w, wc, wm);
+                        y[v] = sov_step_f32p(sm.af[o + v], sm.bf[o + v], sm.a[o + v], sm.b[o + v],
+                                             sm.ainf[o + v], sm.binf[o + v], s[v], Dt[tri(v, v)],
+                                             w, wc, wm, dh, dl, dex);
+                        lp.mul(dh, dl, dex);
+                        while (next_k == db + v + 1) {
+                            if (valid) P.logw_prefix[(int64_t)pf * P.Ntot + p] = lp.log_value();
+                            ++pf;
+                            next_k = (pf < P.nprefix) ? P.prefix[pf] : -1;
+                        }
+                        // right-looking update of the later dimensions of the sub-block
+#pragma unroll
+                        for (int u = v + 1; u < TC_B; ++u) s[u] = fmaf(Dt[tri(u, v)], y[v], s[u]);
+                    } else {
+                        y[v] = 0.0f;
+                    }
+                }
+                // y of this sub-block -> operand buffer of the later super-blocks (read back by
+                // the async proxy: fence before the barrier that precedes those loads)
+                if (db + TC_B < n) {
+                    tc_write_y(Ybuf, db / TC_KS, t, y);
+                    tc::fence_proxy_async_global();
+                }
+            }
+            tc::tc_fence_before();
+            __syncthreads();
+            tc::tc_fence_after();
         }
         if (valid && P.logw) P.logw[p] = lp.log_value();
         __syncthreads();
     }
-    tc_quiesce(sm, pp);
+    tc_quiesce(sm, pp, dphase);
     tc_teardown(sm);
 }
 
@@ -401,18 +557,53 @@ __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
 static size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 
 static int tc_grid(mvn_ctx* ctx, int64_t ntiles) {
-    // two CTAs per SM (shared memory ~106 KB, 256 TMEM columns each)
+    // two CTAs per SM (shared memory ~103 KB, 256 TMEM columns each)
     return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 2 * (int64_t)ctx->sm_count));
 }
 
+static int tc_nsb(int n) { return (std::max(n, 1) + TC_N - 1) / TC_N; }
+
+static size_t tc_factor_bytes(int nsb) {
+    return ws_round(tc_lt_off(nsb, 0)) + ws_round(sizeof(int) * (size_t)nsb * TC_N) +
+           ws_round(sizeof(unsigned long long) * (size_t)nsb * TC_N) +
+           ws_round(sizeof(float) * (size_t)nsb * TC_N) +
+           ws_round(sizeof(float) * (size_t)nsb * TC_DPACK);
+}
+
 size_t sov_tc_ws_bytes(mvn_ctx* ctx, int nprob, int nmax, int64_t ntiles) {
-    const int nrb = (std::max(nmax, 1) + TC_B - 1) / TC_B;
+    const int nsb = tc_nsb(nmax);
     size_t b = ws_round(sizeof(int));
     if (nprob > 1)
         b += ws_round(sizeof(SovProblem) * nprob) + ws_round(sizeof(int2) * (size_t)ntiles);
-    b += ws_round((size_t)2 * nrb * nrb * TC_LT_BYTES);
-    b += ws_round((size_t)tc_grid(ctx, ntiles) * nrb * 2 * TC_YT_BYTES);
+    b += tc_factor_bytes(nsb);
+    b += ws_round((size_t)tc_grid(ctx, ntiles) * nsb * 4 * 2 * TC_TILE);
     return b;
+}
+
+// Operand copies of the factor: split tiles, row scales and packed diagonal blocks.
+static mvn_status tc_prepare_factor(mvn_ctx* ctx, int n, const double* L, int64_t ld, int nsb,
+                                    WsCarver& wc, uint8_t*& Lt, float*& escale, float*& Dpack) {
+    Lt = wc.take<uint8_t>(tc_lt_off(nsb, 0));
+    int* eL = wc.take<int>((size_t)nsb * TC_N);
+    unsigned long long* rowmax = wc.take<unsigned long long>((size_t)nsb * TC_N);
+    escale = wc.take<float>((size_t)nsb * TC_N);
+    Dpack = wc.take<float>((size_t)nsb * TC_DPACK);
+    const int rows = nsb * TC_N;
+    MVN_CUDA(ctx, cudaMemsetAsync(rowmax, 0, sizeof(unsigned long long) * rows, ctx->stream));
+    if (n > 0) {
+        k_row_max<<<dim3(nsb, (n + TC_RM_COLS - 1) / TC_RM_COLS), TC_N, 0, ctx->stream>>>(
+            n, L, ld, rowmax);
+        MVN_LAUNCHED(ctx);
+    }
+    k_row_exp<<<(rows + 127) / 128, 128, 0, ctx->stream>>>(rows, rowmax, eL, escale);
+    MVN_LAUNCHED(ctx);
+    if (nsb > 1) {
+        k_split_L<<<dim3(4 * (nsb - 1), nsb), 128, 0, ctx->stream>>>(n, L, ld, eL, Lt);
+        MVN_LAUNCHED(ctx);
+    }
+    k_pack_D<<<nsb, 256, 0, ctx->stream>>>(n, L, ld, Dpack);
+    MVN_LAUNCHED(ctx);
+    return MVN_OK;
 }
 
 // All problems of a batch share one factor L (the batched problems use its leading blocks).
@@ -425,7 +616,7 @@ mvn_status sov_run_tc(mvn_ctx* ctx, const std::vector<SovProblem>& probs_h, char
         if (P.n > 0) ntiles += (P.Ntot + TC_P - 1) / TC_P;
     }
     if (ntiles == 0) return MVN_OK;
-    const int nrb = (nmax + TC_B - 1) / TC_B;
+    const int nsb = tc_nsb(nmax);
     const int grid = tc_grid(ctx, ntiles);
     WsCarver wc(ws);
     TcBatch bt;
@@ -455,20 +646,19 @@ mvn_status sov_run_tc(mvn_ctx* ctx, const std::vector<SovProblem>& probs_h, char
         bt.probs = d_probs;
         bt.items = d_items;
     }
-    __half* Lt = wc.take<__half>((size_t)2 * nrb * nrb * TC_LT_BYTES / 2);
-    bt.Lt = reinterpret_cast<const uint8_t*>(Lt);
-    bt.nrb = nrb;
-    bt.ystride = (int64_t)nrb * 2 * TC_YT_BYTES;
-    bt.Yscratch = wc.take<uint8_t>((size_t)grid * bt.ystride);
-    bt.status = ctx->d_status;
-    // split the shared factor into FP16 operand tiles (lower tiles only)
     const SovProblem& P0 = probs_h[0];
     for (auto& P : probs_h)
         if (P.L != P0.L || P.ld != P0.ld)
             return mvn_fail(ctx, MVN_ERR_ARG, "tensor-core batch needs one shared factor");
-    const int64_t ltiles = (int64_t)nrb * (nrb + 1) / 2;
-    k_split_L<<<(unsigned)ltiles, 256, 0, ctx->stream>>>(nmax, P0.L, P0.ld, nrb, Lt);
-    MVN_LAUNCHED(ctx);
+    uint8_t* Lt;
+    float *escale, *Dpack;
+    MVN_TRY(tc_prepare_factor(ctx, nmax, P0.L, P0.ld, nsb, wc, Lt, escale, Dpack));
+    bt.Lt = Lt;
+    bt.escale = escale;
+    bt.Dpack = Dpack;
+    bt.ystride = (int64_t)nsb * 4 * 2 * TC_TILE;
+    bt.Yscratch = wc.take<uint8_t>((size_t)grid * bt.ystride);
+    bt.status = ctx->d_status;
     MVN_CUDA(ctx, cudaMemsetAsync(bt.counter, 0, sizeof(int), ctx->stream));
     const size_t smem = tc_smem_bytes();
     MVN_CUDA(ctx, cudaFuncSetAttribute(k_sov_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -479,60 +669,51 @@ mvn_status sov_run_tc(mvn_ctx* ctx, const std::vector<SovProblem>& probs_h, char
 
 // ---------------------------------------------------------------- GEMM self-test
 
-// S (128 x 64, row-major) = Y (128 x K) L (64 x K)^T through exactly the operand split, tile
-// layout, bulk-copy pipeline, descriptors, MMAs and TMEM read of the SOV kernel.
-__global__ void k_tc_selftest_prep(int K, const double* __restrict__ Y,
-                                   const double* __restrict__ Lr, uint8_t* __restrict__ Ybuf,
-                                   __half* __restrict__ Lt, int nrb) {
-    // Y rows: one thread per path; L rows: tiles (rb = kcs, kc) of a factor whose row block kcs
-    // holds the test rows
+// S (128 x 128, row-major) = Y (128 x K) L (128 x K)^T through exactly the operand split, tile
+// layout, bulk-copy pipeline, descriptors, MMAs, TMEM drains and row scaling of the sweep's far
+// GEMM: the test rows form super-block rb = ceil(K / 128) of a factor whose earlier columns are
+// the K test columns.  Y rows are written by one thread per path (as the sweep does).
+__global__ void k_tc_selftest_fill(int K, const double* __restrict__ L, int rb, int nf,
+                                   double* __restrict__ F) {
+    // F(128 rb + r, k) = L(r, k), F column-major with leading dimension nf
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < TC_N * K; e += gridDim.x * blockDim.x) {
+        const int r = e % TC_N, k = e / TC_N;
+        F[(TC_N * rb + r) + (int64_t)k * nf] = L[(int64_t)r * K + k];
+    }
+}
+
+__global__ void k_tc_selftest_prep(int K, const double* __restrict__ Y, uint8_t* __restrict__ Ybuf) {
     const int t = threadIdx.x;
-    for (int kc = 0; kc * TC_B < K; ++kc) {
+    for (int kc2 = 0; kc2 * TC_B < K; ++kc2) {
         float y[TC_B];
 #pragma unroll
         for (int v = 0; v < TC_B; ++v) {
-            const int k = kc * TC_B + v;
+            const int k = kc2 * TC_B + v;
             y[v] = (k < K) ? (float)Y[(int64_t)t * K + k] : 0.0f;
         }
-        tc_write_y(Ybuf, kc, t, y);
+        tc_write_y(Ybuf, 2 * kc2, t, y);
     }
-    const size_t slice = (size_t)nrb * nrb * (TC_LT_BYTES / 2);
-    for (int kc = 0; kc * TC_B < K; ++kc) {
-        const int rbt = (K + TC_B - 1) / TC_B;
-        __half* hi = Lt + ((size_t)kc * nrb + rbt) * (TC_LT_BYTES / 2);
-        __half* lo = hi + slice;
-        for (int e = t; e < 64 * 64; e += blockDim.x) {
-            const int r = e & 63, k = e >> 6;
-            const int kk = kc * TC_B + k;
-            double v = (kk < K) ? Lr[(int64_t)r * K + kk] * 4096.0 : 0.0;
-            __half h = __double2half(v);
-            __half l = __double2half((v - (double)__half2float(h)) * 2048.0);
-            const uint32_t off = tc::sw128_off(r, k) >> 1;
-            hi[off] = h;
-            lo[off] = l;
-        }
-    }
-    __syncthreads();
     tc::fence_proxy_async_global();
 }
 
-__global__ void __launch_bounds__(TC_P, 2) k_tc_selftest(int K, const uint8_t* __restrict__ Ybuf,
-                                                          const uint8_t* __restrict__ Lt, int nrb,
+__global__ void __launch_bounds__(TC_P, 2) k_tc_selftest(int rb, const uint8_t* __restrict__ Ybuf,
+                                                          const uint8_t* __restrict__ Lt,
+                                                          const float* __restrict__ escale,
                                                           float* __restrict__ S, int* status) {
     extern __shared__ uint8_t smem_raw[];
     TcSmem& sm = tc_smem(smem_raw);
     const int t = threadIdx.x;
     tc_setup(sm);
     TcPipe pp;
-    uint64_t g_all = 0;
-    float s[TC_B];
-    const int kcs = (K + TC_B - 1) / TC_B;
-    // row block kcs of a factor whose tiles (kcs, kc) hold the test rows: the block has kcs chunks
-    const bool ok = tc_block_shift(sm, pp, Ybuf, Lt, nrb, kcs, g_all, s);
+    sm.escale[t] = escale[TC_N * rb + t];
+    if (t == 0) tc_far_begin(pp, Ybuf, Lt, rb, 4 * rb);
+    __syncthreads();
+    float s[TC_N];
+    const bool ok = tc_far(sm, pp, rb, 0u, s);
     if (!ok && t == 0) dev_raise(status, MVN_ERR_TIMEOUT, 0);
     if (ok)
-        for (int v = 0; v < TC_B; ++v) S[t * TC_B + v] = s[v];
-    tc_quiesce(sm, pp);
+        for (int v = 0; v < TC_N; ++v) S[t * TC_N + v] = s[v];
+    tc_quiesce(sm, pp, 0);
     tc_teardown(sm);
 }
 
@@ -542,21 +723,30 @@ extern "C" mvn_status mvn_tc_selftest(mvn_ctx* ctx, int K, const double* Y, cons
     if (K < 1 || K > 65536 || !Y || !L || !S)
         return mvn_fail(ctx, MVN_ERR_ARG, "mvn_tc_selftest: invalid argument");
     MVN_CUDA(ctx, cudaSetDevice(ctx->device));
-    const int kcs = (K + TC_B - 1) / TC_B;
-    const int nrb = kcs + 1;
-    const size_t ybytes = (size_t)kcs * 2 * TC_YT_BYTES;
-    const size_t lbytes = (size_t)2 * nrb * nrb * TC_LT_BYTES;
-    MVN_TRY(ws_reserve(ctx, ws_round(ybytes) + ws_round(lbytes) + 1024));
+    // factor of order n = 128 (rb + 1) whose rows 128 rb .. hold the test rows of L in columns
+    // 0 .. K-1 (zero elsewhere); built densely on the device, then split like the sweep's factor
+    const int rb = (K + TC_N - 1) / TC_N;
+    const int nsb = rb + 1;
+    const int nf = TC_N * nsb;
+    const size_t fbytes = sizeof(double) * (size_t)nf * nf;
+    const size_t ybytes = (size_t)nsb * 4 * 2 * TC_TILE;
+    MVN_TRY(ws_reserve(ctx, ws_round(fbytes) + tc_factor_bytes(nsb) + ws_round(ybytes) + 1024));
     WsCarver wc(ctx->ws);
+    double* F = wc.take<double>((size_t)nf * nf);
+    MVN_CUDA(ctx, cudaMemsetAsync(F, 0, fbytes, ctx->stream));
+    k_tc_selftest_fill<<<64, 256, 0, ctx->stream>>>(K, L, rb, nf, F);
+    MVN_LAUNCHED(ctx);
+    uint8_t* Lt;
+    float *escale, *Dpack;
+    MVN_TRY(tc_prepare_factor(ctx, nf, F, nf, nsb, wc, Lt, escale, Dpack));
     uint8_t* Ybuf = wc.take<uint8_t>(ybytes);
-    __half* Lt = wc.take<__half>(lbytes / 2);
-    k_tc_selftest_prep<<<1, TC_P, 0, ctx->stream>>>(K, Y, L, Ybuf, Lt, nrb);
+    MVN_CUDA(ctx, cudaMemsetAsync(Ybuf, 0, ybytes, ctx->stream));
+    k_tc_selftest_prep<<<1, TC_P, 0, ctx->stream>>>(K, Y, Ybuf);
     MVN_LAUNCHED(ctx);
     const size_t smem = tc_smem_bytes();
     MVN_CUDA(ctx, cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-    k_tc_selftest<<<1, TC_P, smem, ctx->stream>>>(K, Ybuf, reinterpret_cast<const uint8_t*>(Lt),
-                                                  nrb, S, ctx->d_status);
+    k_tc_selftest<<<1, TC_P, smem, ctx->stream>>>(rb, Ybuf, Lt, escale, S, ctx->d_status);
     MVN_LAUNCHED(ctx);
     return MVN_OK;
 }

@@ -332,13 +332,13 @@ def mvn_lattice_shifts(seed: int, M: int, n: int) -> torch.Tensor:
 
 
 def mvn_tc_selftest(Y: torch.Tensor, L: torch.Tensor) -> torch.Tensor:
-    """S = Y (128 x K) L (64 x K)^T through the tensor-core path of MVN_MIXED (FP32 result)."""
+    """S = Y (128 x K) L (128 x K)^T through the tensor-core path of MVN_MIXED (FP32 result)."""
     K = Y.shape[1]
-    assert Y.shape == (128, K) and L.shape == (64, K)
-    S = torch.empty((128, 64), dtype=torch.float32, device=Y.device)
+    assert Y.shape == (128, K) and L.shape == (128, K)
+    S = torch.empty((128, 128), dtype=torch.float32, device=Y.device)
     c = context()
     c.check(lib().mvn_tc_selftest(c.h, K, _vec(Y.contiguous(), 128 * K, "Y"),
-                                  _vec(L.contiguous(), 64 * K, "L"), _P(S.data_ptr())))
+                                  _vec(L.contiguous(), 128 * K, "L"), _P(S.data_ptr())))
     return S
 
 

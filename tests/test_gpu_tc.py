@@ -26,17 +26,19 @@ def _t(x):
     return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
 
-@pytest.mark.parametrize("K", [16, 64, 100, 640, 1000])
+@pytest.mark.parametrize("K", [16, 64, 100, 640, 1000, 4100])
 def test_tc_gemm_selftest(mvn, K):
     rng = np.random.default_rng(K)
     Y = rng.standard_normal((128, K)) * 1.5
-    # entries spanning the magnitudes of a Cholesky factor (1 down to 1e-9)
-    L = rng.standard_normal((64, K)) * 10.0 ** rng.uniform(-9, 0, (64, K))
+    # entries spanning the magnitudes of a Cholesky factor (1 down to 1e-9), and rows of very
+    # different scale (the per-row power-of-two scaling keeps the FP16 slices in range)
+    L = rng.standard_normal((128, K)) * 10.0 ** rng.uniform(-9, 0, (128, K))
+    L *= 10.0 ** rng.uniform(-6, 6, (128, 1))
     S = mvn.mvn_tc_selftest(_t(Y), _t(L)).cpu().numpy().astype(np.float64)
     mvn.sync()
     ref = Y @ L.T
     scale = np.abs(Y) @ np.abs(L).T
-    err = np.abs(S - ref) / (scale + 1e-30)
+    err = np.abs(S - ref) / (scale + 1e-300)
     # two FP16 slices per operand and FP32 accumulation: ~2^-21 of the absolute-value product
     assert err.max() < 4e-6, err.max()
 

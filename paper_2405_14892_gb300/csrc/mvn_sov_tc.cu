@@ -6,21 +6,23 @@
 // that comes from all earlier dimensions,
 //   S(paths, d0:d0+128) = Y(paths, 0:d0) L(d0:d0+128, 0:d0)^T,
 // is an M = 128, N = 128, K = d0 GEMM whose operands stream through shared memory with 1-D bulk
-// copies (K = 32 per stage, 2-stage mbarrier ring) and accumulate in tensor memory.  FP32
-// accuracy of the shift is recovered from FP16 operands by two-slice splits,
+// copies (K = 32 per stage, 3-stage mbarrier ring, later stages prefetched into L2) and
+// accumulate in tensor memory.  FP32 accuracy of the shift is recovered from FP16 operands by
+// two-slice splits,
 //   L 2^-e_v = Lh + Ll,  y = Yh + Yl,   S_v = 2^e_v (Yh Lh^T + Yh Ll^T + Yl Lh^T)
 // (the Yl Ll^T term, ~2^-22 relative, dropped), all three products into one TMEM accumulator;
 // e_v is a per-row power of two that keeps row v of L below 2^12 (no FP16 overflow for any
 // scale of Sigma).  The tensor cores accumulate in FP32 with truncation, so the accumulator is
 // drained into FP32 registers every K = 128 (two ping-pong TMEM buffers), which keeps the
-// accumulated error near that of an FP32 sum.  The 128 x 128 diagonal block of the super-block
-// (two 64-dimension triangles and the 64 x 64 block between them) runs on the CUDA cores in FP32
-// (Alg. 3), from a packed copy that one bulk copy brings into shared memory.  Each thread then
-// writes its path's new y values (both slices) to a per-CTA global buffer in the swizzled
-// operand layout, from where later super-blocks stream them back.  Thread 0 also drives the
-// copy/MMA pipeline without blocking: it issues whatever is ready while the other threads wait
-// for the accumulator, and it prefetches the next super-block's first stages before the
-// diagonal work.  Paths are independent: no CTA waits on another.
+// accumulated error near that of an FP32 sum.  Warp 0 drives the copy/MMA pipeline without
+// blocking while the other warps wait for the accumulator.
+// The 128 x 128 diagonal block (Alg. 3) then runs on the CUDA cores in FP32, one dimension at a
+// time in a rolled loop: the far shifts and the new y values sit in tensor memory (one column
+// per dimension, one lane per path), the packed lower triangle of the block is brought into the
+// idle stage area by one bulk copy, and s_v = far_v + sum_{u<v} L_vu y_u is a left-looking dot
+// over y read back 16 columns at a time.  Each thread finally writes its path's y values (both
+// slices) to a per-CTA global buffer in the swizzled operand layout, from where later
+// super-blocks stream them back.  Paths are independent: no CTA waits on another.
 #include <cuda_fp16.h>
 #include <math.h>
 #include <string.h>
@@ -35,15 +37,14 @@
 
 #define TC_P 128            // paths per CTA (MMA M, TMEM lanes)
 #define TC_N 128            // dimensions per super-block (MMA N)
-#define TC_B 64             // dimensions per diagonal sub-block
 #define TC_KS 32            // K per pipeline stage (one 64-byte swizzled row of FP16)
-#define TC_NST 2            // pipeline stages
+#define TC_NST 3            // pipeline stages
+#define TC_PF 6             // stages prefetched into L2 ahead of the shared-memory copy
 #define TC_G 4              // stages per TMEM accumulation group (K = 128), then drained
 #define TC_TILE 8192        // one FP16 slice of a 128-row x 32-column tile (64-byte swizzle)
 #define TC_STAGE (4 * TC_TILE)  // Yh, Yl, Lh, Ll
 #define TC_TMEM_COLS 256    // two accumulation buffers of 128 columns
-#define TC_TRI (TC_B * (TC_B + 1) / 2)
-#define TC_DPACK (2 * TC_TRI + TC_B * TC_B)  // floats of one packed diagonal block
+#define TC_DPACK (TC_N * (TC_N + 1) / 2 + 16)  // floats of one packed diagonal block (+ zero pad)
 #define TC_WAIT_BUDGET 4000000000LL  // cycles (~2 s) before a wait gives up
 
 // Split-factor tile pair (hi, lo) of super-block rb (rows 128 rb ..) and K sub-chunk kc < 4 rb.
@@ -109,9 +110,9 @@ __global__ void __launch_bounds__(128) k_split_L(int n, const double* __restrict
     }
 }
 
-// Packed FP32 diagonal block of super-block rb: [triangle of sub-block 0 | triangle of sub-block
-// 1 | near block N[u][v] = L(d0 + 64 + v, d0 + u)], triangles row-packed (v (v + 1) / 2 + u).
-// Entries outside the factor are zero, diagonal entries beyond n are one.
+// Packed FP32 diagonal block of super-block rb: the lower triangle of L(d0:d0+128, d0:d0+128),
+// row-packed (v (v + 1) / 2 + u), then 16 zeros (the left-looking dot reads up to 15 entries past
+// a row; they meet y values that are still zero).  Rows beyond n: zero, diagonal one.
 __global__ void k_pack_D(int n, const double* __restrict__ L, int64_t ld, float* __restrict__ D) {
     const int rb = blockIdx.x, d0 = TC_N * rb;
     float* out = D + (size_t)rb * TC_DPACK;
@@ -123,21 +124,20 @@ __global__ void k_pack_D(int n, const double* __restrict__ L, int64_t ld, float*
             x = (float)L[(d0 + v) + (int64_t)(d0 + u) * ld];
         else
             x = (u == v) ? 1.0f : 0.0f;
-        if (v < TC_B)
-            out[v * (v + 1) / 2 + u] = x;
-        else if (u >= TC_B)
-            out[TC_TRI + (v - TC_B) * (v - TC_B + 1) / 2 + (u - TC_B)] = x;
-        else
-            out[2 * TC_TRI + u * TC_B + (v - TC_B)] = x;
+        out[v * (v + 1) / 2 + u] = x;
     }
+    if (threadIdx.x < 16) out[TC_N * (TC_N + 1) / 2 + threadIdx.x] = 0.0f;
 }
 
 // ---------------------------------------------------------------- shared memory
 
-// ~103 KB: two CTAs fit on one SM (157 tiles of 20,000 paths are resident at once).
+// ~102 KB: two CTAs fit on one SM (157 tiles of 20,000 paths are resident at once).  The
+// stages (far GEMM) and the packed diagonal block (diagonal work) are never live together.
 struct __align__(1024) TcSmem {
-    uint8_t stage[TC_NST][TC_STAGE];  // [Yh 8K | Yl 8K | Lh 8K | Ll 8K]
-    float D[TC_DPACK];                // packed diagonal block of the super-block
+    union {
+        uint8_t stage[TC_NST][TC_STAGE];  // [Yh 8K | Yl 8K | Lh 8K | Ll 8K]
+        float D[TC_DPACK];                // packed diagonal block of the super-block
+    };
     double a[TC_N], b[TC_N];
     float af[TC_N], bf[TC_N];
     float escale[TC_N];
@@ -150,6 +150,7 @@ struct __align__(1024) TcSmem {
 };
 
 static_assert(sizeof(TcSmem) <= 112 * 1024, "two CTAs per SM need <= 112 KB each");
+static_assert(TC_DPACK * 4 <= TC_NST * TC_STAGE, "the diagonal block lives in the stage area");
 
 // ---------------------------------------------------------------- GEMM pipeline (thread 0)
 //
@@ -167,8 +168,6 @@ struct TcPipe {
     const uint8_t* Ybuf = nullptr;
     const uint8_t* Lsb = nullptr;  // tile pairs of the current super-block
     int kcs = 0;           // stages of the current far GEMM
-    int kready = 0;        // stages whose Y tiles are written (loads beyond wait)
-    int rb = -1;           // super-block of the current far GEMM (-1: none begun in this item)
     int next_load = 0, next_mma = 0;
 };
 
@@ -179,7 +178,7 @@ __device__ void tc_pump(TcSmem& sm, TcPipe& pp) {
     const uint32_t idesc = tc::idesc_f16_f32(TC_P, TC_N);
     for (;;) {
         bool progress = false;
-        if (pp.next_load < pp.kready && pp.next_load < pp.next_mma + TC_NST) {
+        if (pp.next_load < pp.kcs && pp.next_load < pp.next_mma + TC_NST) {
             const uint32_t q = pp.q_load;
             const int slot = (int)(q % TC_NST);
             if (q < TC_NST || tc::mbar_test_wait(&sm.empty[slot], ((q / TC_NST) - 1) & 1u)) {
@@ -189,6 +188,13 @@ __device__ void tc_pump(TcSmem& sm, TcPipe& pp) {
                 tc::bulk_g2s(st, pp.Ybuf + (size_t)kc * 2 * TC_TILE, 2 * TC_TILE, &sm.full[slot]);
                 tc::bulk_g2s(st + 2 * TC_TILE, pp.Lsb + (size_t)kc * 2 * TC_TILE, 2 * TC_TILE,
                              &sm.full[slot]);
+                // the stage TC_PF ahead into L2, so that its copy into shared memory does not
+                // wait for HBM (only two stages fit in shared memory)
+                const int kp = kc + TC_PF;
+                if (kp < pp.kcs) {
+                    tc::bulk_prefetch_l2(pp.Ybuf + (size_t)kp * 2 * TC_TILE, 2 * TC_TILE);
+                    tc::bulk_prefetch_l2(pp.Lsb + (size_t)kp * 2 * TC_TILE, 2 * TC_TILE);
+                }
                 ++pp.q_load;
                 ++pp.next_load;
                 progress = true;
@@ -226,19 +232,20 @@ __device__ void tc_pump(TcSmem& sm, TcPipe& pp) {
     }
 }
 
-// Set up the far GEMM of super-block rb (K = 128 rb) after the previous one has been drained;
-// `ready` = stages whose Y tiles are already written (all of them unless this is a prefetch
-// made before the previous super-block's diagonal work).
+// Set up the far GEMM of super-block rb (K = 128 rb) after the previous one has been drained
+// (every Y tile it reads is written), and start its first stages on their way into L2.
 __device__ __forceinline__ void tc_far_begin(TcPipe& pp, const uint8_t* Ybuf, const uint8_t* Lt,
-                                             int rb, int ready) {
+                                             int rb) {
     pp.g0 = pp.drained;
     pp.Ybuf = Ybuf;
     pp.Lsb = Lt + tc_lt_off(rb, 0);
     pp.kcs = 4 * rb;
-    pp.kready = ready;
-    pp.rb = rb;
     pp.next_load = 0;
     pp.next_mma = 0;
+    for (int kp = 0; kp < min(pp.kcs, TC_PF); ++kp) {
+        tc::bulk_prefetch_l2(pp.Ybuf + (size_t)kp * 2 * TC_TILE, 2 * TC_TILE);
+        tc::bulk_prefetch_l2(pp.Lsb + (size_t)kp * 2 * TC_TILE, 2 * TC_TILE);
+    }
 }
 
 // Far part of the limit shift of this thread's path for super-block rb (K = 128 rb): the groups
@@ -255,13 +262,22 @@ __device__ bool tc_far(TcSmem& sm, TcPipe& pp, int rb, uint32_t g0, float (&s)[T
     for (int gi = 0; gi < ng; ++gi) {
         const uint32_t g = g0 + (uint32_t)gi;
         const uint32_t par = (g >> 1) & 1u;
-        if (t == 0) {
-            pp.kready = pp.kcs;  // every Y tile of this far GEMM is written by now
+        if (t < 32) {
+            // warp 0 polls as a whole (a waiting lane must not hold back lane 0, which keeps
+            // the pipeline moving); the other warps wait on the barrier
             const long long t0 = clock64();
             for (;;) {
-                tc_pump(sm, pp);
-                if (tc::mbar_test_wait(&sm.accf[g & 1u], par)) break;
-                if (clock64() - t0 > TC_WAIT_BUDGET) {
+                int state = 0;  // lane 0 decides for the warp: 1 done, 2 timed out
+                if (t == 0) {
+                    tc_pump(sm, pp);
+                    if (tc::mbar_test_wait(&sm.accf[g & 1u], par))
+                        state = 1;
+                    else if (clock64() - t0 > TC_WAIT_BUDGET)
+                        state = 2;
+                }
+                state = __shfl_sync(0xffffffffu, state, 0);
+                if (state == 1) break;
+                if (state == 2) {
                     ok = false;
                     sm.abort = 1;
                     break;
@@ -296,27 +312,24 @@ __device__ bool tc_far(TcSmem& sm, TcPipe& pp, int rb, uint32_t g0, float (&s)[T
     return ok;
 }
 
-// Write this thread's 64 new y values (two FP16 slices) as row `t` of the Y tiles of sub-chunks
-// kc and kc + 1.
-__device__ __forceinline__ void tc_write_y(uint8_t* __restrict__ Ybuf, int kc, int t,
-                                           const float (&y)[TC_B]) {
+// Write 32 y values of this thread's path (two FP16 slices) as row `t` of the Y tiles of
+// sub-chunk kc.
+__device__ __forceinline__ void tc_write_y32(uint8_t* __restrict__ Ybuf, int kc, int t,
+                                             const float (&y)[32]) {
+    uint8_t* hi = Ybuf + (size_t)kc * 2 * TC_TILE;
+    uint8_t* lo = hi + TC_TILE;
 #pragma unroll
-    for (int h2 = 0; h2 < 2; ++h2) {
-        uint8_t* hi = Ybuf + (size_t)(kc + h2) * 2 * TC_TILE;
-        uint8_t* lo = hi + TC_TILE;
+    for (int c = 0; c < 4; ++c) {
+        __align__(16) __half h[8], l[8];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            __align__(16) __half h[8], l[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const float v = y[32 * h2 + 8 * c + e];
-                h[e] = __float2half_rn(v);
-                l[e] = __float2half_rn(v - __half2float(h[e]));
-            }
-            const uint32_t off = tc::sw64_off((uint32_t)t, (uint32_t)(8 * c));
-            *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<const uint4*>(h);
-            *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<const uint4*>(l);
+        for (int e = 0; e < 8; ++e) {
+            const float v = y[8 * c + e];
+            h[e] = __float2half_rn(v);
+            l[e] = __float2half_rn(v - __half2float(h[e]));
         }
+        const uint32_t off = tc::sw64_off((uint32_t)t, (uint32_t)(8 * c));
+        *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<const uint4*>(h);
+        *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<const uint4*>(l);
     }
 }
 
@@ -415,20 +428,10 @@ __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
         int pf = 0;
         int next_k = (P.nprefix > 0) ? P.prefix[0] : -1;
         const int nsb = (n + TC_N - 1) / TC_N;
-        if (t == 0) pp.rb = -1;
 
         for (int rb = 0; rb < nsb; ++rb) {
             const int d0 = rb * TC_N;
             const int nb2 = min(TC_N, n - d0);
-            // packed diagonal block of this super-block (shared memory is free: the previous
-            // super-block's diagonal work ended at a barrier)
-            if (t == 0) {
-                tc::fence_proxy_async_smem();
-                tc::mbar_arrive_expect_tx(&sm.dbar, TC_DPACK * 4);
-                tc::bulk_g2s(sm.D, bt.Dpack + (size_t)rb * TC_DPACK, TC_DPACK * 4, &sm.dbar);
-                if (rb > 0 && pp.rb != rb) tc_far_begin(pp, Ybuf, bt.Lt, rb, 4 * rb);
-            }
-            ++dphase;
             if (t < TC_N) {
                 const int v = d0 + t;
                 const double av = (t < nb2) ? P.a[v] : 0.0;
@@ -442,105 +445,91 @@ __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
                 sm.alpha[t] = (t < nb2) ? alpha[v] : 0u;
                 sm.escale[t] = bt.escale[v];
             }
+            if (t == 0 && rb > 0) tc_far_begin(pp, Ybuf, bt.Lt, rb);
             __syncthreads();
-            float s[TC_N];
-            if (rb > 0) {
-                if (!tc_far(sm, pp, rb, g_all, s) && t == 0)
-                    dev_raise(bt.status, MVN_ERR_TIMEOUT, 0);
-                g_all += (uint32_t)((4 * rb + TC_G - 1) / TC_G);
-            } else {
-#pragma unroll
-                for (int v = 0; v < TC_N; ++v) s[v] = 0.0f;
-            }
-            if (sm.abort) break;
-            if (t == 0) {
-                // next super-block: its first group of stages reads only y of earlier
-                // super-blocks; no more than that group, whose MMAs write TMEM buffer g_all % 2,
-                // so the other buffer stays free for the parked shifts below
-                if (rb + 1 < nsb && rb > 0) {
-                    tc_far_begin(pp, Ybuf, bt.Lt, rb + 1, min(4 * rb, TC_G));
-                    tc_pump(sm, pp);
-                }
-                if (!tc::mbar_wait(&sm.dbar, (dphase - 1) & 1u, TC_WAIT_BUDGET)) {
-                    sm.abort = 1;
-                    dev_raise(bt.status, MVN_ERR_TIMEOUT, 0);
-                }
-            }
-            __syncthreads();
-            if (sm.abort) break;
-            // second half of the far shifts parked in TMEM (cols 0..63 of the buffer that the
-            // prefetched stages, all in group g_all, do not write) while the first sub-block runs
-            const uint32_t park = sm.tmem + lane_base + tc_buf_col(g_all + 1u);
+            // far part of the shifts (Alg. 2 step (c) over all earlier super-blocks) -> TMEM
+            // buffer 1; buffer 0 holds this super-block's y, zero until written
+            const uint32_t sbuf = sm.tmem + lane_base + TC_N, ybuf = sm.tmem + lane_base;
             {
-                float h[32];
+                float s[TC_N];
+                if (rb > 0) {
+                    if (!tc_far(sm, pp, rb, g_all, s) && t == 0)
+                        dev_raise(bt.status, MVN_ERR_TIMEOUT, 0);
+                    g_all += (uint32_t)((4 * rb + TC_G - 1) / TC_G);
+                } else {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) h[i] = s[TC_B + i];
-                tc::tmem_st32(park, h);
+                    for (int v = 0; v < TC_N; ++v) s[v] = 0.0f;
+                }
+                if (sm.abort) break;
+                // packed diagonal block into the (now idle) stage area
+                if (t == 0) {
+                    tc::fence_proxy_async_smem();
+                    tc::mbar_arrive_expect_tx(&sm.dbar, TC_DPACK * 4);
+                    tc::bulk_g2s(sm.D, bt.Dpack + (size_t)rb * TC_DPACK, TC_DPACK * 4, &sm.dbar);
+                }
+                ++dphase;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) h[i] = s[TC_B + 32 + i];
-                tc::tmem_st32(park + 32, h);
-            }
-            float y[TC_B];
-#pragma unroll 1
-            for (int sb = 0; sb < 2; ++sb) {
-                const int db = d0 + TC_B * sb;
-                const int nb = min(TC_B, n - db);
-                if (nb <= 0) break;
-                const float* Dt = sm.D + sb * TC_TRI;
-                if (sb == 1) {
+                for (int c = 0; c < TC_N; c += 32) {
                     float h[32];
-                    tc::tmem_ld32(park, h);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) s[i] = h[i];
-                    tc::tmem_ld32(park + 32, h);
+                    for (int i = 0; i < 32; ++i) h[i] = s[c + i];
+                    tc::tmem_st32(sbuf + c, h);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) s[32 + i] = h[i];
-                    // near block: s_v += sum_u L(db + v, d0 + u) y_u
-                    const float4* Dn = reinterpret_cast<const float4*>(sm.D + 2 * TC_TRI);
-#pragma unroll
-                    for (int u = 0; u < TC_B; ++u) {
-                        const float yu = y[u];
-#pragma unroll
-                        for (int v4 = 0; v4 < TC_B / 4; ++v4) {
-                            const float4 d = Dn[u * (TC_B / 4) + v4];
-                            s[4 * v4 + 0] = fmaf(d.x, yu, s[4 * v4 + 0]);
-                            s[4 * v4 + 1] = fmaf(d.y, yu, s[4 * v4 + 1]);
-                            s[4 * v4 + 2] = fmaf(d.z, yu, s[4 * v4 + 2]);
-                            s[4 * v4 + 3] = fmaf(d.w, yu, s[4 * v4 + 3]);
-                        }
-                    }
-                }
-                const int o = TC_B * sb;  // offset of the sub-block in the super-block arrays
-#pragma unroll
-                for (int v = 0; v < TC_B; ++v) {
-                    if (v < nb) {
-                        float w, wc, dh, dl;
-                        uint64_t wm;
-                        int dex;
-                        lattice_wf(j, sm.alpha[o + v], dq[db + v], w, wc, wm);
-                        y[v] = sov_step_f32p(sm.af[o + v], sm.bf[o + v], sm.a[o + v], sm.b[o + v],
-                                             sm.ainf[o + v], sm.binf[o + v], s[v], Dt[tri(v, v)],
-                                             w, wc, wm, dh, dl, dex);
-                        lp.mul(dh, dl, dex);
-                        while (next_k == db + v + 1) {
-                            if (valid) P.logw_prefix[(int64_t)pf * P.Ntot + p] = lp.log_value();
-                            ++pf;
-                            next_k = (pf < P.nprefix) ? P.prefix[pf] : -1;
-                        }
-                        // right-looking update of the later dimensions of the sub-block
-#pragma unroll
-                        for (int u = v + 1; u < TC_B; ++u) s[u] = fmaf(Dt[tri(u, v)], y[v], s[u]);
-                    } else {
-                        y[v] = 0.0f;
-                    }
-                }
-                // y of this sub-block -> operand buffer of the later super-blocks (read back by
-                // the async proxy: fence before the barrier that precedes those loads)
-                if (db + TC_B < n) {
-                    tc_write_y(Ybuf, db / TC_KS, t, y);
-                    tc::fence_proxy_async_global();
+                    for (int i = 0; i < 32; ++i) h[i] = 0.0f;
+                    tc::tmem_st32(ybuf + c, h);
                 }
             }
+            if (t == 0 && !tc::mbar_wait(&sm.dbar, (dphase - 1) & 1u, TC_WAIT_BUDGET)) {
+                sm.abort = 1;
+                dev_raise(bt.status, MVN_ERR_TIMEOUT, 0);
+            }
+            __syncthreads();
+            if (sm.abort) break;
+            // diagonal block (Alg. 3), one dimension at a time: s_v = far_v + sum_{u<v} L_vu y_u
+            // (left-looking, y from TMEM 16 at a time), then the elementwise step of Eq. 2
+#pragma unroll 1
+            for (int v = 0; v < nb2; ++v) {
+                const float* Dr = sm.D + v * (v + 1) / 2;
+                float a0 = tc::tmem_ld1(sbuf + v), a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+#pragma unroll 1
+                for (int u0 = 0; u0 < v; u0 += 16) {
+                    float yy[16];
+                    tc::tmem_ld16(ybuf + u0, yy);  // entries u >= v are still zero
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4) {
+                        a0 = fmaf(Dr[u0 + i], yy[i], a0);
+                        a1 = fmaf(Dr[u0 + i + 1], yy[i + 1], a1);
+                        a2 = fmaf(Dr[u0 + i + 2], yy[i + 2], a2);
+                        a3 = fmaf(Dr[u0 + i + 3], yy[i + 3], a3);
+                    }
+                }
+                const float sv = (a0 + a1) + (a2 + a3);
+                float w, wc, dh, dl;
+                uint64_t wm;
+                int dex;
+                lattice_wf(j, sm.alpha[v], dq[d0 + v], w, wc, wm);
+                const float y = sov_step_f32p(sm.af[v], sm.bf[v], sm.a[v], sm.b[v], sm.ainf[v],
+                                              sm.binf[v], sv, Dr[v], w, wc, wm, dh, dl, dex);
+                lp.mul(dh, dl, dex);
+                while (next_k == d0 + v + 1) {
+                    if (valid) P.logw_prefix[(int64_t)pf * P.Ntot + p] = lp.log_value();
+                    ++pf;
+                    next_k = (pf < P.nprefix) ? P.prefix[pf] : -1;
+                }
+                tc::tmem_st1(ybuf + v, y);
+            }
+            // y of this super-block -> operand buffer of the later super-blocks (read back by
+            // the async proxy: fence before the barrier that precedes those loads)
+            if (d0 + TC_N < n) {
+#pragma unroll 1
+                for (int c = 0; c < TC_N; c += 32) {
+                    float yy[32];
+                    tc::tmem_ld32(ybuf + c, yy);
+                    tc_write_y32(Ybuf, (d0 + c) / TC_KS, t, yy);
+                }
+                tc::fence_proxy_async_global();
+            }
+            tc::fence_proxy_async_smem();  // the stage area is rewritten by bulk copies next
             tc::tc_fence_before();
             __syncthreads();
             tc::tc_fence_after();
@@ -684,14 +673,14 @@ __global__ void k_tc_selftest_fill(int K, const double* __restrict__ L, int rb, 
 
 __global__ void k_tc_selftest_prep(int K, const double* __restrict__ Y, uint8_t* __restrict__ Ybuf) {
     const int t = threadIdx.x;
-    for (int kc2 = 0; kc2 * TC_B < K; ++kc2) {
-        float y[TC_B];
+    for (int kc = 0; kc * TC_KS < K; ++kc) {
+        float y[32];
 #pragma unroll
-        for (int v = 0; v < TC_B; ++v) {
-            const int k = kc2 * TC_B + v;
+        for (int v = 0; v < 32; ++v) {
+            const int k = kc * TC_KS + v;
             y[v] = (k < K) ? (float)Y[(int64_t)t * K + k] : 0.0f;
         }
-        tc_write_y(Ybuf, 2 * kc2, t, y);
+        tc_write_y32(Ybuf, kc, t, y);
     }
     tc::fence_proxy_async_global();
 }
@@ -706,7 +695,7 @@ __global__ void __launch_bounds__(TC_P, 2) k_tc_selftest(int rb, const uint8_t* 
     tc_setup(sm);
     TcPipe pp;
     sm.escale[t] = escale[TC_N * rb + t];
-    if (t == 0) tc_far_begin(pp, Ybuf, Lt, rb, 4 * rb);
+    if (t == 0) tc_far_begin(pp, Ybuf, Lt, rb);
     __syncthreads();
     float s[TC_N];
     const bool ok = tc_far(sm, pp, rb, 0u, s);

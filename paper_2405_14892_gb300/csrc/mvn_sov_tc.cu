@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
             if (t == 0 && rb > 0) tc_far_begin(pp, Ybuf, bt.Lt, rb);
             __syncthreads();
             // far part of the shifts (Alg. 2 step (c) over all earlier super-blocks) -> TMEM
-            // buffer 1; buffer 0 holds this super-block's y, zero until written
+            // buffer 1; buffer 0 receives this super-block's y
             const uint32_t sbuf = sm.tmem + lane_base + TC_N, ybuf = sm.tmem + lane_base;
             {
                 float s[TC_N];
@@ -474,9 +474,7 @@ __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
 #pragma unroll
                     for (int i = 0; i < 32; ++i) h[i] = s[c + i];
                     tc::tmem_st32(sbuf + c, h);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) h[i] = 0.0f;
-                    tc::tmem_st32(ybuf + c, h);
+
                 }
             }
             if (t == 0 && !tc::mbar_wait(&sm.dbar, (dphase - 1) & 1u, TC_WAIT_BUDGET)) {
@@ -485,38 +483,61 @@ __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
             }
             __syncthreads();
             if (sm.abort) break;
-            // diagonal block (Alg. 3), one dimension at a time: s_v = far_v + sum_{u<v} L_vu y_u
-            // (left-looking, y from TMEM 16 at a time), then the elementwise step of Eq. 2
+            // diagonal block (Alg. 3) in blocks of 16 dimensions.  For block c the shifts of its
+            // dimensions start as q_i = far_i + sum_{u < 16c} L(16c + i, u) y_u (a 16 x 16c
+            // mat-vec over the earlier y, read back from TMEM 16 at a time); inside the block the
+            // dimensions go one at a time, q being a queue whose head is the current dimension:
+            // after the elementwise step of Eq. 2 gives y_v, the later dimensions of the block
+            // get L(v + p, v) y_v added (right-looking) and the queue shifts by one.  One copy
+            // of the step code serves every dimension.
 #pragma unroll 1
-            for (int v = 0; v < nb2; ++v) {
-                const float* Dr = sm.D + v * (v + 1) / 2;
-                float a0 = tc::tmem_ld1(sbuf + v), a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+            for (int c0 = 0; c0 < nb2; c0 += 16) {
+                float q[16];
+                tc::tmem_ld16(sbuf + c0, q);
 #pragma unroll 1
-                for (int u0 = 0; u0 < v; u0 += 16) {
+                for (int u0 = 0; u0 < c0; u0 += 16) {
                     float yy[16];
-                    tc::tmem_ld16(ybuf + u0, yy);  // entries u >= v are still zero
+                    tc::tmem_ld16(ybuf + u0, yy);
 #pragma unroll
-                    for (int i = 0; i < 16; i += 4) {
-                        a0 = fmaf(Dr[u0 + i], yy[i], a0);
-                        a1 = fmaf(Dr[u0 + i + 1], yy[i + 1], a1);
-                        a2 = fmaf(Dr[u0 + i + 2], yy[i + 2], a2);
-                        a3 = fmaf(Dr[u0 + i + 3], yy[i + 3], a3);
+                    for (int i = 0; i < 16; ++i) {
+                        const float* Dr = sm.D + tri(c0 + i, u0);
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) q[i] = fmaf(Dr[k], yy[k], q[i]);
                     }
                 }
-                const float sv = (a0 + a1) + (a2 + a3);
-                float w, wc, dh, dl;
-                uint64_t wm;
-                int dex;
-                lattice_wf(j, sm.alpha[v], dq[d0 + v], w, wc, wm);
-                const float y = sov_step_f32p(sm.af[v], sm.bf[v], sm.a[v], sm.b[v], sm.ainf[v],
-                                              sm.binf[v], sv, Dr[v], w, wc, wm, dh, dl, dex);
-                lp.mul(dh, dl, dex);
-                while (next_k == d0 + v + 1) {
-                    if (valid) P.logw_prefix[(int64_t)pf * P.Ntot + p] = lp.log_value();
-                    ++pf;
-                    next_k = (pf < P.nprefix) ? P.prefix[pf] : -1;
+                float y16[16];
+#pragma unroll 1
+                for (int i = 0; i < 16; ++i) {
+                    const int v = c0 + i;
+                    float y = 0.0f;
+                    if (v < nb2) {
+                        float w, wc, dh, dl;
+                        uint64_t wm;
+                        int dex;
+                        lattice_wf(j, sm.alpha[v], dq[d0 + v], w, wc, wm);
+                        y = sov_step_f32p(sm.af[v], sm.bf[v], sm.a[v], sm.b[v], sm.ainf[v],
+                                          sm.binf[v], q[0], sm.D[tri(v, v)], w, wc, wm, dh, dl,
+                                          dex);
+                        lp.mul(dh, dl, dex);
+                        while (next_k == d0 + v + 1) {
+                            if (valid) P.logw_prefix[(int64_t)pf * P.Ntot + p] = lp.log_value();
+                            ++pf;
+                            next_k = (pf < P.nprefix) ? P.prefix[pf] : -1;
+                        }
+                    }
+                    // later dimensions of the block, then shift the queues
+#pragma unroll
+                    for (int pp2 = 1; pp2 < 16; ++pp2)
+                        if (pp2 < 16 - i) q[pp2] = fmaf(sm.D[tri(v + pp2, v)], y, q[pp2]);
+#pragma unroll
+                    for (int k = 0; k < 15; ++k) {
+                        q[k] = q[k + 1];
+                        y16[k] = y16[k + 1];
+                    }
+                    q[15] = 0.0f;
+                    y16[15] = y;
                 }
-                tc::tmem_st1(ybuf + v, y);
+                tc::tmem_st16(ybuf + c0, y16);
             }
             // y of this super-block -> operand buffer of the later super-blocks (read back by
             // the async proxy: fence before the barrier that precedes those loads)

@@ -146,11 +146,11 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- rooflines
 
 # kernels whose launches the library brackets with CUDA events when timing is on
-TIMED_KERNELS = ("k_oz_update", "k_oz_potrf", "k_oz_trsm", "k_oz_split", "k_sov_tc", "k_syrk",
+TIMED_KERNELS = ("k_oz_update", "k_oz_potrf", "k_oz_trsm", "k_sov_tc", "k_syrk",
                  "k_sov_simt_f64", "k_sov_simt_f32")
 
 
-def kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src):
+def kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src, steps):
     """Achieved rate of the main kernels of the step: algorithmic work per launch (stated per
     kernel) over the kernel's average launch duration, measured by the library's CUDA events on
     the launching stream during the timed region."""
@@ -165,7 +165,6 @@ def kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src):
     ms, cnt = kt.get("k_oz_update", (0.0, 0))
     if cnt:
         nbc = (n + 63) // 64
-        steps = max(1, cnt // max(1, nbc - 1))
         mac = sum((n - 64 * j) * 64 * 64 * j for j in range(1, nbc))
         fl = 2.0 * 21 * mac * steps
         out.append({"kernel": "k_oz_update", "bound": "tensor", "unit": "TFLOP/s",
@@ -176,15 +175,17 @@ def kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src):
                     "work": "21 BF16 MMA products per FP64 product of the left-looking update"})
     ms, cnt = kt.get("k_sov_tc", (0.0, 0))
     if cnt:
-        nb = (n + 63) // 64
-        mac = tiles * 128 * 64 * 64 * (nb * (nb - 1) // 2)
+        # far limit-update GEMM on the tensor cores: super-block R (128 dimensions) takes
+        # K = 128 R for every 128-path tile (the 128 x 128 diagonal blocks run on the CUDA cores)
+        nsb = (n + 127) // 128
+        mac = tiles * 128 * 128 * 128 * (nsb * (nsb - 1) // 2)
         fl = 2.0 * 3 * mac * cnt
         out.append({"kernel": "k_sov_tc", "bound": "tensor", "unit": "TFLOP/s",
                     "achieved": fl / (ms * 1e-3) / 1e12, "peak": tens_peak,
                     "frac": fl / (ms * 1e-3) / 1e12 / tens_peak, "traffic": None,
                     "launches": cnt, "total_ms": ms, "peak_source": tens_src,
-                    "work": "3 FP16 MMAs per K step of the limit GEMM (two-slice split), "
-                            "128-path tiles x 64-dim blocks"})
+                    "work": "3 FP16 MMAs per multiply-add of the far limit-update GEMM "
+                            "(two-slice split), 128-path tiles x 128-dimension super-blocks"})
     for name in ("k_syrk", "k_sov_simt_f64", "k_sov_simt_f32"):
         ms, cnt = kt.get(name, (0.0, 0))
         if not cnt:
@@ -327,7 +328,7 @@ def run_gpu(args):
     sov_ms = statistics.median(phase["sov"])
     chol_ms = statistics.median(phase["cholesky"])
     value = world * n * Ntot / (ms * 1e-3)
-    rooflines = kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src)
+    rooflines = kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src, args.steps)
     dominant = max(rooflines, key=lambda r: r["total_ms"]) if rooflines else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -83,7 +83,7 @@ mvn_status mvn_sync(mvn_ctx* ctx, int* info);
 /* Number of kernels this context has launched since creation (host counter). */
 int64_t mvn_launch_count(const mvn_ctx* ctx);
 /* Per-kernel timing: with enable != 0, CUDA events are recorded on the context's stream around
- * every launch of the main kernels (k_oz_update, k_oz_potrf, k_oz_trsm, k_oz_split, k_syrk,
+ * every launch of the main kernels (k_oz_update, k_oz_potrf, k_oz_trsm, k_syrk,
  * k_sov_tc, k_sov_simt_f64, k_sov_simt_f32); the call waits for the stream and clears earlier
  * records. */
 mvn_status mvn_timing(mvn_ctx* ctx, int enable);

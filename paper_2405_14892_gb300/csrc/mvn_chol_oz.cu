@@ -37,11 +37,14 @@
 #define OZ_AT 8192          // one digit tile: 128 rows x 32 K, BF16, 64-byte swizzle
 #define OZ_BT 4096          // 64 rows of such a tile (the B operand)
 #define OZ_STAGE (OZ_S * (OZ_AT + OZ_BT))
-#define OZ_NST 3            // pipeline stages (K = 32 each)
+#define OZ_NST 2            // pipeline stages (K = 32 each; 145 KB, so that the panel kernels
+                            // fit beside an update CTA on one SM)
 #define OZ_GRP 8            // stages accumulated in TMEM between drains (K = 256)
 #define OZ_DW 8             // drain warps
 #define OZ_THREADS (32 * (OZ_DW + 2))
 #define OZ_WAIT 4000000000LL
+#define OZ_BULK_P 16        // K sub-chunks per work item of the bulk update (short CTAs: the
+                            // chain kernels get SMs as they retire)
 
 __device__ __forceinline__ bool oz_failed(const int* status) {
     return *(volatile const int*)status != 0;
@@ -78,46 +81,60 @@ __global__ void k_oz_exps(int n, const double* __restrict__ A, int64_t ld, int* 
     E[i] = e;
 }
 
-// Digits of the finished block column j (columns c0 .. c0+63, rows >= c0) into the digit tiles of
-// sub-chunks 2j and 2j+1.  One CTA of 256 threads per row tile rt >= c0/128; thread = (row, half),
-// each writing whole 64-byte tile rows.  x = L_ik 2^-E_i is rounded once to 42-bit fixed point
-// v = rint(x 2^42) and the balanced digits are peeled off with integer shifts:
-// d = (v + 2^(k-1)) >> k, v -= d 2^k.  Entries above the diagonal, and rows or columns >= n, are 0.
-__global__ void __launch_bounds__(256) k_oz_split(int n, const double* __restrict__ A, int64_t ld,
-                                                  const int* __restrict__ E, int j, int nrt,
-                                                  uint8_t* __restrict__ Z) {
-    const int c0 = j * OZ_NB;
-    const int rt = c0 / OZ_RT + blockIdx.x;
-    const int r = threadIdx.x & (OZ_RT - 1), kh = threadIdx.x >> 7;
-    const int i = rt * OZ_RT + r;
-    const int ei = (i < n) ? E[i] : 0;
-    const int kc = 2 * j + kh;
-#pragma unroll 1
-    for (int c8 = 0; c8 < 4; ++c8) {
-        uint32_t pk[OZ_S][4];
+// rint(x 2^sh) as a 64-bit integer from the bits of an FP32 value (integer ALU only; GB300's
+// FP64 pipe is narrow).  Requires |x 2^sh| < 2^62; ties round away from zero.
+__device__ __forceinline__ long long oz_f2fix(float x, int sh) {
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 255u);
+    if (e == 0) return 0;  // zero (FP32 subnormals lie far below 2^-42 of any row here)
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);  // x = m 2^(e - 150)
+    const int s2 = e - 150 + sh;
+    long long v;
+    if (s2 >= 0)
+        v = m << s2;
+    else if (s2 < -25)
+        v = 0;
+    else
+        v = (m + (1ll << (-s2 - 1))) >> (-s2);
+    return (b >> 31) ? -v : v;
+}
+
+// Digits of 8 consecutive entries x = hi + lo (double-float) of row i of the finished factor
+// (one 16-byte chunk of a 64-byte swizzled tile row per digit): v = rint(hi 2^(42 - E_i)) +
+// rint(lo 2^(42 - E_i)) (the value in 42-bit fixed point, to one unit), then balanced 7-bit digits
+// peeled off with integer shifts: d = (v + 2^(k-1)) >> k, v -= d 2^k.  Zero entries (above the
+// diagonal, beyond n) give zero digits.
+__device__ __forceinline__ void oz_digits8(const float (&xh)[8], const float (&xl)[8], int ei,
+                                           uint4 (&out)[OZ_S]) {
+    uint32_t pk[OZ_S][4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int col = c0 + 32 * kh + 8 * c8 + e;
-            long long v = 0;
-            if (i < n && col < n && col <= i) v = llrint(ldexp(A[i + (int64_t)col * ld], 42 - ei));
+    for (int e = 0; e < 8; ++e) {
+        long long v = oz_f2fix(xh[e], 42 - ei) + oz_f2fix(xl[e], 42 - ei);
 #pragma unroll
-            for (int s = 0; s < OZ_S; ++s) {
-                const int sh = 7 * (OZ_S - 1 - s);
-                const long long d = (sh > 0) ? ((v + (1ll << (sh - 1))) >> sh) : v;
-                v -= d * (1ll << sh);
-                const uint32_t b = (uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn((int)d));
-                if (e & 1)
-                    pk[s][e >> 1] |= b << 16;
-                else
-                    pk[s][e >> 1] = b;
-            }
+        for (int s = 0; s < OZ_S; ++s) {
+            const int sh = 7 * (OZ_S - 1 - s);
+            const long long d = (sh > 0) ? ((v + (1ll << (sh - 1))) >> sh) : v;
+            v -= d * (1ll << sh);
+            const uint32_t b = (uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn((int)d));
+            if (e & 1)
+                pk[s][e >> 1] |= b << 16;
+            else
+                pk[s][e >> 1] = b;
         }
-        const uint32_t off = tc::sw64_off((uint32_t)r, (uint32_t)(8 * c8));
-#pragma unroll
-        for (int s = 0; s < OZ_S; ++s)
-            *reinterpret_cast<uint4*>(Z + oz_tile(kc, s, rt, nrt) + off) =
-                make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
     }
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) out[s] = make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
+}
+
+// Store the digits of row r (global row index), columns c0 + 8 c8 .. of block column j (c0 =
+// 64 j) into the digit tiles of sub-chunk 2 j + c8 / 4.
+__device__ __forceinline__ void oz_store_digits(uint8_t* __restrict__ Z, int nrt, int j, int r,
+                                                int c8, const uint4 (&dg)[OZ_S]) {
+    const int rt = r / OZ_RT, rr = r % OZ_RT;
+    const int kc = 2 * j + (c8 >> 2);
+    const uint32_t off = tc::sw64_off((uint32_t)rr, (uint32_t)(8 * (c8 & 3)));
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) *reinterpret_cast<uint4*>(Z + oz_tile(kc, s, rt, nrt) + off) = dg[s];
 }
 
 struct __align__(1024) OzSmem {
@@ -319,19 +336,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(const OzWork w,
     }
 }
 
-// C(i, c) - 2^(E_i + E_c - 49) T(i, c): the block column after its update (FP64).
-__device__ __forceinline__ double oz_apply(const double* __restrict__ A, int64_t ld,
-                                           long long* __restrict__ T, int64_t ldT, int i, int c0,
-                                           int c, int ei, int ec) {
-    long long* tp = T + i + (int64_t)c * ldT;
-    const long long tv = *tp;
-    double a = A[i + (int64_t)(c0 + c) * ld];
-    if (tv != 0) {
-        a -= (double)tv * oz_pow2(ei + ec - 49);
-        *tp = 0;
-    }
-    return a;
-}
 
 // Double-float (FP32 pair) arithmetic: x = hi + lo with |lo| <= ulp(hi) / 2 (Dekker 1971;
 // Knuth's two-sum).  GB300 runs FP32 at 64 times its FP64 rate and FP64 division and square root
@@ -385,97 +389,230 @@ __device__ __forceinline__ DF df_rcp(DF l) {
 }
 
 // POTRF of the diagonal block (c0, c0), nb <= 64, after applying the update, and the inverse
-// W = L_jj^-1 for the panel solve.  One CTA of 256 threads (a 16 x 16 grid), double-float in
-// shared memory.  The inverse rides along the right-looking sweep: once column k of L is final,
-// row k of W is scaled by 1 / L_kk and removed from the rows below (the forward substitution
-// L W = I column-oriented), so both share the three barriers of each step.  W (lower
-// triangular) is kept transposed in the strict upper triangle of the tile, its diagonal in rinv.
-// Writes L_jj to A (FP64) and W^T as pairs Wt[u][c] = W[c][u].
+// W = L_jj^-1 for the panel solve (double-float).  256 threads as a 16 x 16 grid; thread (ty, tx)
+// with tx <= ty keeps the 4 x 4 blocks (rows 4 ty .., columns 4 tx ..) of S (becoming L) and of W
+// in registers.  Step k of the right-looking sweep: the owner of S(k, k) publishes 1 / L_kk; the
+// owners of column k of L and of row k of W scale them and publish them; every thread updates its
+// entries S(i, m) -= L(i, k) L(m, k) (k < m <= i) and W(i, c) -= L(i, k) W(k, c) (c <= k < i).
+// (W = L^-1 is the column-oriented forward substitution L W = I riding along the same sweep.)
+// Rows and columns beyond nb are the identity, so the padded factor stays regular.  Writes L_jj
+// to A (FP64), W^T as pairs Wt[u][c] = W[c][u], and the digits of the diagonal rows.
+__device__ __forceinline__ DF df_sel4(const DF (&x)[4], int b) {
+    DF v = x[0];
+    if (b == 1) v = x[1];
+    if (b == 2) v = x[2];
+    if (b == 3) v = x[3];
+    return v;
+}
+
 __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_t ld, int c0,
                                                   int nb, const int* __restrict__ E,
                                                   long long* __restrict__ T, int64_t ldT,
-                                                  float* __restrict__ Wt, int* status) {
-    __shared__ float Sh[OZ_NB][OZ_NB + 1], Sl[OZ_NB][OZ_NB + 1];
+                                                  float* __restrict__ Wt, uint8_t* __restrict__ Z,
+                                                  int nrt, int* status) {
+    __shared__ DF colk[2][OZ_NB], rowk[2][OZ_NB];  // L(:, k) and W(k, :), by step parity
+    __shared__ DF piv;                         // 1 / L_kk
+    __shared__ float Sh[OZ_NB][OZ_NB + 1], Sl[OZ_NB][OZ_NB + 1];  // staging (load, store, digits)
     __shared__ DF rinv[OZ_NB];
+    __shared__ int Eb[OZ_NB];
     __shared__ int bad;
     if (oz_failed(status)) return;
     const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+    const bool act = (tx <= ty);
     if (t == 0) bad = 0;
-    for (int m = ty; m < OZ_NB; m += 16)
-        for (int i = tx; i < OZ_NB; i += 16) {
+    if (t < OZ_NB) Eb[t] = (t < nb) ? E[c0 + t] : 0;
+    if (t < 2 * OZ_NB) {
+        // finite contents from the start: masked updates multiply stale entries by zero
+        colk[t >> 6][t & 63] = DF{0.0f, 0.0f};
+        rowk[t >> 6][t & 63] = DF{0.0f, 0.0f};
+    }
+    __syncthreads();
+    {
+        // all loads first (16 per thread, independent), then the update is applied
+        double av[16];
+        long long tv[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int e = t + 256 * k, i = e % OZ_NB, m = e / OZ_NB;
+            const bool in = (i < nb && m <= i);
+            av[k] = in ? A[(c0 + i) + (int64_t)(c0 + m) * ld] : 0.0;
+            tv[k] = in ? T[(c0 + i) + (int64_t)m * ldT] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int e = t + 256 * k, i = e % OZ_NB, m = e / OZ_NB;
             DF v{0.0f, 0.0f};
-            if (i < nb && m <= i)
-                v = df_from(oz_apply(A, ld, T, ldT, c0 + i, c0, m, E[c0 + i], E[c0 + m]));
-            else if (i == m)
-                v = DF{1.0f, 0.0f};  // identity beyond nb: the padded factor stays regular
+            if (i < nb && m <= i) {
+                double a = av[k];
+                if (tv[k] != 0) {
+                    a -= (double)tv[k] * oz_pow2(Eb[i] + Eb[m] - 49);
+                    T[(c0 + i) + (int64_t)m * ldT] = 0;
+                }
+                v = df_from(a);
+            } else if (i == m) {
+                v = DF{1.0f, 0.0f};
+            }
             Sh[i][m] = v.hi;
             Sl[i][m] = v.lo;
         }
+    }
     __syncthreads();
+    DF Lr[4][4], Wr[4][4];  // this thread's blocks of S/L and of W
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = 4 * ty + a, m = 4 * tx + b;
+            Lr[a][b] = (act && m <= i) ? DF{Sh[i][m], Sl[i][m]} : DF{0.0f, 0.0f};
+            Wr[a][b] = (act && i == m) ? DF{1.0f, 0.0f} : DF{0.0f, 0.0f};
+        }
     for (int k = 0; k < OZ_NB; ++k) {
-        if (t == 0) {
-            const DF d{Sh[k][k], Sl[k][k]};
+        const int kb = k >> 2, kk = k & 3;
+        // pivot
+        if (act && ty == kb && tx == kb) {
+            DF d = DF{0.0f, 0.0f};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                if (a == kk) d = df_sel4(Lr[a], kk);
             if (!(d.hi > 0.0f)) {
                 dev_raise(status, MVN_ERR_NOT_PD, c0 + k + 1);
                 bad = 1;
             } else {
                 const DF l = df_sqrt(d);
-                Sh[k][k] = l.hi;
-                Sl[k][k] = l.lo;
-                rinv[k] = df_rcp(l);
+                const DF r = df_rcp(l);
+                piv = r;
+                rinv[k] = r;
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+                    if (a == kk) {
+#pragma unroll
+                        for (int b = 0; b < 4; ++b)
+                            if (b == kk) Lr[a][b] = l;
+                    }
             }
         }
         __syncthreads();
         if (bad) return;
-        const DF r = rinv[k];
-        // column k of L below the diagonal; row k of W left of the diagonal (at S[c][k])
-        if (t < OZ_NB) {
-            if (t > k) {
-                const DF v = df_mul(DF{Sh[t][k], Sl[t][k]}, r);
-                Sh[t][k] = v.hi;
-                Sl[t][k] = v.lo;
-            } else if (t < k) {
-                const DF v = df_mul(DF{Sh[t][k], Sl[t][k]}, r);
-                Sh[t][k] = v.hi;
-                Sl[t][k] = v.lo;
+        const DF r = piv;
+        DF* colp = colk[k & 1];
+        DF* rowp = rowk[k & 1];
+        // column k of L (rows > k) and row k of W (columns <= k), scaled by 1 / L_kk
+        if (act && tx == kb) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int i = 4 * ty + a;
+                if (i > k) {
+                    DF v = DF{0.0f, 0.0f};
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        if (b == kk) v = df_mul(Lr[a][b], r);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        if (b == kk) Lr[a][b] = v;
+                    colp[i] = v;
+                }
             }
         }
-        __syncthreads();
-        for (int i = k + 1 + ty; i < OZ_NB; i += 16) {
-            const DF li{-Sh[i][k], -Sl[i][k]};
-            // L(i, m) -= L(i, k) L(m, k), k < m <= i
-            for (int m = k + 1 + tx; m <= i; m += 16) {
-                DF s{Sh[i][m], Sl[i][m]};
-                df_fma_acc(s, li, DF{Sh[m][k], Sl[m][k]});
-                const DF v = df_norm(s.hi, s.lo);
-                Sh[i][m] = v.hi;
-                Sl[i][m] = v.lo;
-            }
-            // W(i, c) -= L(i, k) W(k, c), c <= k, with W(i, c) at S[c][i] and W(k, k) = rinv[k]
-            for (int c = tx; c <= k; c += 16) {
-                DF s{Sh[c][i], Sl[c][i]};
-                const DF wkc = (c == k) ? r : DF{Sh[c][k], Sl[c][k]};
-                df_fma_acc(s, li, wkc);
-                const DF v = df_norm(s.hi, s.lo);
-                Sh[c][i] = v.hi;
-                Sl[c][i] = v.lo;
-            }
+        if (act && ty == kb) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                if (a == kk) {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int c = 4 * tx + b;
+                        if (c <= k) {
+                            const DF v = df_mul(Wr[a][b], r);
+                            Wr[a][b] = v;
+                            rowp[c] = v;
+                        }
+                    }
+                }
         }
         __syncthreads();
+        if (act) {
+            DF li[4], lm[4], wk[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) li[a] = colp[4 * ty + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                lm[b] = colp[4 * tx + b];
+                wk[b] = rowp[4 * tx + b];
+            }
+            // branch-free: masked entries take an exact zero multiplier, so all 32 double-float
+            // updates are independent and interleave
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int i = 4 * ty + a;
+                const bool row = (i > k);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int m = 4 * tx + b;
+                    const bool fl = row && (m > k) && (m <= i);
+                    const bool fw = row && (m <= k);
+                    const DF nlL{fl ? -li[a].hi : 0.0f, fl ? -li[a].lo : 0.0f};
+                    const DF nlW{fw ? -li[a].hi : 0.0f, fw ? -li[a].lo : 0.0f};
+                    df_fma_acc(Lr[a][b], nlL, lm[b]);
+                    df_fma_acc(Wr[a][b], nlW, wk[b]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    Lr[a][b] = df_norm(Lr[a][b].hi, Lr[a][b].lo);
+                    Wr[a][b] = df_norm(Wr[a][b].hi, Wr[a][b].lo);
+                }
+        }
+        // the other parity's column and row are rewritten next step; this step's are not
+        // touched again until every thread has passed the next step's barriers
     }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int i = 4 * ty + a, m = 4 * tx + b;
+                if (m <= i) {
+                    Sh[i][m] = Lr[a][b].hi;
+                    Sl[i][m] = Lr[a][b].lo;
+                }
+                // W(i, m) for m <= i  ->  Wt[m][i]
+                Wt[m * OZ_NB + i] = (m <= i) ? Wr[a][b].hi : 0.0f;
+                Wt[OZ_NB * OZ_NB + m * OZ_NB + i] = (m <= i) ? Wr[a][b].lo : 0.0f;
+            }
+    } else {
+        // upper blocks of W^T are zero
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int i = 4 * ty + a, m = 4 * tx + b;
+                Wt[m * OZ_NB + i] = 0.0f;
+                Wt[OZ_NB * OZ_NB + m * OZ_NB + i] = 0.0f;
+            }
+    }
+    __syncthreads();
     for (int m = ty; m < nb; m += 16)
         for (int i = m + tx; i < nb; i += 16)
             A[(c0 + i) + (int64_t)(c0 + m) * ld] = df_to(DF{Sh[i][m], Sl[i][m]});
-    // Wt[u][c] = W[c][u]: S[u][c] for c > u, rinv[c] for c == u, 0 for c < u
-    for (int e = t; e < OZ_NB * OZ_NB; e += 256) {
-        const int cc = e % OZ_NB, u = e / OZ_NB;
-        DF v{0.0f, 0.0f};
-        if (cc == u)
-            v = rinv[cc];
-        else if (cc > u)
-            v = DF{Sh[u][cc], Sl[u][cc]};
-        Wt[u * OZ_NB + cc] = v.hi;
-        Wt[OZ_NB * OZ_NB + u * OZ_NB + cc] = v.lo;
+    // digits of the diagonal rows (and zero digits for the rows of the row tile above them)
+    if (Z != nullptr) {
+        for (int e = t; e < 2 * OZ_NB * 8; e += 256) {
+            const int c8 = e & 7, i = (e >> 3) - ((c0 % OZ_RT) ? OZ_NB : 0);
+            if (i >= OZ_NB) continue;
+            float xh[8], xl[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int m = 8 * c8 + q;
+                const bool in = (i >= 0 && i < nb && m <= i);
+                xh[q] = in ? Sh[i][m] : 0.0f;
+                xl[q] = in ? Sl[i][m] : 0.0f;
+            }
+            uint4 dg[OZ_S];
+            oz_digits8(xh, xl, (i >= 0) ? Eb[i] : 0, dg);
+            oz_store_digits(Z, nrt, c0 / OZ_NB, c0 + i, c8, dg);
+        }
     }
 }
 
@@ -486,7 +623,9 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
 __global__ void __launch_bounds__(256) k_oz_trsm(double* __restrict__ A, int64_t ld, int c0,
                                                  int nb, int n, const int* __restrict__ E,
                                                  long long* __restrict__ T, int64_t ldT,
-                                                 const float* __restrict__ Wt, const int* status) {
+                                                 const float* __restrict__ Wt,
+                                                 uint8_t* __restrict__ Z, int nrt,
+                                                 const int* status) {
     extern __shared__ float4 tr_raw[];  // Bh, Bl [NB][ROWS], Wh, Wl [NB][NB] (64 KB)
     float(*Bh)[OZ_TR_ROWS] = reinterpret_cast<float(*)[OZ_TR_ROWS]>(tr_raw);
     float(*Bl)[OZ_TR_ROWS] = Bh + OZ_NB;
@@ -502,13 +641,35 @@ __global__ void __launch_bounds__(256) k_oz_trsm(double* __restrict__ A, int64_t
         Wl[e / OZ_NB][e % OZ_NB] = Wt[OZ_NB * OZ_NB + e];
     }
     __syncthreads();
-    for (int e = t; e < OZ_NB * OZ_TR_ROWS; e += 256) {
-        const int rr = e % OZ_TR_ROWS, u = e / OZ_TR_ROWS;  // consecutive threads: consecutive rows
-        const int r = r0 + rr;
-        DF v{0.0f, 0.0f};
-        if (r < n && u < nb) v = df_from(oz_apply(A, ld, T, ldT, r, c0, u, E[r], Ec[u]));
-        Bh[u][rr] = v.hi;
-        Bl[u][rr] = v.lo;
+    {
+        // all loads first (16 per thread, independent), then the update is applied
+        constexpr int PER = OZ_NB * OZ_TR_ROWS / 256;
+        double av[PER];
+        long long tv[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = t + 256 * k, rr = e % OZ_TR_ROWS, u = e / OZ_TR_ROWS;
+            const int r = r0 + rr;
+            const bool in = (r < n && u < nb);
+            av[k] = in ? A[r + (int64_t)(c0 + u) * ld] : 0.0;
+            tv[k] = in ? T[r + (int64_t)u * ldT] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = t + 256 * k, rr = e % OZ_TR_ROWS, u = e / OZ_TR_ROWS;
+            const int r = r0 + rr;
+            DF v{0.0f, 0.0f};
+            if (r < n && u < nb) {
+                double a = av[k];
+                if (tv[k] != 0) {
+                    a -= (double)tv[k] * oz_pow2(E[r] + Ec[u] - 49);
+                    T[r + (int64_t)u * ldT] = 0;
+                }
+                v = df_from(a);
+            }
+            Bh[u][rr] = v.hi;
+            Bl[u][rr] = v.lo;
+        }
     }
     __syncthreads();
     const int ty = t >> 4, tx = t & 15;  // rows 4 ty .. 4 ty + 3, columns 4 tx .. 4 tx + 3
@@ -531,14 +692,38 @@ __global__ void __launch_bounds__(256) k_oz_trsm(double* __restrict__ A, int64_t
 #pragma unroll
             for (int b = 0; b < 4; ++b) df_fma_acc(acc[a][b], bv[a], wv[b]);
     }
+    __syncthreads();  // the staging area below reuses the operand tiles
+    float(*Xh)[OZ_NB + 1] = reinterpret_cast<float(*)[OZ_NB + 1]>(tr_raw);
+    float(*Xl)[OZ_NB + 1] = Xh + OZ_TR_ROWS;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int r = r0 + 4 * ty + a;
-        if (r >= n) continue;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int cc = 4 * tx + b;
-            if (cc < nb) A[r + (int64_t)(c0 + cc) * ld] = df_to(df_norm(acc[a][b].hi, acc[a][b].lo));
+            DF x{0.0f, 0.0f};
+            if (r < n && cc < nb) {
+                x = df_norm(acc[a][b].hi, acc[a][b].lo);
+                A[r + (int64_t)(c0 + cc) * ld] = df_to(x);
+            }
+            Xh[4 * ty + a][cc] = x.hi;
+            Xl[4 * ty + a][cc] = x.lo;
+        }
+    }
+    // digits of these rows for the later updates (whole 16-byte chunks per thread)
+    if (Z != nullptr) {
+        __syncthreads();
+        for (int e = t; e < OZ_TR_ROWS * 8; e += 256) {
+            const int rr = e >> 3, c8 = e & 7, r = r0 + rr;
+            float xh[8], xl[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                xh[q] = Xh[rr][8 * c8 + q];
+                xl[q] = Xl[rr][8 * c8 + q];
+            }
+            uint4 dg[OZ_S];
+            oz_digits8(xh, xl, (r < n) ? E[r] : 0, dg);
+            oz_store_digits(Z, nrt, c0 / OZ_NB, r, c8, dg);
         }
     }
 }
@@ -549,71 +734,107 @@ static int oz_nrt(int n) { return (n + OZ_RT - 1) / OZ_RT; }
 static int oz_nbc(int n) { return (n + OZ_NB - 1) / OZ_NB; }
 
 static size_t oz_trsm_smem() { return sizeof(float) * 2 * OZ_NB * (OZ_TR_ROWS + OZ_NB); }
+static_assert(sizeof(float) * 2 * OZ_TR_ROWS * (OZ_NB + 1) <= sizeof(float) * 2 * OZ_NB * (OZ_TR_ROWS + OZ_NB),
+              "the digit staging fits the operand tiles");
 
 size_t chol_oz_ws_bytes(int n) {
     const int nrt = oz_nrt(n), nbc = oz_nbc(n);
     return ws_round(sizeof(int) * (size_t)n) +
            ws_round((size_t)2 * nbc * OZ_S * nrt * OZ_AT) +
-           ws_round(sizeof(long long) * (size_t)OZ_NB * nrt * OZ_RT) +
+           ws_round(sizeof(long long) * 2 * (size_t)OZ_NB * nrt * OZ_RT) +
            ws_round(sizeof(float) * 2 * OZ_NB * OZ_NB);
 }
 
+// Update of block column j from the block columns [c_lo, c_hi) (K sub-chunks [2 c_lo, 2 c_hi)),
+// cut into work items of P sub-chunks, one CTA per item.
+static mvn_status oz_update_launch(mvn_ctx* ctx, cudaStream_t st, int n, int nrt, int j, int c_lo,
+                                   int c_hi, int P, const uint8_t* Z, const int* E,
+                                   long long* Tj, int64_t ldT, size_t ssm) {
+    OzWork w;
+    w.n = n;
+    w.j = j;
+    w.nrt = nrt;
+    w.rt0 = (j * OZ_NB) / OZ_RT;
+    w.n_rt = nrt - w.rt0;
+    w.kc0 = 2 * c_lo;
+    w.kc1 = 2 * c_hi;
+    w.ldT = ldT;
+    w.P = P;
+    w.n_items = w.n_rt * ((w.kc1 - w.kc0 + P - 1) / P);
+    MVN_TIMED_ON(ctx, st, "k_oz_update",
+                 (k_oz_update<<<w.n_items, OZ_THREADS, ssm, st>>>(w, Z, E, Tj, ctx->d_status)));
+    return MVN_OK;
+}
+
+// Left-looking factorisation over 64-wide block columns.  The update of block column j is the
+// bulk (block columns 0 .. j-2) plus the tail (block column j-1).  The bulk of column j+1 needs
+// only digits that exist once column j-1 is split, so it runs on a low-priority stream while the
+// high-priority stream does the tail, POTRF, TRSM and split of column j (the chain every later
+// column waits for); the two update sums of a column go into one of two integer accumulators
+// (column parity).  The update kernel is launched one CTA per work item, so that the chain's
+// kernels get SMs as the bulk's CTAs retire.  Both streams fork from and join the caller's stream.
 mvn_status chol_oz_launch(mvn_ctx* ctx, int n, double* A, int64_t ld, char* ws) {
     const int nrt = oz_nrt(n), nbc = oz_nbc(n);
     const int64_t ldT = (int64_t)nrt * OZ_RT;
     WsCarver wc(ws);
     int* E = wc.take<int>((size_t)n);
     uint8_t* Z = wc.take<uint8_t>((size_t)2 * nbc * OZ_S * nrt * OZ_AT);
-    long long* T = wc.take<long long>((size_t)OZ_NB * ldT);
+    long long* T = wc.take<long long>((size_t)2 * OZ_NB * ldT);
     float* Wt = wc.take<float>((size_t)2 * OZ_NB * OZ_NB);
-    MVN_CUDA(ctx, cudaMemsetAsync(T, 0, sizeof(long long) * (size_t)OZ_NB * ldT, ctx->stream));
-    k_oz_exps<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, A, ld, E);
-    MVN_LAUNCHED(ctx);
+    MVN_TRY(ctx_aux(ctx));
+    cudaStream_t hi = ctx->aux[0], lo = ctx->aux[1];
+    cudaEvent_t ev_fork = ctx->aux_ev[0], ev_split = ctx->aux_ev[1];
+    cudaEvent_t ev_bulk[2] = {ctx->aux_ev[2], ctx->aux_ev[3]};
+    cudaEvent_t ev_join = ctx->aux_ev[4];
     const size_t ssm = oz_smem();
     MVN_CUDA(ctx, cudaFuncSetAttribute(k_oz_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)ssm));
     const size_t tsm = oz_trsm_smem();
     MVN_CUDA(ctx, cudaFuncSetAttribute(k_oz_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tsm));
+    MVN_CUDA(ctx, cudaEventRecord(ev_fork, ctx->stream));
+    MVN_CUDA(ctx, cudaStreamWaitEvent(hi, ev_fork, 0));
+    MVN_CUDA(ctx, cudaMemsetAsync(T, 0, sizeof(long long) * 2 * (size_t)OZ_NB * ldT, hi));
+    k_oz_exps<<<(n + 255) / 256, 256, 0, hi>>>(n, A, ld, E);
+    MVN_LAUNCHED(ctx);
+    bool lo_used = false;
     for (int j = 0; j < nbc; ++j) {
         const int c0 = j * OZ_NB;
         const int nb = std::min(OZ_NB, n - c0);
-        const int rt0 = c0 / OZ_RT;
-        if (j > 0) {
-            OzWork w;
-            w.n = n;
-            w.j = j;
-            w.nrt = nrt;
-            w.rt0 = rt0;
-            w.n_rt = nrt - rt0;
-            w.kc0 = 0;
-            w.kc1 = 2 * j;
-            w.ldT = ldT;
-            // pieces of whole drain groups, about four work items per SM
-            const int64_t stages = (int64_t)w.n_rt * w.kc1;
-            int64_t P = (stages + 4ll * ctx->sm_count - 1) / (4ll * ctx->sm_count);
-            P = ((P + OZ_GRP - 1) / OZ_GRP) * OZ_GRP;
-            w.P = (int)std::max<int64_t>(OZ_GRP, std::min<int64_t>(P, w.kc1));
-            const int npieces = (w.kc1 + w.P - 1) / w.P;
-            w.n_items = w.n_rt * npieces;
-            const int grid = std::min(w.n_items, ctx->sm_count);
-            MVN_TIMED(ctx, "k_oz_update",
-                      (k_oz_update<<<grid, OZ_THREADS, ssm, ctx->stream>>>(w, Z, E, T,
-                                                                           ctx->d_status)));
+        long long* Tj = T + (size_t)(j & 1) * OZ_NB * ldT;
+        // bulk of column j+1 (block columns 0 .. j-1): split(j-1) is the last digit write it reads
+        if (j >= 1 && j + 1 < nbc) {
+            MVN_CUDA(ctx, cudaStreamWaitEvent(lo, ev_split, 0));
+            long long* Tn = T + (size_t)((j + 1) & 1) * OZ_NB * ldT;
+            MVN_TRY(oz_update_launch(ctx, lo, n, nrt, j + 1, 0, j, OZ_BULK_P, Z, E, Tn, ldT, ssm));
+            MVN_CUDA(ctx, cudaEventRecord(ev_bulk[(j + 1) & 1], lo));
+            lo_used = true;
         }
-        MVN_TIMED(ctx, "k_oz_potrf",
-                  (k_oz_potrf<<<1, 256, 0, ctx->stream>>>(A, ld, c0, nb, E, T, ldT, Wt,
-                                                          ctx->d_status)));
-        const int rows = n - c0 - nb;
+        if (j >= 1) {
+            // tail of column j (block column j-1), then wait for its bulk
+            MVN_TRY(oz_update_launch(ctx, hi, n, nrt, j, j - 1, j, 2, Z, E, Tj, ldT, ssm));
+            if (j >= 2) MVN_CUDA(ctx, cudaStreamWaitEvent(hi, ev_bulk[j & 1], 0));
+        }
+        // the digits of block column j are written by POTRF (diagonal rows) and TRSM (the rows
+        // below, up to the end of the last row tile) when a later column needs them
+        uint8_t* Zj = (j + 1 < nbc) ? Z : nullptr;
+        MVN_TIMED_ON(ctx, hi, "k_oz_potrf",
+                     (k_oz_potrf<<<1, 256, 0, hi>>>(A, ld, c0, nb, E, Tj, ldT, Wt, Zj, nrt,
+                                                    ctx->d_status)));
+        const int rows = (Zj != nullptr) ? nrt * OZ_RT - c0 - nb : n - c0 - nb;
         if (rows > 0) {
-            MVN_TIMED(ctx, "k_oz_trsm",
-                      (k_oz_trsm<<<(rows + OZ_TR_ROWS - 1) / OZ_TR_ROWS, 256, tsm, ctx->stream>>>(
-                          A, ld, c0, nb, n, E, T, ldT, Wt, ctx->d_status)));
+            MVN_TIMED_ON(ctx, hi, "k_oz_trsm",
+                         (k_oz_trsm<<<(rows + OZ_TR_ROWS - 1) / OZ_TR_ROWS, 256, tsm, hi>>>(
+                             A, ld, c0, nb, n, E, Tj, ldT, Wt, Zj, nrt, ctx->d_status)));
         }
-        if (j + 1 < nbc) {
-            MVN_TIMED(ctx, "k_oz_split",
-                      (k_oz_split<<<nrt - rt0, 256, 0, ctx->stream>>>(n, A, ld, E, j, nrt, Z)));
-        }
+        if (j + 1 < nbc) MVN_CUDA(ctx, cudaEventRecord(ev_split, hi));
+    }
+    // join both streams back into the caller's stream
+    MVN_CUDA(ctx, cudaEventRecord(ev_join, hi));
+    MVN_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ev_join, 0));
+    if (lo_used) {
+        MVN_CUDA(ctx, cudaEventRecord(ev_join, lo));
+        MVN_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ev_join, 0));
     }
     return MVN_OK;
 }

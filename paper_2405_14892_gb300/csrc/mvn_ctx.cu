@@ -42,7 +42,9 @@ extern "C" mvn_status mvn_create(mvn_ctx** out, int device, void* cuda_stream) {
     return MVN_OK;
 }
 
-cudaEvent_t timing_event(mvn_ctx* ctx) {
+cudaEvent_t timing_event(mvn_ctx* ctx) { return timing_event_on(ctx, ctx->stream); }
+
+cudaEvent_t timing_event_on(mvn_ctx* ctx, cudaStream_t stream) {
     if (!ctx->timing) return nullptr;
     if (ctx->ev_used == ctx->ev_pool.size()) {
         cudaEvent_t e;
@@ -53,8 +55,18 @@ cudaEvent_t timing_event(mvn_ctx* ctx) {
         ctx->ev_pool.push_back(e);
     }
     cudaEvent_t e = ctx->ev_pool[ctx->ev_used++];
-    cudaEventRecord(e, ctx->stream);
+    cudaEventRecord(e, stream);
     return e;
+}
+
+mvn_status ctx_aux(mvn_ctx* ctx) {
+    if (ctx->aux[0]) return MVN_OK;
+    int least = 0, greatest = 0;
+    MVN_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    MVN_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->aux[0], cudaStreamNonBlocking, greatest));
+    MVN_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->aux[1], cudaStreamNonBlocking, least));
+    for (auto& e : ctx->aux_ev) MVN_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return MVN_OK;
 }
 
 void timing_record(mvn_ctx* ctx, const char* name, cudaEvent_t a, cudaEvent_t b) {
@@ -92,6 +104,10 @@ extern "C" mvn_status mvn_destroy(mvn_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    for (auto e : ctx->aux_ev)
+        if (e) cudaEventDestroy(e);
+    for (auto s : ctx->aux)
+        if (s) cudaStreamDestroy(s);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->d_alpha) cudaFree(ctx->d_alpha);
     if (ctx->d_status) cudaFree(ctx->d_status);

@@ -31,6 +31,10 @@ struct mvn_ctx {
     // lattice generators alpha_i (u64) for i < n_alpha, computed on the device once
     uint64_t* d_alpha = nullptr;
     int n_alpha = 0;
+    // internal streams (high and low priority) and events for work that forks off `stream`
+    // and joins it again within one call (created on first use)
+    cudaStream_t aux[2] = {nullptr, nullptr};
+    cudaEvent_t aux_ev[8] = {};
     // per-kernel timing (mvn_timing): CUDA events recorded around selected launches
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -40,6 +44,9 @@ struct mvn_ctx {
 
 // Events around one launch when timing is enabled (returns nullptr otherwise).
 cudaEvent_t timing_event(mvn_ctx* ctx);
+cudaEvent_t timing_event_on(mvn_ctx* ctx, cudaStream_t stream);
+// Create the internal streams and events (aux[0] high priority, aux[1] low priority).
+mvn_status ctx_aux(mvn_ctx* ctx);
 void timing_record(mvn_ctx* ctx, const char* name, cudaEvent_t a, cudaEvent_t b);
 #define MVN_TIMED(ctx, name, launch)                                                         \
     do {                                                                                     \
@@ -47,6 +54,16 @@ void timing_record(mvn_ctx* ctx, const char* name, cudaEvent_t a, cudaEvent_t b)
         launch;                                                                              \
         MVN_LAUNCHED(ctx);                                                                   \
         cudaEvent_t tb_ = timing_event(ctx);                                                 \
+        timing_record(ctx, name, ta_, tb_);                                                  \
+    } while (0)
+
+// The same for a launch on another stream of the context.
+#define MVN_TIMED_ON(ctx, strm, name, launch)                                                \
+    do {                                                                                     \
+        cudaEvent_t ta_ = timing_event_on(ctx, strm);                                        \
+        launch;                                                                              \
+        MVN_LAUNCHED(ctx);                                                                   \
+        cudaEvent_t tb_ = timing_event_on(ctx, strm);                                        \
         timing_record(ctx, name, ta_, tb_);                                                  \
     } while (0)
 

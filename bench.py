@@ -150,6 +150,25 @@ TIMED_KERNELS = ("k_oz_update", "k_oz_potrf", "k_oz_trsm", "k_sov_tc", "k_syrk",
                  "k_sov_simt_f64", "k_sov_simt_f32")
 
 
+# DRAM bytes per launch measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) at
+# n = 9,216 with 20,000 paths (profiles/k_sov_tc_n9216.md, profiles/k_oz_update_n9216.md) and
+# scaled to the run's size by the growth the kernels' structure gives: the sweep's Y re-reads go as
+# (path tiles) x n^2, the update's digit-tile reads as n^2 per launch.
+TRAFFIC_N0 = 9216
+TRAFFIC_TILES0 = 157
+TRAFFIC_BYTES0 = {"k_sov_tc": 26.46e9 + 0.75e9, "k_oz_update": 89.6e6}
+
+
+def _traffic(name, n, tiles):
+    b = TRAFFIC_BYTES0.get(name)
+    if b is None:
+        return None
+    scale = (n / TRAFFIC_N0) ** 2
+    if name == "k_sov_tc":
+        scale *= tiles / TRAFFIC_TILES0
+    return b * scale
+
+
 def kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src, steps):
     """Achieved rate of the main kernels of the step: algorithmic work per launch (stated per
     kernel) over the kernel's average launch duration, measured by the library's CUDA events on
@@ -169,7 +188,10 @@ def kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src, steps):
         fl = 2.0 * 21 * mac * steps
         out.append({"kernel": "k_oz_update", "bound": "tensor", "unit": "TFLOP/s",
                     "achieved": fl / (ms * 1e-3) / 1e12, "peak": tens_peak,
-                    "frac": fl / (ms * 1e-3) / 1e12 / tens_peak, "traffic": None,
+                    "frac": fl / (ms * 1e-3) / 1e12 / tens_peak,
+                    "traffic": _traffic("k_oz_update", n, tiles),
+                    "traffic_note": "bytes per launch, averaged over the launches of a "
+                                    "factorisation; ncu at n=9216 scaled by (n/9216)^2",
                     "fp64_equivalent_tflops": 2.0 * mac * steps / (ms * 1e-3) / 1e12,
                     "launches": cnt, "total_ms": ms, "peak_source": tens_src,
                     "work": "21 BF16 MMA products per FP64 product of the left-looking update"})
@@ -182,7 +204,10 @@ def kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src, steps):
         fl = 2.0 * 3 * mac * cnt
         out.append({"kernel": "k_sov_tc", "bound": "tensor", "unit": "TFLOP/s",
                     "achieved": fl / (ms * 1e-3) / 1e12, "peak": tens_peak,
-                    "frac": fl / (ms * 1e-3) / 1e12 / tens_peak, "traffic": None,
+                    "frac": fl / (ms * 1e-3) / 1e12 / tens_peak,
+                    "traffic": _traffic("k_sov_tc", n, tiles),
+                    "traffic_note": "ncu at n=9216, 157 path tiles, scaled by (n/9216)^2 x "
+                                    "tiles/157",
                     "launches": cnt, "total_ms": ms, "peak_source": tens_src,
                     "work": "3 FP16 MMAs per multiply-add of the far limit-update GEMM "
                             "(two-slice split), 128-path tiles x 128-dimension super-blocks"})

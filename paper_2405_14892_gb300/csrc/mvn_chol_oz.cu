@@ -529,7 +529,9 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
                 }
         }
         __syncthreads();
-        if (act) {
+        // rows 4 ty .. 4 ty + 3 all <= k: nothing left to update (uniform for a warp once both
+        // of its row groups are done)
+        if (act && 4 * ty + 3 > k) {
             DF li[4], lm[4], wk[4];
 #pragma unroll
             for (int a = 0; a < 4; ++a) li[a] = colp[4 * ty + a];

@@ -162,7 +162,10 @@ static __device__ __noinline__ float sov_step_slow_pair(double ai, double bi, fl
 }
 
 // One dimension of Eq. 2 in FP32 (see above).  af/bf: the limits as floats; ai/bi: as doubles
-// (used only by the fallback); ainf/binf: the limits are infinite.
+// (used only by the fallback); ainf/binf: the limits are infinite.  Written without per-path
+// branches on the common path (the paths of a warp take different tails): one erfcf of |x| gives
+// both tails, one normcdfinvf of the smaller of p and 1 - p gives y, and the shift is scaled by
+// 1 / L_ii, which does not depend on it.
 __device__ __forceinline__ float sov_step_f32p(float af, float bf, double ai, double bi, bool ainf,
                                                bool binf, float s, float lii, float w, float wc,
                                                uint64_t m, float& dh, float& dl, int& dex) {
@@ -172,41 +175,40 @@ __device__ __forceinline__ float sov_step_f32p(float af, float bf, double ai, do
         dh = 1.0f;
         return phinv_two_sided_f32(w, wc);
     }
+    const float rl = 1.0f / lii;
     if (ainf) {  // Delta = Phi(b'),  p = w Phi(b'),  1 - p = (1 - w) + w Q(b')
-        const float bp = (bf - s) / lii;
+        const float bp = (bf - s) * rl;
         if (bp > -9.0f) {
-            float pb, qb;
-            if (bp < 0.0f) {
-                pb = 0.5f * erfcf(-bp * 0.70710678f);
-                qb = 1.0f - pb;
-                dh = pb;
-            } else {
-                qb = 0.5f * erfcf(bp * 0.70710678f);
-                pb = 1.0f - qb;
-                dh = pb;
-                dl = -(qb + (pb - 1.0f));  // exact: pb - 1 is exact (Sterbenz)
-            }
+            const float e = 0.5f * erfcf(fabsf(bp) * 0.70710678f);  // the smaller tail
+            const bool neg = bp < 0.0f;
+            const float pb = neg ? e : 1.0f - e;
+            const float qb = neg ? 1.0f - e : e;
+            dh = pb;
+            dl = neg ? 0.0f : -(qb + (pb - 1.0f));  // exact: pb - 1 is exact (Sterbenz)
             const float p = w * pb, q = wc + w * qb;
-            if (fminf(p, q) > 1e-30f) return phinv_two_sided_f32(p, q);
+            if (fminf(p, q) > 1e-30f) {
+                const bool lo = p <= 0.5f;
+                const float y0 = normcdfinvf(lo ? p : q);
+                return lo ? y0 : -y0;
+            }
         }
         return sov_step_slow_pair(ai, bi, s, lii, m, &dh, &dl, &dex);
     }
     if (binf) {  // Delta = Q(a'),  p = Phi(a') + w Q(a'),  1 - p = (1 - w) Q(a')
-        const float ap = (af - s) / lii;
+        const float ap = (af - s) * rl;
         if (ap < 9.0f) {
-            float pa, qa;
-            if (ap > 0.0f) {
-                qa = 0.5f * erfcf(ap * 0.70710678f);
-                pa = 1.0f - qa;
-                dh = qa;
-            } else {
-                pa = 0.5f * erfcf(-ap * 0.70710678f);
-                qa = 1.0f - pa;
-                dh = qa;
-                dl = -(pa + (qa - 1.0f));
-            }
+            const float e = 0.5f * erfcf(fabsf(ap) * 0.70710678f);
+            const bool pos = ap > 0.0f;
+            const float qa = pos ? e : 1.0f - e;
+            const float pa = pos ? 1.0f - e : e;
+            dh = qa;
+            dl = pos ? 0.0f : -(pa + (qa - 1.0f));
             const float p = pa + w * qa, q = wc * qa;
-            if (fminf(p, q) > 1e-30f) return phinv_two_sided_f32(p, q);
+            if (fminf(p, q) > 1e-30f) {
+                const bool lo = p <= 0.5f;
+                const float y0 = normcdfinvf(lo ? p : q);
+                return lo ? y0 : -y0;
+            }
         }
         return sov_step_slow_pair(ai, bi, s, lii, m, &dh, &dl, &dex);
     }

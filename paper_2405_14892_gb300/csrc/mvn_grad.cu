@@ -280,9 +280,13 @@ __global__ void __launch_bounds__(256) k_grad_L(int n, int ntiles, int64_t Ntot,
             for (int e = t; e < 32 * 64; e += 256) {
                 const int pp = e % 32, r = e / 32;
                 const int64_t pth = (int64_t)tl * SOV_P + c0 + pp;
-                const double wv = (pth < Ntot) ? omega[pth] : 0.0;
-                As[pp][r] = (R0 + r < n) ? wv * St[(int64_t)(R0 + r) * SOV_P + c0 + pp] : 0.0;
-                Bs[pp][r] = (C0 + r < n) ? Yt[(int64_t)(C0 + r) * SOV_P + c0 + pp] : 0.0;
+                // padding paths of the last tile are masked, not weighted by zero: their y and
+                // sbar slots are never written
+                const bool vp = pth < Ntot;
+                As[pp][r] = (vp && R0 + r < n)
+                                ? omega[pth] * St[(int64_t)(R0 + r) * SOV_P + c0 + pp]
+                                : 0.0;
+                Bs[pp][r] = (vp && C0 + r < n) ? Yt[(int64_t)(C0 + r) * SOV_P + c0 + pp] : 0.0;
             }
             __syncthreads();
 #pragma unroll 4

@@ -3,11 +3,73 @@
 
 // C(h)/sigma2 for nu in {1/2, 3/2, 5/2} (closed forms of Eq. 6's Bessel K_nu):
 //   nu=1/2: e^-x;  nu=3/2: (1+x) e^-x;  nu=5/2: (1 + x + x^2/3) e^-x,  x = h / range.
-__device__ __forceinline__ double matern_unit(double x, int nu2) {
-    double e = exp(-x);
-    if (nu2 == 1) return e;
-    if (nu2 == 3) return (1.0 + x) * e;
-    return (1.0 + x + x * x * (1.0 / 3.0)) * e;
+// ---------------------------------------------------------------- double-float arithmetic
+// GB300's FP64 pipe runs at ~1/64 of FP32, so the distance's square root and the exponential run
+// in double-float (FP32 pairs, Dekker 1971; ~48 bits): the squared distance is formed in FP64
+// (exact differences), everything after it in pairs.
+struct MF {
+    float hi, lo;
+};
+__device__ __forceinline__ MF mf_norm(float h, float l) {
+    const float s = h + l;
+    return MF{s, l - (s - h)};
+}
+__device__ __forceinline__ MF mf_from(double x) {
+    const float h = __double2float_rn(x);
+    return MF{h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double mf_to(MF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ MF mf_mul(MF a, MF b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return mf_norm(p, e);
+}
+__device__ __forceinline__ MF mf_add(MF a, MF b) {
+    const float s = a.hi + b.hi;
+    const float bp = s - a.hi;
+    const float e = (a.hi - (s - bp)) + (b.hi - bp);
+    return mf_norm(s, e + a.lo + b.lo);
+}
+__device__ __forceinline__ MF mf_sqrt(MF d) {  // sqrtf, then one Newton correction
+    if (!(d.hi > 0.0f)) return MF{0.0f, 0.0f};
+    const float s0 = sqrtf(d.hi);
+    const float p = s0 * s0;
+    const float pe = fmaf(s0, s0, -p);
+    const float diff = ((d.hi - p) - pe) + d.lo;
+    return mf_norm(s0, diff * (0.5f / s0));
+}
+// e^-x = 2^-k e^-r for x >= 0: Cody-Waite reduction x = k ln 2 + r, |r| <= ln 2 / 2, with
+// ln 2 = c1 + c2 + c3 (c1 with a short mantissa; each k c_i formed exactly as a pair), then
+// e^-r = (e^u)^8 with u = -r / 8 (|u| < 0.044) from the Taylor polynomial of degree 7 (truncation
+// below 4e-16 relative; three squarings multiply the relative error by 8).  Returns the pair
+// e^-r; the caller applies 2^-k in FP64 (no FP32 underflow).
+__device__ __forceinline__ MF mf_exp_neg_red(MF x, int& k) {
+    const float kf = rintf(x.hi * 1.44269504f);  // x / ln 2
+    k = (int)kf;
+    const float c1 = 0.693145751953125f;
+    const float c2 = 1.428606765330187e-06f;
+    const float c3 = 5.497923148104107e-14f;
+    MF r = x;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float c = (i == 0) ? c1 : ((i == 1) ? c2 : c3);
+        const float p = kf * c;
+        r = mf_add(r, MF{-p, -fmaf(kf, c, -p)});
+    }
+    const MF u{-r.hi * 0.125f, -r.lo * 0.125f};
+    MF q{1.0f, 0.0f};  // Horner: q = 1 + (u / m) q, m = 7 .. 1
+#pragma unroll
+    for (int m = 7; m >= 1; --m) {
+        const float fm = (float)m;
+        const float uh = u.hi / fm;
+        const float ul = (fmaf(-uh, fm, u.hi) + u.lo) / fm;  // u / m as a pair
+        q = mf_add(MF{1.0f, 0.0f}, mf_mul(q, MF{uh, ul}));
+    }
+    q = mf_mul(q, q);
+    q = mf_mul(q, q);
+    return mf_mul(q, q);
 }
 
 // One block: 256 rows x 8 columns of the lower triangle, column-major writes.
@@ -17,15 +79,26 @@ __global__ void k_matern(int n, const double* __restrict__ xy, double sigma2, do
     const int j0 = blockIdx.y * 8;
     if (i >= n || i < j0) return;
     const double xi = xy[2 * i], yi = xy[2 * i + 1];
+    const MF sg = mf_from(sigma2), ir = mf_from(inv_range);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         int j = j0 + c;
         if (j > i || j >= n) break;
-        double dx = xi - xy[2 * j], dy = yi - xy[2 * j + 1];
-        double h = sqrt(dx * dx + dy * dy);
-        double v = sigma2 * matern_unit(h * inv_range, nu2);
-        if (i == j) v = sigma2 + nugget;
-        S[i + (int64_t)j * ld] = v;
+        const double dx = xi - xy[2 * j], dy = yi - xy[2 * j + 1];
+        const MF x = mf_mul(mf_sqrt(mf_from(fma(dx, dx, dy * dy))), ir);
+        double out = 0.0;
+        if (x.hi < 700.0f) {
+            int k;
+            const MF e = mf_exp_neg_red(x, k);
+            MF poly{1.0f, 0.0f};
+            if (nu2 >= 3) poly = mf_add(poly, x);
+            if (nu2 == 5)
+                poly = mf_add(poly, mf_mul(mf_mul(x, x), MF{0.3333333432674408f, -9.934107758624577e-09f}));
+            out = mf_to(mf_mul(sg, mf_mul(poly, e))) *
+                  __longlong_as_double((long long)(1023 - k) << 52);  // 2^-k, k <= 1010
+        }
+        if (i == j) out = sigma2 + nugget;
+        S[i + (int64_t)j * ld] = out;
     }
 }
 

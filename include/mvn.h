@@ -45,12 +45,14 @@ typedef enum {
 
 /* Arithmetic of the compute path.
  *   MVN_FP64       : every step in FP64 (the plain FP64 GPU path).
- *   MVN_MIXED      : Cholesky in FP64; SOV limit-update GEMM on the tcgen05 tensor cores with
- *                    each operand split into two FP16 slices (3 MMAs per K step, FP32
- *                    accumulation in TMEM drained to FP32 registers every 256 K), limits and
- *                    transformed variables in FP32, the running log-weight in FP64, deep tails
- *                    of Phi and Phi^-1 in FP64.
- *   MVN_MIXED_SIMT : as MVN_MIXED with the limit-update GEMM in FP32 on the CUDA cores. */
+ *   MVN_MIXED      : Cholesky updates exact from BF16 digit slices on the tcgen05 tensor cores
+ *                    with a double-float panel (see mvn_cholesky); SOV limit-update GEMM on the
+ *                    tcgen05 tensor cores with each operand split into two FP16 slices (3 MMAs
+ *                    per K step, FP32 accumulation in TMEM drained to FP32 registers every
+ *                    128 K), limits and transformed variables in FP32, the running log-weight in
+ *                    FP64, deep tails of Phi and Phi^-1 in FP64.
+ *   MVN_MIXED_SIMT : as MVN_MIXED for the sweep, with the limit-update GEMM in FP32 on the CUDA
+ *                    cores; the Cholesky as MVN_FP64. */
 typedef enum { MVN_FP64 = 0, MVN_MIXED = 1, MVN_MIXED_SIMT = 2 } mvn_prec;
 
 /* Randomly shifted rank-1 (Richtmyer) lattice rule that replaces the uniforms R of Alg. 2:
@@ -169,10 +171,11 @@ mvn_status mvn_sov_batched(mvn_ctx* ctx, int nprob, const int* dims,
                            mvn_prec prec, double* out3);
 
 /* FP64 SOV estimate that allocates nothing (the paper has no counterpart; this is a service for
- * callers that cannot allocate device memory at call time -- code inside a CUDA graph capture,
- * under a caching allocator that must not see foreign cudaMalloc calls, in a real-time loop
- * where an allocation's implicit synchronisation is not allowed, or an embedding that only
- * hands over device buffers).  Same arithmetic as mvn_sov with MVN_FP64, without a context:
+ * callers that cannot allocate device memory at call time -- code under a caching allocator
+ * that must not see foreign cudaMalloc calls, a real-time loop where an allocation's implicit
+ * synchronisation is not allowed, or an embedding that only hands over device buffers and
+ * cannot create a context with its own workspace).  Same arithmetic as mvn_sov with MVN_FP64,
+ * without a context:
  *   - work is enqueued on `cuda_stream` (a cudaStream_t, NULL = legacy default stream) of the
  *     current device;
  *   - all scratch lives in one fixed file-scope device array of about 10.2 MiB that every GPU

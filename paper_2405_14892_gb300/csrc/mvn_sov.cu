@@ -332,9 +332,9 @@ extern "C" mvn_status mvn_sov_batched(mvn_ctx* ctx, int nprob, const int* dims,
 // ---------------------------------------------------------------- ABI: mvn_sov_fp64_noalloc
 //
 // FP64 SOV estimate for callers that cannot allocate device memory at call time: code that
-// runs inside a CUDA graph being captured, under a caching allocator that must not see
-// foreign cudaMalloc calls, in a real-time loop where an allocation's implicit synchronisation
-// is not allowed, or in an embedding that hands the library device buffers and nothing else.
+// runs under a caching allocator that must not see foreign cudaMalloc calls, in a real-time
+// loop where an allocation's implicit synchronisation is not allowed, or in an embedding that
+// hands the library device buffers and nothing else.
 // Such a caller cannot create an mvn_ctx (which owns a growing workspace), so this entry point
 // takes a stream instead and keeps all of its scratch in one file-scope device array of fixed
 // size, which every GPU that loads the library holds until the process exits.

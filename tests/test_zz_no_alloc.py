@@ -1,7 +1,7 @@
 """The FP64 SOV entry point that allocates nothing (mvn_sov_fp64_noalloc), for callers that
-cannot allocate device memory at call time (inside a CUDA graph capture, under a caching
-allocator that must not see foreign cudaMalloc calls, in a real-time loop, or in an embedding
-that only hands over device buffers).  It keeps its scratch in a fixed array inside the
+cannot allocate device memory at call time (under a caching allocator that must not see
+foreign cudaMalloc calls, in a real-time loop that cannot take an allocation's implicit
+synchronisation, or in an embedding that only hands over device buffers).  It keeps its scratch in a fixed array inside the
 library; this test checks it through the C ABI against the regular entry point (mvn_sov,
 MVN_FP64) on two calls in a row, and that sizes beyond its fixed limits are refused.
 

@@ -132,21 +132,48 @@ def run(args):
         c = t(inputs.grid_coords(w["g"]))
         n = c.shape[0]
         _, b = inputs.limits_for(w, n)
-        bt = t(b).requires_grad_(True)
-        s2 = torch.tensor(w["sigma2"], dtype=torch.float64, device=dev, requires_grad=True)
-        rg = torch.tensor(w["range"], dtype=torch.float64, device=dev, requires_grad=True)
+        res, ms, kms = {}, {}, {}
+        names = ("k_sov_grad_fwd_f64", "k_sov_grad_fwd_f32", "k_sov_rev_f64", "k_sov_rev_f32",
+                 "k_grad_L_f64", "k_grad_L_f32", "k_oz_update", "k_oz_potrf", "k_oz_trsm",
+                 "k_syrk")
+        for prec in ("mixed", "fp64"):
+            bt = t(b).requires_grad_(True)
+            s2 = torch.tensor(w["sigma2"], dtype=torch.float64, device=dev, requires_grad=True)
+            rg = torch.tensor(w["range"], dtype=torch.float64, device=dev, requires_grad=True)
 
-        def step():
-            bt.grad = None
-            s2.grad = None
-            rg.grad = None
-            lp = mvn_log_prob(bt, s2, rg, c, nu=w["nu"], nugget=w["nugget"], n_points=w["Ns"],
-                              n_shifts=w["M"], seed=w["seed"])
-            lp.backward()
-        ms = _timed(step, steps, warm, stream)
+            def step():
+                bt.grad = None
+                s2.grad = None
+                rg.grad = None
+                lp = mvn_log_prob(bt, s2, rg, c, nu=w["nu"], nugget=w["nugget"],
+                                  n_points=w["Ns"], n_shifts=w["M"], seed=w["seed"], prec=prec)
+                lp.backward()
+                res[prec] = lp.detach()
+            ms[prec] = _timed(step, steps, warm, stream)
+            res[prec] = (float(res[prec]), bt.grad.cpu().numpy(), float(s2.grad), float(rg.grad))
+            # per-kernel device time of one more step, from the library's own events
+            ctx.timing(True)
+            keep = res[prec]
+            step()
+            res[prec] = keep
+            torch.cuda.synchronize()
+            kms[prec] = {k: round(v[0], 3) for k in names
+                         for v in [ctx.kernel_time(k)] if v[1]}
+            ctx.timing(False)
+        l64, gb64, s64, r64 = res["fp64"]
+        lmx, gbmx, smx, rmx = res["mixed"]
         _line(args, w["name"], "gradients/s of log P w.r.t. (b, sigma2, range), n=4096",
-              1e3 / ms, "gradients/s", ms, {"dtype": "f64", "dsigma2": float(s2.grad),
-                                            "drange": float(rg.grad)})
+              1e3 / ms["mixed"], "gradients/s", ms["mixed"],
+              {"dtype": "f64+f32 (mixed) vs f64", "fp64_ms": ms["fp64"],
+               "fp64_gradients_per_sec": 1e3 / ms["fp64"],
+               "mixed_over_fp64_speedup": ms["fp64"] / ms["mixed"],
+               "logP": {"mixed": lmx, "fp64": l64},
+               "mixed_vs_fp64": {"dlogP": abs(lmx - l64),
+                                 "db_rel": float(np.abs(gbmx - gb64).max() /
+                                                 max(1.0, np.abs(gb64).max())),
+                                 "dsigma2_rel": abs(smx - s64) / max(1.0, abs(s64)),
+                                 "drange_rel": abs(rmx - r64) / max(1.0, abs(r64))},
+               "dsigma2": smx, "drange": rmx, "kernel_ms_one_step": kms})
         return
 
     if args.workload == "w5":

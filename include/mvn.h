@@ -86,7 +86,8 @@ mvn_status mvn_sync(mvn_ctx* ctx, int* info);
 int64_t mvn_launch_count(const mvn_ctx* ctx);
 /* Per-kernel timing: with enable != 0, CUDA events are recorded on the context's stream around
  * every launch of the main kernels (k_oz_update, k_oz_potrf, k_oz_trsm, k_syrk,
- * k_sov_tc, k_sov_simt_f64, k_sov_simt_f32); the call waits for the stream and clears earlier
+ * k_sov_tc, k_sov_simt_f64, k_sov_simt_f32, and in mvn_sov_grad k_sov_grad_fwd_f64/_f32,
+ * k_sov_rev_f64/_f32, k_grad_L_f64/_f32); the call waits for the stream and clears earlier
  * records. */
 mvn_status mvn_timing(mvn_ctx* ctx, int enable);
 /* Total device time (ms, host) and number of launches (host) of kernel `name` recorded since
@@ -153,9 +154,16 @@ mvn_status mvn_sov(mvn_ctx* ctx, int n, const double* a, const double* b, const 
  *   dlogp_da, dlogp_db: device n-vectors of d log P-hat / d a_i, d b_i (either may be NULL);
  *   dlogp_dL: optional device n x n (ld) lower-triangle d log P-hat / d L_ik.
  * The reverse sweep recomputes each block's elementwise terms from the stored transformed
- * variables instead of storing them.  The adjoint runs in FP64 for every value of prec (the
- * forward estimate in out3 is the FP64 one).  dlogp_dL uses the leading dimension ld of L; its
- * strict upper part is not written.  out3 as in mvn_sov. */
+ * variables instead of storing them.
+ * prec = MVN_FP64: every step in FP64; out3 equals mvn_sov's MVN_FP64 estimate.
+ * prec = MVN_MIXED or MVN_MIXED_SIMT: the forward sweep forms the limit shifts in FP32 and keeps
+ *   the transformed variables in FP32, with the elementwise step of Eq. 2 in FP64 (out3 is this
+ *   sweep's estimate); the reverse sweep forms the limit shifts and the sums over later
+ *   dimensions in FP32 and the elementwise derivative terms in FP64; dlogp_dL sums FP32 products
+ *   within each 128-path tile and the tiles in FP64.  Workspace per 128 paths: 2 * n * 128 * 8 bytes (FP64) or
+ *   * 4 bytes (mixed).
+ * dlogp_dL uses the leading dimension ld of L; its strict upper part is not written.  out3 as
+ * in mvn_sov. */
 mvn_status mvn_sov_grad(mvn_ctx* ctx, int n, const double* a, const double* b,
                         const double* L, int64_t ld, const mvn_qmc* qmc, mvn_prec prec,
                         double* out3, double* dlogp_da, double* dlogp_db, double* dlogp_dL);

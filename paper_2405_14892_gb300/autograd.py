@@ -5,7 +5,11 @@ covariance parameters theta = (sigma2, range).
 The forward pass runs the library's chain Matern -> Cholesky -> SOV sweep; the gradient comes
 from the library's adjoints (reverse SOV sweep -> Cholesky adjoint -> Matern contraction), all in
 CUDA kernels.  The gradients are those of the estimator on its fixed lattice points (the exact
-derivative of the estimate), computed in FP64.
+derivative of the estimate).
+
+prec="fp64": every step in FP64.  prec="mixed": the tensor-core Cholesky (MVN_MIXED), the sweep
+and its reverse with FP32 limit sums and transformed variables (FP64 elementwise steps,
+log-weights and derivative terms), the Cholesky adjoint and the Matern contraction in FP64.
 """
 from __future__ import annotations
 
@@ -16,14 +20,14 @@ from . import mvn
 
 class MVNLogProb(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, b, sigma2, rng, coords, a, nu, nugget, n_points, n_shifts, seed):
+    def forward(ctx, b, sigma2, rng, coords, a, nu, nugget, n_points, n_shifts, seed, prec):
         s2 = float(sigma2)
         rg = float(rng)
         S = mvn.mvn_matern(coords, s2, rg, nu, nugget)
-        mvn.mvn_cholesky(S)
+        mvn.mvn_cholesky(S, prec=prec)
         want_theta = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
         out3, ga, gb, gL = mvn.mvn_sov_grad(a.contiguous(), b.contiguous(), S, n_points, n_shifts,
-                                            seed, want_L=want_theta)
+                                            seed, prec=prec, want_L=want_theta)
         if want_theta:
             Sbar = mvn.mvn_cholesky_grad(S, gL)
             th = mvn.mvn_matern_grad(coords, s2, rg, nu, Sbar)
@@ -35,12 +39,14 @@ class MVNLogProb(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         gb, th = ctx.saved_tensors
-        return (g * gb, g * th[0], g * th[1], None, None, None, None, None, None, None)
+        return (g * gb, g * th[0], g * th[1], None, None, None, None, None, None, None, None)
 
 
 def mvn_log_prob(b, sigma2, rng, coords, a=None, nu=1.5, nugget=0.0, n_points=1000,
-                 n_shifts=10, seed=0):
+                 n_shifts=10, seed=0, prec="fp64"):
     """log P-hat(a <= X <= b) with autograd support for b, sigma2 and range."""
+    if prec not in ("fp64", "mixed"):
+        raise ValueError("prec must be 'fp64' or 'mixed'")
     if a is None:
         a = torch.full_like(b, float("-inf"))
-    return MVNLogProb.apply(b, sigma2, rng, coords, a, nu, nugget, n_points, n_shifts, seed)
+    return MVNLogProb.apply(b, sigma2, rng, coords, a, nu, nugget, n_points, n_shifts, seed, prec)

@@ -71,9 +71,12 @@ __global__ void k_weights(const double* __restrict__ logw, int64_t N,
 
 // ---------------------------------------------------------------- reverse sweep
 
+// T = type of the stored y and sbar and of the two per-block sums over dimensions (double: the
+// FP64 adjoint; float: the mixed adjoint).  The elementwise derivative terms are FP64 for both.
+template <typename T>
 struct RevSmem {
-    double Lk[RV_B][RV_B];      // GEMM operand tile
-    double Ld[RV_B][RV_B + 1];  // diagonal block L(r0+v, r0+u)
+    T Lk[RV_B][RV_B];           // GEMM operand tile
+    T Ld[RV_B][RV_B + 1];       // diagonal block L(r0+v, r0+u)
     double a[RV_B], b[RV_B];
     uint64_t alpha[RV_B];
     double red[3][RV_B][4];     // per-warp partial sums of the three path reductions
@@ -82,10 +85,12 @@ struct RevSmem {
 // One tile of 128 paths, blocks in reverse order.  Y and Sbar of tile `tile` live at
 // Yt/St[k * 128 + t].  part[(tile * 3 + c) * n + i] receives the tile's sum over its paths of
 // w_p a'bar/L_ii (c = 0), w_p b'bar/L_ii (c = 1) and w_p dL_ii (c = 2).
+template <typename T>
 __device__ void rev_tile(const SovProblem& P, int tile, const uint64_t* __restrict__ alpha,
-                         const double* __restrict__ Yt, double* __restrict__ St,
+                         const T* __restrict__ Yt, T* __restrict__ St,
                          const double* __restrict__ omega, double* __restrict__ part,
-                         RevSmem& sm) {
+                         RevSmem<T>& sm) {
+    constexpr bool kF32 = sizeof(T) == 4;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int n = P.n;
     const int64_t p = (int64_t)tile * SOV_P + t;
@@ -101,11 +106,11 @@ __device__ void rev_tile(const SovProblem& P, int tile, const uint64_t* __restri
     for (int blk = nblk - 1; blk >= 0; --blk) {
         const int r0 = blk * RV_B;
         const int nb = min(RV_B, n - r0);
-        double acc[RV_B], yb[RV_B];
+        T acc[RV_B], yb[RV_B];
 #pragma unroll
         for (int v = 0; v < RV_B; ++v) {
-            acc[v] = 0.0;
-            yb[v] = 0.0;
+            acc[v] = (T)0;
+            yb[v] = (T)0;
         }
         // (a) limit shift from earlier blocks: acc[v] = sum_{k < r0} L(r0+v, k) y_k
         for (int k0 = 0; k0 < r0; k0 += RV_B) {
@@ -113,15 +118,21 @@ __device__ void rev_tile(const SovProblem& P, int tile, const uint64_t* __restri
             for (int e = t; e < RV_B * RV_B; e += SOV_P) {
                 const int v = e % RV_B, kk = e / RV_B;
                 const int row = r0 + v;
-                sm.Lk[kk][v] = (row < n) ? L[row + (int64_t)(k0 + kk) * ld] : 0.0;
+                sm.Lk[kk][v] = (row < n) ? (T)L[row + (int64_t)(k0 + kk) * ld] : (T)0;
             }
             __syncthreads();
+            // FP32: per-block partial sums (as in the forward sweep of the mixed adjoint)
+            T part[RV_B];
+#pragma unroll
+            for (int v = 0; v < RV_B; ++v) part[v] = kF32 ? (T)0 : acc[v];
 #pragma unroll 4
             for (int kk = 0; kk < RV_B; ++kk) {
-                const double yk = Yt[(int64_t)(k0 + kk) * SOV_P + t];
+                const T yk = Yt[(int64_t)(k0 + kk) * SOV_P + t];
 #pragma unroll
-                for (int v = 0; v < RV_B; ++v) acc[v] = fma(sm.Lk[kk][v], yk, acc[v]);
+                for (int v = 0; v < RV_B; ++v) part[v] = fma(sm.Lk[kk][v], yk, part[v]);
             }
+#pragma unroll
+            for (int v = 0; v < RV_B; ++v) acc[v] = kF32 ? acc[v] + part[v] : part[v];
         }
         // (b) ybar from the later dimensions: yb[v] = sum_{i >= r0+nb} L(i, r0+v) sbar_i
         for (int i0 = r0 + RV_B; i0 < n; i0 += RV_B) {
@@ -129,21 +140,26 @@ __device__ void rev_tile(const SovProblem& P, int tile, const uint64_t* __restri
             for (int e = t; e < RV_B * RV_B; e += SOV_P) {
                 const int ii = e % RV_B, v = e / RV_B;
                 const int row = i0 + ii;
-                sm.Lk[ii][v] = (row < n && v < nb) ? L[row + (int64_t)(r0 + v) * ld] : 0.0;
+                sm.Lk[ii][v] = (row < n && v < nb) ? (T)L[row + (int64_t)(r0 + v) * ld] : (T)0;
             }
             __syncthreads();
             const int ni = min(RV_B, n - i0);
-            for (int ii = 0; ii < ni; ++ii) {
-                const double sb = St[(int64_t)(i0 + ii) * SOV_P + t];
+            T part[RV_B];
 #pragma unroll
-                for (int v = 0; v < RV_B; ++v) yb[v] = fma(sm.Lk[ii][v], sb, yb[v]);
+            for (int v = 0; v < RV_B; ++v) part[v] = kF32 ? (T)0 : yb[v];
+            for (int ii = 0; ii < ni; ++ii) {
+                const T sb = St[(int64_t)(i0 + ii) * SOV_P + t];
+#pragma unroll
+                for (int v = 0; v < RV_B; ++v) part[v] = fma(sm.Lk[ii][v], sb, part[v]);
             }
+#pragma unroll
+            for (int v = 0; v < RV_B; ++v) yb[v] = kF32 ? yb[v] + part[v] : part[v];
         }
         // (c) block operands
         __syncthreads();
         for (int e = t; e < RV_B * RV_B; e += SOV_P) {
             const int v = e % RV_B, u = e / RV_B;
-            sm.Ld[v][u] = (v < nb && u <= v) ? L[(r0 + v) + (int64_t)(r0 + u) * ld] : 0.0;
+            sm.Ld[v][u] = (v < nb && u <= v) ? (T)L[(r0 + v) + (int64_t)(r0 + u) * ld] : (T)0;
         }
         if (t < RV_B) {
             sm.a[t] = (t < nb) ? P.a[r0 + t] : 0.0;
@@ -151,27 +167,28 @@ __device__ void rev_tile(const SovProblem& P, int tile, const uint64_t* __restri
             sm.alpha[t] = (t < nb) ? alpha[r0 + t] : 0u;
         }
         __syncthreads();
-        double y[RV_B], ap[RV_B], bp[RV_B];
+        T y[RV_B];
+        double ap[RV_B], bp[RV_B];
 #pragma unroll
         for (int v = 0; v < RV_B; ++v) {
-            y[v] = (v < nb) ? Yt[(int64_t)(r0 + v) * SOV_P + t] : 0.0;
+            y[v] = (v < nb) ? Yt[(int64_t)(r0 + v) * SOV_P + t] : (T)0;
         }
         // (d) forward in the block: limits of each dimension
 #pragma unroll
         for (int v = 0; v < RV_B; ++v) {
-            double s = acc[v];
+            T s = acc[v];
 #pragma unroll
             for (int u = 0; u < v; ++u) s = fma(sm.Ld[v][u], y[u], s);
-            const double lii = (v < nb) ? sm.Ld[v][v] : 1.0;
-            ap[v] = (sm.a[v] - s) / lii;
-            bp[v] = (sm.b[v] - s) / lii;
+            const double lii = (v < nb) ? (double)sm.Ld[v][v] : 1.0;
+            ap[v] = (sm.a[v] - (double)s) / lii;
+            bp[v] = (sm.b[v] - (double)s) / lii;
         }
         // (e) reverse in the block
 #pragma unroll
         for (int v = RV_B - 1; v >= 0; --v) {
             double ga = 0.0, gb = 0.0, gd = 0.0, sbar = 0.0;
             if (v < nb && live) {
-                const double lii = sm.Ld[v][v];
+                const double lii = (double)sm.Ld[v][v];
                 const double w = lattice_w(j, sm.alpha[v], dq[r0 + v]);
                 const double A = ap[v], Bv = bp[v];
                 double delta;
@@ -184,9 +201,10 @@ __device__ void rev_tile(const SovProblem& P, int tile, const uint64_t* __restri
                 }
                 const double pa = (A == -INFINITY) ? 0.0 : phi_d(A);
                 const double pb = (Bv == INFINITY) ? 0.0 : phi_d(Bv);
-                const double py = phi_d(y[v]);
-                const double apbar = -pa / delta + yb[v] * (1.0 - w) * pa / py;
-                const double bpbar = pb / delta + yb[v] * w * pb / py;
+                const double py = phi_d((double)y[v]);
+                const double ybv = (double)yb[v];
+                const double apbar = -pa / delta + ybv * (1.0 - w) * pa / py;
+                const double bpbar = pb / delta + ybv * w * pb / py;
                 sbar = -(apbar + bpbar) / lii;
                 ga = wp * apbar / lii;
                 gb = wp * bpbar / lii;
@@ -194,10 +212,11 @@ __device__ void rev_tile(const SovProblem& P, int tile, const uint64_t* __restri
                 if (pa != 0.0) lb -= apbar * A;
                 if (pb != 0.0) lb -= bpbar * Bv;
                 gd = wp * lb / lii;
+                const T sbt = (T)sbar;
 #pragma unroll
-                for (int u = 0; u < v; ++u) yb[u] = fma(sbar, sm.Ld[v][u], yb[u]);
+                for (int u = 0; u < v; ++u) yb[u] = fma(sbt, sm.Ld[v][u], yb[u]);
             }
-            if (v < nb) St[(int64_t)(r0 + v) * SOV_P + t] = sbar;
+            if (v < nb) St[(int64_t)(r0 + v) * SOV_P + t] = (T)sbar;
             // reductions over the tile's paths (warp shuffles, then 4 warps in shared memory)
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -223,14 +242,15 @@ __device__ void rev_tile(const SovProblem& P, int tile, const uint64_t* __restri
     }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(SOV_P) k_sov_rev(const SovProblem P, int nitems,
                                                    int* __restrict__ counter,
                                                    const uint64_t* __restrict__ alpha,
-                                                   const double* __restrict__ Y,
-                                                   double* __restrict__ Sbar, int64_t ystride,
+                                                   const T* __restrict__ Y,
+                                                   T* __restrict__ Sbar, int64_t ystride,
                                                    const double* __restrict__ omega,
                                                    double* __restrict__ part) {
-    __shared__ RevSmem sm;
+    __shared__ RevSmem<T> sm;
     __shared__ int s_item;
     for (;;) {
         __syncthreads();
@@ -256,14 +276,17 @@ __global__ void k_sum_parts(const double* __restrict__ part, int ntiles, int n,
 
 // dL(i, k) for i > k: sum over paths of w_p sbar_{p,i} y_{p,k}; dL(i, i) = dsum[2n + i].
 // Paths are laid out per tile: X[tile][dim][128].  One 64 x 64 lower output tile per block.
+// The products of one 128-path tile are summed in T, the tiles' partial sums in FP64 (for
+// T = float the rounding error then grows with the tile's 128 terms, not with all N paths).
+template <typename T>
 __global__ void __launch_bounds__(256) k_grad_L(int n, int ntiles, int64_t Ntot,
-                                                const double* __restrict__ Sbar,
-                                                const double* __restrict__ Y,
+                                                const T* __restrict__ Sbar,
+                                                const T* __restrict__ Y,
                                                 const double* __restrict__ omega,
                                                 const double* __restrict__ dsum,
                                                 double* __restrict__ G, int64_t ldg) {
-    __shared__ double As[32][64 + 1];  // As[pp][r] = w_p sbar_{p, R0 + r}
-    __shared__ double Bs[32][64 + 1];  // Bs[pp][c] = y_{p, C0 + c}
+    __shared__ T As[32][64 + 1];  // As[pp][r] = w_p sbar_{p, R0 + r}
+    __shared__ T Bs[32][64 + 1];  // Bs[pp][c] = y_{p, C0 + c}
     const int x = blockIdx.x;
     int ti = (int)((sqrt(8.0 * x + 1.0) - 1.0) * 0.5);
     while ((ti + 1) * (ti + 2) / 2 <= x) ++ti;
@@ -273,8 +296,13 @@ __global__ void __launch_bounds__(256) k_grad_L(int n, int ntiles, int64_t Ntot,
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
     double acc[4][4] = {};
     for (int tl = 0; tl < ntiles; ++tl) {
-        const double* St = Sbar + (int64_t)tl * n * SOV_P;
-        const double* Yt = Y + (int64_t)tl * n * SOV_P;
+        const T* St = Sbar + (int64_t)tl * n * SOV_P;
+        const T* Yt = Y + (int64_t)tl * n * SOV_P;
+        T tacc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) tacc[u][v] = (T)0;
         for (int c0 = 0; c0 < SOV_P; c0 += 32) {
             __syncthreads();
             for (int e = t; e < 32 * 64; e += 256) {
@@ -284,14 +312,14 @@ __global__ void __launch_bounds__(256) k_grad_L(int n, int ntiles, int64_t Ntot,
                 // sbar slots are never written
                 const bool vp = pth < Ntot;
                 As[pp][r] = (vp && R0 + r < n)
-                                ? omega[pth] * St[(int64_t)(R0 + r) * SOV_P + c0 + pp]
-                                : 0.0;
-                Bs[pp][r] = (vp && C0 + r < n) ? Yt[(int64_t)(C0 + r) * SOV_P + c0 + pp] : 0.0;
+                                ? (T)(omega[pth] * (double)St[(int64_t)(R0 + r) * SOV_P + c0 + pp])
+                                : (T)0;
+                Bs[pp][r] = (vp && C0 + r < n) ? Yt[(int64_t)(C0 + r) * SOV_P + c0 + pp] : (T)0;
             }
             __syncthreads();
 #pragma unroll 4
             for (int pp = 0; pp < 32; ++pp) {
-                double a[4], b[4];
+                T a[4], b[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) a[u] = As[pp][tx + 16 * u];
 #pragma unroll
@@ -299,9 +327,13 @@ __global__ void __launch_bounds__(256) k_grad_L(int n, int ntiles, int64_t Ntot,
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+                    for (int v = 0; v < 4; ++v) tacc[u][v] = fma(a[u], b[v], tacc[u][v]);
             }
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += (double)tacc[u][v];
     }
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -516,28 +548,29 @@ extern "C" mvn_status mvn_cholesky_grad(mvn_ctx* ctx, int n, const double* L, in
 
 // ---------------------------------------------------------------- SOV gradient
 
-extern "C" mvn_status mvn_sov_grad(mvn_ctx* ctx, int n, const double* a, const double* b,
-                                   const double* L, int64_t ld, const mvn_qmc* qmc,
-                                   mvn_prec prec, double* out3, double* dlogp_da,
-                                   double* dlogp_db, double* dlogp_dL) {
-    if (!ctx) return MVN_ERR_ARG;
-    MVN_TRY(check_qmc(ctx, qmc));
-    MVN_TRY(check_problem_host(ctx, n, a, b, L, ld));
-    if (!out3) return mvn_fail(ctx, MVN_ERR_ARG, "out3 is null");
-    if (prec != MVN_FP64 && prec != MVN_MIXED && prec != MVN_MIXED_SIMT)
-        return mvn_fail(ctx, MVN_ERR_ARG, "unknown precision");
-    MVN_CUDA(ctx, cudaSetDevice(ctx->device));
+// T = double: the FP64 adjoint (forward k_sov_simt<32, double>, FP64 everywhere).
+// T = float: the mixed adjoint.  Its forward sweep forms the limit shifts in FP32 and keeps every
+// tile's y in FP32, with the elementwise step of Eq. 2 in FP64 (k_sov_simt<32, float, true>): the
+// per-dimension errors of an FP32 step add up along the n dimensions of log P, those of the FP32
+// limit sums much less.  The reverse sweep forms the limit shifts and ybar in FP32 and the
+// elementwise derivative terms in FP64; dL sums FP32 products per 128-path tile and the tiles in
+// FP64.
+template <typename T>
+static mvn_status sov_grad_run(mvn_ctx* ctx, int n, const double* a, const double* b,
+                               const double* L, int64_t ld, const mvn_qmc* qmc, double* out3,
+                               double* dlogp_da, double* dlogp_db, double* dlogp_dL) {
+    constexpr bool F64 = sizeof(T) == 8;
     const int M = qmc->n_shifts;
     const int64_t Ns = qmc->n_points, Ntot = Ns * M;
     const int64_t ntiles = (Ntot + SOV_P - 1) / SOV_P;
     const int nn = std::max(n, 1);
     const int64_t ystride = (int64_t)nn * SOV_P;
-    if ((double)ntiles * ystride * 16.0 > 200e9)
+    if ((double)ntiles * ystride * 2.0 * sizeof(T) > 200e9)
         return mvn_fail(ctx, MVN_ERR_ARG, "gradient workspace beyond 200 GB");
     MVN_TRY(lattice_ensure(ctx, nn));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 2 * (int64_t)ctx->sm_count));
     const size_t need = ws_round(sizeof(uint64_t) * (size_t)M * nn) + ws_round(sizeof(double) * Ntot) * 2 +
-                        2 * ws_round(sizeof(double) * (size_t)ntiles * ystride) +
+                        2 * ws_round(sizeof(T) * (size_t)ntiles * ystride) +
                         ws_round(sizeof(double) * 3 * (size_t)ntiles * nn) +
                         ws_round(sizeof(double) * 3 * (size_t)nn) + 4 * ws_round(sizeof(double)) + 4096;
     MVN_TRY(ws_reserve(ctx, need));
@@ -545,8 +578,8 @@ extern "C" mvn_status mvn_sov_grad(mvn_ctx* ctx, int n, const double* a, const d
     uint64_t* delta = wc.take<uint64_t>((size_t)M * nn);
     double* logw = wc.take<double>(Ntot);
     double* omega = wc.take<double>(Ntot);
-    double* Y = wc.take<double>((size_t)ntiles * ystride);
-    double* Sb = wc.take<double>((size_t)ntiles * ystride);
+    T* Y = wc.take<T>((size_t)ntiles * ystride);
+    T* Sb = wc.take<T>((size_t)ntiles * ystride);
     double* part = wc.take<double>(3 * (size_t)ntiles * nn);
     double* dsum = wc.take<double>(3 * (size_t)nn);
     double* lse = wc.take<double>(1);
@@ -577,9 +610,15 @@ extern "C" mvn_status mvn_sov_grad(mvn_ctx* ctx, int n, const double* a, const d
         batch.counter = counter;
         batch.y_per_tile = 1;
         MVN_CUDA(ctx, cudaMemsetAsync(counter, 0, 2 * sizeof(int), ctx->stream));
-        k_sov_simt<32, double, true><<<grid, SOV_P, 0, ctx->stream>>>(batch, ctx->d_alpha, Y,
-                                                                       ystride);
-        MVN_LAUNCHED(ctx);
+        if constexpr (F64) {
+            MVN_TIMED(ctx, "k_sov_grad_fwd_f64",
+                      (k_sov_simt<32, double, true><<<grid, SOV_P, 0, ctx->stream>>>(
+                          batch, ctx->d_alpha, Y, ystride)));
+        } else {
+            MVN_TIMED(ctx, "k_sov_grad_fwd_f32",
+                      (k_sov_simt<32, float, true><<<grid, SOV_P, 0, ctx->stream>>>(
+                          batch, ctx->d_alpha, Y, ystride)));
+        }
     }
     MVN_TRY(sov_reduce_launch_opt(ctx, logw, Ns, M, qmc->err_k, out3, 1, Ntot, true));
     k_lse_all<<<1, 512, 0, ctx->stream>>>(logw, Ntot, lse);
@@ -588,9 +627,10 @@ extern "C" mvn_status mvn_sov_grad(mvn_ctx* ctx, int n, const double* a, const d
     MVN_LAUNCHED(ctx);
     if (n == 0) return MVN_OK;
     // reverse sweep
-    k_sov_rev<<<grid, SOV_P, 0, ctx->stream>>>(P, (int)ntiles, counter + 1, ctx->d_alpha, Y, Sb,
-                                               ystride, omega, part);
-    MVN_LAUNCHED(ctx);
+    MVN_TIMED(ctx, F64 ? "k_sov_rev_f64" : "k_sov_rev_f32",
+              (k_sov_rev<T><<<grid, SOV_P, 0, ctx->stream>>>(P, (int)ntiles, counter + 1,
+                                                              ctx->d_alpha, Y, Sb, ystride, omega,
+                                                              part)));
     k_sum_parts<<<dim3((n + 255) / 256, 3), 256, 0, ctx->stream>>>(part, (int)ntiles, n, dsum);
     MVN_LAUNCHED(ctx);
     if (dlogp_da)
@@ -600,10 +640,26 @@ extern "C" mvn_status mvn_sov_grad(mvn_ctx* ctx, int n, const double* a, const d
         MVN_CUDA(ctx, cudaMemcpyAsync(dlogp_db, dsum + n, sizeof(double) * n,
                                       cudaMemcpyDeviceToDevice, ctx->stream));
     if (dlogp_dL) {
-        const int T = (n + 63) / 64;
-        k_grad_L<<<(unsigned)((int64_t)T * (T + 1) / 2), 256, 0, ctx->stream>>>(
-            n, (int)ntiles, Ntot, Sb, Y, omega, dsum, dlogp_dL, ld);
-        MVN_LAUNCHED(ctx);
+        const int T64 = (n + 63) / 64;
+        MVN_TIMED(ctx, F64 ? "k_grad_L_f64" : "k_grad_L_f32",
+                  (k_grad_L<T><<<(unsigned)((int64_t)T64 * (T64 + 1) / 2), 256, 0, ctx->stream>>>(
+                      n, (int)ntiles, Ntot, Sb, Y, omega, dsum, dlogp_dL, ld)));
     }
     return MVN_OK;
+}
+
+extern "C" mvn_status mvn_sov_grad(mvn_ctx* ctx, int n, const double* a, const double* b,
+                                   const double* L, int64_t ld, const mvn_qmc* qmc,
+                                   mvn_prec prec, double* out3, double* dlogp_da,
+                                   double* dlogp_db, double* dlogp_dL) {
+    if (!ctx) return MVN_ERR_ARG;
+    MVN_TRY(check_qmc(ctx, qmc));
+    MVN_TRY(check_problem_host(ctx, n, a, b, L, ld));
+    if (!out3) return mvn_fail(ctx, MVN_ERR_ARG, "out3 is null");
+    if (prec != MVN_FP64 && prec != MVN_MIXED && prec != MVN_MIXED_SIMT)
+        return mvn_fail(ctx, MVN_ERR_ARG, "unknown precision");
+    MVN_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (prec == MVN_FP64)
+        return sov_grad_run<double>(ctx, n, a, b, L, ld, qmc, out3, dlogp_da, dlogp_db, dlogp_dL);
+    return sov_grad_run<float>(ctx, n, a, b, L, ld, qmc, out3, dlogp_da, dlogp_db, dlogp_dL);
 }

@@ -159,3 +159,60 @@ def test_w4_gradients_vs_central_fd(mvn):
     fd = (f(b0 + h * v, s2, rg) - f(b0 - h * v, s2, rg)) / (2 * h)
     dd = float((bt.grad * v).sum())
     assert abs(dd - fd) <= 1e-5 * max(1.0, abs(fd)), (dd, fd)
+
+
+@pytest.mark.parametrize("n,Ns,M", [(20, 100, 3), (150, 64, 4), (600, 97, 3)])
+def test_sov_grad_mixed_vs_oracle(mvn, n, Ns, M):
+    """The mixed adjoint (FP32 limit sums and transformed variables, FP64 elementwise terms)
+    against the FP64 oracle on identical lattice points.  The test field is strongly correlated
+    (conditional standard deviations L_ii down to 0.07, so FP32 errors of the limit sums grow
+    ~15x in a' and b') and the per-dimension errors add up along log P: the bound is
+    |d log P| <= 1e-4 + 2e-7 n (a CPU emulation of the kernel's blocked FP32 sums gives 8e-5 at
+    n = 600, log P = -938; one unblocked FP32 chain gives 6.6e-4).  Every gradient entry within
+    5e-5 of the largest."""
+    S, a, b = _problem(n, n)
+    Lo, _ = oracle.cholesky(S)
+    q = oracle.QMC(Ns, M, 5 + n)
+    logP, ga, gb, gL = oracle.sov_grad(a, b, Lo, q)
+    L = mvn.to_colmajor(_t(Lo))
+    out3, ga_g, gb_g, gL_g = mvn.mvn_sov_grad(_t(a), _t(b), L, Ns, M, 5 + n, prec="mixed",
+                                              want_L=True)
+    mvn.sync()
+    o = out3.cpu().numpy()
+    scale = max(1.0, np.abs(gb).max(), np.abs(ga).max())
+    e_lp = abs(o[0] - logP)
+    e_a = np.abs(ga_g.cpu().numpy() - ga).max() / scale
+    e_b = np.abs(gb_g.cpu().numpy() - gb).max() / scale
+    e_L = np.abs(np.tril(gL_g.cpu().numpy()) - np.tril(gL)).max() / max(1.0, np.abs(gL).max())
+    print(f"mixed adjoint n={n}: dlogP {e_lp:.2e} da {e_a:.2e} db {e_b:.2e} dL {e_L:.2e}")
+    assert e_lp <= 1e-4 + 2e-7 * n
+    assert max(e_a, e_b, e_L) <= 5e-5
+
+
+def test_w4_mixed_gradients_vs_fp64(mvn):
+    """Workload W4 through the autograd chain with prec="mixed" (tensor-core Cholesky, mixed
+    sweep adjoint) against prec="fp64" (whose gradients the oracle and finite-difference tests
+    pin): log P within 1e-4 and every gradient within 1e-3 relative."""
+    from paper_2405_14892_gb300.autograd import mvn_log_prob
+    w = inputs.WORKLOADS["W4"]
+    c = _t(inputs.grid_coords(w["g"]))
+    n = c.shape[0]
+    _, b = inputs.limits_for(w, n)
+    kw = dict(nu=w["nu"], nugget=w["nugget"], n_points=w["Ns"], n_shifts=w["M"], seed=w["seed"])
+    res = {}
+    for prec in ("fp64", "mixed"):
+        bt = _t(b).requires_grad_(True)
+        s2t = torch.tensor(w["sigma2"], dtype=torch.float64, device="cuda", requires_grad=True)
+        rgt = torch.tensor(w["range"], dtype=torch.float64, device="cuda", requires_grad=True)
+        lp = mvn_log_prob(bt, s2t, rgt, c, prec=prec, **kw)
+        lp.backward()
+        res[prec] = (lp.item(), bt.grad.cpu().numpy(), s2t.grad.item(), rgt.grad.item())
+    l64, gb64, s64, r64 = res["fp64"]
+    lmx, gbmx, smx, rmx = res["mixed"]
+    e_b = np.abs(gbmx - gb64).max() / max(1.0, np.abs(gb64).max())
+    e_s = abs(smx - s64) / max(1.0, abs(s64))
+    e_r = abs(rmx - r64) / max(1.0, abs(r64))
+    print(f"W4 mixed vs fp64: logP {lmx:.8f} vs {l64:.8f} (d {abs(lmx - l64):.2e}); "
+          f"db {e_b:.2e} dsigma2 {e_s:.2e} drange {e_r:.2e}")
+    assert abs(lmx - l64) <= 1e-4
+    assert max(e_b, e_s, e_r) <= 1e-3

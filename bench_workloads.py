@@ -94,6 +94,16 @@ def run(args):
                                          prefix_dims=dims, prec="mixed")
         ms_exc = _timed(exc, steps, warm, stream)
         r = res["r"]
+        # the same pipeline captured once as a CUDA graph: one launch per confidence region
+        G = mvn.mvn_excursion_graph(mud, Sd, w["u"], w["level"], w["Ns"], w["M"], w["seed"],
+                                    prefix_dims=dims, prec="mixed")
+        l0 = ctx.launches()
+        ms_graph = _timed(G.launch, steps, warm, stream)
+        graph_launches = (ctx.launches() - l0) // (steps + warm) * steps
+        if G.sync() != 0:
+            raise RuntimeError("graph replay raised a device error")
+        same = all(torch.equal(G.result[k], r[k]) for k in ("order", "F", "region"))
+        G.close()
         order = r["order"].cpu().numpy()
         Lp = mvn.to_colmajor(t(Spost[np.ix_(order, order)]))
         mvn.mvn_cholesky(Lp)
@@ -116,9 +126,13 @@ def run(args):
         sd_sample = sum(int(dims[p]) ** 2 for p in sample)
         sd_all = sum(int(k) ** 2 for k in dims)
         ms_loop = ms_loop_sample * sd_all / sd_sample
-        _line(args, w["name"], "confidence-region MVN probs/s (256 prefix problems, one sweep)",
-              len(dims) / (ms_exc * 1e-3), "probs/s", ms_exc,
-              {"dtype": "f64+f32+fp16x2", "batched_independent_ms": ms_bat,
+        _line(args, w["name"],
+              "confidence-region MVN probs/s (256 prefix problems, one sweep, one graph launch)",
+              len(dims) / (ms_graph * 1e-3), "probs/s", ms_graph,
+              {"dtype": "f64+f32+fp16x2+bf16 digits", "eager_ms": ms_exc,
+               "eager_probs_per_sec": len(dims) / (ms_exc * 1e-3),
+               "graph_equals_eager": bool(same), "gpu_launches": graph_launches,
+               "kernels_per_graph": G.kernels, "batched_independent_ms": ms_bat,
                "batched_probs_per_sec": len(dims) / (ms_bat * 1e-3),
                "loop_fp64_single_ms_estimated": ms_loop,
                "loop_sample": f"{len(sample)} of {len(dims)} problems timed, scaled by sum k^2",

@@ -210,12 +210,42 @@ mvn_status mvn_sov_fp64_noalloc(int n, const double* a, const double* b, const d
  *   lengths k_t = prefix_dims[t] (host array, NULL = all 1..n, then nprob = n);
  *   region[i] = 1 for i in order[0..K), K = the largest listed k_t with F[t] >= 1-alpha.
  * The prefix problems share the lattice, so every F[t] comes from one sweep over n dimensions.
+ * prec: the factorisation of Sigma[order, order] and the sweep as in mvn_cholesky and mvn_sov
+ * (MVN_MIXED: tensor-core Cholesky and sweep; MVN_MIXED_SIMT: FP64 Cholesky, FP32 sweep).
  * mu (n), Sigma (n x n, ld, lower triangle read) are inputs; order (int32, n), marginal (n),
  * F (nprob), region (uint8, n) are outputs.  Workspace holds the permuted factor (n x n). */
 mvn_status mvn_excursion(mvn_ctx* ctx, int n, const double* mu, const double* Sigma,
                          int64_t ld, double u, double one_minus_alpha, int nprob,
                          const int* prefix_dims, const mvn_qmc* qmc, mvn_prec prec, int tile,
                          int32_t* order, double* marginal, double* F, uint8_t* region);
+
+/* The confidence-region pipeline of mvn_excursion (marginals, order, permuted Cholesky, the
+ * prefix sweep, estimates, region) captured once into a CUDA graph and replayed with one launch
+ * (Alg. 1 run repeatedly on fields of one shape, e.g. successive posterior updates).
+ * Arguments as in mvn_excursion.  The call runs the pipeline once eagerly (outputs valid after
+ * it returns; a non-positive pivot fails the call with MVN_ERR_NOT_PD), then captures the same
+ * work on a private stream.  The graph owns a private workspace, lattice table and status word,
+ * so calls on ctx between launches cannot disturb it; it allocates them here (the workspace of
+ * mvn_excursion for this size, plus the three index tables).
+ * Every launch reads mu and Sigma from the device buffers given here (their contents may change
+ * between launches) and writes order, marginal, F and region given here; these buffers must
+ * outlive the graph.  Launches of one graph must not overlap (launch it on one stream).
+ * Synchronous.  Errors: as mvn_excursion; MVN_ERR_CUDA if capture or instantiation fails. */
+typedef struct mvn_graph mvn_graph;
+mvn_status mvn_excursion_graph(mvn_ctx* ctx, int n, const double* mu, const double* Sigma,
+                               int64_t ld, double u, double one_minus_alpha, int nprob,
+                               const int* prefix_dims, const mvn_qmc* qmc, mvn_prec prec,
+                               int32_t* order, double* marginal, double* F, uint8_t* region,
+                               mvn_graph** out);
+/* Enqueue one replay of the graph on the stream of the context it was created with. */
+mvn_status mvn_graph_launch(mvn_graph* g);
+/* Wait for that stream; return (and clear) the graph's device status word (info as in
+ * mvn_sync). */
+mvn_status mvn_graph_sync(mvn_graph* g, int* info);
+/* Number of kernels one launch of the graph runs. */
+int64_t mvn_graph_kernels(const mvn_graph* g);
+/* Wait for the creating context's stream, then free the graph and everything it owns. */
+mvn_status mvn_graph_destroy(mvn_graph* g);
 
 /* ------------------------------------------------------------------ tile low-rank (Sec. III-E) */
 

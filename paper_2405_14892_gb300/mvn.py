@@ -59,6 +59,12 @@ SIGNATURES = {
     "mvn_sov_grad": (_I, [_P, _I, _P, _P, _P, _I64, _QP, _I, _P, _P, _P, _P]),
     "mvn_sov_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _I64, _QP, _I, _P]),
     "mvn_excursion": (_I, [_P, _I, _P, _P, _I64, _D, _D, _I, _P, _QP, _I, _I, _P, _P, _P, _P]),
+    "mvn_excursion_graph": (_I, [_P, _I, _P, _P, _I64, _D, _D, _I, _P, _QP, _I, _P, _P, _P, _P,
+                                 ctypes.POINTER(_P)]),
+    "mvn_graph_launch": (_I, [_P]),
+    "mvn_graph_sync": (_I, [_P, ctypes.POINTER(_I)]),
+    "mvn_graph_kernels": (_I64, [_P]),
+    "mvn_graph_destroy": (_I, [_P]),
     "mvn_tlr_compress": (_I, [_P, _I, _P, _I64, _I, _D, _I, ctypes.POINTER(_P),
                               ctypes.POINTER(_I)]),
     "mvn_tlr_cholesky": (_I, [_P, _P, ctypes.POINTER(_I)]),
@@ -315,6 +321,66 @@ def mvn_excursion(mu: torch.Tensor, Sigma: torch.Tensor, u: float, level: float,
                                 PREC[prec], 0, _P(order.data_ptr()), _P(marg.data_ptr()),
                                 _P(F.data_ptr()), _P(region.data_ptr())))
     return dict(order=order, marginal=marg, F=F, region=region)
+
+
+class ExcursionGraph:
+    """The confidence-region pipeline captured as one CUDA graph (mvn_excursion_graph).  Every
+    launch() re-reads the mu and Sigma tensors given at creation (update them in place) and
+    rewrites the output tensors in .result."""
+
+    def __init__(self, handle, ctx, keep, result):
+        self.h = handle
+        self.ctx = ctx
+        self._keep = keep          # the input tensors the graph reads
+        self.result = result
+        self.kernels = int(lib().mvn_graph_kernels(handle))
+
+    def launch(self):
+        self.ctx.check(lib().mvn_graph_launch(self.h))
+
+    def sync(self) -> int:
+        info = _I(0)
+        self.ctx.check(lib().mvn_graph_sync(self.h, ctypes.byref(info)))
+        return info.value
+
+    def close(self):
+        if self.h:
+            lib().mvn_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mvn_excursion_graph(mu: torch.Tensor, Sigma: torch.Tensor, u: float, level: float,
+                        n_points: int, n_shifts: int, seed: int, prefix_dims=None, prec="fp64",
+                        err_k=3.0) -> ExcursionGraph:
+    """Capture mvn_excursion's pipeline for these buffers into a CUDA graph (runs it once)."""
+    n = mu.numel()
+    Sp, ld = _mat(Sigma, n, "Sigma")
+    dev = mu.device
+    order = torch.empty(n, dtype=torch.int32, device=dev)
+    marg = torch.empty(n, dtype=torch.float64, device=dev)
+    region = torch.empty(n, dtype=torch.uint8, device=dev)
+    if prefix_dims is None:
+        nprob, pk = n, None
+    else:
+        nprob = len(prefix_dims)
+        pk = (ctypes.c_int * nprob)(*[int(x) for x in prefix_dims])
+    F = torch.empty(nprob, dtype=torch.float64, device=dev)
+    q = _qmc(n_points, n_shifts, seed, err_k)
+    c = context()
+    h = _P()
+    c.check(lib().mvn_excursion_graph(c.h, n, _vec(mu, n, "mu"), Sp, ld, u, level, nprob,
+                                      ctypes.cast(pk, _P) if pk is not None else None,
+                                      ctypes.byref(q), PREC[prec], _P(order.data_ptr()),
+                                      _P(marg.data_ptr()), _P(F.data_ptr()),
+                                      _P(region.data_ptr()), ctypes.byref(h)))
+    return ExcursionGraph(h, c, (mu, Sigma),
+                          dict(order=order, marginal=marg, F=F, region=region))
 
 
 def mvn_lattice_alpha(n: int) -> torch.Tensor:

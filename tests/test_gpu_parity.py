@@ -290,6 +290,58 @@ def test_excursion_all_prefixes_and_ties(mvn):
     assert np.array_equal(r["region"].cpu().numpy(), ref["region"])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_excursion_graph_replays_match_eager(mvn, prec):
+    """The captured confidence-region pipeline (mvn_excursion_graph) gives bit-identical results
+    to the eager call, on the field it was captured with and, after the field is updated in
+    place, on the new field; two launches in a row."""
+    g = 11
+    c = inputs.grid_coords(g)
+    n = g * g
+    S = mvn.to_colmajor(_t(oracle.matern(c, 1.0, 0.15, 0.5, nugget=1e-6)))
+    mu0 = 0.9 + 0.7 * inputs.standard_normals(n, 41)
+    mu1 = 1.0 + 0.6 * inputs.standard_normals(n, 42)
+    ks = [2, 9, 40, 41, 77, n]
+    mud = _t(mu0)
+    G = mvn.mvn_excursion_graph(mud, S, 0.8, 0.9, 96, 4, 23, prefix_dims=ks, prec=prec)
+    try:
+        for mu in (mu0, mu1, mu1):
+            mud.copy_(_t(mu))
+            G.launch()
+            assert G.sync() == 0
+            ref = mvn.mvn_excursion(_t(mu), S, 0.8, 0.9, 96, 4, 23, prefix_dims=ks, prec=prec)
+            mvn.sync()
+            for k in ("order", "marginal", "F", "region"):
+                assert torch.equal(G.result[k], ref[k]), k
+        assert G.kernels > 10
+    finally:
+        G.close()
+
+
+def test_excursion_mixed_vs_oracle(mvn):
+    """MVN_MIXED confidence region (tensor-core Cholesky of the permuted covariance and
+    tensor-core sweep) against the FP64 oracle: order bit-exact, |d log F| <= 1e-4 (the bound
+    stated for the mixed paths), and the region equal wherever F is not within that bound of
+    the level."""
+    g = 12
+    c = inputs.grid_coords(g)
+    n = g * g
+    S = oracle.matern(c, 1.0, 0.15, 0.5)
+    mu = 0.9 + 0.7 * inputs.standard_normals(n, 31)
+    ks = [1, 3, 17, 50, 51, 100, n]
+    r = mvn.mvn_excursion(_t(mu), mvn.to_colmajor(_t(S)), 0.8, 0.9, 128, 4, 17, prefix_dims=ks,
+                          prec="mixed")
+    mvn.sync()
+    ref = oracle.excursion(mu, S, 0.8, 0.9, oracle.QMC(128, 4, 17), prefix_dims=ks)
+    assert np.array_equal(r["order"].cpu().numpy(), ref["order"])
+    F = r["F"].cpu().numpy()
+    d = np.abs(np.log(F) - np.log(ref["F"]))
+    print(f"mixed excursion: max |d log F| {d.max():.2e}")
+    assert d.max() <= 1e-4
+    if np.all(np.abs(np.log(ref["F"]) - np.log(0.9)) > 1e-4):
+        assert np.array_equal(r["region"].cpu().numpy(), ref["region"])
+
+
 # ------------------------------------------------------------------ mixed path: stated error
 
 def test_mixed_simt_error_w4(mvn):

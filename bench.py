@@ -284,6 +284,9 @@ def run_gpu(args):
         if timed_phases:
             ev["s3"].record(stream)
 
+    # launch shapes picked by the library's autotuner for this size (untimed; the JSON-lines
+    # cache named by MVN_TUNE_CACHE is reused when it has this device and size)
+    tuned = mvn.mvn_autotune(n, Ntot, prec, cache=os.environ.get("MVN_TUNE_CACHE"))
     for _ in range(args.warmup):
         step(False)
     torch.cuda.synchronize()
@@ -363,7 +366,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": w["name"], "n": n, "paths": Ntot, "shifts": M, "points": Ns,
                    "prec": prec, "l2": "inputs larger than L2 (Sigma n^2 FP64 = 2.1 GB)",
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": f"replicas{world}", "launch_shapes_autotuned": tuned},
         "probs_per_sec": world / (ms * 1e-3),
         "phases_ms": {"matern": statistics.median(phase["matern"]), "cholesky": chol_ms,
                       "sov": sov_ms},

@@ -88,6 +88,7 @@ def run(args):
         dims = inputs.prefix_problem_dims(w["nprob"], w["dims_lo"], w["dims_hi"], w["dims_seed"])
         mud, Sd = t(mu), mvn.to_colmajor(t(Spost))
         res = {}
+        tuned = mvn.mvn_autotune(n, w["Ns"] * w["M"], "mixed")
 
         def exc():
             res["r"] = mvn.mvn_excursion(mud, Sd, w["u"], w["level"], w["Ns"], w["M"], w["seed"],
@@ -132,6 +133,7 @@ def run(args):
               {"dtype": "f64+f32+fp16x2+bf16 digits", "eager_ms": ms_exc,
                "eager_probs_per_sec": len(dims) / (ms_exc * 1e-3),
                "graph_equals_eager": bool(same), "gpu_launches": graph_launches,
+               "launch_shapes_autotuned": tuned,
                "kernels_per_graph": G.kernels, "batched_independent_ms": ms_bat,
                "batched_probs_per_sec": len(dims) / (ms_bat * 1e-3),
                "loop_fp64_single_ms_estimated": ms_loop,

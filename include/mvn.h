@@ -266,6 +266,38 @@ mvn_status mvn_tlr_to_dense(mvn_ctx* ctx, const mvn_tlr* tlr, double* L, int64_t
 mvn_status mvn_tlr_ranks(const mvn_tlr* tlr, int* ranks);
 mvn_status mvn_tlr_free(mvn_tlr* tlr);
 
+/* ------------------------------------------------------------------ autotuner (launch shapes) */
+
+/* Launch shapes of the hot kernels (not in the paper, whose tile size is a parameter of its CPU
+ * runtime).  No choice changes a result bit: the MVN_MIXED Cholesky update sums exact integers
+ * in any order, and the sweeps compute every path on its own whatever the grid.
+ *   chol_bulk_p, chol_tail_p: K sub-chunks (32 columns each) per work item (one CTA) of the bulk
+ *     and the tail update of a block column in the MVN_MIXED Cholesky (defaults 16 and 2);
+ *   sweep_ctas_per_sm: persistent grid of the sweep, CTAs per SM (tensor-core sweep 1..2,
+ *     CUDA-core sweeps 1..3; default 2);
+ *   from_cache: 1 if mvn_autotune took the entry from its cache file, else 0. */
+typedef struct {
+    int32_t chol_bulk_p;
+    int32_t chol_tail_p;
+    int32_t sweep_ctas_per_sm;
+    int32_t from_cache;
+} mvn_tune_result;
+
+/* Pick the launch shapes for problems of dimension n with n_paths lattice paths at precision
+ * prec: time every candidate on a synthetic problem of that size on the context's device (an
+ * exponential covariance on a regular grid, b = 0.5; the Cholesky at order n, the sweep on the
+ * same number of 128-path tiles over min(n, 2048) dimensions), keep the fastest in the context
+ * (used by later calls whose n and path-tile count fall in the same power-of-two buckets) and,
+ * if cache_path (host string) is not NULL, append it there as one JSON line keyed by device
+ * name, SM count, precision and the two buckets.  A matching line already in cache_path is used
+ * without timing.  Synchronous; allocates ~2 n^2 * 8 bytes while it runs; *out (host) receives
+ * the choice.  Errors: MVN_ERR_ARG (n outside 1..65536), MVN_ERR_OOM, MVN_ERR_CUDA. */
+mvn_status mvn_autotune(mvn_ctx* ctx, int n, int64_t n_paths, mvn_prec prec,
+                        const char* cache_path, mvn_tune_result* out);
+/* Set the launch shapes for (n, n_paths, prec) by hand (host struct; from_cache ignored). */
+mvn_status mvn_tune_set(mvn_ctx* ctx, int n, int64_t n_paths, mvn_prec prec,
+                        const mvn_tune_result* params);
+
 /* ------------------------------------------------------------------ lattice tables (testing) */
 
 /* Copy the lattice generators alpha_0..alpha_{n-1} (u64, see mvn_qmc) to the device buffer out.

@@ -43,8 +43,8 @@
 #define OZ_DW 8             // drain warps
 #define OZ_THREADS (32 * (OZ_DW + 2))
 #define OZ_WAIT 4000000000LL
-#define OZ_BULK_P 16        // K sub-chunks per work item of the bulk update (short CTAs: the
-                            // chain kernels get SMs as they retire)
+// K sub-chunks per work item of the bulk and tail updates: TuneParams (default 16 and 2; short
+// CTAs, so that the chain kernels get SMs as they retire)
 
 __device__ __forceinline__ bool oz_failed(const int* status) {
     return *(volatile const int*)status != 0;
@@ -778,6 +778,7 @@ static mvn_status oz_update_launch(mvn_ctx* ctx, cudaStream_t st, int n, int nrt
 mvn_status chol_oz_launch(mvn_ctx* ctx, int n, double* A, int64_t ld, char* ws) {
     const int nrt = oz_nrt(n), nbc = oz_nbc(n);
     const int64_t ldT = (int64_t)nrt * OZ_RT;
+    const TuneParams tp = tune_chol(ctx, n);
     WsCarver wc(ws);
     int* E = wc.take<int>((size_t)n);
     uint8_t* Z = wc.take<uint8_t>((size_t)2 * nbc * OZ_S * nrt * OZ_AT);
@@ -808,13 +809,15 @@ mvn_status chol_oz_launch(mvn_ctx* ctx, int n, double* A, int64_t ld, char* ws) 
         if (j >= 1 && j + 1 < nbc) {
             MVN_CUDA(ctx, cudaStreamWaitEvent(lo, ev_split, 0));
             long long* Tn = T + (size_t)((j + 1) & 1) * OZ_NB * ldT;
-            MVN_TRY(oz_update_launch(ctx, lo, n, nrt, j + 1, 0, j, OZ_BULK_P, Z, E, Tn, ldT, ssm));
+            MVN_TRY(oz_update_launch(ctx, lo, n, nrt, j + 1, 0, j, tp.chol_bulk_p, Z, E, Tn, ldT,
+                                     ssm));
             MVN_CUDA(ctx, cudaEventRecord(ev_bulk[(j + 1) & 1], lo));
             lo_used = true;
         }
         if (j >= 1) {
             // tail of column j (block column j-1), then wait for its bulk
-            MVN_TRY(oz_update_launch(ctx, hi, n, nrt, j, j - 1, j, 2, Z, E, Tj, ldT, ssm));
+            MVN_TRY(oz_update_launch(ctx, hi, n, nrt, j, j - 1, j, tp.chol_tail_p, Z, E, Tj, ldT,
+                                     ssm));
             if (j >= 2) MVN_CUDA(ctx, cudaStreamWaitEvent(hi, ev_bulk[j & 1], 0));
         }
         // the digits of block column j are written by POTRF (diagonal rows) and TRSM (the rows

@@ -311,6 +311,7 @@ extern "C" mvn_status mvn_excursion_graph(mvn_ctx* ctx, int n, const double* mu,
     if ((st = mvn_create(&g->priv, ctx->device, g->cap)) != MVN_OK)
         return fail(st, "context creation failed");
     mvn_ctx* pv = g->priv;
+    pv->tune = ctx->tune;  // the caller's autotuned launch shapes
     const size_t tb = ws_round(sizeof(int) * pl.nprob);
     if (cudaMalloc(&g->d_tables, 3 * tb) != cudaSuccess)
         return fail(MVN_ERR_OOM, "table allocation failed");

@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -16,6 +17,15 @@
 //   [1] LAPACK-style info of the last failed factorisation (1-based column)
 //   [2] scratch counter used by persistent kernels
 #define MVN_STATUS_WORDS 8
+
+// Launch shapes the autotuner chooses (mvn_tune.cu); every choice gives bit-identical results
+// (the Cholesky update sums exact integers, the sweeps are per path), only the time differs.
+struct TuneParams {
+    int chol_bulk_p = 16;      // K sub-chunks (32 wide) per work item of the bulk Cholesky update
+    int chol_tail_p = 2;       // the same for the tail update (one 64-wide block column)
+    int tc_ctas_per_sm = 2;    // persistent grid of the tensor-core sweep
+    int simt_ctas_per_sm = 2;  // persistent grid of the CUDA-core sweep
+};
 
 struct mvn_ctx {
     int device = 0;
@@ -35,6 +45,8 @@ struct mvn_ctx {
     // and joins it again within one call (created on first use)
     cudaStream_t aux[2] = {nullptr, nullptr};
     cudaEvent_t aux_ev[8] = {};
+    // autotuned launch shapes, keyed by (precision, log2 bucket of n, log2 bucket of path tiles)
+    std::map<std::tuple<int, int, int>, TuneParams> tune;
     // per-kernel timing (mvn_timing): CUDA events recorded around selected launches
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -88,6 +100,11 @@ mvn_status mvn_fail(mvn_ctx* ctx, mvn_status st, const char* fmt, ...);
         (ctx)->launches++;                                                                   \
         MVN_CUDA((ctx), cudaGetLastError());                                                 \
     } while (0)
+
+// Tuned launch shapes for a Cholesky of order n (MVN_MIXED) and for a sweep of problems of
+// dimension up to n over `ntiles` 128-path tiles; defaults where the tuner has no entry.
+TuneParams tune_chol(const mvn_ctx* ctx, int n);
+TuneParams tune_sweep(const mvn_ctx* ctx, mvn_prec prec, int n, int64_t ntiles);
 
 // Workspace: reserve `bytes` (256-byte aligned partition) of the arena, growing it if needed.
 // Growth synchronises the stream first (an allocation never happens mid-stream).

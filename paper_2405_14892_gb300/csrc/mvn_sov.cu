@@ -136,15 +136,15 @@ mvn_status check_limits_device(mvn_ctx* ctx, int n, const double* a, const doubl
     return MVN_OK;
 }
 
-static int sov_grid(mvn_ctx* ctx, int64_t ntiles) {
-    const int occ = 2;
+static int sov_grid(mvn_ctx* ctx, mvn_prec prec, int nmax, int64_t ntiles) {
+    const int occ = tune_sweep(ctx, prec, nmax, ntiles).simt_ctas_per_sm;
     int64_t g = std::min<int64_t>(ntiles, (int64_t)ctx->sm_count * occ);
     return (int)std::max<int64_t>(g, 1);
 }
 
 size_t sov_simt_ws_bytes(mvn_ctx* ctx, int nprob, int nmax, int64_t ntiles, mvn_prec prec) {
     const size_t elt = (prec == MVN_FP64) ? sizeof(double) : sizeof(float);
-    const int grid = sov_grid(ctx, ntiles);
+    const int grid = sov_grid(ctx, prec, nmax, ntiles);
     size_t b = ws_round(sizeof(int));
     if (nprob > 1)
         b += ws_round(sizeof(SovProblem) * nprob) + ws_round(sizeof(int2) * (size_t)ntiles);
@@ -164,7 +164,7 @@ mvn_status sov_run_simt(mvn_ctx* ctx, const std::vector<SovProblem>& probs_h, mv
     if (ntiles == 0) return MVN_OK;
     if (ntiles > (1 << 30)) return mvn_fail(ctx, MVN_ERR_ARG, "too many path tiles");
     const bool f64 = (prec == MVN_FP64);
-    const int grid = sov_grid(ctx, ntiles);
+    const int grid = sov_grid(ctx, prec, nmax, ntiles);
     const size_t elt = f64 ? sizeof(double) : sizeof(float);
     const int64_t ystride = (int64_t)std::max(nmax, 1) * SOV_P;
     WsCarver wc(ws);

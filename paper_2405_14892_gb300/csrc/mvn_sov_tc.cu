@@ -566,9 +566,10 @@ __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
 
 static size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 
-static int tc_grid(mvn_ctx* ctx, int64_t ntiles) {
-    // two CTAs per SM (shared memory ~103 KB, 256 TMEM columns each)
-    return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 2 * (int64_t)ctx->sm_count));
+static int tc_grid(mvn_ctx* ctx, int nmax, int64_t ntiles) {
+    // up to two CTAs per SM (shared memory ~103 KB, 256 TMEM columns each); the autotuner picks
+    const int per_sm = tune_sweep(ctx, MVN_MIXED, nmax, ntiles).tc_ctas_per_sm;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, per_sm * (int64_t)ctx->sm_count));
 }
 
 static int tc_nsb(int n) { return (std::max(n, 1) + TC_N - 1) / TC_N; }
@@ -586,7 +587,7 @@ size_t sov_tc_ws_bytes(mvn_ctx* ctx, int nprob, int nmax, int64_t ntiles) {
     if (nprob > 1)
         b += ws_round(sizeof(SovProblem) * nprob) + ws_round(sizeof(int2) * (size_t)ntiles);
     b += tc_factor_bytes(nsb);
-    b += ws_round((size_t)tc_grid(ctx, ntiles) * nsb * 4 * 2 * TC_TILE);
+    b += ws_round((size_t)tc_grid(ctx, nmax, ntiles) * nsb * 4 * 2 * TC_TILE);
     return b;
 }
 
@@ -627,7 +628,7 @@ mvn_status sov_run_tc(mvn_ctx* ctx, const std::vector<SovProblem>& probs_h, char
     }
     if (ntiles == 0) return MVN_OK;
     const int nsb = tc_nsb(nmax);
-    const int grid = tc_grid(ctx, ntiles);
+    const int grid = tc_grid(ctx, nmax, ntiles);
     WsCarver wc(ws);
     TcBatch bt;
     memset(&bt, 0, sizeof(bt));

@@ -37,6 +37,11 @@ class mvn_qmc(ctypes.Structure):
                 ("err_k", ctypes.c_double)]
 
 
+class mvn_tune_result(ctypes.Structure):
+    _fields_ = [("chol_bulk_p", ctypes.c_int32), ("chol_tail_p", ctypes.c_int32),
+                ("sweep_ctas_per_sm", ctypes.c_int32), ("from_cache", ctypes.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -65,6 +70,8 @@ SIGNATURES = {
     "mvn_graph_sync": (_I, [_P, ctypes.POINTER(_I)]),
     "mvn_graph_kernels": (_I64, [_P]),
     "mvn_graph_destroy": (_I, [_P]),
+    "mvn_autotune": (_I, [_P, _I, _I64, _I, ctypes.c_char_p, ctypes.POINTER(mvn_tune_result)]),
+    "mvn_tune_set": (_I, [_P, _I, _I64, _I, ctypes.POINTER(mvn_tune_result)]),
     "mvn_tlr_compress": (_I, [_P, _I, _P, _I64, _I, _D, _I, ctypes.POINTER(_P),
                               ctypes.POINTER(_I)]),
     "mvn_tlr_cholesky": (_I, [_P, _P, ctypes.POINTER(_I)]),
@@ -381,6 +388,25 @@ def mvn_excursion_graph(mu: torch.Tensor, Sigma: torch.Tensor, u: float, level: 
                                       _P(region.data_ptr()), ctypes.byref(h)))
     return ExcursionGraph(h, c, (mu, Sigma),
                           dict(order=order, marginal=marg, F=F, region=region))
+
+
+def mvn_autotune(n: int, n_paths: int, prec: str = "mixed", cache: str | None = None) -> dict:
+    """Time the candidate launch shapes for (n, n_paths, prec) on this device, keep the fastest
+    in the context (and in the JSON-lines file `cache`, if given); returns the choice."""
+    r = mvn_tune_result()
+    c = context()
+    c.check(lib().mvn_autotune(c.h, n, n_paths, PREC[prec],
+                               cache.encode() if cache else None, ctypes.byref(r)))
+    return {"chol_bulk_p": r.chol_bulk_p, "chol_tail_p": r.chol_tail_p,
+            "sweep_ctas_per_sm": r.sweep_ctas_per_sm, "from_cache": bool(r.from_cache)}
+
+
+def mvn_tune_set(n: int, n_paths: int, prec: str, chol_bulk_p: int = 16, chol_tail_p: int = 2,
+                 sweep_ctas_per_sm: int = 2) -> None:
+    """Set the launch shapes for (n, n_paths, prec) by hand."""
+    r = mvn_tune_result(chol_bulk_p, chol_tail_p, sweep_ctas_per_sm, 0)
+    c = context()
+    c.check(lib().mvn_tune_set(c.h, n, n_paths, PREC[prec], ctypes.byref(r)))
 
 
 def mvn_lattice_alpha(n: int) -> torch.Tensor:

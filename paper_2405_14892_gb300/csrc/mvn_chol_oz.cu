@@ -390,13 +390,17 @@ __device__ __forceinline__ DF df_rcp(DF l) {
 
 // POTRF of the diagonal block (c0, c0), nb <= 64, after applying the update, and the inverse
 // W = L_jj^-1 for the panel solve (double-float).  256 threads as a 16 x 16 grid; thread (ty, tx)
-// with tx <= ty keeps the 4 x 4 blocks (rows 4 ty .., columns 4 tx ..) of S (becoming L) and of W
-// in registers.  Step k of the right-looking sweep: the owner of S(k, k) publishes 1 / L_kk; the
-// owners of column k of L and of row k of W scale them and publish them; every thread updates its
-// entries S(i, m) -= L(i, k) L(m, k) (k < m <= i) and W(i, c) -= L(i, k) W(k, c) (c <= k < i).
-// (W = L^-1 is the column-oriented forward substitution L W = I riding along the same sweep.)
-// Rows and columns beyond nb are the identity, so the padded factor stays regular.  Writes L_jj
-// to A (FP64), W^T as pairs Wt[u][c] = W[c][u], and the digits of the diagonal rows.
+// with tx <= ty keeps the 4 x 4 block X (rows 4 ty .., columns 4 tx ..) in registers.
+// One array carries both factors: at step k of the right-looking sweep the columns m > k of X
+// hold the Schur complement S, the columns m <= k hold W (the column-oriented forward
+// substitution L W = I riding along), so the two updates of step k are one symmetric rank-1
+// update of the rows i > k:
+//     X(i, m) -= V(i) V(m),   V(m) = L(m, k) for m > k,  V(m) = W(k, m) for m <= k,
+// where W(k, m) = X(k, m) / L_kk (m < k) and W(k, k) = 1 / L_kk; column k itself is zeroed by
+// its owners before the update (W(i, k) = -L(i, k) W(k, k)).  Columns of L leave the array as
+// they are finished (staged in shared memory).  Rows and columns beyond nb are the identity and
+// are never touched.  Writes L_jj to A (FP64), W^T as pairs Wt[u][c] = W[c][u], and the digits of
+// the diagonal rows.
 __device__ __forceinline__ DF df_sel4(const DF (&x)[4], int b) {
     DF v = x[0];
     if (b == 1) v = x[1];
@@ -410,10 +414,10 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
                                                   long long* __restrict__ T, int64_t ldT,
                                                   float* __restrict__ Wt, uint8_t* __restrict__ Z,
                                                   int nrt, int* status) {
-    __shared__ DF colk[2][OZ_NB], rowk[2][OZ_NB];  // L(:, k) and W(k, :), by step parity
-    __shared__ DF piv;                         // 1 / L_kk
-    __shared__ float Sh[OZ_NB][OZ_NB + 1], Sl[OZ_NB][OZ_NB + 1];  // staging (load, store, digits)
-    __shared__ DF rinv[OZ_NB];
+    __shared__ DF Vs[2][OZ_NB];  // step vector V, by step parity
+    __shared__ DF piv[2];        // 1 / L_kk, by step parity
+    // staging: the loaded block, then the columns of L as they are finished
+    __shared__ float Sh[OZ_NB][OZ_NB + 1], Sl[OZ_NB][OZ_NB + 1];
     __shared__ int Eb[OZ_NB];
     __shared__ int bad;
     if (oz_failed(status)) return;
@@ -421,11 +425,6 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
     const bool act = (tx <= ty);
     if (t == 0) bad = 0;
     if (t < OZ_NB) Eb[t] = (t < nb) ? E[c0 + t] : 0;
-    if (t < 2 * OZ_NB) {
-        // finite contents from the start: masked updates multiply stale entries by zero
-        colk[t >> 6][t & 63] = DF{0.0f, 0.0f};
-        rowk[t >> 6][t & 63] = DF{0.0f, 0.0f};
-    }
     __syncthreads();
     {
         // all loads first (16 per thread, independent), then the update is applied
@@ -457,47 +456,48 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
         }
     }
     __syncthreads();
-    DF Lr[4][4], Wr[4][4];  // this thread's blocks of S/L and of W
+    DF X[4][4];  // this thread's block: lower entries of S, becoming W; upper entries unused
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int i = 4 * ty + a, m = 4 * tx + b;
-            Lr[a][b] = (act && m <= i) ? DF{Sh[i][m], Sl[i][m]} : DF{0.0f, 0.0f};
-            Wr[a][b] = (act && i == m) ? DF{1.0f, 0.0f} : DF{0.0f, 0.0f};
+            X[a][b] = (act && m <= i) ? DF{Sh[i][m], Sl[i][m]} : DF{0.0f, 0.0f};
         }
-    for (int k = 0; k < OZ_NB; ++k) {
+    __syncthreads();  // Sh/Sl now receive the finished columns of L
+    for (int k = 0; k < nb; ++k) {
         const int kb = k >> 2, kk = k & 3;
-        // pivot
-        if (act && ty == kb && tx == kb) {
+        DF* V = Vs[k & 1];
+        // pivot: L_kk = sqrt(S_kk); X(k, k) becomes W(k, k) = 1 / L_kk
+        if (ty == kb && tx == kb) {
             DF d = DF{0.0f, 0.0f};
 #pragma unroll
             for (int a = 0; a < 4; ++a)
-                if (a == kk) d = df_sel4(Lr[a], kk);
+                if (a == kk) d = df_sel4(X[a], kk);
             if (!(d.hi > 0.0f)) {
                 dev_raise(status, MVN_ERR_NOT_PD, c0 + k + 1);
                 bad = 1;
             } else {
                 const DF l = df_sqrt(d);
                 const DF r = df_rcp(l);
-                piv = r;
-                rinv[k] = r;
+                piv[k & 1] = r;
+                V[k] = r;
+                Sh[k][k] = l.hi;
+                Sl[k][k] = l.lo;
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
                     if (a == kk) {
 #pragma unroll
                         for (int b = 0; b < 4; ++b)
-                            if (b == kk) Lr[a][b] = l;
+                            if (b == kk) X[a][b] = r;
                     }
             }
         }
         __syncthreads();
         if (bad) return;
-        const DF r = piv;
-        DF* colp = colk[k & 1];
-        DF* rowp = rowk[k & 1];
-        // column k of L (rows > k) and row k of W (columns <= k), scaled by 1 / L_kk
-        if (act && tx == kb) {
+        const DF r = piv[k & 1];
+        // column k below the pivot: L(i, k) = S(i, k) / L_kk leaves the array (entry zeroed)
+        if (act && tx == kb && 4 * ty + 3 > k) {
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const int i = 4 * ty + a;
@@ -505,83 +505,67 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
                     DF v = DF{0.0f, 0.0f};
 #pragma unroll
                     for (int b = 0; b < 4; ++b)
-                        if (b == kk) v = df_mul(Lr[a][b], r);
-#pragma unroll
-                    for (int b = 0; b < 4; ++b)
-                        if (b == kk) Lr[a][b] = v;
-                    colp[i] = v;
+                        if (b == kk) {
+                            v = df_mul(X[a][b], r);
+                            X[a][b] = DF{0.0f, 0.0f};
+                        }
+                    V[i] = v;
+                    Sh[i][k] = v.hi;
+                    Sl[i][k] = v.lo;
                 }
             }
         }
-        if (act && ty == kb) {
+        // row k left of the pivot: W(k, c) = X(k, c) / L_kk, final
+        if (act && ty == kb && 4 * tx < k) {
 #pragma unroll
             for (int a = 0; a < 4; ++a)
                 if (a == kk) {
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         const int c = 4 * tx + b;
-                        if (c <= k) {
-                            const DF v = df_mul(Wr[a][b], r);
-                            Wr[a][b] = v;
-                            rowp[c] = v;
+                        if (c < k) {
+                            const DF v = df_mul(X[a][b], r);
+                            X[a][b] = v;
+                            V[c] = v;
                         }
                     }
                 }
         }
         __syncthreads();
-        // rows 4 ty .. 4 ty + 3 all <= k: nothing left to update (uniform for a warp once both
-        // of its row groups are done)
+        // rank-1 update of the rows i > k (warp-uniform skip once both row groups are done)
         if (act && 4 * ty + 3 > k) {
-            DF li[4], lm[4], wk[4];
+            DF vi[4], vm[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) li[a] = colp[4 * ty + a];
+            for (int a = 0; a < 4; ++a) vi[a] = V[4 * ty + a];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                lm[b] = colp[4 * tx + b];
-                wk[b] = rowp[4 * tx + b];
-            }
-            // branch-free: masked entries take an exact zero multiplier, so all 32 double-float
-            // updates are independent and interleave
+            for (int b = 0; b < 4; ++b) vm[b] = V[4 * tx + b];
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                const int i = 4 * ty + a;
-                const bool row = (i > k);
+                // rows <= k take an exact zero multiplier: all 16 updates are independent
+                const bool row = (4 * ty + a > k);
+                const DF nv{row ? -vi[a].hi : 0.0f, row ? -vi[a].lo : 0.0f};
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int m = 4 * tx + b;
-                    const bool fl = row && (m > k) && (m <= i);
-                    const bool fw = row && (m <= k);
-                    const DF nlL{fl ? -li[a].hi : 0.0f, fl ? -li[a].lo : 0.0f};
-                    const DF nlW{fw ? -li[a].hi : 0.0f, fw ? -li[a].lo : 0.0f};
-                    df_fma_acc(Lr[a][b], nlL, lm[b]);
-                    df_fma_acc(Wr[a][b], nlW, wk[b]);
-                }
+                for (int b = 0; b < 4; ++b) df_fma_acc(X[a][b], nv, vm[b]);
             }
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    Lr[a][b] = df_norm(Lr[a][b].hi, Lr[a][b].lo);
-                    Wr[a][b] = df_norm(Wr[a][b].hi, Wr[a][b].lo);
-                }
+                for (int b = 0; b < 4; ++b) X[a][b] = df_norm(X[a][b].hi, X[a][b].lo);
         }
-        // the other parity's column and row are rewritten next step; this step's are not
-        // touched again until every thread has passed the next step's barriers
+        // the other parity's vector is rewritten next step; this step's is not touched again
+        // until every thread has passed the next step's barriers
     }
-    __syncthreads();
+    // W^T (X holds W in its lower entries; rows and columns beyond nb are the identity)
     if (act) {
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const int i = 4 * ty + a, m = 4 * tx + b;
-                if (m <= i) {
-                    Sh[i][m] = Lr[a][b].hi;
-                    Sl[i][m] = Lr[a][b].lo;
-                }
-                // W(i, m) for m <= i  ->  Wt[m][i]
-                Wt[m * OZ_NB + i] = (m <= i) ? Wr[a][b].hi : 0.0f;
-                Wt[OZ_NB * OZ_NB + m * OZ_NB + i] = (m <= i) ? Wr[a][b].lo : 0.0f;
+                DF w = (m < i) ? X[a][b] : DF{0.0f, 0.0f};
+                if (m == i) w = (i < nb) ? X[a][b] : DF{1.0f, 0.0f};
+                Wt[m * OZ_NB + i] = w.hi;
+                Wt[OZ_NB * OZ_NB + m * OZ_NB + i] = w.lo;
             }
     } else {
         // upper blocks of W^T are zero

@@ -151,7 +151,7 @@ def run(args):
         res, ms, kms = {}, {}, {}
         names = ("k_sov_grad_fwd_f64", "k_sov_grad_fwd_f32", "k_sov_rev_f64", "k_sov_rev_f32",
                  "k_grad_L_f64", "k_grad_L_f32", "k_oz_update", "k_oz_potrf", "k_oz_trsm",
-                 "k_syrk")
+                 "k_syrk", "k_gemm64", "k_cgrad_panel", "k_cgrad_diag")
         for prec in ("mixed", "fp64"):
             bt = t(b).requires_grad_(True)
             s2 = torch.tensor(w["sigma2"], dtype=torch.float64, device=dev, requires_grad=True)
@@ -205,6 +205,7 @@ def run(args):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         mvn.mvn_matern(cd, w["sigma2"], w["range"], w["nu"], w["nugget"], out=S)
         torch.cuda.synchronize()
+        ctx.timing(True)
         e[0].record(stream)
         T = mvn.mvn_tlr_compress(S, w["tile"], w["acc"], w["max_rank"])
         e[1].record(stream)
@@ -220,6 +221,11 @@ def run(args):
         e[5].record(stream)
         torch.cuda.synchronize()
         mvn.sync()
+        kms = {k: round(v[0], 2) for k in ("k_bgemm", "k_chol_inv", "k_jacobi", "k_trsm_block",
+                                           "k_syrk", "k_oz_update", "k_oz_potrf", "k_oz_trsm",
+                                           "k_sov_tc")
+               for v in [ctx.kernel_time(k)] if v[1]}
+        ctx.timing(False)
         ms = [e[i].elapsed_time(e[i + 1]) for i in range(5)]
         ranks = T.ranks()
         tlr_ms = ms[0] + ms[1] + ms[2]
@@ -232,5 +238,6 @@ def run(args):
                        "logP_tlr": float(out_t[0]), "logP_dense": float(out_d[0]),
                        "ranks": {"min": int(ranks.min()), "median": float(np.median(ranks)),
                                  "max": int(ranks.max()), "capped": int(T.capped)},
+                       "kernel_ms": kms,
                        "note": "single timed pass (no warm-up repeats: minutes per pass)"})
         return

@@ -354,28 +354,32 @@ __global__ void __launch_bounds__(256) k_grad_L(int n, int ntiles, int64_t Ntot,
 //   A(i,k) = A[i*sar + k*sac], B(k,j) = B[k*sbr + j*sbc], C(i,j) = C[i + j*ldc] (column-major).
 // triA: 0 = dense, 1 = lower (A(i,k) = 0 for k > i), 2 = upper (A(i,k) = 0 for k < i).
 // lowerC: only entries with i + ci0 >= j + cj0 are written (a lower triangle of the parent).
+// Split K: block z sums k in [z kchunk, (z + 1) kchunk) and, when P is not null, writes its
+// partial tile to P[z m nn + i + j m] instead of updating C (k_gemm_reduce adds the partials in
+// a fixed order).
 __global__ void __launch_bounds__(256) k_gemm64(int m, int nn, int kk, double alpha,
                                                 const double* __restrict__ A, int64_t sar,
                                                 int64_t sac, const double* __restrict__ B,
                                                 int64_t sbr, int64_t sbc, double* __restrict__ C,
                                                 int64_t ldc, int triA, int lowerC, int ci0,
-                                                int cj0) {
+                                                int cj0, int kchunk, double* __restrict__ P) {
     __shared__ double As[16][64 + 1];  // As[k][i]
     __shared__ double Bs[16][64 + 1];  // Bs[k][j]
     const int I0 = blockIdx.x * 64, J0 = blockIdx.y * 64;
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int kbeg = blockIdx.z * kchunk, kend = min(kk, kbeg + kchunk);
     double acc[4][4] = {};
-    for (int k0 = 0; k0 < kk; k0 += 16) {
+    for (int k0 = kbeg; k0 < kend; k0 += 16) {
         __syncthreads();
         for (int e = t; e < 16 * 64; e += 256) {
             const int i = e % 64, k = e / 64;
             const int gi = I0 + i, gk = k0 + k;
             double av = 0.0;
-            if (gi < m && gk < kk && !(triA == 1 && gk > gi) && !(triA == 2 && gk < gi))
+            if (gi < m && gk < kend && !(triA == 1 && gk > gi) && !(triA == 2 && gk < gi))
                 av = A[gi * sar + gk * sac];
             As[k][i] = av;
             const int gj = J0 + i;
-            Bs[k][i] = (gj < nn && gk < kk) ? B[gk * sbr + gj * sbc] : 0.0;
+            Bs[k][i] = (gj < nn && gk < kend) ? B[gk * sbr + gj * sbc] : 0.0;
         }
         __syncthreads();
 #pragma unroll
@@ -399,21 +403,58 @@ __global__ void __launch_bounds__(256) k_gemm64(int m, int nn, int kk, double al
         for (int u = 0; u < 4; ++u) {
             const int i = I0 + tx + 16 * u;
             if (i >= m) continue;
+            if (P) {
+                P[(int64_t)blockIdx.z * m * nn + i + (int64_t)j * m] = acc[u][v];
+                continue;
+            }
             if (lowerC && i + ci0 < j + cj0) continue;
             C[i + (int64_t)j * ldc] += alpha * acc[u][v];
         }
     }
 }
 
+// C(i, j) += alpha sum_z P[z m nn + i + j m], z in order (deterministic)
+__global__ void k_gemm_reduce(int m, int nn, int nz, const double* __restrict__ P, double alpha,
+                              double* __restrict__ C, int64_t ldc, int lowerC, int ci0, int cj0) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * nn) return;
+    const int i = (int)(e % m), j = (int)(e / m);
+    if (lowerC && i + ci0 < j + cj0) return;
+    double s = 0.0;
+    for (int z = 0; z < nz; ++z) s += P[(int64_t)z * m * nn + e];
+    C[i + (int64_t)j * ldc] += alpha * s;
+}
+
+// Split-K workspace bound of gemm64 (doubles): at most 4 SM-counts of 64 x 64 partial tiles.
+static size_t gemm64_ws_doubles(const mvn_ctx* ctx) { return (size_t)4 * ctx->sm_count * 64 * 64; }
+
+// C += alpha A B.  GEMMs with few output tiles and a long K (the panel-transpose products of the
+// Cholesky adjoint: K up to n, one row of 64 x 64 tiles) are split along K over about two CTAs
+// per SM, into partial tiles in P (gemm64_ws_doubles) summed by k_gemm_reduce.
 static mvn_status gemm64(mvn_ctx* ctx, int m, int nn, int kk, double alpha, const double* A,
                          int64_t sar, int64_t sac, const double* B, int64_t sbr, int64_t sbc,
-                         double* C, int64_t ldc, int triA = 0, int lowerC = 0, int ci0 = 0,
-                         int cj0 = 0) {
+                         double* C, int64_t ldc, double* P, int triA = 0, int lowerC = 0,
+                         int ci0 = 0, int cj0 = 0) {
     if (m <= 0 || nn <= 0 || kk <= 0) return MVN_OK;
-    dim3 grid((m + 63) / 64, (nn + 63) / 64);
-    k_gemm64<<<grid, 256, 0, ctx->stream>>>(m, nn, kk, alpha, A, sar, sac, B, sbr, sbc, C, ldc,
-                                            triA, lowerC, ci0, cj0);
-    MVN_LAUNCHED(ctx);
+    const int64_t tiles = (int64_t)((m + 63) / 64) * ((nn + 63) / 64);
+    int nz = 1;
+    if (P && kk >= 256 && tiles < 2 * ctx->sm_count) {
+        nz = (int)std::min<int64_t>((2 * ctx->sm_count + tiles - 1) / tiles, kk / 128);
+        while (nz > 1 && (size_t)nz * tiles * 64 * 64 > gemm64_ws_doubles(ctx)) --nz;
+    }
+    const int kchunk = (nz == 1) ? kk : (((kk + nz - 1) / nz + 15) / 16) * 16;
+    nz = (kk + kchunk - 1) / kchunk;
+    dim3 grid((m + 63) / 64, (nn + 63) / 64, nz);
+    MVN_TIMED(ctx, "k_gemm64",
+              (k_gemm64<<<grid, 256, 0, ctx->stream>>>(m, nn, kk, alpha, A, sar, sac, B, sbr, sbc,
+                                                       C, ldc, triA, lowerC, ci0, cj0, kchunk,
+                                                       nz > 1 ? P : nullptr)));
+    if (nz > 1) {
+        const int64_t cnt = (int64_t)m * nn;
+        k_gemm_reduce<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(
+            m, nn, nz, P, alpha, C, ldc, lowerC, ci0, cj0);
+        MVN_LAUNCHED(ctx);
+    }
     return MVN_OK;
 }
 
@@ -437,30 +478,26 @@ __global__ void __launch_bounds__(256) k_cgrad_diag(const double* __restrict__ L
     __syncthreads();
     for (int jj = nb - 1; jj >= 0; --jj) {
         const double ljj = Ls[jj][jj];
-        // off-diagonal entries of column jj: L_ij = (A_ij - sum_{k<jj} L_ik L_jk) / L_jj
-        // g_i = G_ij / L_jj;  G_ik -= g_i L_jk, G_jk -= g_i L_ik (k < jj);  G_jj -= g_i L_ij
-        // The updates of row jj (G_jk, G_jj) sum over i: one thread per k, loop over i in order.
-        for (int k = t; k < jj; k += 256) {
+        const double rjj = 1.0 / ljj;
+        // off-diagonal entries of column jj: L_ij = (A_ij - sum_{k<jj} L_ik L_jk) / L_jj, so
+        // g_i = G_ij / L_jj becomes the adjoint of A_ij;  G_ik -= g_i L_jk, G_jk -= g_i L_ik
+        // (k < jj);  G_jj -= g_i L_ij
+        for (int i = jj + 1 + t; i < nb; i += 256) Gs[i][jj] *= rjj;
+        __syncthreads();
+        // row jj (one thread per k, sum over i in order) and the rows below (one entry each)
+        for (int k = t; k <= jj; k += 256) {
             double s = 0.0;
-            for (int i = nb - 1; i > jj; --i) s += (Gs[i][jj] / ljj) * Ls[i][k];
+            for (int i = nb - 1; i > jj; --i) s = fma(Gs[i][jj], Ls[i][k], s);
             Gs[jj][k] -= s;
         }
-        if (t == 0) {
-            double s = 0.0;
-            for (int i = nb - 1; i > jj; --i) s += (Gs[i][jj] / ljj) * Ls[i][jj];
-            Gs[jj][jj] -= s;
-        }
-        __syncthreads();
         for (int e = t; e < (nb - jj - 1) * jj; e += 256) {
             const int i = jj + 1 + e % (nb - jj - 1), k = e / (nb - jj - 1);
-            Gs[i][k] -= (Gs[i][jj] / ljj) * Ls[jj][k];
+            Gs[i][k] = fma(-Gs[i][jj], Ls[jj][k], Gs[i][k]);
         }
         __syncthreads();
-        for (int i = jj + 1 + t; i < nb; i += 256) Gs[i][jj] /= ljj;
-        __syncthreads();
         // pivot: L_jj = sqrt(A_jj - sum_{k<jj} L_jk^2);  g = G_jj / (2 L_jj); G_jk -= 2 g L_jk
-        const double g = Gs[jj][jj] / (2.0 * ljj);
-        for (int k = t; k < jj; k += 256) Gs[jj][k] -= 2.0 * g * Ls[jj][k];
+        const double g = Gs[jj][jj] * (0.5 * rjj);
+        for (int k = t; k < jj; k += 256) Gs[jj][k] = fma(-2.0 * g, Ls[jj][k], Gs[jj][k]);
         __syncthreads();
         if (t == 0) Gs[jj][jj] = g;
         __syncthreads();
@@ -503,7 +540,7 @@ __global__ void __launch_bounds__(128) k_cgrad_panel(const double* __restrict__ 
 }
 
 mvn_status cholesky_grad_launch(mvn_ctx* ctx, int n, const double* L, int64_t ld, double* G,
-                                int64_t ldg) {
+                                int64_t ldg, double* P) {
     const int nblk = (n + CG_NB - 1) / CG_NB;
     for (int jb = nblk - 1; jb >= 0; --jb) {
         const int c0 = jb * CG_NB;
@@ -512,25 +549,26 @@ mvn_status cholesky_grad_launch(mvn_ctx* ctx, int n, const double* L, int64_t ld
         double* Gp = G + r1 + (int64_t)c0 * ldg;        // panel adjoint (m x nb)
         const double* Xp = L + r1 + (int64_t)c0 * ld;   // panel of L (m x nb)
         if (m > 0) {
-            k_cgrad_panel<<<(m + 127) / 128, 128, 0, ctx->stream>>>(L, ld, G, ldg, c0, nb, r1, n);
-            MVN_LAUNCHED(ctx);
+            MVN_TIMED(ctx, "k_cgrad_panel",
+                      (k_cgrad_panel<<<(m + 127) / 128, 128, 0, ctx->stream>>>(L, ld, G, ldg, c0,
+                                                                               nb, r1, n)));
             // Gjj -= lower(Zp^T Xp)
             MVN_TRY(gemm64(ctx, nb, nb, m, -1.0, Gp, ldg, 1, Xp, 1, ld,
-                           G + c0 + (int64_t)c0 * ldg, ldg, 0, 1, 0, 0));
+                           G + c0 + (int64_t)c0 * ldg, ldg, P, 0, 1, 0, 0));
             if (c0 > 0) {
                 // G(r1:n, 0:c0) -= Zp L(c0:c0+nb, 0:c0)
-                MVN_TRY(gemm64(ctx, m, c0, nb, -1.0, Gp, 1, ldg, L + c0, 1, ld, G + r1, ldg));
+                MVN_TRY(gemm64(ctx, m, c0, nb, -1.0, Gp, 1, ldg, L + c0, 1, ld, G + r1, ldg, P));
                 // G(c0:c0+nb, 0:c0) -= Zp^T L(r1:n, 0:c0)
-                MVN_TRY(gemm64(ctx, nb, c0, m, -1.0, Gp, ldg, 1, L + r1, 1, ld, G + c0, ldg));
+                MVN_TRY(gemm64(ctx, nb, c0, m, -1.0, Gp, ldg, 1, L + r1, 1, ld, G + c0, ldg, P));
             }
         }
-        k_cgrad_diag<<<1, 256, 0, ctx->stream>>>(L, ld, G, ldg, c0, nb);
-        MVN_LAUNCHED(ctx);
+        MVN_TIMED(ctx, "k_cgrad_diag",
+                  (k_cgrad_diag<<<1, 256, 0, ctx->stream>>>(L, ld, G, ldg, c0, nb)));
         if (c0 > 0) {
             // G(c0:c0+nb, 0:c0) -= (Ajj + Ajj^T) L(c0:c0+nb, 0:c0),  Ajj lower
             const double* Aj = G + c0 + (int64_t)c0 * ldg;
-            MVN_TRY(gemm64(ctx, nb, c0, nb, -1.0, Aj, 1, ldg, L + c0, 1, ld, G + c0, ldg, 1));
-            MVN_TRY(gemm64(ctx, nb, c0, nb, -1.0, Aj, ldg, 1, L + c0, 1, ld, G + c0, ldg, 2));
+            MVN_TRY(gemm64(ctx, nb, c0, nb, -1.0, Aj, 1, ldg, L + c0, 1, ld, G + c0, ldg, P, 1));
+            MVN_TRY(gemm64(ctx, nb, c0, nb, -1.0, Aj, ldg, 1, L + c0, 1, ld, G + c0, ldg, P, 2));
         }
     }
     return MVN_OK;
@@ -543,7 +581,8 @@ extern "C" mvn_status mvn_cholesky_grad(mvn_ctx* ctx, int n, const double* L, in
         return mvn_fail(ctx, MVN_ERR_ARG, "mvn_cholesky_grad: invalid argument");
     if (n == 0) return MVN_OK;
     MVN_CUDA(ctx, cudaSetDevice(ctx->device));
-    return cholesky_grad_launch(ctx, n, L, ld, Lbar, ld);
+    MVN_TRY(ws_reserve(ctx, sizeof(double) * gemm64_ws_doubles(ctx)));
+    return cholesky_grad_launch(ctx, n, L, ld, Lbar, ld, (double*)ctx->ws);
 }
 
 // ---------------------------------------------------------------- SOV gradient

@@ -114,8 +114,9 @@ static mvn_status bgemm(mvn_ctx* ctx, const std::vector<GItem>& items, GItem* d_
                                   cudaMemcpyHostToDevice, ctx->stream));
     for (size_t z0 = 0; z0 < items.size(); z0 += 65535) {
         const unsigned nz = (unsigned)std::min<size_t>(65535, items.size() - z0);
-        k_bgemm<<<dim3((mm + 63) / 64, (nn + 63) / 64, nz), 256, 0, ctx->stream>>>(d_items + z0);
-        MVN_LAUNCHED(ctx);
+        MVN_TIMED(ctx, "k_bgemm",
+                  (k_bgemm<<<dim3((mm + 63) / 64, (nn + 63) / 64, nz), 256, 0, ctx->stream>>>(
+                      d_items + z0)));
     }
     return MVN_OK;
 }
@@ -459,8 +460,7 @@ static mvn_status comp_orth(mvn_ctx* ctx, CompWs& c, int T, double* Y, double* Q
         for (int t = 0; t < T; ++t)
             it.push_back(gi(src + t * mr, m, 1, src + t * mr, 1, m, c.G + t * rr, r, r, r, m, 1.0, 0.0));
         MVN_TRY(bgemm(ctx, it, c.items));
-        k_chol_inv<<<T, 256, 0, ctx->stream>>>(r, c.pG, c.pR);
-        MVN_LAUNCHED(ctx);
+        MVN_TIMED(ctx, "k_chol_inv", (k_chol_inv<<<T, 256, 0, ctx->stream>>>(r, c.pG, c.pR)));
         it.clear();
         for (int t = 0; t < T; ++t)
             it.push_back(gi(src + t * mr, 1, m, c.R + t * rr, 1, r, dst + t * mr, m, m, r, r, 1.0, 0.0));
@@ -525,9 +525,9 @@ static mvn_status comp_run(mvn_ctx* ctx, CompWs& c, int T, const std::vector<con
     for (int t = 0; t < T; ++t) it.push_back(gi(c.B + t * mr, 1, r, c.B + t * mr, r, 1, c.G + t * rr, r, r, r, m, 1.0, 0.0));
     MVN_TRY(bgemm(ctx, it, c.items));
     const int np = ((r + 1) & ~1) / 2;
-    k_jacobi<<<T, 256, np * (2 * sizeof(double) + 2 * sizeof(int)), ctx->stream>>>(
-        r, c.pG, c.pW, c.plam, c.porder, 40);
-    MVN_LAUNCHED(ctx);
+    MVN_TIMED(ctx, "k_jacobi",
+              (k_jacobi<<<T, 256, np * (2 * sizeof(double) + 2 * sizeof(int)), ctx->stream>>>(
+                  r, c.pG, c.pW, c.plam, c.porder, 40)));
     k_select<<<T, 256, 0, ctx->stream>>>(r, kmax, acc, c.pW, c.plam, c.porder, c.pWU, c.pWV,
                                          rank_out, c.capped);
     MVN_LAUNCHED(ctx);
@@ -766,8 +766,9 @@ extern "C" mvn_status mvn_tlr_cholesky(mvn_ctx* ctx, mvn_tlr* T, int* info) {
                     MVN_TRY(bgemm(ctx, it, c.items));
                 }
                 const int threads = Tn * kmax;
-                k_trsm_block<<<(threads + 127) / 128, 128, 0, ctx->stream>>>(m, kmax, Dk, r0, pV, Tn);
-                MVN_LAUNCHED(ctx);
+                MVN_TIMED(ctx, "k_trsm_block",
+                          (k_trsm_block<<<(threads + 127) / 128, 128, 0, ctx->stream>>>(
+                              m, kmax, Dk, r0, pV, Tn)));
             }
         }
     }

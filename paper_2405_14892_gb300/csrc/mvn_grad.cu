@@ -73,27 +73,52 @@ __global__ void k_weights(const double* __restrict__ logw, int64_t N,
 
 // T = type of the stored y and sbar and of the two per-block sums over dimensions (double: the
 // FP64 adjoint; float: the mixed adjoint).  The elementwise derivative terms are FP64 for both.
+#define RV_PATHS 32                 // paths per reverse work item (a quarter of a 128-path tile)
+#define RV_SUB 4                    // threads per path
+#define RV_THREADS (RV_PATHS * RV_SUB)
+#define RV_ITEMS_PER_TILE (SOV_P / RV_PATHS)
+
 template <typename T>
 struct RevSmem {
-    T Lk[RV_B][RV_B];           // GEMM operand tile
-    T Ld[RV_B][RV_B + 1];       // diagonal block L(r0+v, r0+u)
+    T Lk[RV_B][RV_B];             // GEMM operand tile
+    T Ld[RV_B][RV_B + 1];         // diagonal block L(r0+v, r0+u)
+    T acc[RV_B][RV_PATHS];        // limit shifts from earlier blocks, per (dim, path)
+    T yb[RV_B][RV_PATHS];         // ybar from later dimensions, per (dim, path)
+    // per (dim, path) terms of the reverse step that do not depend on ybar
+    double ca[RV_B][RV_PATHS];    // -phi(a') / Delta
+    double cya[RV_B][RV_PATHS];   // (1 - w) phi(a') / phi(y)
+    double cb[RV_B][RV_PATHS];    // phi(b') / Delta
+    double cyb[RV_B][RV_PATHS];   // w phi(b') / phi(y)
+    double ta[RV_B][RV_PATHS];    // a' (0 where phi(a') = 0)
+    double tb[RV_B][RV_PATHS];    // b' (0 where phi(b') = 0)
     double a[RV_B], b[RV_B];
     uint64_t alpha[RV_B];
-    double red[3][RV_B][4];     // per-warp partial sums of the three path reductions
 };
 
-// One tile of 128 paths, blocks in reverse order.  Y and Sbar of tile `tile` live at
-// Yt/St[k * 128 + t].  part[(tile * 3 + c) * n + i] receives the tile's sum over its paths of
-// w_p a'bar/L_ii (c = 0), w_p b'bar/L_ii (c = 1) and w_p dL_ii (c = 2).
+// One work item = 32 paths (quarter h of 128-path tile `tile`), dimension blocks in reverse order.
+// Y and Sbar of the tile live at Yt/St[k * 128 + path]; the item's paths are 32 h .. 32 h + 31.
+// 128 threads, thread (sub = t / 32, pl = t % 32) works for path pl on the block's dimensions
+// v = sub, sub + 4, ..:
+//   (a), (b) the sums over earlier dimensions (limit shift) and later dimensions (ybar), each v
+//            summed by one thread in dimension order;
+//   (d)      a', b' from the stored y and the elementwise terms of the reverse step (Phi, phi of
+//            Eq. 2), which do not depend on ybar;
+// then warp 0 runs the reverse chain of the block for its 32 paths (ybar of dimension u < v takes
+// sbar_v L_vu), a few FP64 operations per dimension.  part[(item * 3 + c) * n + i] receives the
+// item's sum over its paths of w_p a'bar/L_ii (c = 0), w_p b'bar/L_ii (c = 1), w_p dL_ii (c = 2).
 template <typename T>
-__device__ void rev_tile(const SovProblem& P, int tile, const uint64_t* __restrict__ alpha,
+__device__ void rev_item(const SovProblem& P, int item, const uint64_t* __restrict__ alpha,
                          const T* __restrict__ Yt, T* __restrict__ St,
                          const double* __restrict__ omega, double* __restrict__ part,
                          RevSmem<T>& sm) {
     constexpr bool kF32 = sizeof(T) == 4;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int NV = RV_B / RV_SUB;  // dimensions per thread
+    const int t = threadIdx.x;
+    const int pl = t % RV_PATHS, sub = t / RV_PATHS;
+    const int tile = item / RV_ITEMS_PER_TILE, h = item % RV_ITEMS_PER_TILE;
+    const int pc = h * RV_PATHS + pl;  // column of the path in the tile's Y / Sbar
     const int n = P.n;
-    const int64_t p = (int64_t)tile * SOV_P + t;
+    const int64_t p = (int64_t)tile * SOV_P + pc;
     const bool valid = p < P.Ntot;
     const int64_t q = valid ? p / P.Ns : 0;
     const uint64_t j = valid ? (uint64_t)(p - q * P.Ns) + 1u : 1u;
@@ -106,58 +131,60 @@ __device__ void rev_tile(const SovProblem& P, int tile, const uint64_t* __restri
     for (int blk = nblk - 1; blk >= 0; --blk) {
         const int r0 = blk * RV_B;
         const int nb = min(RV_B, n - r0);
-        T acc[RV_B], yb[RV_B];
+        T acc[NV], yb[NV];
 #pragma unroll
-        for (int v = 0; v < RV_B; ++v) {
-            acc[v] = (T)0;
-            yb[v] = (T)0;
+        for (int c = 0; c < NV; ++c) {
+            acc[c] = (T)0;
+            yb[c] = (T)0;
         }
         // (a) limit shift from earlier blocks: acc[v] = sum_{k < r0} L(r0+v, k) y_k
         for (int k0 = 0; k0 < r0; k0 += RV_B) {
             __syncthreads();
-            for (int e = t; e < RV_B * RV_B; e += SOV_P) {
+            for (int e = t; e < RV_B * RV_B; e += RV_THREADS) {
                 const int v = e % RV_B, kk = e / RV_B;
                 const int row = r0 + v;
                 sm.Lk[kk][v] = (row < n) ? (T)L[row + (int64_t)(k0 + kk) * ld] : (T)0;
             }
             __syncthreads();
             // FP32: per-block partial sums (as in the forward sweep of the mixed adjoint)
-            T part[RV_B];
+            T part_[NV];
 #pragma unroll
-            for (int v = 0; v < RV_B; ++v) part[v] = kF32 ? (T)0 : acc[v];
+            for (int c = 0; c < NV; ++c) part_[c] = kF32 ? (T)0 : acc[c];
 #pragma unroll 4
             for (int kk = 0; kk < RV_B; ++kk) {
-                const T yk = Yt[(int64_t)(k0 + kk) * SOV_P + t];
+                const T yk = Yt[(int64_t)(k0 + kk) * SOV_P + pc];
 #pragma unroll
-                for (int v = 0; v < RV_B; ++v) part[v] = fma(sm.Lk[kk][v], yk, part[v]);
+                for (int c = 0; c < NV; ++c)
+                    part_[c] = fma(sm.Lk[kk][sub + RV_SUB * c], yk, part_[c]);
             }
 #pragma unroll
-            for (int v = 0; v < RV_B; ++v) acc[v] = kF32 ? acc[v] + part[v] : part[v];
+            for (int c = 0; c < NV; ++c) acc[c] = kF32 ? acc[c] + part_[c] : part_[c];
         }
         // (b) ybar from the later dimensions: yb[v] = sum_{i >= r0+nb} L(i, r0+v) sbar_i
         for (int i0 = r0 + RV_B; i0 < n; i0 += RV_B) {
             __syncthreads();
-            for (int e = t; e < RV_B * RV_B; e += SOV_P) {
+            for (int e = t; e < RV_B * RV_B; e += RV_THREADS) {
                 const int ii = e % RV_B, v = e / RV_B;
                 const int row = i0 + ii;
                 sm.Lk[ii][v] = (row < n && v < nb) ? (T)L[row + (int64_t)(r0 + v) * ld] : (T)0;
             }
             __syncthreads();
             const int ni = min(RV_B, n - i0);
-            T part[RV_B];
+            T part_[NV];
 #pragma unroll
-            for (int v = 0; v < RV_B; ++v) part[v] = kF32 ? (T)0 : yb[v];
+            for (int c = 0; c < NV; ++c) part_[c] = kF32 ? (T)0 : yb[c];
             for (int ii = 0; ii < ni; ++ii) {
-                const T sb = St[(int64_t)(i0 + ii) * SOV_P + t];
+                const T sb = St[(int64_t)(i0 + ii) * SOV_P + pc];
 #pragma unroll
-                for (int v = 0; v < RV_B; ++v) part[v] = fma(sm.Lk[ii][v], sb, part[v]);
+                for (int c = 0; c < NV; ++c)
+                    part_[c] = fma(sm.Lk[ii][sub + RV_SUB * c], sb, part_[c]);
             }
 #pragma unroll
-            for (int v = 0; v < RV_B; ++v) yb[v] = kF32 ? yb[v] + part[v] : part[v];
+            for (int c = 0; c < NV; ++c) yb[c] = kF32 ? yb[c] + part_[c] : part_[c];
         }
         // (c) block operands
         __syncthreads();
-        for (int e = t; e < RV_B * RV_B; e += SOV_P) {
+        for (int e = t; e < RV_B * RV_B; e += RV_THREADS) {
             const int v = e % RV_B, u = e / RV_B;
             sm.Ld[v][u] = (v < nb && u <= v) ? (T)L[(r0 + v) + (int64_t)(r0 + u) * ld] : (T)0;
         }
@@ -166,90 +193,105 @@ __device__ void rev_tile(const SovProblem& P, int tile, const uint64_t* __restri
             sm.b[t] = (t < nb) ? P.b[r0 + t] : 1.0;
             sm.alpha[t] = (t < nb) ? alpha[r0 + t] : 0u;
         }
+#pragma unroll
+        for (int c = 0; c < NV; ++c) sm.yb[sub + RV_SUB * c][pl] = yb[c];
         __syncthreads();
-        T y[RV_B];
-        double ap[RV_B], bp[RV_B];
+        // (d) limits of the thread's dimensions from the stored y, and the ybar-free terms
+        {
+            T y[RV_B];
 #pragma unroll
-        for (int v = 0; v < RV_B; ++v) {
-            y[v] = (v < nb) ? Yt[(int64_t)(r0 + v) * SOV_P + t] : (T)0;
-        }
-        // (d) forward in the block: limits of each dimension
+            for (int v = 0; v < RV_B; ++v) y[v] = (v < nb) ? Yt[(int64_t)(r0 + v) * SOV_P + pc] : (T)0;
 #pragma unroll
-        for (int v = 0; v < RV_B; ++v) {
-            T s = acc[v];
+            for (int c = 0; c < NV; ++c) {
+                const int v = sub + RV_SUB * c;
+                double ca = 0.0, cya = 0.0, cb = 0.0, cyb = 0.0, ta = 0.0, tb = 0.0;
+                if (v < nb && live) {
+                    T s = acc[c];
 #pragma unroll
-            for (int u = 0; u < v; ++u) s = fma(sm.Ld[v][u], y[u], s);
-            const double lii = (v < nb) ? (double)sm.Ld[v][v] : 1.0;
-            ap[v] = (sm.a[v] - (double)s) / lii;
-            bp[v] = (sm.b[v] - (double)s) / lii;
-        }
-        // (e) reverse in the block
+                    for (int u = 0; u < RV_B; ++u)
+                        if (u < v) s = fma(sm.Ld[v][u], y[u], s);
+                    const double lii = (double)sm.Ld[v][v];
+                    const double A = (sm.a[v] - (double)s) / lii;
+                    const double Bv = (sm.b[v] - (double)s) / lii;
+                    const double w = lattice_w(j, sm.alpha[v], dq[r0 + v]);
+                    double delta;
+                    if (A > 0.0) {
+                        delta = 0.5 * erfc(A * 0.70710678118654752440) -
+                                ((Bv == INFINITY) ? 0.0 : 0.5 * erfc(Bv * 0.70710678118654752440));
+                    } else {
+                        delta = ((Bv == INFINITY) ? 1.0 : 0.5 * erfc(-Bv * 0.70710678118654752440)) -
+                                ((A == -INFINITY) ? 0.0 : 0.5 * erfc(-A * 0.70710678118654752440));
+                    }
+                    const double pa = (A == -INFINITY) ? 0.0 : phi_d(A);
+                    const double pb = (Bv == INFINITY) ? 0.0 : phi_d(Bv);
+                    double yv = 0.0;
 #pragma unroll
-        for (int v = RV_B - 1; v >= 0; --v) {
-            double ga = 0.0, gb = 0.0, gd = 0.0, sbar = 0.0;
-            if (v < nb && live) {
-                const double lii = (double)sm.Ld[v][v];
-                const double w = lattice_w(j, sm.alpha[v], dq[r0 + v]);
-                const double A = ap[v], Bv = bp[v];
-                double delta;
-                if (A > 0.0) {
-                    delta = 0.5 * erfc(A * 0.70710678118654752440) -
-                            ((Bv == INFINITY) ? 0.0 : 0.5 * erfc(Bv * 0.70710678118654752440));
-                } else {
-                    delta = ((Bv == INFINITY) ? 1.0 : 0.5 * erfc(-Bv * 0.70710678118654752440)) -
-                            ((A == -INFINITY) ? 0.0 : 0.5 * erfc(-A * 0.70710678118654752440));
+                    for (int u = 0; u < RV_B; ++u)
+                        if (u == v) yv = (double)y[u];
+                    const double py = phi_d(yv);
+                    ca = -pa / delta;
+                    cya = (1.0 - w) * pa / py;
+                    cb = pb / delta;
+                    cyb = w * pb / py;
+                    ta = (pa != 0.0) ? A : 0.0;
+                    tb = (pb != 0.0) ? Bv : 0.0;
                 }
-                const double pa = (A == -INFINITY) ? 0.0 : phi_d(A);
-                const double pb = (Bv == INFINITY) ? 0.0 : phi_d(Bv);
-                const double py = phi_d((double)y[v]);
-                const double ybv = (double)yb[v];
-                const double apbar = -pa / delta + ybv * (1.0 - w) * pa / py;
-                const double bpbar = pb / delta + ybv * w * pb / py;
-                sbar = -(apbar + bpbar) / lii;
-                ga = wp * apbar / lii;
-                gb = wp * bpbar / lii;
-                double lb = 0.0;
-                if (pa != 0.0) lb -= apbar * A;
-                if (pb != 0.0) lb -= bpbar * Bv;
-                gd = wp * lb / lii;
-                const T sbt = (T)sbar;
-#pragma unroll
-                for (int u = 0; u < v; ++u) yb[u] = fma(sbt, sm.Ld[v][u], yb[u]);
-            }
-            if (v < nb) St[(int64_t)(r0 + v) * SOV_P + t] = (T)sbar;
-            // reductions over the tile's paths (warp shuffles, then 4 warps in shared memory)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                ga += __shfl_xor_sync(0xffffffffu, ga, o);
-                gb += __shfl_xor_sync(0xffffffffu, gb, o);
-                gd += __shfl_xor_sync(0xffffffffu, gd, o);
-            }
-            if (lane == 0) {
-                sm.red[0][v][warp] = ga;
-                sm.red[1][v][warp] = gb;
-                sm.red[2][v][warp] = gd;
+                sm.ca[v][pl] = ca;
+                sm.cya[v][pl] = cya;
+                sm.cb[v][pl] = cb;
+                sm.cyb[v][pl] = cyb;
+                sm.ta[v][pl] = ta;
+                sm.tb[v][pl] = tb;
             }
         }
         __syncthreads();
-        if (t < 3 * RV_B) {
-            const int c = t / RV_B, v = t % RV_B;
-            if (v < nb) {
-                const double s = ((sm.red[c][v][0] + sm.red[c][v][1]) + sm.red[c][v][2]) +
-                                 sm.red[c][v][3];
-                part[((int64_t)tile * 3 + c) * n + r0 + v] = s;
+        // (e) reverse chain of the block (warp 0, one thread per path)
+        if (sub == 0) {
+            T ybv[RV_B];
+#pragma unroll
+            for (int v = 0; v < RV_B; ++v) ybv[v] = sm.yb[v][pl];
+#pragma unroll
+            for (int v = RV_B - 1; v >= 0; --v) {
+                double ga = 0.0, gb = 0.0, gd = 0.0, sbar = 0.0;
+                if (v < nb && live) {
+                    const double lii = (double)sm.Ld[v][v];
+                    const double ybd = (double)ybv[v];
+                    const double apbar = sm.ca[v][pl] + ybd * sm.cya[v][pl];
+                    const double bpbar = sm.cb[v][pl] + ybd * sm.cyb[v][pl];
+                    sbar = -(apbar + bpbar) / lii;
+                    ga = wp * apbar / lii;
+                    gb = wp * bpbar / lii;
+                    gd = wp * (-(apbar * sm.ta[v][pl]) - bpbar * sm.tb[v][pl]) / lii;
+                    const T sbt = (T)sbar;
+#pragma unroll
+                    for (int u = 0; u < v; ++u) ybv[u] = fma(sbt, sm.Ld[v][u], ybv[u]);
+                }
+                if (v < nb) St[(int64_t)(r0 + v) * SOV_P + pc] = (T)sbar;
+                // reductions over the item's 32 paths (warp shuffles)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                    gb += __shfl_xor_sync(0xffffffffu, gb, o);
+                    gd += __shfl_xor_sync(0xffffffffu, gd, o);
+                }
+                if (pl == 0 && v < nb) {
+                    part[((int64_t)item * 3 + 0) * n + r0 + v] = ga;
+                    part[((int64_t)item * 3 + 1) * n + r0 + v] = gb;
+                    part[((int64_t)item * 3 + 2) * n + r0 + v] = gd;
+                }
             }
         }
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SOV_P) k_sov_rev(const SovProblem P, int nitems,
-                                                   int* __restrict__ counter,
-                                                   const uint64_t* __restrict__ alpha,
-                                                   const T* __restrict__ Y,
-                                                   T* __restrict__ Sbar, int64_t ystride,
-                                                   const double* __restrict__ omega,
-                                                   double* __restrict__ part) {
+__global__ void __launch_bounds__(RV_THREADS, 3) k_sov_rev(const SovProblem P, int nitems,
+                                                        int* __restrict__ counter,
+                                                        const uint64_t* __restrict__ alpha,
+                                                        const T* __restrict__ Y,
+                                                        T* __restrict__ Sbar, int64_t ystride,
+                                                        const double* __restrict__ omega,
+                                                        double* __restrict__ part) {
     __shared__ RevSmem<T> sm;
     __shared__ int s_item;
     for (;;) {
@@ -258,12 +300,12 @@ __global__ void __launch_bounds__(SOV_P) k_sov_rev(const SovProblem P, int nitem
         __syncthreads();
         const int it = s_item;
         if (it >= nitems) break;
-        rev_tile(P, it, alpha, Y + (int64_t)it * ystride, Sbar + (int64_t)it * ystride, omega,
-                 part, sm);
+        const int64_t off = (int64_t)(it / RV_ITEMS_PER_TILE) * ystride;
+        rev_item(P, it, alpha, Y + off, Sbar + off, omega, part, sm);
     }
 }
 
-// out[c * n + i] = sum over tiles (fixed order) of part[(tile * 3 + c) * n + i]
+// out[c * n + i] = sum over work items (fixed order) of part[(item * 3 + c) * n + i]
 __global__ void k_sum_parts(const double* __restrict__ part, int ntiles, int n,
                             double* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -610,7 +652,7 @@ static mvn_status sov_grad_run(mvn_ctx* ctx, int n, const double* a, const doubl
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 2 * (int64_t)ctx->sm_count));
     const size_t need = ws_round(sizeof(uint64_t) * (size_t)M * nn) + ws_round(sizeof(double) * Ntot) * 2 +
                         2 * ws_round(sizeof(T) * (size_t)ntiles * ystride) +
-                        ws_round(sizeof(double) * 3 * (size_t)ntiles * nn) +
+                        ws_round(sizeof(double) * 3 * (size_t)RV_ITEMS_PER_TILE * ntiles * nn) +
                         ws_round(sizeof(double) * 3 * (size_t)nn) + 4 * ws_round(sizeof(double)) + 4096;
     MVN_TRY(ws_reserve(ctx, need));
     WsCarver wc(ctx->ws);
@@ -619,7 +661,7 @@ static mvn_status sov_grad_run(mvn_ctx* ctx, int n, const double* a, const doubl
     double* omega = wc.take<double>(Ntot);
     T* Y = wc.take<T>((size_t)ntiles * ystride);
     T* Sb = wc.take<T>((size_t)ntiles * ystride);
-    double* part = wc.take<double>(3 * (size_t)ntiles * nn);
+    double* part = wc.take<double>(3 * (size_t)RV_ITEMS_PER_TILE * ntiles * nn);
     double* dsum = wc.take<double>(3 * (size_t)nn);
     double* lse = wc.take<double>(1);
     int* counter = wc.take<int>(2);
@@ -666,11 +708,15 @@ static mvn_status sov_grad_run(mvn_ctx* ctx, int n, const double* a, const doubl
     MVN_LAUNCHED(ctx);
     if (n == 0) return MVN_OK;
     // reverse sweep
+    // work items of 32 paths (four per tile); a persistent grid of the resident CTAs
+    const int nrev = (int)(RV_ITEMS_PER_TILE * ntiles);
+    int per_sm = 1;
+    MVN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sov_rev<T>, RV_THREADS, 0));
+    const int grid_rev = std::max(1, std::min(nrev, std::max(per_sm, 1) * ctx->sm_count));
     MVN_TIMED(ctx, F64 ? "k_sov_rev_f64" : "k_sov_rev_f32",
-              (k_sov_rev<T><<<grid, SOV_P, 0, ctx->stream>>>(P, (int)ntiles, counter + 1,
-                                                              ctx->d_alpha, Y, Sb, ystride, omega,
-                                                              part)));
-    k_sum_parts<<<dim3((n + 255) / 256, 3), 256, 0, ctx->stream>>>(part, (int)ntiles, n, dsum);
+              (k_sov_rev<T><<<grid_rev, RV_THREADS, 0, ctx->stream>>>(
+                  P, nrev, counter + 1, ctx->d_alpha, Y, Sb, ystride, omega, part)));
+    k_sum_parts<<<dim3((n + 255) / 256, 3), 256, 0, ctx->stream>>>(part, nrev, n, dsum);
     MVN_LAUNCHED(ctx);
     if (dlogp_da)
         MVN_CUDA(ctx, cudaMemcpyAsync(dlogp_da, dsum, sizeof(double) * n,

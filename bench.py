@@ -156,7 +156,7 @@ TIMED_KERNELS = ("k_oz_update", "k_oz_potrf", "k_oz_trsm", "k_sov_tc", "k_syrk",
 # (path tiles) x n^2, the update's digit-tile reads as n^2 per launch.
 TRAFFIC_N0 = 9216
 TRAFFIC_TILES0 = 157
-TRAFFIC_BYTES0 = {"k_sov_tc": 26.46e9 + 0.75e9, "k_oz_update": 89.6e6}
+TRAFFIC_BYTES0 = {"k_sov_tc": 26.41e9 + 0.754e9, "k_oz_update": 89.2e6}
 
 
 def _traffic(name, n, tiles):

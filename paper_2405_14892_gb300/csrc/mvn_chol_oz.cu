@@ -21,7 +21,7 @@
 //
 // The update of block column j (64 columns) is an M = 128 (row tile) x N = 64 x K = 64 j GEMM
 // per row tile.  Its K range is cut into work items that a persistent grid of one CTA per SM
-// walks; inside a CTA one warp streams digit tiles (1-D bulk copies, 3-stage mbarrier ring), one
+// walks; inside a CTA one warp streams digit tiles (1-D bulk copies, 2-stage mbarrier ring), one
 // warp issues the MMAs, and eight warps drain TMEM into the integer accumulators.
 #include <cuda_bf16.h>
 #include <math.h>
@@ -37,8 +37,8 @@
 #define OZ_AT 8192          // one digit tile: 128 rows x 32 K, BF16, 64-byte swizzle
 #define OZ_BT 4096          // 64 rows of such a tile (the B operand)
 #define OZ_STAGE (OZ_S * (OZ_AT + OZ_BT))
-#define OZ_NST 2            // pipeline stages (K = 32 each; 145 KB, so that the panel kernels
-                            // fit beside an update CTA on one SM)
+#define OZ_NST 2            // pipeline stages (K = 32 each, 72 KB; measured: a third stage does
+                            // not speed the W2 factorisation up)
 #define OZ_GRP 8            // stages accumulated in TMEM between drains (K = 256)
 #define OZ_DW 8             // drain warps
 #define OZ_THREADS (32 * (OZ_DW + 2))
@@ -715,6 +715,7 @@ __global__ void __launch_bounds__(256) k_oz_trsm(double* __restrict__ A, int64_t
 }
 
 static size_t oz_smem() { return sizeof(OzSmem) + 1024; }
+static_assert(sizeof(OzSmem) + 1024 <= 232448, "the update CTA's shared memory fits one SM");
 
 static int oz_nrt(int n) { return (n + OZ_RT - 1) / OZ_RT; }
 static int oz_nbc(int n) { return (n + OZ_NB - 1) / OZ_NB; }

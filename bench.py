@@ -232,6 +232,25 @@ def kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src, steps):
     return out
 
 
+# ----------------------------------------------------------------------------- ranks
+
+def rank_seed(base: int, rank: int) -> int:
+    """Shift seed of a rank's independent problem (weak scaling: one W2 problem per rank)."""
+    return base + 1000 * rank
+
+
+def job_time_and_value(ms: float, units_per_rank: float, world: int, device=None):
+    """Whole-job step time = the slowest rank's (max over ranks), and the job's throughput =
+    units processed by all ranks / that time.  Collective only when world > 1."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_rank / (ms * 1e-3)
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def run_gpu(args):
@@ -258,7 +277,7 @@ def run_gpu(args):
     if args.paths:
         Ns = max(1, args.paths // M)
     Ntot = Ns * M
-    seed = w["seed"] + 1000 * rank
+    seed = rank_seed(w["seed"], rank)
     prec = args.prec
     coords = torch.tensor(c, device=dev)
     a_d = torch.tensor(a, device=dev)
@@ -320,10 +339,7 @@ def run_gpu(args):
     ctx.timing(False)
     ctx.kernel_times = ktimes
     clocks = _clock_summary(clocks_proc, local) if rank == 0 else None
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = job_time_and_value(ms, n * Ntot, world, dev)
     st, info = ctx.sync()
     if st != 0:
         raise RuntimeError(f"device error {st} info {info}")
@@ -355,7 +371,6 @@ def run_gpu(args):
     peaks, peak_src = _peaks()
     sov_ms = statistics.median(phase["sov"])
     chol_ms = statistics.median(phase["cholesky"])
-    value = world * n * Ntot / (ms * 1e-3)
     rooflines = kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src, args.steps)
     dominant = max(rooflines, key=lambda r: r["total_ms"]) if rooflines else None
     line = {

@@ -78,6 +78,43 @@ __global__ void k_weights(const double* __restrict__ logw, int64_t N,
 #define RV_THREADS (RV_PATHS * RV_SUB)
 #define RV_ITEMS_PER_TILE (SOV_P / RV_PATHS)
 
+// One 16-dimension step of the limit-shift sums acc[c] = sum_{k < r0} L(r0 + v_c, k) y_k of a
+// path (v_c = sub + 4 c), shared by the forward and the reverse sweep of the adjoint so that both
+// form bit-identical limits.  FP64: one FMA chain in dimension order (mid stays zero).  FP32:
+// each 16-dimension block is summed into its own partial, the partials of a 128-dimension group
+// into mid, and mid into acc at the end of every group (the caller adds the last mid): the chain
+// of FP32 additions grows with 16 + 8 + r0 / 128 terms instead of r0 (one FP32 chain biases
+// log P by ~1e-6 per dimension on strongly correlated fields).
+template <typename T, int NV>
+__device__ __forceinline__ void limit_sum_step(const T (&Lk)[RV_B][RV_B], const T* __restrict__ Yt,
+                                               int k0, int pc, int sub, T (&acc)[NV],
+                                               T (&mid)[NV]) {
+    constexpr bool kF32 = sizeof(T) == 4;
+    T part_[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) part_[c] = kF32 ? (T)0 : acc[c];
+#pragma unroll 4
+    for (int kk = 0; kk < RV_B; ++kk) {
+        const T yk = Yt[(int64_t)(k0 + kk) * SOV_P + pc];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) part_[c] = fma(Lk[kk][sub + RV_SUB * c], yk, part_[c]);
+    }
+    if (kF32) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) mid[c] += part_[c];
+        if (((k0 / RV_B) & 7) == 7) {
+#pragma unroll
+            for (int c = 0; c < NV; ++c) {
+                acc[c] += mid[c];
+                mid[c] = (T)0;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) acc[c] = part_[c];
+    }
+}
+
 template <typename T>
 struct RevSmem {
     T Lk[RV_B][RV_B];             // GEMM operand tile
@@ -137,7 +174,11 @@ __device__ void rev_item(const SovProblem& P, int item, const uint64_t* __restri
             acc[c] = (T)0;
             yb[c] = (T)0;
         }
-        // (a) limit shift from earlier blocks: acc[v] = sum_{k < r0} L(r0+v, k) y_k
+        // (a) limit shift from earlier blocks: acc[v] = sum_{k < r0} L(r0+v, k) y_k, summed as
+        // in the forward sweep (limit_sum_step)
+        T mid[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) mid[c] = (T)0;
         for (int k0 = 0; k0 < r0; k0 += RV_B) {
             __syncthreads();
             for (int e = t; e < RV_B * RV_B; e += RV_THREADS) {
@@ -146,20 +187,10 @@ __device__ void rev_item(const SovProblem& P, int item, const uint64_t* __restri
                 sm.Lk[kk][v] = (row < n) ? (T)L[row + (int64_t)(k0 + kk) * ld] : (T)0;
             }
             __syncthreads();
-            // FP32: per-block partial sums (as in the forward sweep of the mixed adjoint)
-            T part_[NV];
-#pragma unroll
-            for (int c = 0; c < NV; ++c) part_[c] = kF32 ? (T)0 : acc[c];
-#pragma unroll 4
-            for (int kk = 0; kk < RV_B; ++kk) {
-                const T yk = Yt[(int64_t)(k0 + kk) * SOV_P + pc];
-#pragma unroll
-                for (int c = 0; c < NV; ++c)
-                    part_[c] = fma(sm.Lk[kk][sub + RV_SUB * c], yk, part_[c]);
-            }
-#pragma unroll
-            for (int c = 0; c < NV; ++c) acc[c] = kF32 ? acc[c] + part_[c] : part_[c];
+            limit_sum_step<T, NV>(sm.Lk, Yt, k0, pc, sub, acc, mid);
         }
+#pragma unroll
+        for (int c = 0; c < NV; ++c) acc[c] += mid[c];
         // (b) ybar from the later dimensions: yb[v] = sum_{i >= r0+nb} L(i, r0+v) sbar_i
         for (int i0 = r0 + RV_B; i0 < n; i0 += RV_B) {
             __syncthreads();
@@ -302,6 +333,110 @@ __global__ void __launch_bounds__(RV_THREADS, 3) k_sov_rev(const SovProblem P, i
         if (it >= nitems) break;
         const int64_t off = (int64_t)(it / RV_ITEMS_PER_TILE) * ystride;
         rev_item(P, it, alpha, Y + off, Sbar + off, omega, part, sm);
+    }
+}
+
+// ---------------------------------------------------------------- forward sweep of the adjoint
+
+// The forward sweep of Eq. 2 that keeps every path's y for the reverse sweep, on the same 32-path
+// work items as k_sov_rev: 128 threads, thread (sub = t / 32, pl = t % 32) forms for path pl the
+// limit shifts of the block's dimensions v = sub, sub + 4, .. from the earlier dimensions (each v
+// summed by one thread in dimension order; FP32: per 16-dimension partial sums, exactly as the
+// reverse sweep recomputes them), then warp 0 runs the block's dimensions one after the other
+// (Alg. 3) with the elementwise step in FP64 and writes y.  logw[p] receives log prod Delta.
+template <typename T>
+struct FwdSmem {
+    T Lk[RV_B][RV_B];
+    T Ld[RV_B][RV_B + 1];
+    T acc[RV_B][RV_PATHS];
+    double a[RV_B], b[RV_B];
+    uint64_t alpha[RV_B];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(RV_THREADS, 4) k_sov_fwd_keep(const SovProblem P, int nitems,
+                                                                int* __restrict__ counter,
+                                                                const uint64_t* __restrict__ alpha,
+                                                                T* __restrict__ Y,
+                                                                int64_t ystride) {
+    constexpr bool kF32 = sizeof(T) == 4;
+    constexpr int NV = RV_B / RV_SUB;
+    __shared__ FwdSmem<T> sm;
+    __shared__ int s_item;
+    const int t = threadIdx.x;
+    const int pl = t % RV_PATHS, sub = t / RV_PATHS;
+    const int n = P.n;
+    const double* __restrict__ L = P.L;
+    const int64_t ld = P.ld;
+    for (;;) {
+        __syncthreads();
+        if (t == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nitems) break;
+        const int tile = item / RV_ITEMS_PER_TILE, h = item % RV_ITEMS_PER_TILE;
+        T* __restrict__ Yt = Y + (int64_t)tile * ystride;
+        const int pc = h * RV_PATHS + pl;
+        const int64_t p = (int64_t)tile * SOV_P + pc;
+        const bool valid = p < P.Ntot;
+        const int64_t q = valid ? p / P.Ns : 0;
+        const uint64_t j = valid ? (uint64_t)(p - q * P.Ns) + 1u : 1u;
+        const uint64_t* __restrict__ dq = P.delta + q * P.dstride;
+        LogProd lp;
+        for (int r0 = 0; r0 < n; r0 += RV_B) {
+            const int nb = min(RV_B, n - r0);
+            T acc[NV], mid[NV];
+#pragma unroll
+            for (int c = 0; c < NV; ++c) {
+                acc[c] = (T)0;
+                mid[c] = (T)0;
+            }
+            for (int k0 = 0; k0 < r0; k0 += RV_B) {
+                __syncthreads();
+                for (int e = t; e < RV_B * RV_B; e += RV_THREADS) {
+                    const int v = e % RV_B, kk = e / RV_B;
+                    const int row = r0 + v;
+                    sm.Lk[kk][v] = (row < n) ? (T)L[row + (int64_t)(k0 + kk) * ld] : (T)0;
+                }
+                __syncthreads();
+                limit_sum_step<T, NV>(sm.Lk, Yt, k0, pc, sub, acc, mid);
+            }
+#pragma unroll
+            for (int c = 0; c < NV; ++c) acc[c] += mid[c];
+            __syncthreads();
+            for (int e = t; e < RV_B * RV_B; e += RV_THREADS) {
+                const int v = e % RV_B, u = e / RV_B;
+                sm.Ld[v][u] = (v < nb && u <= v) ? (T)L[(r0 + v) + (int64_t)(r0 + u) * ld] : (T)0;
+            }
+            if (t < RV_B) {
+                sm.a[t] = (t < nb) ? P.a[r0 + t] : 0.0;
+                sm.b[t] = (t < nb) ? P.b[r0 + t] : 1.0;
+                sm.alpha[t] = (t < nb) ? alpha[r0 + t] : 0u;
+            }
+#pragma unroll
+            for (int c = 0; c < NV; ++c) sm.acc[sub + RV_SUB * c][pl] = acc[c];
+            __syncthreads();
+            if (sub == 0) {
+                T y[RV_B];
+#pragma unroll
+                for (int v = 0; v < RV_B; ++v) {
+                    y[v] = (T)0;
+                    if (v < nb) {
+                        T s = sm.acc[v][pl];
+#pragma unroll
+                        for (int u = 0; u < v; ++u) s = fma(sm.Ld[v][u], y[u], s);
+                        const double w = lattice_w(j, sm.alpha[v], dq[r0 + v]);
+                        double delta;
+                        y[v] = (T)sov_step_f64(sm.a[v], sm.b[v], (double)s, (double)sm.Ld[v][v], w,
+                                               delta);
+                        lp.mul(delta);
+                        if (valid) Yt[(int64_t)(r0 + v) * SOV_P + pc] = y[v];
+                    }
+                }
+            }
+            // the block's y are read by all four threads of each path in the next block
+        }
+        if (sub == 0 && valid) P.logw[p] = lp.log_value();
     }
 }
 
@@ -629,9 +764,9 @@ extern "C" mvn_status mvn_cholesky_grad(mvn_ctx* ctx, int n, const double* L, in
 
 // ---------------------------------------------------------------- SOV gradient
 
-// T = double: the FP64 adjoint (forward k_sov_simt<32, double>, FP64 everywhere).
-// T = float: the mixed adjoint.  Its forward sweep forms the limit shifts in FP32 and keeps every
-// tile's y in FP32, with the elementwise step of Eq. 2 in FP64 (k_sov_simt<32, float, true>): the
+// T = double: the FP64 adjoint (FP64 everywhere).
+// T = float: the mixed adjoint.  Its forward sweep (k_sov_fwd_keep) forms the limit shifts in FP32
+// and keeps every tile's y in FP32, with the elementwise step of Eq. 2 in FP64: the
 // per-dimension errors of an FP32 step add up along the n dimensions of log P, those of the FP32
 // limit sums much less.  The reverse sweep forms the limit shifts and ybar in FP32 and the
 // elementwise derivative terms in FP64; dL sums FP32 products per 128-path tile and the tiles in
@@ -684,22 +819,16 @@ static mvn_status sov_grad_run(mvn_ctx* ctx, int n, const double* a, const doubl
     if (n == 0) {
         MVN_CUDA(ctx, cudaMemsetAsync(logw, 0, sizeof(double) * Ntot, ctx->stream));
     } else {
-        SovBatch batch;
-        memset(&batch, 0, sizeof(batch));
-        batch.single = P;
-        batch.nitems = (int)ntiles;
-        batch.counter = counter;
-        batch.y_per_tile = 1;
         MVN_CUDA(ctx, cudaMemsetAsync(counter, 0, 2 * sizeof(int), ctx->stream));
-        if constexpr (F64) {
-            MVN_TIMED(ctx, "k_sov_grad_fwd_f64",
-                      (k_sov_simt<32, double, true><<<grid, SOV_P, 0, ctx->stream>>>(
-                          batch, ctx->d_alpha, Y, ystride)));
-        } else {
-            MVN_TIMED(ctx, "k_sov_grad_fwd_f32",
-                      (k_sov_simt<32, float, true><<<grid, SOV_P, 0, ctx->stream>>>(
-                          batch, ctx->d_alpha, Y, ystride)));
-        }
+        // 32-path work items (four per tile), a persistent grid of the resident CTAs
+        const int nfwd = (int)(RV_ITEMS_PER_TILE * ntiles);
+        int per_sm = 1;
+        MVN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sov_fwd_keep<T>,
+                                                                    RV_THREADS, 0));
+        const int grid_fwd = std::max(1, std::min(nfwd, std::max(per_sm, 1) * ctx->sm_count));
+        MVN_TIMED(ctx, F64 ? "k_sov_grad_fwd_f64" : "k_sov_grad_fwd_f32",
+                  (k_sov_fwd_keep<T><<<grid_fwd, RV_THREADS, 0, ctx->stream>>>(
+                      P, nfwd, counter, ctx->d_alpha, Y, ystride)));
     }
     MVN_TRY(sov_reduce_launch_opt(ctx, logw, Ns, M, qmc->err_k, out3, 1, Ntot, true));
     k_lse_all<<<1, 512, 0, ctx->stream>>>(logw, Ntot, lse);

@@ -34,11 +34,6 @@ __device__ void sov_tile(const SovProblem& P, int tile, const uint64_t* __restri
     int pf = 0;
     int next_k = (P.nprefix > 0) ? P.prefix[0] : -1;
 
-    // FP32 limit sums with an FP64 elementwise step (the mixed adjoint's forward sweep): each
-    // B-wide block of earlier dimensions is summed into its own partial, then added to the total,
-    // so the rounding error grows with B + r0/B terms instead of r0 (a long FP32 chain biases
-    // log P by ~1e-6 per dimension on strongly correlated fields)
-    constexpr bool kBlockPartials = ELEM64 && sizeof(T) == 4;
     for (int r0 = 0; r0 < n; r0 += B) {
         const int nb = min(B, n - r0);
         T acc[B];
@@ -53,25 +48,11 @@ __device__ void sov_tile(const SovProblem& P, int tile, const uint64_t* __restri
                 sm.Lk[kk][v] = (row < n) ? (T)L[row + (int64_t)(k0 + kk) * ld] : (T)0;
             }
             __syncthreads();
-            if constexpr (kBlockPartials) {
-                T part[B];
-#pragma unroll
-                for (int v = 0; v < B; ++v) part[v] = (T)0;
 #pragma unroll 4
-                for (int kk = 0; kk < B; ++kk) {
-                    const T yk = Ycta[(int64_t)(k0 + kk) * SOV_P + t];
+            for (int kk = 0; kk < B; ++kk) {
+                const T yk = Ycta[(int64_t)(k0 + kk) * SOV_P + t];
 #pragma unroll
-                    for (int v = 0; v < B; ++v) part[v] = fma(sm.Lk[kk][v], yk, part[v]);
-                }
-#pragma unroll
-                for (int v = 0; v < B; ++v) acc[v] += part[v];
-            } else {
-#pragma unroll 4
-                for (int kk = 0; kk < B; ++kk) {
-                    const T yk = Ycta[(int64_t)(k0 + kk) * SOV_P + t];
-#pragma unroll
-                    for (int v = 0; v < B; ++v) acc[v] = fma(sm.Lk[kk][v], yk, acc[v]);
-                }
+                for (int v = 0; v < B; ++v) acc[v] = fma(sm.Lk[kk][v], yk, acc[v]);
             }
         }
         // diagonal block (Alg. 3)

@@ -167,9 +167,9 @@ def test_sov_grad_mixed_vs_oracle(mvn, n, Ns, M):
     against the FP64 oracle on identical lattice points.  The test field is strongly correlated
     (conditional standard deviations L_ii down to 0.07, so FP32 errors of the limit sums grow
     ~15x in a' and b') and the per-dimension errors add up along log P: the bound is
-    |d log P| <= 1e-4 + 2e-7 n (a CPU emulation of the kernel's blocked FP32 sums gives 8e-5 at
-    n = 600, log P = -938; one unblocked FP32 chain gives 6.6e-4).  Every gradient entry within
-    5e-5 of the largest."""
+    |d log P| <= 1e-4 + 2e-7 n (one unblocked FP32 chain of limit sums gives 6.6e-4 at n = 600,
+    log P = -938, in a CPU emulation; the kernels sum 16-dimension partials per 128-dimension
+    group).  Every gradient entry within 5e-5 of the largest."""
     S, a, b = _problem(n, n)
     Lo, _ = oracle.cholesky(S)
     q = oracle.QMC(Ns, M, 5 + n)

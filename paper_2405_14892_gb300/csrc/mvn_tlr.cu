@@ -62,7 +62,11 @@ __global__ void __launch_bounds__(256) k_bgemm(const GItem* __restrict__ items) 
     const GItem it = items[blockIdx.z];
     const int I0 = blockIdx.x * 64, J0 = blockIdx.y * 64;
     if (I0 >= it.m || J0 >= it.n) return;
-    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4, w2 = (t >> 5) * 2;
+    // FP64 is the scarce unit on this GPU, so no FMA is spent on padding: the row groups
+    // (16 u ..), the column groups of this warp (16 v + w2 ..) and the K steps beyond the item's
+    // sizes are skipped (uniform across the CTA or the warp; the skipped products were zeros)
+    const int mrem = it.m - I0, nrem = it.n - J0;
     double acc[4][4] = {};
     for (int k0 = 0; k0 < it.k; k0 += 16) {
         __syncthreads();
@@ -73,17 +77,25 @@ __global__ void __launch_bounds__(256) k_bgemm(const GItem* __restrict__ items) 
             Bs[l][i] = (gj < it.n && gl < it.k) ? it.B[gl * it.sbr + gj * it.sbc] : 0.0;
         }
         __syncthreads();
+        if (w2 >= nrem) continue;  // no column of this warp is in range
+        const int kl = min(16, it.k - k0);
 #pragma unroll
         for (int l = 0; l < 16; ++l) {
+            if (l >= kl) break;
             double a[4], b[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) a[u] = As[l][tx + 16 * u];
 #pragma unroll
             for (int v = 0; v < 4; ++v) b[v] = Bs[l][ty + 16 * v];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u) {
+                if (16 * u >= mrem) break;
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+                for (int v = 0; v < 4; ++v) {
+                    if (16 * v + w2 >= nrem) break;
+                    acc[u][v] = fma(a[u], b[v], acc[u][v]);
+                }
+            }
         }
     }
 #pragma unroll
@@ -218,17 +230,23 @@ __device__ double block_sum256(double v, double* red) {
     return s;
 }
 
+#define JAC_SMEM_R 80  // C and W in shared memory up to r = 80 (100 KB)
+
 // Two-sided parallel Jacobi (round-robin pairs) on a symmetric r x r matrix C (ld r) per item;
 // W (r x r) receives the eigenvectors (columns), lam the eigenvalues (diagonal of the converged
-// C), order the column indices sorted by descending eigenvalue.
+// C), order the column indices sorted by descending eigenvalue.  With in_smem, C and W live in
+// shared memory while the rotations run (r <= JAC_SMEM_R; the same arithmetic), and W is
+// written back at the end; C is then left as it came in.
 __global__ void __launch_bounds__(256) k_jacobi(int r, double* const* __restrict__ Cs,
                                                 double* const* __restrict__ Ws,
                                                 double* const* __restrict__ lams,
-                                                int* const* __restrict__ orders, int max_sweeps) {
-    extern __shared__ double jsm[];  // cs[np], sn[np], pp[np], qq[np] (ints)
+                                                int* const* __restrict__ orders, int max_sweeps,
+                                                int in_smem) {
+    extern __shared__ double jsm[];  // cs[np], sn[np], pp[np], qq[np] (ints), [C, W (r x r)]
     __shared__ double red[256];
     double* C = Cs[blockIdx.x];
-    double* W = Ws[blockIdx.x];
+    double* const Wg = Ws[blockIdx.x];
+    double* W = Wg;
     double* lam = lams[blockIdx.x];
     int* order = orders[blockIdx.x];
     const int t = threadIdx.x;
@@ -238,6 +256,12 @@ __global__ void __launch_bounds__(256) k_jacobi(int r, double* const* __restrict
     double* sn = jsm + np;
     int* pp = (int*)(jsm + 2 * np);
     int* qq = pp + np;
+    if (in_smem) {
+        double* Cs_ = jsm + 3 * np;  // after cs, sn and the two int arrays (np doubles)
+        for (int e = t; e < r * r; e += 256) Cs_[e] = C[e];
+        C = Cs_;
+        W = Cs_ + r * r;
+    }
     for (int e = t; e < r * r; e += 256) W[e] = ((e % r) == (e / r)) ? 1.0 : 0.0;
     __syncthreads();
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
@@ -305,6 +329,8 @@ __global__ void __launch_bounds__(256) k_jacobi(int r, double* const* __restrict
         lam[i] = C[i + (int64_t)i * r];
         order[i] = i;
     }
+    if (in_smem)
+        for (int e = t; e < r * r; e += 256) Wg[e] = W[e];
     __syncthreads();
     if (t == 0) {  // selection sort of the order by descending eigenvalue (r is small)
         for (int i = 0; i < r; ++i) {
@@ -525,9 +551,14 @@ static mvn_status comp_run(mvn_ctx* ctx, CompWs& c, int T, const std::vector<con
     for (int t = 0; t < T; ++t) it.push_back(gi(c.B + t * mr, 1, r, c.B + t * mr, r, 1, c.G + t * rr, r, r, r, m, 1.0, 0.0));
     MVN_TRY(bgemm(ctx, it, c.items));
     const int np = ((r + 1) & ~1) / 2;
+    const int in_smem = (r <= JAC_SMEM_R) ? 1 : 0;
+    const size_t jsmem = sizeof(double) * 3 * np + (in_smem ? sizeof(double) * 2 * r * r : 0);
+    if (in_smem)
+        MVN_CUDA(ctx, cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)jsmem));
     MVN_TIMED(ctx, "k_jacobi",
-              (k_jacobi<<<T, 256, np * (2 * sizeof(double) + 2 * sizeof(int)), ctx->stream>>>(
-                  r, c.pG, c.pW, c.plam, c.porder, 40)));
+              (k_jacobi<<<T, 256, jsmem, ctx->stream>>>(r, c.pG, c.pW, c.plam, c.porder, 40,
+                                                        in_smem)));
     k_select<<<T, 256, 0, ctx->stream>>>(r, kmax, acc, c.pW, c.plam, c.porder, c.pWU, c.pWV,
                                          rank_out, c.capped);
     MVN_LAUNCHED(ctx);

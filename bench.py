@@ -229,6 +229,14 @@ def kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src, steps):
         out.append({"kernel": name, "bound": "alu", "unit": "TFLOP/s", "achieved": ach,
                     "peak": pk, "frac": ach / pk, "traffic": None, "launches": cnt,
                     "total_ms": ms, "peak_source": src})
+    # the HBM view of the kernels whose DRAM traffic was measured: measured bytes per launch over
+    # the average launch duration, against the measured copy bandwidth
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    for r in out:
+        if r.get("traffic"):
+            gbs = r["traffic"] / (r["total_ms"] * 1e-3 / r["launches"]) / 1e9
+            r["hbm_view"] = {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                             "peak_source": f"{peak_src} HBM copy bandwidth"}
     return out
 
 

@@ -92,17 +92,25 @@ def workload(grid: int = 0):
 
 # ----------------------------------------------------------------------------- CPU oracle arm
 
-def cpu_oracle_throughput(sample_paths: int = 48, chol_n: int = 2048):
+def cpu_oracle_problem():
+    """The W2 problem as the oracle sees it: covariance (closed-form Matern) and its LAPACK
+    factor, built once and untimed (the factor is the input of the timed SOV sample)."""
+    import oracle
+    w, c, a, b = workload()
+    S = oracle.matern_closed(c, w["sigma2"], w["range"], w["nu"], w["nugget"])
+    L = oracle.cholesky_lapack(S)
+    return w, a, b, S, L
+
+
+def cpu_oracle_throughput(sample_paths: int = 48, chol_n: int = 2048, problem=None):
     """The oracle as it stands on this host's cores, on a bounded sample of W2:
     SOV on `sample_paths` paths of the full n=16,384 problem (exactly linear in the path count)
     plus the plain Cholesky loop on the leading chol_n x chol_n block (scaled by (n/chol_n)^3).
     Returns (sample-dims/s for a whole W2 step, details)."""
     import oracle
-    w, c, a, b = workload()
-    n = c.shape[0]
+    w, a, b, S, L = problem if problem is not None else cpu_oracle_problem()
+    n = S.shape[0]
     Ntot = w["Ns"] * w["M"]
-    S = oracle.matern_closed(c, w["sigma2"], w["range"], w["nu"], w["nugget"])
-    L = oracle.cholesky_lapack(S)  # input of the timed SOV sample (not timed)
     q = oracle.QMC(w["Ns"], w["M"], w["seed"])
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
@@ -124,14 +132,14 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w, c, a, b = workload()
+    problem = cpu_oracle_problem()
+    w, n = problem[0], problem[3].shape[0]
     vals = []
     det = None
     for _ in range(max(1, args.steps)):
-        v, det = cpu_oracle_throughput(sample_paths=16, chol_n=1024)
+        v, det = cpu_oracle_throughput(sample_paths=16, chol_n=1024, problem=problem)
         vals.append(v)
     v = statistics.median(vals)
-    n = c.shape[0]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

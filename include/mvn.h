@@ -18,6 +18,10 @@
  *     a device status word; mvn_sync waits for the stream and returns it.
  *   - No exception or exit crosses the ABI.  A context is not thread-safe; separate contexts
  *     are independent.
+ *   - A NULL context, graph or TLR handle is rejected before any CUDA call: the entry point
+ *     returns MVN_ERR_ARG (mvn_last_error(NULL) returns "null context", mvn_launch_count(NULL)
+ *     returns -1, mvn_graph_kernels(NULL) returns 0, and mvn_graph_destroy(NULL) is a no-op
+ *     that returns MVN_OK).
  */
 #ifndef MVN_H
 #define MVN_H

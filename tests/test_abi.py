@@ -57,3 +57,30 @@ def test_null_context_is_an_argument_error(libpath):
     assert lib.mvn_sov(None, 1, None, None, None, 1, None, 0, None, None) == mvn.MVN_ERR_ARG
     assert lib.mvn_destroy(None) == mvn.MVN_ERR_ARG
     assert lib.mvn_last_error(None) == b"null context"
+
+
+def _zero_args(argtypes):
+    vals = []
+    for t in argtypes:
+        if t is ctypes.c_double:
+            vals.append(0.0)
+        elif t in (ctypes.c_int, ctypes.c_int64, ctypes.c_uint64):
+            vals.append(0)
+        else:
+            vals.append(None)  # every pointer, handle and string argument NULL
+    return vals
+
+
+def test_every_entry_point_rejects_null_handles(libpath):
+    """Each exported call, given NULL for its context/graph/TLR handle (and every other
+    pointer), returns the error the header's conventions state without reaching CUDA (this host
+    has no GPU, so a call that reached CUDA would report MVN_ERR_CUDA instead)."""
+    from paper_2405_14892_gb300 import mvn
+    lib = mvn.lib()
+    special = {"mvn_last_error": b"null context", "mvn_launch_count": -1,
+               "mvn_graph_kernels": 0, "mvn_graph_destroy": mvn.MVN_OK}
+    got = {}
+    for name, (_, argtypes) in mvn.SIGNATURES.items():
+        got[name] = getattr(lib, name)(*_zero_args(argtypes))
+    want = {name: special.get(name, mvn.MVN_ERR_ARG) for name in mvn.SIGNATURES}
+    assert got == want

@@ -292,16 +292,20 @@ def mvn_sov_batched(dims, offsets, a, b, L, n_points, n_shifts, seed, prec="fp64
     """Independent problems (dims[p], limits a[off_p:off_p+dims[p]]) sharing the leading blocks
     of L; returns a (nprob, 3) device tensor of {log P-hat, P-hat, err}."""
     nprob = len(dims)
+    if len(offsets) != nprob:
+        raise ValueError("dims and offsets must have the same length")
     d = (ctypes.c_int * nprob)(*[int(x) for x in dims])
     o = (ctypes.c_int64 * nprob)(*[int(x) for x in offsets])
     nmax = max([int(x) for x in dims] + [0])
+    # the library sees raw pointers: the limit vectors must hold every problem's slice
+    need = max([int(x) + int(y) for x, y in zip(offsets, dims) if int(y) > 0] + [0])
     Lp, ld = _mat(L, nmax, "L")
     out = torch.empty((nprob, 3), dtype=torch.float64, device=a.device)
     q = _qmc(n_points, n_shifts, seed, err_k)
     c = context()
     c.check(lib().mvn_sov_batched(c.h, nprob, ctypes.cast(d, _P), ctypes.cast(o, _P),
-                                  _vec(a, 0, "a"), _vec(b, 0, "b"), Lp, ld, ctypes.byref(q),
-                                  PREC[prec], _P(out.data_ptr())))
+                                  _vec(a, need, "a"), _vec(b, need, "b"), Lp, ld,
+                                  ctypes.byref(q), PREC[prec], _P(out.data_ptr())))
     return out
 
 

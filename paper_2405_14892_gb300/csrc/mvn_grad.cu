@@ -359,7 +359,6 @@ __global__ void __launch_bounds__(RV_THREADS, 4) k_sov_fwd_keep(const SovProblem
                                                                 const uint64_t* __restrict__ alpha,
                                                                 T* __restrict__ Y,
                                                                 int64_t ystride) {
-    constexpr bool kF32 = sizeof(T) == 4;
     constexpr int NV = RV_B / RV_SUB;
     __shared__ FwdSmem<T> sm;
     __shared__ int s_item;

@@ -377,6 +377,7 @@ def run_gpu(args):
         res_h.copy_(out3, non_blocking=True)
         torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    e2e_ms, e2e_value = job_time_and_value(e2e_ms, n * Ntot, world, dev)
     h2d = c_h.numel() * 8 + a_h.numel() * 8 + b_h.numel() * 8
     d2h = 3 * 8
 
@@ -407,7 +408,7 @@ def run_gpu(args):
         "rooflines": rooflines,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ctx.kernel_times.items()
                                if v[1]},
-        "e2e": {"value": world * n * Ntot / (e2e_ms * 1e-3), "unit": UNIT,
+        "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,

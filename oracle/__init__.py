@@ -406,6 +406,26 @@ def excursion(mu, Sigma, u, one_minus_alpha, qmc: QMC, prefix_dims=None, err_k: 
     return dict(order=order, marginal=pM, F=F, prefixes=ks, region=region, L=L)
 
 
+def posterior(mu, Sigma, obs, y, noise_var: float):
+    """Posterior of the field x ~ N(mu, Sigma) given y = A x + e, e ~ N(0, noise_var I), where the
+    indicator matrix A (n_obs x n) has A[k, obs[k]] = 1 (Sec. V-B):
+      Sigma_post = (Sigma^-1 + A^T A / noise_var)^-1                        (Eq. 7)
+      mu_post    = mu + Sigma_post A^T (y - A mu) / noise_var                 (Eq. 8)
+    written as printed, with explicit inverses (numpy's inv as the library step).  mu may be
+    None (zero mean).  Returns (mu_post, Sigma_post), Sigma_post full and symmetric."""
+    Sigma = np.asarray(Sigma, dtype=np.float64)
+    n = Sigma.shape[0]
+    obs = np.asarray(obs, dtype=np.int64)
+    y = np.asarray(y, dtype=np.float64)
+    mu = np.zeros(n) if mu is None else np.asarray(mu, dtype=np.float64)
+    A = np.zeros((obs.size, n))
+    A[np.arange(obs.size), obs] = 1.0
+    Sigma_post = np.linalg.inv(np.linalg.inv(Sigma) + A.T @ A / noise_var)
+    Sigma_post = 0.5 * (Sigma_post + Sigma_post.T)
+    mu_post = mu + Sigma_post @ (A.T @ (y - A @ mu)) / noise_var
+    return mu_post, Sigma_post
+
+
 # --------------------------------------------------------------------------- tile low rank (Sec. III-E)
 
 def tlr_tile_index(i: int, j: int, nt: int) -> int:

@@ -464,6 +464,78 @@ def test_excursion_mc_validation():
         assert abs(pmc - r["F"][k - 1]) < 4 * se + 3e-3, (k, pmc, r["F"][k - 1])
 
 
+# ----------------------------------------------------------------- posterior (Sec. V-B, Eqs. 7-8)
+
+def test_posterior_scalar_closed_form():
+    """One site observed once: precision adds, var = 1/(1/s2 + 1/t2), and the mean moves by
+    var/t2 of the residual (conjugate normal update)."""
+    s2, t2, m, yv = 2.0, 0.25, 0.3, 1.1
+    mp, P = oracle.posterior(np.array([m]), np.array([[s2]]), [0], [yv], t2)
+    var = 1.0 / (1.0 / s2 + 1.0 / t2)
+    assert P[0, 0] == pytest.approx(var, rel=1e-14)
+    assert mp[0] == pytest.approx(m + var / t2 * (yv - m), rel=1e-14)
+
+
+def _random_spd(n, seed):
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((n, n))
+    return G @ G.T / n + 0.1 * np.eye(n), rng
+
+
+def test_posterior_is_the_gaussian_conditional():
+    """(x, y) is jointly Gaussian with Cov(y) = A Sigma A^T + t2 I and Cov(x, y) = Sigma A^T, so
+    the posterior is the textbook conditional (Schur-complement form, no inverse of Sigma);
+    includes a site observed twice and an unobserved mean offset."""
+    n = 30
+    S, rng = _random_spd(n, 40)
+    mu = rng.standard_normal(n)
+    obs = np.array([3, 7, 7, 0, 29, 12, 18, 5, 22, 9, 14, 26])
+    y = rng.standard_normal(obs.size)
+    t2 = 0.3
+    mp, P = oracle.posterior(mu, S, obs, y, t2)
+    A = np.zeros((obs.size, n))
+    A[np.arange(obs.size), obs] = 1.0
+    Cyy = A @ S @ A.T + t2 * np.eye(obs.size)
+    Cxy = S @ A.T
+    P_ref = S - Cxy @ np.linalg.solve(Cyy, Cxy.T)
+    mp_ref = mu + Cxy @ np.linalg.solve(Cyy, y - A @ mu)
+    assert np.abs(P - P_ref).max() < 1e-12 * np.abs(S).max() * 100
+    assert np.abs(mp - mp_ref).max() < 1e-11
+
+
+def test_posterior_leaves_an_independent_block_unchanged():
+    S1, rng = _random_spd(8, 41)
+    S2, _ = _random_spd(5, 42)
+    S = np.zeros((13, 13))
+    S[:8, :8], S[8:, 8:] = S1, S2
+    mu = rng.standard_normal(13)
+    mp, P = oracle.posterior(mu, S, [1, 4, 6], rng.standard_normal(3), 0.5)
+    assert np.allclose(P[8:, 8:], S2, atol=1e-13)
+    assert np.allclose(P[8:, :8], 0.0, atol=1e-13)
+    assert np.allclose(mp[8:], mu[8:], atol=1e-13)
+    assert not np.allclose(P[:8, :8], S1)
+
+
+def test_posterior_repeated_observation_is_an_average():
+    """Observing a site twice (values y1, y2, noise t2 each) equals observing it once with the
+    mean of the two values and noise t2 / 2."""
+    S, rng = _random_spd(10, 43)
+    mu = rng.standard_normal(10)
+    m2, P2 = oracle.posterior(mu, S, [4, 4, 2], [0.7, 1.5, -0.2], 0.4)
+    m1, P1 = oracle.posterior(mu, S, [4], [1.1], 0.2)
+    m1b, P1b = oracle.posterior(m1, P1, [2], [-0.2], 0.4)   # then the third observation
+    assert np.allclose(P2, P1b, atol=1e-12) and np.allclose(m2, m1b, atol=1e-12)
+
+
+def test_posterior_noiseless_limit():
+    S, rng = _random_spd(12, 44)
+    obs = [2, 5, 11]
+    y = rng.standard_normal(3)
+    mp, P = oracle.posterior(None, S, obs, y, 1e-9)
+    assert np.allclose(mp[obs], y, atol=1e-6)
+    assert np.all(np.abs(np.diag(P)[obs]) < 1e-8)
+
+
 # ----------------------------------------------------------------- TLR (Sec. III-E)
 
 def test_tlr_truncation_eckart_young_and_planted_rank():

@@ -206,6 +206,35 @@ mvn_status mvn_sov_fp64_noalloc(int n, const double* a, const double* b, const d
                                 int64_t ld, const mvn_qmc* qmc, double* out3, double* path_logw,
                                 void* cuda_stream);
 
+/* ------------------------------------------------------------------ posterior field (Sec. V-B) */
+
+/* Posterior of a Gaussian field x ~ N(mu, Sigma) given noisy observations y = A x + e,
+ * e ~ N(0, noise_var I), of the sites obs[0..n_obs) (A = the n_obs x n indicator matrix):
+ *   Sigma_post = (Sigma^-1 + A^T A / noise_var)^-1                  (Eq. 7)
+ *   mu_post    = mu + Sigma_post A^T (y - A mu) / noise_var           (Eq. 8)
+ * computed without inverting Sigma, as the Schur complement that n_obs steps of the FP64 tile
+ * Cholesky leave in the bordered matrix [K, .; Sigma[:, obs], Sigma; (y - mu[obs])^T, 0] with
+ * K = Sigma[obs, obs] + noise_var I (the same matrices by the Woodbury identity).  The outputs
+ * feed mvn_excursion (Alg. 1: Sigma_post as the covariance, mu_post in the limits).
+ *   n        : number of sites; n = 0 does nothing.
+ *   mu       : device double[n], prior mean; NULL = zero mean.
+ *   Sigma    : device n x n, column-major, leading dimension ld >= n; lower triangle read.
+ *   obs      : device int32[n_obs], site indices in [0, n); a site may appear more than once
+ *              (repeated observations); n_obs = 0 gives the prior back.
+ *   y        : device double[n_obs], the observations.
+ *   noise_var: host, > 0 and finite.
+ *   mu_post  : device double[n] (output; may be mu itself).
+ *   Sigma_post: device n x n, leading dimension ld_post >= n; lower triangle written, strict
+ *              upper part untouched; may be Sigma itself (ld_post == ld).
+ *   info     : host, optional.  If given, the call waits for the stream and returns the device
+ *              status (MVN_ERR_NOT_PD with *info = the failing column of K; MVN_ERR_ARG with
+ *              *info = the 1-based position of an index outside [0, n) in obs).
+ * Workspace: (n_obs + n + 1)^2 doubles (grown on demand).  Asynchronous unless info is given.
+ * Errors: MVN_ERR_ARG (sizes, pointers, noise_var), MVN_ERR_OOM, MVN_ERR_CUDA. */
+mvn_status mvn_posterior(mvn_ctx* ctx, int n, const double* mu, const double* Sigma, int64_t ld,
+                         int n_obs, const int32_t* obs, const double* y, double noise_var,
+                         double* mu_post, double* Sigma_post, int64_t ld_post, int* info);
+
 /* ------------------------------------------------------------------ confidence region (Alg. 1) */
 
 /* Positive confidence region of level 1-alpha above threshold u for X ~ N(mu, Sigma):

@@ -137,9 +137,12 @@ __global__ void __launch_bounds__(256) k_syrk(double* __restrict__ A, int64_t ld
     }
 }
 
-mvn_status chol_f64_launch(mvn_ctx* ctx, int n, double* A, int64_t ld) {
-    for (int k0 = 0; k0 < n; k0 += CH_NB) {
-        const int nb = (n - k0 < CH_NB) ? n - k0 : CH_NB;
+// The first `ncols` steps of the right-looking factorisation of the order-n matrix A: columns
+// 0..ncols-1 become the factor's, and the trailing block A(ncols:, ncols:) is left holding the
+// Schur complement A22 - A21 A11^-1 A12 (lower triangle).  ncols = n is the full factorisation.
+mvn_status chol_f64_partial(mvn_ctx* ctx, int n, double* A, int64_t ld, int ncols) {
+    for (int k0 = 0; k0 < ncols; k0 += CH_NB) {
+        const int nb = (ncols - k0 < CH_NB) ? ncols - k0 : CH_NB;
         k_potrf<<<1, 256, 0, ctx->stream>>>(A, ld, k0, nb, ctx->d_status);
         MVN_LAUNCHED(ctx);
         const int r0 = k0 + nb;
@@ -154,6 +157,10 @@ mvn_status chol_f64_launch(mvn_ctx* ctx, int n, double* A, int64_t ld) {
                                                                    ctx->d_status)));
     }
     return MVN_OK;
+}
+
+mvn_status chol_f64_launch(mvn_ctx* ctx, int n, double* A, int64_t ld) {
+    return chol_f64_partial(ctx, n, A, ld, n);
 }
 
 extern "C" mvn_status mvn_cholesky(mvn_ctx* ctx, int n, double* A, int64_t ld, int tile,

@@ -1,9 +1,8 @@
 """Seeded synthetic inputs shared by the GPU library's tests/bench and the CPU oracle.
 
-This module holds none of the estimator's arithmetic: it only makes locations, limits, seeds
-and problem lists (numpy PCG64 generators), plus the data preparation of the paper's synthetic
-protocol (posterior mean/covariance from noisy observations, Sec. V-B Eqs. 7-8), which acts on a
-covariance matrix handed to it.
+This module holds none of the method's arithmetic: it only makes locations, limits, seeds,
+problem lists and the synthetic field observations of the paper's protocol (Sec. V-B), from
+numpy PCG64 generators.  The posterior of Eqs. 7-8 is not computed here.
 
 Workloads (the paper's Sec. V uses fields on regular grids in [0,1]^2; its datasets are not
 available, so these seeded inputs stand in for them):
@@ -11,8 +10,8 @@ available, so these seeded inputs stand in for them):
                 b_i ~ U(-1,1) (seed 1); tile 64; 10,000 lattice points x 20 shifts.
   W2  n=16384 : 128x128 grid, Matern nu=3/2, range 0.05, nugget 1e-4; a=-inf, b_i=0.5;
                 tile 512; 20,000 paths = 10 shifts x 2,000 points.
-  W3  n=4096  : 64x64 grid, Matern nu=1/2, range 0.1; posterior field from 640 noisy
-                observations (noise sd 0.5); threshold u=0.8, level 0.95; 256 prefix problems
+  W3  n=4096  : 64x64 grid, Matern nu=1/2, range 0.1; posterior field (Eqs. 7-8) from 640
+                noisy observations (noise sd 0.5); threshold u=0.8, level 0.95; 256 prefix problems
                 with dims ~ U{64..4096} (seed 3); 10,000 paths = 10 x 1,000.
   W4  n=4096  : 64x64 grid, Matern nu=3/2, sigma2=1, range 0.1, nugget 1e-4; a=-inf, b_i=0.5;
                 10,000 paths = 10 x 1,000.
@@ -62,25 +61,19 @@ def standard_normals(shape, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal(shape)
 
 
-def posterior_field(Sigma_prior: np.ndarray, n_obs: int, noise_sd: float, seed: int):
-    """Synthetic posterior protocol of Sec. V-B (Eqs. 7-8) on a given prior covariance:
-    draw a truth field x ~ N(0, Sigma_prior), observe n_obs random locations with additive
-    N(0, noise_sd^2) noise, and return (mu_post, Sigma_post, obs_index).  Eq. 7 is evaluated in
-    Woodbury form Sigma - Sigma A^T (A Sigma A^T + s^2 I)^-1 A Sigma, Eq. 8 with mu = 0."""
+def observations(Sigma_prior: np.ndarray, n_obs: int, noise_sd: float, seed: int):
+    """Synthetic observations of the protocol of Sec. V-B: a truth field x ~ N(0, Sigma_prior)
+    (drawn through a Cholesky factor of Sigma_prior + 1e-10 I), n_obs distinct sites chosen at
+    random (sorted), and y = x[sites] + N(0, noise_sd^2) noise.  Returns (sites int32, y, x).
+    The posterior given these (Eqs. 7-8) is computed by the library (mvn_posterior) and by the
+    oracle, not here."""
     rng = np.random.default_rng(seed)
     n = Sigma_prior.shape[0]
     C = np.linalg.cholesky(Sigma_prior + 1e-10 * np.eye(n))
     x = C @ rng.standard_normal(n)
     idx = np.sort(rng.choice(n, size=n_obs, replace=False))
     y = x[idx] + noise_sd * rng.standard_normal(n_obs)
-    SAt = Sigma_prior[:, idx]                                  # Sigma A^T
-    K = Sigma_prior[np.ix_(idx, idx)] + noise_sd ** 2 * np.eye(n_obs)
-    Kc = np.linalg.cholesky(K)
-    T = np.linalg.solve(Kc, SAt.T)                             # Kc^-1 A Sigma
-    Sigma_post = Sigma_prior - T.T @ T
-    Sigma_post = 0.5 * (Sigma_post + Sigma_post.T)
-    mu_post = SAt @ np.linalg.solve(Kc.T, np.linalg.solve(Kc, y))
-    return mu_post, Sigma_post, idx
+    return idx.astype(np.int32), y, x
 
 
 WORKLOADS = {

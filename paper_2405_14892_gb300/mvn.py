@@ -63,6 +63,8 @@ SIGNATURES = {
     "mvn_sov": (_I, [_P, _I, _P, _P, _P, _I64, _QP, _I, _P, _P]),
     "mvn_sov_grad": (_I, [_P, _I, _P, _P, _P, _I64, _QP, _I, _P, _P, _P, _P]),
     "mvn_sov_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _I64, _QP, _I, _P]),
+    "mvn_posterior": (_I, [_P, _I, _P, _P, _I64, _I, _P, _P, _D, _P, _P, _I64,
+                           ctypes.POINTER(_I)]),
     "mvn_excursion": (_I, [_P, _I, _P, _P, _I64, _D, _D, _I, _P, _QP, _I, _I, _P, _P, _P, _P]),
     "mvn_excursion_graph": (_I, [_P, _I, _P, _P, _I64, _D, _D, _I, _P, _QP, _I, _P, _P, _P, _P,
                                  ctypes.POINTER(_P)]),
@@ -307,6 +309,32 @@ def mvn_sov_batched(dims, offsets, a, b, L, n_points, n_shifts, seed, prec="fp64
                                   _vec(a, need, "a"), _vec(b, need, "b"), Lp, ld,
                                   ctypes.byref(q), PREC[prec], _P(out.data_ptr())))
     return out
+
+
+def mvn_posterior(mu: torch.Tensor | None, Sigma: torch.Tensor, obs: torch.Tensor,
+                  y: torch.Tensor, noise_var: float, out_Sigma: torch.Tensor | None = None,
+                  out_mu: torch.Tensor | None = None, check: bool = True):
+    """Posterior mean and covariance (Eqs. 7-8) of the field N(mu, Sigma) given y observed with
+    noise variance noise_var at the sites obs (int32 CUDA tensor).  Returns (mu_post, Sigma_post),
+    Sigma_post column-major with its lower triangle written (out_Sigma may be Sigma itself).
+    With check=True the call waits and raises MVNError on a device-side error."""
+    n = Sigma.shape[0]
+    Sp, ld = _mat(Sigma, n, "Sigma")
+    if out_Sigma is None:
+        out_Sigma = colmajor_empty(n, n, Sigma.device)
+    Op, ldo = _mat(out_Sigma, n, "out_Sigma")
+    if out_mu is None:
+        out_mu = torch.empty(n, dtype=torch.float64, device=Sigma.device)
+    n_obs = obs.numel()
+    if y.numel() != n_obs:
+        raise ValueError("y and obs must have the same length")
+    c = context()
+    info = _I(0)
+    c.check(lib().mvn_posterior(c.h, n, _vec(mu, n, "mu"), Sp, ld, n_obs,
+                                _vec(obs, n_obs, "obs", dtype=torch.int32),
+                                _vec(y, n_obs, "y"), float(noise_var), _vec(out_mu, n, "out_mu"),
+                                Op, ldo, ctypes.byref(info) if check else None))
+    return out_mu, out_Sigma
 
 
 def mvn_excursion(mu: torch.Tensor, Sigma: torch.Tensor, u: float, level: float, n_points: int,

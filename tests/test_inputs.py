@@ -1,6 +1,6 @@
 """The seeded input recipe on CPU: grid layout and Morton order, limits, problem lists and the
-synthetic posterior protocol (Sec. V-B, Eqs. 7-8), each checked against a property that does not
-restate the generator's own code."""
+synthetic observations of Sec. V-B, each checked against a property that does not restate the
+generator's own code."""
 import numpy as np
 import pytest
 
@@ -59,30 +59,19 @@ def test_prefix_problem_dims():
     assert abs(d.mean() - 2080) < 3 * 1164 / np.sqrt(256)
 
 
-def test_posterior_field_matches_the_information_form():
-    """Eq. 7 as returned (covariance form) against the information form
-    (Sigma^-1 + A^T A / s^2)^-1, and Eq. 8's mean against Sigma_post A^T y / s^2; the observation
-    vector is recovered from the generator's seeded draws."""
-    g, n_obs, sd, seed = 8, 20, 0.5, 3
+def test_observations_of_the_synthetic_protocol():
+    """Sec. V-B protocol: distinct sorted sites, y = truth at the sites plus N(0, sd^2) noise;
+    seeded.  (The posterior given them is the oracle's and the library's, not the input
+    module's.)"""
+    w = inputs.WORKLOADS["W3"]
+    g = 32
     c = inputs.grid_coords(g)
     h = np.sqrt(((c[:, None, :] - c[None, :, :]) ** 2).sum(-1))
-    S = np.exp(-h / 0.3) + 1e-8 * np.eye(g * g)
-    mu, P, idx = inputs.posterior_field(S, n_obs, sd, seed)
-    n = g * g
-    A = np.zeros((n_obs, n))
-    A[np.arange(n_obs), idx] = 1.0
-    P_info = np.linalg.inv(np.linalg.inv(S) + A.T @ A / sd ** 2)
-    assert np.allclose(P, P_info, atol=1e-9)
-    assert np.allclose(P, P.T)
-    assert np.linalg.eigvalsh(P).min() > 0
-    # observed sites: posterior variance below both the prior variance and the noise variance
-    pv = np.diag(P)[idx]
-    assert np.all(pv < np.diag(S)[idx]) and np.all(pv < sd ** 2)
-    # the same draws: truth x = chol(S + 1e-10 I) z, then the site choice, then the noise
-    rng = np.random.default_rng(seed)
-    C = np.linalg.cholesky(S + 1e-10 * np.eye(n))
-    x = C @ rng.standard_normal(n)
-    idx2 = np.sort(rng.choice(n, size=n_obs, replace=False))
-    y = x[idx2] + sd * rng.standard_normal(n_obs)
-    assert np.array_equal(idx, idx2)
-    assert np.allclose(mu, P_info @ A.T @ y / sd ** 2, atol=1e-8)
+    S = np.exp(-h / w["range"])
+    idx, y, x = inputs.observations(S, 400, w["noise_sd"], w["field_seed"])
+    assert idx.dtype == np.int32 and idx.shape == (400,) and y.shape == (400,)
+    assert np.all(np.diff(idx) > 0) and idx[0] >= 0 and idx[-1] < g * g
+    e = y - x[idx]
+    assert abs(e.std() - w["noise_sd"]) < 0.1 * w["noise_sd"] and abs(e.mean()) < 0.1
+    i2, y2, _ = inputs.observations(S, 400, w["noise_sd"], w["field_seed"])
+    assert np.array_equal(idx, i2) and np.array_equal(y, y2)

@@ -473,8 +473,10 @@ def tlr_cholesky(T: dict):
       A_ik  = U_ik V_ik^T - sum_{l<k} U_il (V_il^T V_kl) U_kl^T   (accumulated densely)
       A_ik ~= U' V'^T truncated at acc (recompression);  L_ik = U' (L_kk^-1 V')^T.
     Returns a new dict with the factor in the same form (D holds the L_kk).
-    parity unpinned beyond: acc -> 0 reduces to the dense Cholesky (pinned), and the
-    reconstruction error of the factor is of the order of acc (checked)."""
+    Pinned by its exact cases: acc -> 0 reduces to the dense Cholesky, and a covariance
+    D + U U^T (D block-diagonal on the tiles, U of rank r), whose tiles and factor tiles all have
+    rank r, is factorised exactly with the rank capped at r.  At a truncating acc the result is
+    an approximation; its reconstruction error is checked to be of the order of acc."""
     nt, acc, kmax = T["nt"], T["acc"], T["max_rank"]
     D = [d.copy() for d in T["D"]]
     U = dict(T["U"])

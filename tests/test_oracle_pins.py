@@ -564,6 +564,36 @@ def test_tlr_compress_and_cholesky_reduce_to_dense():
     np.testing.assert_allclose(L, np.linalg.cholesky(S), atol=1e-9)
 
 
+def test_tlr_cholesky_planted_low_rank_is_exact():
+    """Sigma = D + U U^T with D block-diagonal on the tiles and U of rank r: every off-diagonal
+    tile of Sigma and of its Cholesky factor has rank r, so the TLR factorisation capped at rank r
+    loses nothing and must equal the dense factor to rounding, with factor ranks r (ragged last
+    tile included); compressed at a cap of r - 1 every tile reports the cap and loses its
+    smallest singular value."""
+    rng = np.random.default_rng(31)
+    m, nt, r = 24, 5, 3
+    n = m * nt - 7
+    D = np.zeros((n, n))
+    for i in range(nt):
+        b = slice(i * m, min(n, (i + 1) * m))
+        k = b.stop - b.start
+        G = rng.standard_normal((k, k))
+        D[b, b] = G @ G.T / k + np.eye(k)
+    U = rng.standard_normal((n, r))
+    S = D + U @ U.T
+    T = oracle.tlr_compress(S, m, 1e-12, r)
+    assert np.all(T["ranks"] == r) and T["capped"] == 0
+    F = oracle.tlr_cholesky(T)
+    assert np.all(F["ranks"] == r)
+    np.testing.assert_allclose(oracle.tlr_to_dense(F), np.linalg.cholesky(S), atol=1e-12)
+    T2 = oracle.tlr_compress(S, m, 1e-12, r - 1)
+    assert T2["capped"] == len(T2["ranks"]) and np.all(T2["ranks"] == r - 1)
+    A = S[2 * m:3 * m, 0:m]
+    E = A - T2["U"][(2, 0)] @ T2["V"][(2, 0)].T
+    assert np.linalg.norm(E, 2) == pytest.approx(np.linalg.svd(A, compute_uv=False)[r - 1],
+                                                 rel=1e-10)
+
+
 def test_tlr_cholesky_error_follows_accuracy():
     c = inputs.grid_coords(16, order="morton")
     S = oracle.matern(c, 1.0, 0.1, 0.5, nugget=1e-6)

@@ -9,8 +9,9 @@ and never imports it; both sides are fed by the seeded generators in
 
 Every function names the passage of the paper it follows (Eq. / Alg. / Sec. numbers of
 arXiv 2405.14892).  Library primitives used as single steps: libm ``erfc``, scipy's Bessel
-``kv`` and ``gamma`` (Eq. 6), numpy's ``argsort`` (Alg. 1 ordering) and ``svd`` (TLR
-compression), Python's exact integer ``isqrt`` (lattice generators).
+``kv`` and ``gamma`` (Eq. 6), numpy's ``argsort`` (Alg. 1 ordering), ``svd`` (TLR
+compression) and ``inv`` (the inverses printed in Eq. 7), Python's exact integer ``isqrt``
+(lattice generators).
 
 Pins (tests/test_oracle_*.py) tie each function to something other than itself: closed forms,
 quadrature, brute-force Monte Carlo, textbook special cases and invariants.  Parts with no such

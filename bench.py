@@ -110,6 +110,7 @@ def cpu_oracle_throughput(sample_paths: int = 48, chol_n: int = 2048, problem=No
     import oracle
     w, a, b, S, L = problem if problem is not None else cpu_oracle_problem()
     n = S.shape[0]
+    chol_n = min(chol_n, n)
     Ntot = w["Ns"] * w["M"]
     q = oracle.QMC(w["Ns"], w["M"], w["seed"])
     cores = os.cpu_count() or 1

@@ -1,6 +1,6 @@
 """Host logic of bench.py on CPU: the clock-record parser, the algorithmic work counted per
-kernel launch (checked against closed forms of the same sums), the DRAM-traffic scaling and the
-single-rank throughput.  No GPU."""
+kernel launch (checked against closed forms of the same sums), the DRAM-traffic scaling, the
+single-rank throughput and the reference arm's JSON line.  No GPU."""
 import math
 
 import pytest
@@ -117,3 +117,33 @@ def test_single_rank_throughput():
     ms, v = bench.job_time_and_value(109.1, 16384 * 20000, 1)
     assert ms == 109.1
     assert v == pytest.approx(16384 * 20000 / 0.1091)
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """`bench.py --impl reference` prints one JSON line with the keys the bench contract asks
+    of the reference arm (here on a 16 x 16 grid instead of the 128 x 128 one, to stay fast)."""
+    import json
+    import types
+
+    from paper_2405_14892_gb300 import inputs
+
+    def small_workload(grid=0):
+        w = dict(inputs.WORKLOADS["W2"], g=16, name="sov-n256-matern32-test")
+        c = inputs.grid_coords(16)
+        a, b = inputs.limits_for(w, c.shape[0])
+        return w, c, a, b
+
+    monkeypatch.setattr(bench, "workload", small_workload)
+    monkeypatch.delenv("RANK", raising=False)
+    bench.run_reference(types.SimpleNamespace(steps=2, warmup=1, gpus=1))
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == bench.UNIT and d["metric"] == bench.METRIC
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
+    assert "16 of 20000 paths at n=256" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "sov-n256-matern32-test"

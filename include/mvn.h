@@ -195,7 +195,9 @@ mvn_status mvn_sov_batched(mvn_ctx* ctx, int nprob, const int* dims,
  *   - limits: n <= 256, n_points * n_shifts <= 262144, n_shifts <= 64; larger sizes return
  *     MVN_ERR_ARG before any work is enqueued;
  *   - the first call on each device looks up the array's device address (cudaGetSymbolAddress);
- *     make that first call before any stream capture on that device;
+ *     make that first call before any stream capture on that device.  A device reset
+ *     (cudaDeviceReset) or a new primary context invalidates that address: the first call in the
+ *     new context looks it up again (so it too should come before any capture);
  *   - every call shares the one array: calls that overlap on the GPU (other streams, other host
  *     threads) race and give wrong results -- serialise them;
  *   - no device-side argument check: limits with a_i > b_i or NaN give NaN results; every path
@@ -345,6 +347,17 @@ mvn_status mvn_lattice_shifts(mvn_ctx* ctx, uint64_t seed, int M, int n, uint64_
  * pipeline, tcgen05 MMAs and TMEM drains as the sweep's far GEMM.  1 <= K <= 65536; the call
  * uses workspace of ~(K + 256)^2 * 8 bytes.  Asynchronous; errors via mvn_sync. */
 mvn_status mvn_tc_selftest(mvn_ctx* ctx, int K, const double* Y, const double* L, float* S);
+
+/* The elementwise step of Eq. 2 (Alg. 3's inner step) as the sweeps of precision prec run it,
+ * on `count` independent inputs: a' = (a - s) / lii, b' = (b - s) / lii with the lattice point
+ * w = ((W >> 11) + 1/2) 2^-53 of the 64-bit integer W; writes y (the transformed variable) and
+ * delta (the factor Phi(b') - Phi(a'), 0 when it underflows).  MVN_FP64: the FP64 step of the
+ * FP64 sweep; MVN_MIXED_SIMT: the FP32 step of the CUDA-core mixed sweep (s and lii rounded to
+ * FP32); MVN_MIXED: the FP32-only step of the tensor-core sweep (likewise).  All arrays are
+ * device arrays of `count` entries (W: uint64).  Asynchronous; errors: MVN_ERR_ARG. */
+mvn_status mvn_sov_step_test(mvn_ctx* ctx, mvn_prec prec, int64_t count, const double* a,
+                             const double* b, const double* s, const double* lii,
+                             const uint64_t* W, double* y, double* delta);
 
 /* Self-test of the bounded device-side waits: a kernel waits on an mbarrier that nothing
  * completes, gives up after budget_cycles (1e3 .. 4e9 SM clock cycles) and raises

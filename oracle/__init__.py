@@ -75,7 +75,10 @@ def _load():
     lib.orc_cholesky_grad.restype = None
     lib.orc_cholesky_grad.argtypes = [i32, P, i64, P]
     lib.orc_sov_paths.restype = None
-    lib.orc_sov_paths.argtypes = [i32, P, P, P, i64, i64, P, P, i64, i64, P, P, i32, P, P, i32]
+    lib.orc_sov_paths.argtypes = [i32, P, P, P, i64, i64, P, P, i64, i64, P, P, P, i32, P, P,
+                                  i32]
+    lib.orc_sov_step_vec.restype = None
+    lib.orc_sov_step_vec.argtypes = [i64, P, P, P, P, P, P, P]
     lib.orc_sov_grad.restype = None
     lib.orc_sov_grad.argtypes = [i32, P, P, P, i64, i64, i64, P, P, P, P, P, P]
     _lib = lib
@@ -271,11 +274,33 @@ class QMC:
         return self.Ns * self.M
 
 
+def sov_step(a, b, s, lii, W):
+    """One dimension of Eq. 2 (Alg. 3's inner step) on independent inputs: the standardised
+    limits a' = (a - s)/L_ii, b' = (b - s)/L_ii, the factor Delta = Phi(b') - Phi(a') (upper-tail
+    form Q(a') - Q(b') when a' > 0) and y = Phi^-1(Phi(a') + w Delta) (-Phi^-1(Q(a') - w Delta)
+    when a' > 0), with w = ((W >> 11) + 1/2) 2^-53 from the 64-bit lattice integer W.  Delta = 0
+    gives y = the finite limit; a Phi^-1 argument rounded to 0 or 1 is moved inside (0, 1).
+    Returns (y, Delta), broadcast over the inputs."""
+    a, b, s, lii, W = np.broadcast_arrays(np.asarray(a, dtype=np.float64),
+                                          np.asarray(b, dtype=np.float64),
+                                          np.asarray(s, dtype=np.float64),
+                                          np.asarray(lii, dtype=np.float64),
+                                          np.asarray(W, dtype=np.uint64))
+    a, b, s, lii, W = (np.ascontiguousarray(x) for x in (a, b, s, lii, W))
+    y = np.empty(a.shape)
+    d = np.empty(a.shape)
+    _load().orc_sov_step_vec(a.size, _ptr(a), _ptr(b), _ptr(s), _ptr(lii), _ptr(W), _ptr(y),
+                             _ptr(d))
+    return y, d
+
+
 def sov_logw(a, b, L, qmc: QMC, paths: Sequence[int] | None = None, return_y: bool = False,
-             prefixes: Sequence[int] | None = None, nthreads: int = 0):
+             prefixes: Sequence[int] | None = None, nthreads: int = 0,
+             return_delta: bool = False):
     """Per-path log-weights logw_p = sum_i log(Phi(b'_i) - Phi(a'_i)) of Eq. 2/3 (Alg. 3 on one
     path), on the shifted lattice.  `paths` is a contiguous range (p0, p1) or None = all.
-    With `prefixes`, also returns the log-weight after each prefix length (for Alg. 1)."""
+    With `return_y` / `return_delta`, also returns y and the factors Delta (paths x n), and with
+    `prefixes` the log-weight after each prefix length (for Alg. 1), in that order."""
     a = np.ascontiguousarray(a, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
     n = a.size
@@ -285,6 +310,7 @@ def sov_logw(a, b, L, qmc: QMC, paths: Sequence[int] | None = None, return_y: bo
     p0, p1 = (0, qmc.Ntot) if paths is None else (int(paths[0]), int(paths[1]))
     logw = np.empty(p1 - p0)
     Y = np.empty((p1 - p0, n)) if return_y else None
+    D = np.empty((p1 - p0, n)) if return_delta else None
     kp = None
     lp = None
     if prefixes is not None:
@@ -293,11 +319,14 @@ def sov_logw(a, b, L, qmc: QMC, paths: Sequence[int] | None = None, return_y: bo
     _load().orc_sov_paths(n, _ptr(a), _ptr(b), _ptr(Lf), max(n, 1), qmc.Ns, _ptr(alpha),
                           _ptr(delta), p0, p1, _ptr(logw),
                           _ptr(Y) if Y is not None else None,
+                          _ptr(D) if D is not None else None,
                           0 if kp is None else kp.size, _ptr(kp) if kp is not None else None,
                           _ptr(lp) if lp is not None else None, int(nthreads))
     out = [logw]
     if return_y:
         out.append(Y)
+    if return_delta:
+        out.append(D)
     if prefixes is not None:
         out.append(lp)
     return out[0] if len(out) == 1 else tuple(out)

@@ -209,12 +209,43 @@ static double orc_interior(double p) {
     return p;
 }
 
+/* One dimension of Eq. 2 with the tail-stable branches, given the standardised limits a', b'
+ * and the path's uniform w: returns Delta = Phi(b') - Phi(a') and writes y.
+ *   a' > 0 : Delta = Q(a') - Q(b'),    y = -Phi^-1(Q(a') - w Delta)
+ *   else   : Delta = Phi(b') - Phi(a'), y =  Phi^-1(Phi(a') + w Delta)
+ * Delta = 0 (underflow) gives y = the finite limit (a' if a' > 0, else b'). */
+static double orc_step(double ap, double bp, double w, double* y) {
+    double delta;
+    if (ap > 0.0) {
+        double qa = orc_Q(ap), qb = orc_Q(bp);
+        delta = qa - qb;
+        *y = (delta > 0.0) ? -orc_Phinv(orc_interior(qa - w * delta)) : ap;
+    } else {
+        double pa = orc_Phi(ap), pb = orc_Phi(bp);
+        delta = pb - pa;
+        *y = (delta > 0.0) ? orc_Phinv(orc_interior(pa + w * delta)) : bp;
+    }
+    return delta;
+}
+
+/* The step above on `count` independent inputs, each given as the limits a, b, the limit shift
+ * s, the diagonal entry L_ii and the lattice integer W (w = ((W >> 11) + 1/2) 2^-53):
+ * a' = (a - s) / L_ii, b' = (b - s) / L_ii; writes y and Delta. */
+void orc_sov_step_vec(int64_t count, const double* a, const double* b, const double* s,
+                      const double* lii, const uint64_t* W, double* y, double* delta) {
+    for (int64_t t = 0; t < count; ++t) {
+        double w = ((double)(W[t] >> 11) + 0.5) * 0x1p-53;
+        delta[t] = orc_step((a[t] - s[t]) / lii[t], (b[t] - s[t]) / lii[t], w, &y[t]);
+    }
+}
+
 /* One SOV path (Eq. 2, Alg. 3): returns the log-weight sum_i log(Phi(b'_i) - Phi(a'_i)).
- * w[i] are the path's uniforms, y[i] receives the transformed variables.
+ * w[i] are the path's uniforms, y[i] receives the transformed variables; ap_out, bp_out and
+ * d_out (optional) receive a'_i, b'_i and Delta_i.
  * If kprefix != NULL, logw_prefix[t] receives the log-weight after kprefix[t] dimensions. */
 static double orc_sov_one(int n, const double* a, const double* b, const double* L, int64_t ld,
                           const double* w, double* y, double* ap_out, double* bp_out,
-                          int nprefix, const int* kprefix, double* logw_prefix) {
+                          double* d_out, int nprefix, const int* kprefix, double* logw_prefix) {
     double logw = 0.0;
     int t = 0;
     for (int i = 0; i < n; ++i) {
@@ -224,20 +255,11 @@ static double orc_sov_one(int n, const double* a, const double* b, const double*
         double lii = L[i + (int64_t)i * ld];
         double ap = (a[i] - s) / lii; /* -inf stays -inf */
         double bp = (b[i] - s) / lii;
-        double delta, yi;
-        if (ap > 0.0) {
-            double qa = orc_Q(ap), qb = orc_Q(bp);
-            delta = qa - qb;
-            yi = (delta > 0.0) ? -orc_Phinv(orc_interior(qa - w[i] * delta)) : ap;
-        } else {
-            double pa = orc_Phi(ap), pb = orc_Phi(bp);
-            delta = pb - pa;
-            yi = (delta > 0.0) ? orc_Phinv(orc_interior(pa + w[i] * delta)) : bp;
-        }
+        double delta = orc_step(ap, bp, w[i], &y[i]);
         logw += (delta > 0.0) ? log(delta) : -INFINITY;
-        y[i] = yi;
         if (ap_out) ap_out[i] = ap;
         if (bp_out) bp_out[i] = bp;
+        if (d_out) d_out[i] = delta;
     }
     while (t < nprefix && kprefix[t] == n) logw_prefix[t++] = logw;
     return logw;
@@ -249,11 +271,12 @@ static double orc_sov_one(int n, const double* a, const double* b, const double*
  *   delta[q*n+i]  : random shift of shift q, dimension i (u64 fixed point)
  *   logw[p - p0]  : output log-weights
  *   Y (optional)  : Y[(p - p0) * n + i] receives y_i of the path
+ *   D (optional)  : D[(p - p0) * n + i] receives the factor Delta_i of the path
  *   kprefix/nprefix (optional): sorted prefix lengths; logw_prefix[(p-p0)*nprefix + t]. */
 void orc_sov_paths(int n, const double* a, const double* b, const double* L, int64_t ld,
                    int64_t Ns, const uint64_t* alpha, const uint64_t* delta, int64_t p0,
-                   int64_t p1, double* logw, double* Y, int nprefix, const int* kprefix,
-                   double* logw_prefix, int nthreads) {
+                   int64_t p1, double* logw, double* Y, double* D, int nprefix,
+                   const int* kprefix, double* logw_prefix, int nthreads) {
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel
@@ -269,8 +292,9 @@ void orc_sov_paths(int n, const double* a, const double* b, const double* L, int
             uint64_t j = (uint64_t)(p - q * Ns) + 1u;
             for (int i = 0; i < n; ++i) w[i] = orc_point(j, alpha[i], delta[q * n + i]);
             double* lp = logw_prefix ? logw_prefix + (p - p0) * nprefix : NULL;
-            logw[p - p0] = orc_sov_one(n, a, b, L, ld, w, y, NULL, NULL, lp ? nprefix : 0,
-                                       kprefix, lp);
+            logw[p - p0] = orc_sov_one(n, a, b, L, ld, w, y, NULL, NULL,
+                                       D ? D + (p - p0) * n : NULL, lp ? nprefix : 0, kprefix,
+                                       lp);
             if (Y) memcpy(Y + (p - p0) * n, y, sizeof(double) * (size_t)n);
         }
         free(w);
@@ -337,7 +361,7 @@ void orc_sov_grad(int n, const double* a, const double* b, const double* L, int6
         int64_t q = p / Ns;
         uint64_t j = (uint64_t)(p - q * Ns) + 1u;
         for (int i = 0; i < n; ++i) w[i] = orc_point(j, alpha[i], delta[q * n + i]);
-        orc_sov_one(n, a, b, L, ld, w, y, ap, bp, 0, NULL, NULL);
+        orc_sov_one(n, a, b, L, ld, w, y, ap, bp, NULL, 0, NULL, NULL);
         orc_sov_grad_one(n, a, b, L, ld, w, y, ap, bp, weights[p], ybar, ga, gb, gL);
     }
     free(w);

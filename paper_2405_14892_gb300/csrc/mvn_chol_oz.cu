@@ -218,9 +218,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(const OzWork w,
                                      &sm.full[slot]);
                 }
             }
-            // every issued copy has landed before the shared memory is released
+            // every issued copy has landed before the shared memory is released (a wait that
+            // runs out here leaves the result unreliable: it raises the status too)
             for (uint32_t k = (q > OZ_NST ? q - OZ_NST : 0); k < q; ++k)
-                tc::mbar_wait(&sm.full[k % OZ_NST], (k / OZ_NST) & 1u, OZ_WAIT);
+                if (!tc::mbar_wait(&sm.full[k % OZ_NST], (k / OZ_NST) & 1u, OZ_WAIT))
+                    dev_raise(status, MVN_ERR_TIMEOUT, 0);
         }
     } else if (warp == OZ_DW + 1) {
         // ---------------------------------------------------------------- MMA issue
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(const OzWork w,
             }
             // all issued MMAs complete before TMEM and shared memory are released
             tc::mma_commit(&sm.fin);
-            tc::mbar_wait(&sm.fin, 0, OZ_WAIT);
+            if (!tc::mbar_wait(&sm.fin, 0, OZ_WAIT)) dev_raise(status, MVN_ERR_TIMEOUT, 0);
         }
     } else {
         // ---------------------------------------------------------------- drain + epilogue

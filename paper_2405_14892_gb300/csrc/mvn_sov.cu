@@ -329,6 +329,58 @@ extern "C" mvn_status mvn_sov_batched(mvn_ctx* ctx, int nprob, const int* dims,
     return sov_reduce_launch(ctx, logw, Ns, M, qmc->err_k, out3, nprob, Ntot);
 }
 
+// ---------------------------------------------------------------- ABI: mvn_sov_step_test
+//
+// The elementwise step of Eq. 2 exactly as the sweeps run it, on independent inputs (for parity
+// of the tail branches, the underflow branch and the interior clamp, which the lattice reaches
+// only rarely).  The lattice point comes from the 64-bit integer W as in the sweeps.
+__global__ void k_sov_step_test(int prec, int64_t count, const double* __restrict__ a,
+                                const double* __restrict__ b, const double* __restrict__ s,
+                                const double* __restrict__ lii, const uint64_t* __restrict__ W,
+                                double* __restrict__ y, double* __restrict__ delta) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const double av = a[t], bv = b[t];
+    if (prec == MVN_FP64) {
+        double d;
+        y[t] = sov_step_f64(av, bv, s[t], lii[t], lattice_w(1u, W[t], 0u), d);
+        delta[t] = d;
+    } else if (prec == MVN_MIXED_SIMT) {  // the CUDA-core mixed sweep's step
+        double d;
+        y[t] = (double)sov_step_f32(av, bv, (float)s[t], (float)lii[t], lattice_w(1u, W[t], 0u),
+                                    d);
+        delta[t] = d;
+    } else {  // the tensor-core sweep's FP32-only step
+        float w, wc, dh, dl;
+        uint64_t m;
+        int dex;
+        lattice_wf(1u, W[t], 0u, w, wc, m);
+        y[t] = (double)sov_step_f32p((float)av, (float)bv, av, bv, av == -INFINITY,
+                                     bv == INFINITY, (float)s[t], (float)lii[t], w, wc, m, dh,
+                                     dl, dex);
+        delta[t] = ldexp((double)dh + (double)dl, dex);
+    }
+}
+
+extern "C" mvn_status mvn_sov_step_test(mvn_ctx* ctx, mvn_prec prec, int64_t count,
+                                        const double* a, const double* b, const double* s,
+                                        const double* lii, const uint64_t* W, double* y,
+                                        double* delta) {
+    if (!ctx) return MVN_ERR_ARG;
+    if (prec != MVN_FP64 && prec != MVN_MIXED && prec != MVN_MIXED_SIMT)
+        return mvn_fail(ctx, MVN_ERR_ARG, "unknown precision");
+    if (count < 0 || count > ((int64_t)1 << 31))
+        return mvn_fail(ctx, MVN_ERR_ARG, "count out of range");
+    if (count == 0) return MVN_OK;
+    if (!a || !b || !s || !lii || !W || !y || !delta)
+        return mvn_fail(ctx, MVN_ERR_ARG, "null pointer");
+    MVN_CUDA(ctx, cudaSetDevice(ctx->device));
+    k_sov_step_test<<<(unsigned)((count + 255) / 256), 256, 0, ctx->stream>>>(
+        (int)prec, count, a, b, s, lii, W, y, delta);
+    MVN_LAUNCHED(ctx);
+    return MVN_OK;
+}
+
 // ---------------------------------------------------------------- ABI: mvn_sov_fp64_noalloc
 //
 // FP64 SOV estimate for callers that cannot allocate device memory at call time: code that
@@ -365,24 +417,65 @@ __global__ void k_prime_compact(const uint8_t* flag, int bound, int* primes, int
 __global__ void k_alpha(const int* primes, int n, uint64_t* alpha);
 __global__ void k_shifts(uint64_t seed, int M, int n, uint64_t* delta);
 
-// Device address of the scratch array, looked up once per device (the symbol name is only a
-// host-side stand-in: passing it to a kernel would not give the device address).
+// Identity of the calling thread's current CUDA context (driver entry points reached through the
+// runtime, so the library does not link the driver library itself).  Returns false if there is
+// no current context or the entry points are unavailable.
+typedef int (*PfnCtxGetCurrent)(void**);
+typedef int (*PfnCtxGetId)(void*, unsigned long long*);
+static bool current_context_id(unsigned long long* id) {
+    static PfnCtxGetCurrent get_cur = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {  // called with the caller's mutex held
+        looked_up = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = (PfnCtxGetCurrent)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (PfnCtxGetId)f;
+    }
+    if (!get_cur || !get_id) return false;
+    void* ctx = nullptr;
+    if (get_cur(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
+
+// Device address of the scratch array (the symbol name is only a host-side stand-in: passing it
+// to a kernel would not give the device address).  Looked up once per device and context: a
+// device reset (cudaDeviceReset) or a new primary context reloads the module, so a context whose
+// identity differs from the cached one gets a fresh lookup.  Without the context identity (driver
+// entry points unavailable) the address is looked up on every call.
 static NoAllocScratch* noalloc_scratch_ptr(int device, cudaError_t* err) {
-    static NoAllocScratch* ptrs[256] = {};
+    struct Entry {
+        NoAllocScratch* ptr;
+        unsigned long long ctx;
+    };
+    static Entry cache[256] = {};
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
     if (device < 0 || device >= 256) {
         *err = cudaErrorInvalidDevice;
         return nullptr;
     }
-    if (!ptrs[device]) {
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
+    Entry& e = cache[device];
+    if (!e.ptr || !have_id || e.ctx != id) {
         void* p = nullptr;
         *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (*err != cudaSuccess) return nullptr;
-        ptrs[device] = (NoAllocScratch*)p;
+        e.ptr = (NoAllocScratch*)p;
+        // the lookup makes the device's primary context current if it was not yet
+        e.ctx = current_context_id(&id) ? id : 0;
     }
     *err = cudaSuccess;
-    return ptrs[device];
+    return e.ptr;
 }
 
 extern "C" mvn_status mvn_sov_fp64_noalloc(int n, const double* a, const double* b,

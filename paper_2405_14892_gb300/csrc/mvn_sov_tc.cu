@@ -372,15 +372,20 @@ __device__ __forceinline__ void tc_setup(TcSmem& sm) {
 }
 
 // Before shared and tensor memory are released: every copy this CTA issued has landed and every
-// MMA it issued has completed (bounded waits; also after an aborted wait).
-__device__ __forceinline__ void tc_quiesce(TcSmem& sm, const TcPipe& pp, uint32_t dphase) {
+// MMA it issued has completed (bounded waits; also after an aborted wait).  A wait that runs out
+// here means work may still be in flight when the memory is released, so the result cannot be
+// trusted: it raises MVN_ERR_TIMEOUT like the waits of the main loop.
+__device__ __forceinline__ void tc_quiesce(TcSmem& sm, const TcPipe& pp, uint32_t dphase,
+                                           int* status) {
     if (threadIdx.x != 0) return;
+    bool ok = true;
     const uint32_t q0 = pp.q_load > TC_NST ? pp.q_load - TC_NST : 0u;
     for (uint32_t q = q0; q < pp.q_load; ++q)
-        tc::mbar_wait(&sm.full[q % TC_NST], (q / TC_NST) & 1u, TC_WAIT_BUDGET);
-    if (dphase > 0) tc::mbar_wait(&sm.dbar, (dphase - 1) & 1u, TC_WAIT_BUDGET);
+        ok &= tc::mbar_wait(&sm.full[q % TC_NST], (q / TC_NST) & 1u, TC_WAIT_BUDGET);
+    if (dphase > 0) ok &= tc::mbar_wait(&sm.dbar, (dphase - 1) & 1u, TC_WAIT_BUDGET);
     tc::mma_commit(&sm.fin);
-    tc::mbar_wait(&sm.fin, 0, TC_WAIT_BUDGET);
+    ok &= tc::mbar_wait(&sm.fin, 0, TC_WAIT_BUDGET);
+    if (!ok) dev_raise(status, MVN_ERR_TIMEOUT, 0);
 }
 
 __device__ __forceinline__ void tc_teardown(TcSmem& sm) {
@@ -558,7 +563,7 @@ __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
         if (valid && P.logw) P.logw[p] = lp.log_value();
         __syncthreads();
     }
-    tc_quiesce(sm, pp, dphase);
+    tc_quiesce(sm, pp, dphase, bt.status);
     tc_teardown(sm);
 }
 
@@ -724,7 +729,7 @@ __global__ void __launch_bounds__(TC_P, 2) k_tc_selftest(int rb, const uint8_t* 
     if (!ok && t == 0) dev_raise(status, MVN_ERR_TIMEOUT, 0);
     if (ok)
         for (int v = 0; v < TC_N; ++v) S[t * TC_N + v] = s[v];
-    tc_quiesce(sm, pp, 0);
+    tc_quiesce(sm, pp, 0, status);
     tc_teardown(sm);
 }
 

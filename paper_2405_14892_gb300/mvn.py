@@ -83,6 +83,7 @@ SIGNATURES = {
     "mvn_lattice_alpha": (_I, [_P, _I, _P]),
     "mvn_lattice_shifts": (_I, [_P, _U64, _I, _I, _P]),
     "mvn_tc_selftest": (_I, [_P, _I, _P, _P, _P]),
+    "mvn_sov_step_test": (_I, [_P, _I, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "mvn_sov_fp64_noalloc": (_I, [_I, _P, _P, _P, _I64, _QP, _P, _P, _P]),
     "mvn_wait_selftest": (_I, [_P, _I64]),
     "mvn_timing": (_I, [_P, _I]),
@@ -464,6 +465,20 @@ def mvn_tc_selftest(Y: torch.Tensor, L: torch.Tensor) -> torch.Tensor:
     c.check(lib().mvn_tc_selftest(c.h, K, _vec(Y.contiguous(), 128 * K, "Y"),
                                   _vec(L.contiguous(), 128 * K, "L"), _P(S.data_ptr())))
     return S
+
+
+def mvn_sov_step_test(a, b, s, lii, W, prec: str = "fp64"):
+    """The sweeps' elementwise step of Eq. 2 on independent inputs (FP64 CUDA tensors a, b, s,
+    lii and an int64 tensor W holding the lattice integers' bits).  Returns (y, delta)."""
+    n = a.numel()
+    y = torch.empty(n, dtype=torch.float64, device=a.device)
+    d = torch.empty(n, dtype=torch.float64, device=a.device)
+    c = context()
+    c.check(lib().mvn_sov_step_test(c.h, PREC[prec], n, _vec(a, n, "a"), _vec(b, n, "b"),
+                                    _vec(s, n, "s"), _vec(lii, n, "lii"),
+                                    _vec(W, n, "W", dtype=torch.int64), _vec(y, n, "y"),
+                                    _vec(d, n, "delta")))
+    return y, d
 
 
 def mvn_sov_fp64_noalloc(a, b, L, n_points, n_shifts, seed, err_k=3.0, path_logw=None,

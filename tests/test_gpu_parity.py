@@ -235,6 +235,56 @@ def test_sov_w2_full_size_sampled_paths(mvn, w2_oracle):
     assert abs(o[0] - est[0]) <= 1e-9 and abs(o[1] - est[1]) <= 1e-10
 
 
+def test_bench_w2_mixed_launch_vs_oracle_and_fp64(mvn, w2_oracle):
+    """The bench's W2 step exactly as it is timed (mvn_matern -> mvn_cholesky MVN_MIXED ->
+    mvn_sov MVN_MIXED at n = 16,384 with all 20,000 paths): per-path log-weights against the
+    oracle (its own covariance and LAPACK factor) on three windows of sampled paths, and the
+    estimate against the all-FP64 GPU path (FP64 Cholesky and FP64 sweep of the same covariance)
+    on identical lattice points, gated at |d log P| <= 1e-4 (and the literal |d P| <= 1e-4).
+    Per path the mixed error is the factor's (the exact-digit update carries ~42 bits) plus the
+    sweep's; stated bound 1e-5 max(1, |logw|)."""
+    w, c, So, Lo = w2_oracle
+    n = c.shape[0]
+    a, b = inputs.limits_for(w, n)
+    Ns, M = w["Ns"], w["M"]
+    Ntot = Ns * M
+    S = mvn.mvn_matern(_t(c), w["sigma2"], w["range"], w["nu"], w["nugget"])
+    S64 = S.clone()
+    assert S64.stride() == S.stride()
+    assert mvn.mvn_cholesky(S, prec="mixed") == 0
+    lw_mx = torch.empty(Ntot, dtype=torch.float64, device=DEV)
+    o_mx = mvn.mvn_sov(_t(a), _t(b), S, Ns, M, w["seed"], prec="mixed", path_logw=lw_mx)
+    mvn.sync()
+    o_mx = o_mx.cpu().numpy()
+    lw_mx = lw_mx.cpu().numpy()
+    del S
+    assert mvn.mvn_cholesky(S64, prec="fp64") == 0
+    lw_64 = torch.empty(Ntot, dtype=torch.float64, device=DEV)
+    o_64 = mvn.mvn_sov(_t(a), _t(b), S64, Ns, M, w["seed"], prec="fp64", path_logw=lw_64)
+    mvn.sync()
+    o_64 = o_64.cpu().numpy()
+    lw_64 = lw_64.cpu().numpy()
+    del S64
+    q = oracle.QMC(Ns, M, w["seed"])
+    worst = 0.0
+    for p0 in (0, 2000 * 3 + 517, Ntot - 8):
+        ref = oracle.sov_logw(a, b, Lo, q, paths=(p0, p0 + 8))
+        rel = np.abs(lw_mx[p0:p0 + 8] - ref) / np.maximum(1.0, np.abs(ref))
+        rel64 = np.abs(lw_64[p0:p0 + 8] - ref) / np.maximum(1.0, np.abs(ref))
+        print(f"W2 paths {p0}..{p0 + 7}: mixed max rel {rel.max():.3e}, FP64 GPU (its own "
+              f"factor) max rel {rel64.max():.3e}")
+        worst = max(worst, rel.max())
+        assert rel.max() <= 1e-5, (p0, rel.max())
+    assert np.all(np.isfinite(lw_mx)) and np.all(lw_mx <= 0)
+    d = abs(o_mx[0] - o_64[0])
+    print(f"W2 bench launch: log P mixed {o_mx[0]:.10f} FP64 {o_64[0]:.10f} |d log P| {d:.3e} "
+          f"|dP| {abs(o_mx[1] - o_64[1]):.3e} err/P {o_64[2] / o_64[1]:.3e}")
+    assert d <= 1e-4
+    assert abs(o_mx[1] - o_64[1]) <= 1e-4
+    est = oracle.estimate(lw_mx, M)
+    assert abs(o_mx[0] - est[0]) <= 1e-9
+
+
 # ------------------------------------------------------------------ batched problems (Alg. 1 loop)
 
 def test_sov_batched_vs_oracle_loop(mvn):

@@ -326,6 +326,128 @@ def test_sov_invariants():
     assert p2[1] - p1[1] > p1[2] + p2[2]
 
 
+# ----------------------------------------------------------------- Eq. 2 edge cases: underflow and clamp
+
+TINY = 2.0 ** -1074  # smallest subnormal double: the absolute quantum of a subnormal Delta
+
+
+def test_sov_zero_weight_branch_every_path():
+    """Delta underflowing to 0 in a dimension (a' = 40: Q(40) ~ 3.7e-350; b' = -40 likewise)
+    gives weight 0 on every path: log-weight -inf exactly, y = the finite limit, no NaN in the
+    later dimensions, and the estimate (log P, P, err) = (-inf, 0, 0)."""
+    n = 5
+    c = inputs.random_coords(n, 21)
+    S = oracle.matern(c, 1.0, 0.3, 1.5, nugget=1e-3)
+    L, _ = oracle.cholesky(S)
+    for a0, b0, y0 in [(40.0 * L[0, 0], np.inf, 40.0), (-np.inf, -40.0 * L[0, 0], -40.0)]:
+        a = np.full(n, -np.inf)
+        b = np.full(n, 0.5)
+        a[0], b[0] = a0, b0
+        lw, Y = oracle.sov_logw(a, b, L, Q1, return_y=True)
+        assert np.all(lw == -np.inf)
+        assert np.all(np.isfinite(Y))
+        np.testing.assert_allclose(Y[:, 0], y0, rtol=1e-15)
+        assert oracle.estimate(lw, Q1.M) == (-np.inf, 0.0, 0.0)
+    # the underflow lies where the mathematics puts it: log Q(40) < log of the smallest double
+    from scipy.special import log_ndtr
+    assert log_ndtr(-40.0) < math.log(TINY) - 1.0
+
+
+def test_sov_zero_weight_on_some_paths_vs_scipy():
+    """Bivariate case whose second dimension underflows on some paths only: with
+    X2 | y1 ~ N(rho y1, 1 - rho^2) and y1 = Phi^-1(w1) (a = -inf, b = +inf in dimension 1), the
+    factor of dimension 2 is Q((a2 - rho y1)/sqrt(1 - rho^2)) per path, recomputed here with
+    scipy's ndtri and log_ndtr (Cephes and an asymptotic series, implementations other than the
+    oracle's AS241 and libm erfc; exp of log_ndtr reaches the subnormal range where Cephes' ndtr
+    already returns 0).  Paths whose factor is 0 must carry log-weight -inf exactly; the others
+    log(Delta)."""
+    from scipy.special import log_ndtr, ndtri
+    rho = 0.99
+    S = np.array([[1.0, rho], [rho, 1.0]])
+    L, _ = oracle.cholesky(S)
+    s2 = math.sqrt(1 - rho * rho)
+    a = np.array([-np.inf, 5.4])
+    b = np.array([np.inf, np.inf])
+    q = oracle.QMC(512, 4, 23)
+    lw, D = oracle.sov_logw(a, b, L, q, return_delta=True)
+    alpha = oracle.lattice_alpha(2)
+    delta = oracle.lattice_shifts(q.seed, q.M, 2)
+    p = np.arange(q.Ntot)
+    j = (p % q.Ns + 1).astype(np.uint64)
+    w1 = oracle.lattice_points(j, alpha[0], delta[p // q.Ns, 0])
+    y1 = ndtri(w1)
+    ap = (a[1] - rho * y1) / s2
+    lref = log_ndtr(-ap)
+    ref = np.exp(lref)
+    zero = ref == 0.0
+    assert zero.any() and (~zero).any()          # the case exercises both outcomes
+    assert np.all(D[:, 0] == 1.0)
+    # a subnormal factor is known to one quantum absolute; a normal one to ~1e-13 relative
+    # (the condition number of Q at a' ~ 40 is ~a'^2 times the ~1e-16 error of y1)
+    tol = 4 * TINY + 1e-12 * ref
+    assert np.all(np.abs(D[:, 1] - ref) <= tol)
+    clear = (ref > 8 * TINY) | (ap > 39.0)        # away from the underflow boundary
+    assert np.all(lw[clear & zero] == -np.inf)
+    fin = clear & ~zero & (ref > 2.0 ** -1022)
+    np.testing.assert_allclose(lw[fin], lref[fin], rtol=0, atol=1e-12)
+    sub = clear & ~zero & ~fin                    # subnormal factors: one quantum absolute
+    assert sub.any()
+    assert np.all(np.abs(np.exp(lw[sub]) - ref[sub]) <= 4 * TINY + 1e-12 * ref[sub])
+
+
+def test_sov_near_underflow_closed_form_per_path():
+    """Independent dimensions deep in the upper tail (normal Q(37) ~ 5.7e-300 and subnormal
+    Q(38) ~ 2.9e-316): every path's log-weight equals sum_i log Q(a_i/sd_i), against scipy's
+    log_ndtr; the subnormal factor carries one quantum of absolute error (relative 2e-8 here)."""
+    from scipy.special import log_ndtr
+    sd = np.array([1.0, 2.0, 0.5, 1.3])
+    a = np.array([37.0, 38.0, 10.0, -np.inf]) * np.where(np.isfinite([1, 1, 1, np.inf]), sd, 1)
+    b = np.array([np.inf, np.inf, np.inf, 1.0])
+    lw = oracle.sov_logw(a, b, np.diag(sd), Q1)
+    ref = log_ndtr(-37.0) + log_ndtr(-38.0) + log_ndtr(-10.0) + log_ndtr(1.0 / 1.3)
+    tol = 1e-12 * abs(ref) + 2 * TINY / math.exp(log_ndtr(-38.0))
+    assert np.all(np.abs(lw - ref) <= tol), (lw[:3], ref)
+    logP = oracle.estimate(lw, Q1.M)[0]
+    assert abs(logP - ref) <= tol
+
+
+def test_sov_step_interior_clamp():
+    """The Phi^-1 argument of Eq. 2 rounded to exactly 1 or 0 is moved to the nearest interior
+    double, so y stays finite.  The lattice reaches w = 1 exactly: W = 2^64 - 1 gives
+    (2^53 - 1) + 1/2, which rounds to 2^53 (ties to even)."""
+    from scipy.special import ndtr, ndtri
+    W1 = np.uint64(2 ** 64 - 1)
+    assert oracle.lattice_points(1, W1, 0)[0] == 1.0
+    # a' <= 0 branch: Phi(a') + w Delta = 0 + 1 * 1 = 1  ->  1 - 2^-53  ->  y = -Phi^-1(2^-53)
+    y, d = oracle.sov_step(-np.inf, np.inf, 0.0, 1.0, W1)
+    assert d == 1.0 and np.isfinite(y)
+    np.testing.assert_allclose(y, -ndtri(2.0 ** -53), rtol=1e-14)
+    # a' > 0 branch: Q(a') - w Delta = Q(1) - Q(1) = 0  ->  2^-1074  ->  y = -Phi^-1(2^-1074)
+    y, d = oracle.sov_step(1.0, np.inf, 0.0, 1.0, W1)
+    np.testing.assert_allclose(d, ndtr(-1.0), rtol=1e-15)
+    assert np.isfinite(y)
+    np.testing.assert_allclose(y, -ndtri(TINY), rtol=1e-14)
+    # a' <= 0 branch at an ordinary w: w Delta underflows when Delta is a deep subnormal
+    # (Phi(-38.4) is a few quanta), and the clamp gives y = Phi^-1(2^-1074) with Delta > 0
+    Wsmall = np.uint64(1 << 40)   # w ~ 2^-24
+    y, d = oracle.sov_step(-np.inf, -38.4, 0.0, 1.0, Wsmall)
+    assert 0.0 < d < 64 * TINY and np.isfinite(y)
+    np.testing.assert_allclose(y, ndtri(TINY), rtol=1e-14)
+    # away from the clamp the step is Eq. 2 itself: scipy's ndtri of Phi(a') + w Delta
+    rng = np.random.default_rng(24)
+    a = rng.uniform(-3, 1, 200)
+    b = a + rng.uniform(0.1, 3, 200)
+    s = rng.uniform(-1, 1, 200)
+    lii = rng.uniform(0.3, 2, 200)
+    W = rng.integers(0, 2 ** 63, 200).astype(np.uint64) * np.uint64(2)
+    y, d = oracle.sov_step(a, b, s, lii, W)
+    ap, bp = (a - s) / lii, (b - s) / lii
+    w = oracle.lattice_points(1, W, 0)
+    dref = ndtr(bp) - ndtr(ap)
+    np.testing.assert_allclose(d, dref, rtol=1e-12)
+    np.testing.assert_allclose(y, ndtri(ndtr(ap) + w * dref), rtol=1e-9, atol=1e-12)
+
+
 def test_estimate_log_domain():
     rng = np.random.default_rng(17)
     lw = rng.uniform(-5, 0, 40)

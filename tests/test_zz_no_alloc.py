@@ -3,7 +3,8 @@ cannot allocate device memory at call time (under a caching allocator that must 
 foreign cudaMalloc calls, in a real-time loop that cannot take an allocation's implicit
 synchronisation, or in an embedding that only hands over device buffers).  It keeps its scratch in a fixed array inside the
 library; this test checks it through the C ABI against the regular entry point (mvn_sov,
-MVN_FP64) on two calls in a row, and that sizes beyond its fixed limits are refused.
+MVN_FP64) and against the CPU oracle (per-path log-weights on the same factor and lattice) on
+two calls in a row, and that sizes beyond its fixed limits are refused.
 
 Collected last on purpose (file name), so a run that stops at the first failure has run every
 other test first; it also passes alone in a fresh process."""
@@ -12,6 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_2405_14892_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -57,6 +59,12 @@ def test_noalloc_matches_regular_entry_point_twice(mvn):
         go, ro = got.cpu().numpy(), ref.cpu().numpy()
         assert abs(go[0] - ro[0]) <= 1e-9 and abs(go[1] - ro[1]) <= 1e-10, (call, go, ro)
         assert abs(go[2] - ro[2]) <= 1e-9 * max(ro[2], 1e-300) + 1e-14
+        # the oracle on the same factor and lattice: every path, and the estimate
+        Lh = np.tril(L.cpu().numpy())
+        lo = oracle.sov_logw(a, b, Lh, oracle.QMC(Ns, M, seed))
+        assert np.all(np.abs(g - lo) <= 1e-9 * np.maximum(1.0, np.abs(lo))), (call, np.abs(g - lo).max())
+        eo = oracle.estimate(lo, M)
+        assert abs(go[0] - eo[0]) <= 1e-9 and abs(go[1] - eo[1]) <= 1e-10, (call, go, eo)
 
 
 def test_noalloc_without_path_output_and_ragged(mvn):

@@ -123,8 +123,9 @@ def cpu_oracle_throughput(sample_paths: int = 48, chol_n: int = 2048, problem=No
     t_step = t_chol * (n / chol_n) ** 3 + t_sov * Ntot / sample_paths
     det = {"cores": cores, "kind": "oracle",
            "sample": f"SOV: {sample_paths} of {Ntot} paths at n={n} ({t_sov:.1f} s, OpenMP over "
-                     f"paths); Cholesky: plain loop on the leading {chol_n}^2 block ({t_chol:.1f} s,"
-                     f" one thread), scaled by (n/{chol_n})^3; step time {t_step:.0f} s",
+                     f"paths); Cholesky: plain column loop on the leading {chol_n}^2 block "
+                     f"({t_chol:.1f} s, OpenMP over the rows of each column), scaled by "
+                     f"(n/{chol_n})^3; all {cores} host cores; step time {t_step:.0f} s",
            "t_step_s": t_step}
     return n * Ntot / t_step, det
 
@@ -166,6 +167,9 @@ TIMED_KERNELS = ("k_oz_update", "k_oz_potrf", "k_oz_trsm", "k_sov_tc", "k_syrk",
 TRAFFIC_N0 = 9216
 TRAFFIC_TILES0 = 157
 TRAFFIC_BYTES0 = {"k_sov_tc": 26.41e9 + 0.754e9, "k_oz_update": 89.2e6}
+TRAFFIC_NOTE = {"k_oz_update": "bytes per launch, averaged over the launches of a "
+                               "factorisation; ncu at n=9216 scaled by (n/9216)^2",
+                "k_sov_tc": "ncu at n=9216, 157 path tiles, scaled by (n/9216)^2 x tiles/157"}
 
 
 def _traffic(name, n, tiles):
@@ -178,48 +182,58 @@ def _traffic(name, n, tiles):
     return b * scale
 
 
-def kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src, steps):
-    """Achieved rate of the main kernels of the step: algorithmic work per launch (stated per
-    kernel) over the kernel's average launch duration, measured by the library's CUDA events on
-    the launching stream during the timed region."""
+def chol_update_macs(n: int) -> int:
+    """Multiply-adds of the left-looking trailing update of an order-n Cholesky over 64-wide block
+    columns: block column j (c0 = 64 j) takes the (n - c0) x 64 panel times K = c0, i.e.
+    sum_j (n - 64 j) 64 (64 j) ~ n^3/6 (so 2 x this ~ n^3/3 flops, the factorisation's work)."""
+    nbc = (n + 63) // 64
+    return sum((n - 64 * j) * 64 * 64 * j for j in range(1, nbc))
+
+
+def sweep_far_macs(n: int, tiles: int) -> int:
+    """Multiply-adds the tensor-core sweep runs on the tensor cores: super-block R (128
+    dimensions) takes K = 128 R for every 128-path tile (the diagonal blocks run on CUDA cores)."""
+    nsb = (n + 127) // 128
+    return tiles * 128 * 128 * 128 * (nsb * (nsb - 1) // 2)
+
+
+def kernel_rooflines(kt, prec, n, Ntot, peaks, peak_src, steps):
+    """Achieved rate of the main kernels of the step on the METHOD's work (the Cholesky update's
+    ~n^3/3 flops, the SOV limit GEMM's n(n-1) flops per path) over the kernel's launch durations, measured by the library's CUDA events on the launching stream in
+    a pass of `steps` steps after the timed region.  `mma_issue_frac` is the tensor pipe's issue
+    rate (the digit and slice products the kernels actually run), separately."""
     out = []
-    kt = getattr(ctx, "kernel_times", {})
     tens_peak = peaks["bf16_tflops_sustained"]
     tens_src = f"{peak_src} bf16 dense, sustained (the kernel runs inside a long step)"
     tiles = (Ntot + 127) // 128
-    # tensor-core Cholesky update of block column j (64 columns c0 = 64 j, j = 1..nbc-1): the
-    # (n - c0) x 64 lower panel times K = c0, i.e. sum_j (n - 64 j) 64 (64 j) multiply-adds per
-    # factorisation (~n^3/6), each carried by 21 BF16 digit-product MMAs
     ms, cnt = kt.get("k_oz_update", (0.0, 0))
     if cnt:
-        nbc = (n + 63) // 64
-        mac = sum((n - 64 * j) * 64 * 64 * j for j in range(1, nbc))
-        fl = 2.0 * 21 * mac * steps
+        fl = 2.0 * chol_update_macs(n) * steps
+        ach = fl / (ms * 1e-3) / 1e12
         out.append({"kernel": "k_oz_update", "bound": "tensor", "unit": "TFLOP/s",
-                    "achieved": fl / (ms * 1e-3) / 1e12, "peak": tens_peak,
-                    "frac": fl / (ms * 1e-3) / 1e12 / tens_peak,
-                    "traffic": _traffic("k_oz_update", n, tiles),
-                    "traffic_note": "bytes per launch, averaged over the launches of a "
-                                    "factorisation; ncu at n=9216 scaled by (n/9216)^2",
-                    "fp64_equivalent_tflops": 2.0 * mac * steps / (ms * 1e-3) / 1e12,
-                    "launches": cnt, "total_ms": ms, "peak_source": tens_src,
-                    "work": "21 BF16 MMA products per FP64 product of the left-looking update"})
+                    "achieved": ach, "peak": tens_peak, "frac": ach / tens_peak,
+                    "mma_issue_frac": 21 * ach / tens_peak,
+                    "work_flops_per_step": fl / steps, "traffic": _traffic("k_oz_update", n, tiles),
+                    "traffic_note": TRAFFIC_NOTE["k_oz_update"],
+                    "launches": cnt, "total_ms": ms, "launch_ms": ms / cnt,
+                    "peak_source": tens_src,
+                    "work": "method work: 2 sum_j (n-64j) 64 (64j) flops per factorisation "
+                            "(n^3/3); each multiply-add runs as 21 BF16 digit-product MMAs "
+                            "(mma_issue_frac)"})
     ms, cnt = kt.get("k_sov_tc", (0.0, 0))
     if cnt:
-        # far limit-update GEMM on the tensor cores: super-block R (128 dimensions) takes
-        # K = 128 R for every 128-path tile (the 128 x 128 diagonal blocks run on the CUDA cores)
-        nsb = (n + 127) // 128
-        mac = tiles * 128 * 128 * 128 * (nsb * (nsb - 1) // 2)
-        fl = 2.0 * 3 * mac * cnt
+        fl = float(n) * (n - 1) * Ntot * cnt
+        ach = fl / (ms * 1e-3) / 1e12
+        issue = 2.0 * 3 * sweep_far_macs(n, tiles) * cnt / (ms * 1e-3) / 1e12
         out.append({"kernel": "k_sov_tc", "bound": "tensor", "unit": "TFLOP/s",
-                    "achieved": fl / (ms * 1e-3) / 1e12, "peak": tens_peak,
-                    "frac": fl / (ms * 1e-3) / 1e12 / tens_peak,
-                    "traffic": _traffic("k_sov_tc", n, tiles),
-                    "traffic_note": "ncu at n=9216, 157 path tiles, scaled by (n/9216)^2 x "
-                                    "tiles/157",
-                    "launches": cnt, "total_ms": ms, "peak_source": tens_src,
-                    "work": "3 FP16 MMAs per multiply-add of the far limit-update GEMM "
-                            "(two-slice split), 128-path tiles x 128-dimension super-blocks"})
+                    "achieved": ach, "peak": tens_peak, "frac": ach / tens_peak,
+                    "mma_issue_frac": issue / tens_peak,
+                    "work_flops_per_launch": fl / cnt, "traffic": _traffic("k_sov_tc", n, tiles),
+                    "traffic_note": TRAFFIC_NOTE["k_sov_tc"],
+                    "launches": cnt, "total_ms": ms, "launch_ms": ms / cnt,
+                    "peak_source": tens_src,
+                    "work": "method work: n(n-1) flops per path (the limit GEMM); the far part "
+                            "runs as 3 FP16 MMAs per multiply-add (mma_issue_frac)"})
     for name in ("k_syrk", "k_sov_simt_f64", "k_sov_simt_f32"):
         ms, cnt = kt.get(name, (0.0, 0))
         if not cnt:
@@ -237,7 +251,7 @@ def kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src, steps):
         ach = fl / (ms * 1e-3) / 1e12
         out.append({"kernel": name, "bound": "alu", "unit": "TFLOP/s", "achieved": ach,
                     "peak": pk, "frac": ach / pk, "traffic": None, "launches": cnt,
-                    "total_ms": ms, "peak_source": src})
+                    "total_ms": ms, "launch_ms": ms / cnt, "peak_source": src})
     # the HBM view of the kernels whose DRAM traffic was measured: measured bytes per launch over
     # the average launch duration, against the measured copy bandwidth
     hbm = peaks.get("hbm_gbs", 6800.0)
@@ -269,6 +283,32 @@ def job_time_and_value(ms: float, units_per_rank: float, world: int, device=None
 
 
 # ----------------------------------------------------------------------------- GPU arm
+
+def fp64_arm(mvn, coords, w, a_d, b_d, Ns, M, seed, n, dev, stream):
+    """The plain FP64 GPU path on the same W2 step (FP64 Cholesky, FP64 sweep) on the identical
+    lattice points: one untimed step (it grows the context's workspace), then one step timed with
+    CUDA events on the launching stream.  Returns (ms, out3)."""
+    import torch
+    S = mvn.colmajor_empty(n, n, dev)
+    out3 = torch.empty(3, dtype=torch.float64, device=dev)
+
+    def step():
+        mvn.mvn_matern(coords, w["sigma2"], w["range"], w["nu"], w["nugget"], out=S)
+        mvn.mvn_cholesky(S, prec="fp64", check=False)
+        mvn.mvn_sov(a_d, b_d, S, Ns, M, seed, prec="fp64", out3=out3)
+    step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    res = out3.cpu().numpy()
+    del S
+    return ms, res
+
 
 def run_gpu(args):
     import torch
@@ -304,35 +344,35 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     ctx = mvn.context(local)
 
-    ev = {k: torch.cuda.Event(enable_timing=True) for k in ("s0", "s1", "s2", "s3")}
-    phase = {"matern": [], "cholesky": [], "sov": []}
-
-    def step(timed_phases: bool):
-        if timed_phases:
-            ev["s0"].record(stream)
+    def step(evs=None):
+        if evs is not None:
+            evs[0].record(stream)
         mvn.mvn_matern(coords, w["sigma2"], w["range"], w["nu"], w["nugget"], out=S)
-        if timed_phases:
-            ev["s1"].record(stream)
+        if evs is not None:
+            evs[1].record(stream)
         mvn.mvn_cholesky(S, prec=prec, check=False)
-        if timed_phases:
-            ev["s2"].record(stream)
+        if evs is not None:
+            evs[2].record(stream)
         mvn.mvn_sov(a_d, b_d, S, Ns, M, seed, prec=prec, out3=out3)
-        if timed_phases:
-            ev["s3"].record(stream)
+        if evs is not None:
+            evs[3].record(stream)
 
     # launch shapes picked by the library's autotuner for this size (untimed; the JSON-lines
     # cache named by MVN_TUNE_CACHE is reused when it has this device and size)
-    tuned = mvn.mvn_autotune(n, Ntot, prec, cache=os.environ.get("MVN_TUNE_CACHE"))
+    tuned = None if args.no_tune else mvn.mvn_autotune(n, Ntot, prec,
+                                                       cache=os.environ.get("MVN_TUNE_CACHE"))
     for _ in range(args.warmup):
-        step(False)
+        step()
     torch.cuda.synchronize()
     st, info = ctx.sync()
     if st != 0:
         raise RuntimeError(f"device error {st} info {info}: {mvn.lib().mvn_last_error(ctx.h)}")
 
-    # ---- timed region: device clock, inputs resident in HBM
+    # ---- timed region: device clock, inputs resident in HBM, the library's per-kernel event
+    # timing off (phase events only: four per step, read after the region)
+    phase_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                for _ in range(args.steps)]
     clocks_proc = _clock_sampler() if rank == 0 else None
-    ctx.timing(True)
     launches0 = ctx.launches()
     if world > 1:
         dist.barrier()
@@ -340,27 +380,33 @@ def run_gpu(args):
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
-    for _ in range(args.steps):
-        step(True)
-        torch.cuda.synchronize()  # per-phase events read back between steps
-        phase["matern"].append(ev["s0"].elapsed_time(ev["s1"]))
-        phase["cholesky"].append(ev["s1"].elapsed_time(ev["s2"]))
-        phase["sov"].append(ev["s2"].elapsed_time(ev["s3"]))
+    for k in range(args.steps):
+        step(phase_ev[k])
     t_end.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     launches = ctx.launches() - launches0
     ms = t_start.elapsed_time(t_end) / args.steps
-    ktimes = {k: ctx.kernel_time(k) for k in TIMED_KERNELS}
-    ctx.timing(False)
-    ctx.kernel_times = ktimes
     clocks = _clock_summary(clocks_proc, local) if rank == 0 else None
+    phase = {"matern": [e[0].elapsed_time(e[1]) for e in phase_ev],
+             "cholesky": [e[1].elapsed_time(e[2]) for e in phase_ev],
+             "sov": [e[2].elapsed_time(e[3]) for e in phase_ev]}
     ms, value = job_time_and_value(ms, n * Ntot, world, dev)
     st, info = ctx.sync()
     if st != 0:
         raise RuntimeError(f"device error {st} info {info}")
     res = out3.cpu().numpy()
+
+    # ---- kernel shares: the library's CUDA events around every main launch, in a separate
+    # pass after the timed region (the events add a little host work per launch)
+    kt_steps = max(1, min(args.steps, 3))
+    ctx.timing(True)
+    for _ in range(kt_steps):
+        step()
+    torch.cuda.synchronize()
+    ktimes = {k: ctx.kernel_time(k) for k in TIMED_KERNELS}
+    ctx.timing(False)
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     c_h = torch.tensor(c).pin_memory()
@@ -374,13 +420,31 @@ def run_gpu(args):
         coords.copy_(c_h, non_blocking=True)
         a_d.copy_(a_h, non_blocking=True)
         b_d.copy_(b_h, non_blocking=True)
-        step(False)
+        step()
         res_h.copy_(out3, non_blocking=True)
         torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     e2e_ms, e2e_value = job_time_and_value(e2e_ms, n * Ntot, world, dev)
     h2d = c_h.numel() * 8 + a_h.numel() * 8 + b_h.numel() * 8
     d2h = 3 * 8
+
+    # ---- the metric's other arm: the plain FP64 GPU path on identical lattice points
+    fp64 = None
+    if prec == "mixed" and not args.no_fp64_arm and rank == 0:
+        del S
+        torch.cuda.empty_cache()
+        f_ms, f_res = fp64_arm(mvn, coords, w, a_d, b_d, Ns, M, seed, n, dev, stream)
+        st, info = ctx.sync()
+        if st != 0:
+            raise RuntimeError(f"device error {st} info {info} (FP64 arm)")
+        fp64 = {"fp64_ms_per_step": f_ms, "fp64_value": n * Ntot / (f_ms * 1e-3),
+                "mixed_over_fp64": f_ms / ms, "fp64_logP": float(f_res[0]),
+                "fp64_P": float(f_res[1]), "fp64_err": float(f_res[2]),
+                "dlogP_vs_fp64": abs(float(res[0]) - float(f_res[0])),
+                "dP_vs_fp64": abs(float(res[1]) - float(f_res[1])),
+                "gate": "|d log P| <= 1e-4 (relative reading of |dP| <= 1e-4; P ~ 1e-45 here)",
+                "gate_ok": abs(float(res[0]) - float(f_res[0])) <= 1e-4,
+                "note": "one untimed FP64 step, then one timed (CUDA events); same shift seed"}
 
     if rank != 0:
         if world > 1:
@@ -389,7 +453,7 @@ def run_gpu(args):
     peaks, peak_src = _peaks()
     sov_ms = statistics.median(phase["sov"])
     chol_ms = statistics.median(phase["cholesky"])
-    rooflines = kernel_rooflines(ctx, prec, n, Ntot, peaks, peak_src, args.steps)
+    rooflines = kernel_rooflines(ktimes, prec, n, Ntot, peaks, peak_src, kt_steps)
     dominant = max(rooflines, key=lambda r: r["total_ms"]) if rooflines else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -405,15 +469,18 @@ def run_gpu(args):
                       "sov": sov_ms},
         "sov_sample_dims_per_sec": n * Ntot / (sov_ms * 1e-3),
         "logP": float(res[0]), "P": float(res[1]), "err": float(res[2]),
+        "err_over_P": float(res[2]) / float(res[1]) if res[1] > 0 else None,
         "roofline": dominant,
         "rooflines": rooflines,
-        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ctx.kernel_times.items()
-                               if v[1]},
+        "kernel_ms_per_step": {k: v[0] / kt_steps for k, v in ktimes.items() if v[1]},
+        "kernel_timing_pass": f"{kt_steps} steps after the timed region, library events on",
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if fp64 is not None:
+        line["fp64_arm"] = fp64
     if not args.no_cpu_baseline and world == 1:
         v, det = cpu_oracle_throughput()
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": det["cores"],
@@ -431,6 +498,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64", "mixed_simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-arm", action="store_true",
+                    help="skip the plain FP64 GPU step (about 20 s at the default size)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="default launch shapes instead of the autotuner (profiling runs)")
     ap.add_argument("--workload", default="w2", choices=["w1", "w2", "w3", "w4", "w5"],
                     help="w2 (default): the contract line; the others measure the other rows")
     ap.add_argument("--grid", type=int, default=0,

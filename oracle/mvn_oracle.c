@@ -150,7 +150,10 @@ void orc_points(int64_t count, const uint64_t* j, const uint64_t* alpha, const u
 /* In-place lower Cholesky of the column-major n x n matrix A (leading dimension ld).
  * Column j: L_jj = sqrt(A_jj - sum_{k<j} L_jk^2); L_ij = (A_ij - sum_{k<j} L_ik L_jk) / L_jj.
  * Only the lower triangle is read and written.  Returns 0, or the 1-based index of the first
- * column whose pivot is not positive (LAPACK convention). */
+ * column whose pivot is not positive (LAPACK convention).
+ * The entries L_ij of one column (i > j) are independent of each other; with OpenMP they are
+ * shared among threads, each computed by the same loop in the same order as serially, so the
+ * result does not depend on the thread count. */
 int orc_cholesky(int n, double* A, int64_t ld) {
     for (int j = 0; j < n; ++j) {
         double d = A[j + (int64_t)j * ld];
@@ -161,6 +164,9 @@ int orc_cholesky(int n, double* A, int64_t ld) {
         if (!(d > 0.0)) return j + 1;
         double ljj = sqrt(d);
         A[j + (int64_t)j * ld] = ljj;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if ((int64_t)(n - j) * j > 200000)
+#endif
         for (int i = j + 1; i < n; ++i) {
             double s = A[i + (int64_t)j * ld];
             for (int k = 0; k < j; ++k) s -= A[i + (int64_t)k * ld] * A[j + (int64_t)k * ld];

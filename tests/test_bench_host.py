@@ -45,44 +45,49 @@ def test_clock_summary_parses_samples_of_one_gpu():
     assert bench._clock_summary(_FakeSmi(""), 0) is None
 
 
-class _FakeCtx:
-    def __init__(self, kt):
-        self.kernel_times = kt
-
-
 PEAKS = {"hbm_gbs": 6756.2, "bf16_tflops": 1914.9, "bf16_tflops_sustained": 1713.5,
          "sm_max_mhz": 2070.0}
 
 
 @pytest.mark.parametrize("n", [1024, 16384])
 def test_update_work_is_the_left_looking_sum(n):
-    """k_oz_update: sum over block columns j of (n - 64 j) x 64 x (64 j) multiply-adds, which
-    for n a multiple of 64 is (n^3 - 64^2 n) / 6; 21 BF16 digit products of 2 flops each."""
+    """k_oz_update: the method's work is the left-looking update, sum over block columns j of
+    (n - 64 j) x 64 x (64 j) multiply-adds, which for n a multiple of 64 is (n^3 - 64^2 n) / 6
+    (2 flops each, ~n^3/3); the tensor pipe runs 21 BF16 digit products per multiply-add, which
+    the separate issue fraction counts."""
     ms = 10.0
-    r = bench.kernel_rooflines(_FakeCtx({"k_oz_update": (ms, 100)}), "mixed", n, 20000, PEAKS,
+    r = bench.kernel_rooflines({"k_oz_update": (ms, 100)}, "mixed", n, 20000, PEAKS,
                                "measured", steps=1)
     (u,) = r
     mac = (n ** 3 - 64 ** 2 * n) // 6
-    assert u["achieved"] == pytest.approx(2 * 21 * mac / (ms * 1e-3) / 1e12, rel=1e-12)
-    assert u["fp64_equivalent_tflops"] == pytest.approx(2 * mac / (ms * 1e-3) / 1e12, rel=1e-12)
+    assert bench.chol_update_macs(n) == mac
+    assert u["achieved"] == pytest.approx(2 * mac / (ms * 1e-3) / 1e12, rel=1e-12)
     assert u["peak"] == PEAKS["bf16_tflops_sustained"]
     assert u["frac"] == pytest.approx(u["achieved"] / u["peak"], rel=1e-12)
+    assert u["mma_issue_frac"] == pytest.approx(21 * u["frac"], rel=1e-12)
+    assert u["work_flops_per_step"] == 2 * mac
+    assert u["launch_ms"] == pytest.approx(ms / 100)
     assert u["bound"] == "tensor" and u["unit"] == "TFLOP/s"
 
 
 @pytest.mark.parametrize("n,paths", [(9216, 20096), (16384, 20000)])
-def test_sweep_work_is_the_far_lower_triangle(n, paths):
-    """k_sov_tc: the far GEMM covers every entry of L left of the 128 x 128 diagonal blocks,
-    n (n - 128) / 2 multiply-adds per path (n a multiple of 128), for 128-path tiles; 3 FP16
-    MMAs per multiply-add (two-slice split)."""
+def test_sweep_work_is_the_limit_gemm(n, paths):
+    """k_sov_tc: the method's work is the limit GEMM, n (n - 1) flops per path; the far part on
+    the tensor cores covers every entry of L left of the 128 x 128 diagonal blocks,
+    n (n - 128) / 2 multiply-adds per path for 128-path tiles, 3 FP16 MMAs each (issue
+    fraction)."""
     ms, launches = 40.0, 2
-    r = bench.kernel_rooflines(_FakeCtx({"k_sov_tc": (ms, launches)}), "mixed", n, paths, PEAKS,
+    r = bench.kernel_rooflines({"k_sov_tc": (ms, launches)}, "mixed", n, paths, PEAKS,
                                "measured", steps=launches)
     (s,) = r
+    assert s["achieved"] == pytest.approx(n * (n - 1) * paths * launches / (ms * 1e-3) / 1e12,
+                                          rel=1e-12)
     tiles = math.ceil(paths / 128)
     mac = tiles * 128 * n * (n - 128) // 2
-    assert s["achieved"] == pytest.approx(2 * 3 * mac * launches / (ms * 1e-3) / 1e12,
-                                          rel=1e-12)
+    assert bench.sweep_far_macs(n, tiles) == mac
+    issue = 2 * 3 * mac * launches / (ms * 1e-3) / 1e12
+    assert s["mma_issue_frac"] == pytest.approx(issue / PEAKS["bf16_tflops_sustained"], rel=1e-12)
+    assert s["work_flops_per_launch"] == n * (n - 1) * paths
     hv = s["hbm_view"]
     per_launch_s = ms * 1e-3 / launches
     assert hv["achieved"] == pytest.approx(s["traffic"] / per_launch_s / 1e9, rel=1e-12)
@@ -91,9 +96,8 @@ def test_sweep_work_is_the_far_lower_triangle(n, paths):
 
 def test_simt_and_fp64_work():
     n, paths = 256, 200000
-    r = bench.kernel_rooflines(
-        _FakeCtx({"k_sov_simt_f64": (30.0, 1), "k_syrk": (5.0, 3)}), "fp64", n, paths, PEAKS,
-        "measured", steps=1)
+    r = bench.kernel_rooflines({"k_sov_simt_f64": (30.0, 1), "k_syrk": (5.0, 3)}, "fp64", n,
+                               paths, PEAKS, "measured", steps=1)
     by = {x["kernel"]: x for x in r}
     assert by["k_sov_simt_f64"]["achieved"] == pytest.approx(
         n * (n - 1) * paths / 30e-3 / 1e12, rel=1e-12)

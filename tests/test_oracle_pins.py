@@ -109,6 +109,28 @@ def test_cholesky_vs_lapack_and_backward_error():
     assert np.linalg.norm(L @ L.T - A) / np.linalg.norm(A) < 150 * 2.2e-16
 
 
+def test_cholesky_threads_do_not_change_the_result():
+    """The column loop shares the rows of each column among OpenMP threads; every entry is the
+    same serial sum, so one thread and all threads give identical bits."""
+    import subprocess
+    import sys
+    A = _spd(700, 5)
+    L, info = oracle.cholesky(A)
+    assert info == 0
+    code = ("import numpy as np, oracle, sys; A = np.load(sys.argv[1]); "
+            "L, _ = oracle.cholesky(A); np.save(sys.argv[2], L)")
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        fa, fl = os.path.join(d, "a.npy"), os.path.join(d, "l.npy")
+        np.save(fa, A)
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        env["PYTHONPATH"] = root + os.pathsep + env.get("PYTHONPATH", "")
+        subprocess.check_call([sys.executable, "-c", code, fa, fl], env=env)
+        L1 = np.load(fl)
+    assert np.array_equal(L, L1)
+
+
 def test_cholesky_equicorrelated_closed_form():
     n, rho = 40, 0.37
     A = (1 - rho) * np.eye(n) + rho * np.ones((n, n))

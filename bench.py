@@ -6,8 +6,10 @@
 Metric: SOV sample-dims/s (n * paths / step time) and MVN probabilities/s (1 / step time).
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64|mixed_simt]
        [--impl reference]  (the CPU oracle on a bounded sample of the same workload)
-Under torchrun (N > 1) every rank runs its own independent problem (a different shift seed):
-weak scaling, no collective on the data path.
+Under torchrun (N > 1) the ranks split the one W2 problem by lattice paths (strong scaling):
+each rank builds and factors its own copy of Sigma (the Cholesky does not divide into
+independent units), sweeps its path range, and one all-gather of the per-shift pairs
+(2 x 10 doubles per rank, NCCL) precedes the combine.
 """
 from __future__ import annotations
 
@@ -265,14 +267,10 @@ def kernel_rooflines(kt, prec, n, Ntot, peaks, peak_src, steps):
 
 # ----------------------------------------------------------------------------- ranks
 
-def rank_seed(base: int, rank: int) -> int:
-    """Shift seed of a rank's independent problem (weak scaling: one W2 problem per rank)."""
-    return base + 1000 * rank
-
-
 def job_time_and_value(ms: float, units_per_rank: float, world: int, device=None):
     """Whole-job step time = the slowest rank's (max over ranks), and the job's throughput =
-    units processed by all ranks / that time.  Collective only when world > 1."""
+    units processed by all ranks / that time (under torchrun the ranks split one problem's paths,
+    so each processes 1/world of its sample-dims).  Collective only when world > 1."""
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -334,8 +332,10 @@ def run_gpu(args):
     if args.paths:
         Ns = max(1, args.paths // M)
     Ntot = Ns * M
-    seed = rank_seed(w["seed"], rank)
+    seed = w["seed"]
     prec = args.prec
+    from paper_2405_14892_gb300 import shard
+    p0, p1 = shard.shard_range(Ntot, world, rank)
     coords = torch.tensor(c, device=dev)
     a_d = torch.tensor(a, device=dev)
     b_d = torch.tensor(b, device=dev)
@@ -343,6 +343,16 @@ def run_gpu(args):
     out3 = torch.empty(3, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     ctx = mvn.context(local)
+    pairs = torch.empty(2 * M, dtype=torch.float64, device=dev)
+    all_pairs = torch.empty(2 * M * world, dtype=torch.float64, device=dev)
+
+    def sweep():
+        if world == 1:
+            mvn.mvn_sov(a_d, b_d, S, Ns, M, seed, prec=prec, out3=out3)
+            return
+        mvn.mvn_sov_partial(a_d, b_d, S, Ns, M, seed, p0, p1, prec=prec, partial=pairs)
+        dist.all_gather_into_tensor(all_pairs, pairs)
+        mvn.mvn_sov_combine(all_pairs, Ns, M, out3=out3)
 
     def step(evs=None):
         if evs is not None:
@@ -353,7 +363,7 @@ def run_gpu(args):
         mvn.mvn_cholesky(S, prec=prec, check=False)
         if evs is not None:
             evs[2].record(stream)
-        mvn.mvn_sov(a_d, b_d, S, Ns, M, seed, prec=prec, out3=out3)
+        sweep()
         if evs is not None:
             evs[3].record(stream)
 
@@ -392,7 +402,7 @@ def run_gpu(args):
     phase = {"matern": [e[0].elapsed_time(e[1]) for e in phase_ev],
              "cholesky": [e[1].elapsed_time(e[2]) for e in phase_ev],
              "sov": [e[2].elapsed_time(e[3]) for e in phase_ev]}
-    ms, value = job_time_and_value(ms, n * Ntot, world, dev)
+    ms, value = job_time_and_value(ms, n * Ntot / world, world, dev)
     st, info = ctx.sync()
     if st != 0:
         raise RuntimeError(f"device error {st} info {info}")
@@ -424,7 +434,7 @@ def run_gpu(args):
         res_h.copy_(out3, non_blocking=True)
         torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    e2e_ms, e2e_value = job_time_and_value(e2e_ms, n * Ntot, world, dev)
+    e2e_ms, e2e_value = job_time_and_value(e2e_ms, n * Ntot / world, world, dev)
     h2d = c_h.numel() * 8 + a_h.numel() * 8 + b_h.numel() * 8
     d2h = 3 * 8
 
@@ -457,13 +467,17 @@ def run_gpu(args):
     dominant = max(rooflines, key=lambda r: r["total_ms"]) if rooflines else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f64+f32+fp16x2",
                                        "mixed_simt": "f64+f32"}[prec],
         "data": "synthetic",
         "config": {"workload": w["name"], "n": n, "paths": Ntot, "shifts": M, "points": Ns,
                    "prec": prec, "l2": "inputs larger than L2 (Sigma n^2 FP64 = 2.1 GB)",
-                   "parallelism": f"replicas{world}", "launch_shapes_autotuned": tuned},
+                   "parallelism": (f"paths split over {world} ranks (Sigma and its factor on "
+                                   f"every rank, one all-gather of per-shift pairs)"
+                                   if world > 1 else "1 GPU"),
+                   "launch_shapes_autotuned": tuned},
         "probs_per_sec": world / (ms * 1e-3),
         "phases_ms": {"matern": statistics.median(phase["matern"]), "cholesky": chol_ms,
                       "sov": sov_ms},

@@ -154,6 +154,31 @@ mvn_status mvn_sov(mvn_ctx* ctx, int n, const double* a, const double* b, const 
                    int64_t ld, const mvn_qmc* qmc, mvn_prec prec, double* out3,
                    double* path_logw);
 
+/* One shard of mvn_sov: the global paths [p0, p1) of the lattice rule (0 <= p0 <= p1 <=
+ * n_points * n_shifts), for splitting one problem over several GPUs.  The paths are independent
+ * QMC samples (Sec. IV-C; Alg. 2's tasks over the sample tiles), so every GPU sweeps its own range
+ * with the same factor and limits, and the shards' per-shift pairs are combined afterwards
+ * (mvn_sov_combine) after an exchange of 2 * n_shifts doubles per shard.
+ *   partial: device double[2 * n_shifts]; for each shift q, partial[2q] = max of the log-weights
+ *            of the shard's paths of shift q, partial[2q+1] = sum of exp(logw - that max); a
+ *            shift with no path in the range gets (-inf, 0).
+ *   path_logw: optional device double[p1 - p0], the shard's per-path log-weights (local index
+ *            p - p0), identical to mvn_sov's for the same paths.
+ * Other arguments and errors as in mvn_sov (precisions included).  Asynchronous. */
+mvn_status mvn_sov_partial(mvn_ctx* ctx, int n, const double* a, const double* b,
+                           const double* L, int64_t ld, const mvn_qmc* qmc, mvn_prec prec,
+                           int64_t p0, int64_t p1, double* partial, double* path_logw);
+
+/* Combine the pairs of nparts shards (device, partials[r * 2 * n_shifts + ...] as written by
+ * mvn_sov_partial; disjoint path ranges that together cover the rule) into out3 = {log P-hat,
+ * P-hat, err} (device double[3]): per shift, m = max over shards and s = sum of s_r exp(m_r - m)
+ * in shard order, then log P_q = m + log s - log n_points and Alg. 2's mean over the shifts as
+ * in mvn_sov.  One shard covering all paths reproduces mvn_sov's out3 bit for bit; a split
+ * inside a shift agrees to rounding (~1e-16 relative).  MVN_ERR_NUMERIC via mvn_sync if every
+ * weight is 0.  Asynchronous. */
+mvn_status mvn_sov_combine(mvn_ctx* ctx, int nparts, const mvn_qmc* qmc, const double* partials,
+                           double* out3);
+
 /* SOV estimate and its gradient (reverse mode of the per-path recurrence; not in the paper):
  *   dlogp_da, dlogp_db: device n-vectors of d log P-hat / d a_i, d b_i (either may be NULL);
  *   dlogp_dL: optional device n x n (ld) lower-triangle d log P-hat / d L_ik.

@@ -355,6 +355,44 @@ def estimate(logw: np.ndarray, M: int, err_k: float = 3.0):
     return float(logP), P, err_k * sd_rel / math.sqrt(M) * P
 
 
+def shift_partials(logw_shard, p0: int, Ns: int, M: int) -> np.ndarray:
+    """Per-shift statistics of a shard of the lattice paths (Sec. IV-C: the QMC samples are
+    independent, so a problem's paths can be split over workers): the shard holds the
+    log-weights of the global paths [p0, p0 + len); for each shift q returns
+    (max_p logw_p, sum_p exp(logw_p - max)) over the shard's paths of that shift, (-inf, 0) for a
+    shift with none.  Shape (M, 2)."""
+    lw = np.asarray(logw_shard, dtype=np.float64)
+    p1 = p0 + lw.size
+    out = np.zeros((M, 2))
+    out[:, 0] = -np.inf
+    for q in range(M):
+        lo, hi = max(p0, q * Ns), min(p1, (q + 1) * Ns)
+        if hi <= lo:
+            continue
+        r = lw[lo - p0:hi - p0]
+        m = float(np.max(r))
+        out[q] = (m, float(np.sum(np.exp(r - m))) if np.isfinite(m) else 0.0)
+    return out
+
+
+def combine_partials(parts, Ns: int, M: int, err_k: float = 3.0):
+    """Alg. 2 "mean(p)" from the shards' per-shift statistics (a list of (M, 2) arrays from
+    `shift_partials` over disjoint path ranges covering the rule): per shift
+    log P_q = LSE over the shards of (m_r + log s_r) - log Ns, then the estimate of `estimate`.
+    Returns (logP, P, err)."""
+    P = np.stack([np.asarray(x, dtype=np.float64).reshape(M, 2) for x in parts])
+    with np.errstate(divide="ignore"):
+        lr = np.where(P[:, :, 1] > 0, P[:, :, 0] + np.log(P[:, :, 1]), -np.inf)  # (R, M)
+    lq = np.array([_lse(lr[:, q]) for q in range(M)]) - math.log(Ns)
+    logP = _lse(lq) - math.log(M)
+    if not np.isfinite(logP):
+        return float(logP), 0.0, 0.0
+    rel = np.exp(lq - logP)
+    sd_rel = float(np.std(rel, ddof=1)) if M > 1 else 0.0
+    Pm = math.exp(logP)
+    return float(logP), Pm, err_k * sd_rel / math.sqrt(M) * Pm
+
+
 def sov(a, b, L, qmc: QMC, err_k: float = 3.0, nthreads: int = 0):
     """P(a <= X <= b), X ~ N(0, L L^T), by the SOV estimator (Eqs. 2-3, Alg. 2-3).
     Returns (logP, P, err)."""

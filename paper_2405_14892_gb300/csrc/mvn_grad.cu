@@ -157,8 +157,9 @@ __device__ void rev_item(const SovProblem& P, int item, const uint64_t* __restri
     const int n = P.n;
     const int64_t p = (int64_t)tile * SOV_P + pc;
     const bool valid = p < P.Ntot;
-    const int64_t q = valid ? p / P.Ns : 0;
-    const uint64_t j = valid ? (uint64_t)(p - q * P.Ns) + 1u : 1u;
+    const int64_t pg = P.p0 + p;  // index of the path in the whole lattice rule
+    const int64_t q = valid ? pg / P.Ns : 0;
+    const uint64_t j = valid ? (uint64_t)(pg - q * P.Ns) + 1u : 1u;
     const uint64_t* __restrict__ dq = P.delta + q * P.dstride;
     const double* __restrict__ L = P.L;
     const int64_t ld = P.ld;
@@ -378,8 +379,9 @@ __global__ void __launch_bounds__(RV_THREADS, 4) k_sov_fwd_keep(const SovProblem
         const int pc = h * RV_PATHS + pl;
         const int64_t p = (int64_t)tile * SOV_P + pc;
         const bool valid = p < P.Ntot;
-        const int64_t q = valid ? p / P.Ns : 0;
-        const uint64_t j = valid ? (uint64_t)(p - q * P.Ns) + 1u : 1u;
+        const int64_t pg = P.p0 + p;  // index of the path in the whole lattice rule
+        const int64_t q = valid ? pg / P.Ns : 0;
+        const uint64_t j = valid ? (uint64_t)(pg - q * P.Ns) + 1u : 1u;
         const uint64_t* __restrict__ dq = P.delta + q * P.dstride;
         LogProd lp;
         for (int r0 = 0; r0 < n; r0 += RV_B) {

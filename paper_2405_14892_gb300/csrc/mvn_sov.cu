@@ -23,68 +23,137 @@
 
 // ---------------------------------------------------------------- reduction (Alg. 2 mean(p))
 
-// One block per problem: log P_q = LSE_j(logw_qj) - log Ns per shift q; log P = LSE_q - log M;
-// P = exp(log P); err = err_k sd_q(P_q) / sqrt(M) (computed relative to P, then scaled).
+// Block-wide max m and sum_k exp(r_k - m) of r[0 .. cnt) in a fixed order (thread t takes
+// k = t, t + nt, ...; tree reductions in shared memory `red` of blockDim.x doubles), so the
+// pair does not depend on anything but the values and the block size.  Every thread gets it.
+__device__ void block_max_sumexp(const double* __restrict__ r, int64_t cnt, double* red,
+                                 double& m_out, double& s_out) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    double m = -INFINITY;
+    for (int64_t k = t; k < cnt; k += nt) m = fmax(m, r[k]);
+    red[t] = m;
+    __syncthreads();
+    for (int w = nt / 2; w > 0; w >>= 1) {
+        if (t < w) red[t] = fmax(red[t], red[t + w]);
+        __syncthreads();
+    }
+    m = red[0];
+    __syncthreads();
+    double s = 0.0;
+    if (m > -INFINITY)
+        for (int64_t k = t; k < cnt; k += nt) s += exp(r[k] - m);
+    red[t] = s;
+    __syncthreads();
+    for (int w = nt / 2; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    s_out = red[0];
+    m_out = m;
+    __syncthreads();
+}
+
+// log P_q of one shift from its (max, sum of exp(logw - max)) over its Ns paths.
+__device__ __forceinline__ double shift_log_mean(double m, double s, int64_t Ns) {
+    return (m > -INFINITY) ? m + log(s) - log((double)Ns) : -INFINITY;
+}
+
+// Alg. 2 "mean(p)" over the shifts, in the log domain, from the per-shift log means lq[0..M):
+// log P = LSE_q(lq) - log M; P = exp(log P); err = err_k sd_q(P_q) / sqrt(M) (computed relative
+// to P, then scaled); every weight 0 gives (-inf, 0, 0) and, if raise_numeric, MVN_ERR_NUMERIC.
+// One thread, fixed order.
+__device__ void estimate_from_shifts(const double* lq, int M, double err_k, double* o,
+                                     int* status, int raise_numeric) {
+    double m = -INFINITY;
+    for (int qq = 0; qq < M; ++qq) m = fmax(m, lq[qq]);
+    if (!(m > -INFINITY)) {
+        o[0] = -INFINITY;
+        o[1] = 0.0;
+        o[2] = 0.0;
+        if (raise_numeric) dev_raise(status, MVN_ERR_NUMERIC, 0);
+        return;
+    }
+    double s = 0.0;
+    for (int qq = 0; qq < M; ++qq) s += exp(lq[qq] - m);
+    const double logP = m + log(s) - log((double)M);
+    double mean = 0.0;
+    for (int qq = 0; qq < M; ++qq) mean += exp(lq[qq] - logP);
+    mean /= M;
+    double ss = 0.0;
+    for (int qq = 0; qq < M; ++qq) {
+        double d = exp(lq[qq] - logP) - mean;
+        ss += d * d;
+    }
+    const double sd_rel = (M > 1) ? sqrt(ss / (M - 1)) : 0.0;
+    const double P = exp(logP);
+    o[0] = logP;
+    o[1] = P;
+    o[2] = err_k * sd_rel / sqrt((double)M) * P;
+}
+
+// One block per problem: log P_q = LSE_j(logw_qj) - log Ns per shift q, then the estimate.
 // Fixed reduction order (deterministic).  Raises MVN_ERR_NUMERIC if every weight is 0.
 __global__ void k_sov_reduce(const double* __restrict__ logw, int64_t Ns, int M, double err_k,
                              double* __restrict__ out3, int64_t prob_stride, int* status,
                              int raise_numeric) {
     extern __shared__ double red[];  // blockDim.x + M
     double* lq = red + blockDim.x;
-    const int t = threadIdx.x, nt = blockDim.x;
     const double* lw = logw + (int64_t)blockIdx.x * prob_stride;
     for (int qq = 0; qq < M; ++qq) {
-        const double* r = lw + (int64_t)qq * Ns;
-        double m = -INFINITY;
-        for (int64_t k = t; k < Ns; k += nt) m = fmax(m, r[k]);
-        red[t] = m;
-        __syncthreads();
-        for (int w = nt / 2; w > 0; w >>= 1) {
-            if (t < w) red[t] = fmax(red[t], red[t + w]);
-            __syncthreads();
+        double m, s;
+        block_max_sumexp(lw + (int64_t)qq * Ns, Ns, red, m, s);
+        if (threadIdx.x == 0) lq[qq] = shift_log_mean(m, s, Ns);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        estimate_from_shifts(lq, M, err_k, out3 + 3 * blockIdx.x, status, raise_numeric);
+}
+
+// Shard statistics: the local log-weights logw[0 .. p1 - p0) of the global paths [p0, p1);
+// for every shift q, partial[2q], partial[2q+1] = (max, sum of exp(logw - max)) over the shard's
+// paths of shift q, or (-inf, 0) if it has none.  One block; a shard that covers whole shifts
+// gives exactly the pairs k_sov_reduce forms.
+__global__ void k_sov_shift_stats(const double* __restrict__ logw, int64_t p0, int64_t p1,
+                                  int64_t Ns, int M, double* __restrict__ partial) {
+    extern __shared__ double red[];
+    for (int qq = threadIdx.x; qq < M; qq += blockDim.x) {
+        partial[2 * qq] = -INFINITY;
+        partial[2 * qq + 1] = 0.0;
+    }
+    __syncthreads();
+    if (p1 <= p0) return;
+    const int q_first = (int)(p0 / Ns), q_last = (int)((p1 - 1) / Ns);
+    for (int qq = q_first; qq <= q_last; ++qq) {
+        const int64_t lo = max(p0, (int64_t)qq * Ns), hi = min(p1, (int64_t)(qq + 1) * Ns);
+        double m, s;
+        block_max_sumexp(logw + (lo - p0), hi - lo, red, m, s);
+        if (threadIdx.x == 0) {
+            partial[2 * qq] = m;
+            partial[2 * qq + 1] = s;
         }
-        m = red[0];
-        __syncthreads();
+    }
+}
+
+// Combine the per-shift pairs of nparts shards (partials[r][2 M], disjoint path ranges that
+// together cover the rule): per shift m = max_r m_r, s = sum_r s_r exp(m_r - m) in shard order,
+// then the estimate.  With one shard covering all paths this is k_sov_reduce's result bit for
+// bit (s_0 exp(0) = s_0).
+__global__ void k_sov_combine(const double* __restrict__ partials, int nparts, int M, int64_t Ns,
+                              double err_k, double* __restrict__ out3, int* status) {
+    extern __shared__ double lq[];  // M
+    for (int qq = threadIdx.x; qq < M; qq += blockDim.x) {
+        double m = -INFINITY;
+        for (int r = 0; r < nparts; ++r) m = fmax(m, partials[(int64_t)r * 2 * M + 2 * qq]);
         double s = 0.0;
         if (m > -INFINITY)
-            for (int64_t k = t; k < Ns; k += nt) s += exp(r[k] - m);
-        red[t] = s;
-        __syncthreads();
-        for (int w = nt / 2; w > 0; w >>= 1) {
-            if (t < w) red[t] += red[t + w];
-            __syncthreads();
-        }
-        if (t == 0) lq[qq] = (m > -INFINITY) ? m + log(red[0]) - log((double)Ns) : -INFINITY;
-        __syncthreads();
-    }
-    if (t == 0) {
-        double m = -INFINITY;
-        for (int qq = 0; qq < M; ++qq) m = fmax(m, lq[qq]);
-        double* o = out3 + 3 * blockIdx.x;
-        if (!(m > -INFINITY)) {
-            o[0] = -INFINITY;
-            o[1] = 0.0;
-            o[2] = 0.0;
-            if (raise_numeric) dev_raise(status, MVN_ERR_NUMERIC, 0);
-        } else {
-            double s = 0.0;
-            for (int qq = 0; qq < M; ++qq) s += exp(lq[qq] - m);
-            const double logP = m + log(s) - log((double)M);
-            double mean = 0.0;
-            for (int qq = 0; qq < M; ++qq) mean += exp(lq[qq] - logP);
-            mean /= M;
-            double ss = 0.0;
-            for (int qq = 0; qq < M; ++qq) {
-                double d = exp(lq[qq] - logP) - mean;
-                ss += d * d;
+            for (int r = 0; r < nparts; ++r) {
+                const double mr = partials[(int64_t)r * 2 * M + 2 * qq];
+                if (mr > -INFINITY) s += partials[(int64_t)r * 2 * M + 2 * qq + 1] * exp(mr - m);
             }
-            const double sd_rel = (M > 1) ? sqrt(ss / (M - 1)) : 0.0;
-            const double P = exp(logP);
-            o[0] = logP;
-            o[1] = P;
-            o[2] = err_k * sd_rel / sqrt((double)M) * P;
-        }
+        lq[qq] = shift_log_mean(m, s, Ns);
     }
+    __syncthreads();
+    if (threadIdx.x == 0) estimate_from_shifts(lq, M, err_k, out3, status, 1);
 }
 
 mvn_status sov_reduce_launch_opt(mvn_ctx* ctx, const double* logw, int64_t Ns, int M,
@@ -271,6 +340,83 @@ extern "C" mvn_status mvn_sov(mvn_ctx* ctx, int n, const double* a, const double
         MVN_TRY(sov_run_any(ctx, probs, prec, wc.base + ((wc.off + 255) & ~(size_t)255)));
     }
     return sov_reduce_launch(ctx, logw, Ns, M, qmc->err_k, out3, 1, Ntot);
+}
+
+// ---------------------------------------------------------------- ABI: shards of one problem
+//
+// The paths of the lattice rule are independent (Sec. IV-C: the QMC samples are processed in
+// parallel), so one problem can be split into path ranges, one per GPU: each shard sweeps its
+// range and reduces it to per-shift pairs, and the pairs of all shards combine into the estimate.
+
+extern "C" mvn_status mvn_sov_partial(mvn_ctx* ctx, int n, const double* a, const double* b,
+                                      const double* L, int64_t ld, const mvn_qmc* qmc,
+                                      mvn_prec prec, int64_t p0, int64_t p1, double* partial,
+                                      double* path_logw) {
+    if (!ctx) return MVN_ERR_ARG;
+    MVN_TRY(check_qmc(ctx, qmc));
+    MVN_TRY(check_problem_host(ctx, n, a, b, L, ld));
+    if (!partial) return mvn_fail(ctx, MVN_ERR_ARG, "partial is null");
+    if (prec != MVN_FP64 && prec != MVN_MIXED && prec != MVN_MIXED_SIMT)
+        return mvn_fail(ctx, MVN_ERR_ARG, "unknown precision");
+    const int M = qmc->n_shifts;
+    const int64_t Ns = qmc->n_points, Ntot = Ns * M;
+    if (p0 < 0 || p1 < p0 || p1 > Ntot)
+        return mvn_fail(ctx, MVN_ERR_ARG, "path range outside [0, n_points * n_shifts]");
+    MVN_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int64_t cnt = p1 - p0;
+    MVN_TRY(lattice_ensure(ctx, std::max(n, 1)));
+    const size_t need = ws_round(sizeof(uint64_t) * (size_t)M * std::max(n, 1)) +
+                        (path_logw ? 0 : ws_round(sizeof(double) * (size_t)std::max<int64_t>(cnt, 1))) +
+                        sov_any_ws_bytes(ctx, 1, n, (cnt + 127) / 128, prec) + 1024;
+    MVN_TRY(ws_reserve(ctx, need));
+    WsCarver wc(ctx->ws);
+    uint64_t* delta = wc.take<uint64_t>((size_t)M * std::max(n, 1));
+    double* logw = path_logw ? path_logw : wc.take<double>((size_t)std::max<int64_t>(cnt, 1));
+    std::vector<SovProblem> probs(1);
+    SovProblem& P = probs[0];
+    P.n = n;
+    P.M = M;
+    P.Ns = Ns;
+    P.Ntot = cnt;
+    P.p0 = p0;
+    P.a = a;
+    P.b = b;
+    P.L = L;
+    P.ld = ld;
+    P.delta = delta;
+    P.dstride = std::max(n, 1);
+    P.logw = logw;
+    P.nprefix = 0;
+    P.prefix = nullptr;
+    P.logw_prefix = nullptr;
+    MVN_TRY(check_limits_device(ctx, n, a, b));
+    MVN_TRY(lattice_shifts(ctx, qmc->seed, M, n, delta));
+    if (cnt > 0) {
+        if (n == 0) {
+            MVN_CUDA(ctx, cudaMemsetAsync(logw, 0, sizeof(double) * cnt, ctx->stream));
+        } else {
+            MVN_TRY(sov_run_any(ctx, probs, prec, wc.base + ((wc.off + 255) & ~(size_t)255)));
+        }
+    }
+    const int nt = 512;
+    k_sov_shift_stats<<<1, nt, sizeof(double) * nt, ctx->stream>>>(logw, p0, p1, Ns, M, partial);
+    MVN_LAUNCHED(ctx);
+    return MVN_OK;
+}
+
+extern "C" mvn_status mvn_sov_combine(mvn_ctx* ctx, int nparts, const mvn_qmc* qmc,
+                                      const double* partials, double* out3) {
+    if (!ctx) return MVN_ERR_ARG;
+    MVN_TRY(check_qmc(ctx, qmc));
+    if (nparts < 1 || nparts > 65536 || !partials || !out3)
+        return mvn_fail(ctx, MVN_ERR_ARG, "invalid shard list or output");
+    MVN_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int M = qmc->n_shifts;
+    k_sov_combine<<<1, 256, sizeof(double) * M, ctx->stream>>>(partials, nparts, M,
+                                                               qmc->n_points, qmc->err_k, out3,
+                                                               ctx->d_status);
+    MVN_LAUNCHED(ctx);
+    return MVN_OK;
 }
 
 // ---------------------------------------------------------------- ABI: mvn_sov_batched

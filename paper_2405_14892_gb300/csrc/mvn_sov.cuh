@@ -9,7 +9,7 @@ struct SovProblem {
     int n;
     int M;                   // shifts
     int64_t Ns;              // points per shift
-    int64_t Ntot;            // M * Ns paths
+    int64_t Ntot;            // paths of this problem (M * Ns, or a shard's count)
     const double* a;         // n
     const double* b;         // n
     const double* L;         // lower factor, column-major
@@ -20,6 +20,8 @@ struct SovProblem {
     int nprefix;             // optional prefix recording (Alg. 1 loop)
     const int* prefix;       // sorted prefix lengths in 1..n (device)
     double* logw_prefix;     // [t * Ntot + p]
+    int64_t p0 = 0;          // lattice index of the first path (a shard of the rule: local path
+                             // p is path p0 + p of the whole rule; 0 for a whole problem)
 };
 
 mvn_status check_qmc(mvn_ctx* ctx, const mvn_qmc* qmc);

@@ -25,8 +25,9 @@ __device__ void sov_tile(const SovProblem& P, int tile, const uint64_t* __restri
     const int n = P.n;
     const int64_t p = (int64_t)tile * SOV_P + t;
     const bool valid = p < P.Ntot;
-    const int64_t q = valid ? p / P.Ns : 0;
-    const uint64_t j = valid ? (uint64_t)(p - q * P.Ns) + 1u : 1u;
+    const int64_t pg = P.p0 + p;  // index of the path in the whole lattice rule
+    const int64_t q = valid ? pg / P.Ns : 0;
+    const uint64_t j = valid ? (uint64_t)(pg - q * P.Ns) + 1u : 1u;
     const uint64_t* __restrict__ dq = P.delta + q * P.dstride;
     const double* __restrict__ L = P.L;
     const int64_t ld = P.ld;

@@ -81,7 +81,9 @@ __device__ __forceinline__ float phinv_two_sided_f32(float p, float q) {
 __device__ __forceinline__ float sov_step_f32(double ai, double bi, float s, float lii, double w,
                                               double& delta) {
     const bool ainf = (ai == -INFINITY), binf = (bi == INFINITY);
-    const float wf = (float)w, wcf = (float)(1.0 - w);
+    // w is ((W >> 11) + 1/2) 2^-53 rounded to FP64, which is 1 for the top lattice integers:
+    // 1 - w then takes its unrounded value 2^-54 (never 0, so Phi^-1 stays finite)
+    const float wf = (float)w, wcf = (float)fmax(1.0 - w, 0x1p-54);
     if (ainf && binf) {
         delta = 1.0;
         return phinv_two_sided_f32(wf, wcf);

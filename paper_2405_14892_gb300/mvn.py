@@ -62,6 +62,8 @@ SIGNATURES = {
     "mvn_cholesky_grad": (_I, [_P, _I, _P, _I64, _P]),
     "mvn_sov": (_I, [_P, _I, _P, _P, _P, _I64, _QP, _I, _P, _P]),
     "mvn_sov_grad": (_I, [_P, _I, _P, _P, _P, _I64, _QP, _I, _P, _P, _P, _P]),
+    "mvn_sov_partial": (_I, [_P, _I, _P, _P, _P, _I64, _QP, _I, _I64, _I64, _P, _P]),
+    "mvn_sov_combine": (_I, [_P, _I, _QP, _P, _P]),
     "mvn_sov_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _I64, _QP, _I, _P]),
     "mvn_posterior": (_I, [_P, _I, _P, _P, _I64, _I, _P, _P, _D, _P, _P, _I64,
                            ctypes.POINTER(_I)]),
@@ -269,6 +271,39 @@ def mvn_sov(a: torch.Tensor, b: torch.Tensor, L: torch.Tensor, n_points: int, n_
     c.check(lib().mvn_sov(c.h, n, _vec(a, n, "a"), _vec(b, n, "b"), Lp, ld, ctypes.byref(q),
                           PREC[prec], _vec(out3, 3, "out3"),
                           _vec(path_logw, n_points * n_shifts, "path_logw")))
+    return out3
+
+
+def mvn_sov_partial(a: torch.Tensor, b: torch.Tensor, L: torch.Tensor, n_points: int,
+                    n_shifts: int, seed: int, p0: int, p1: int, prec: str = "fp64",
+                    err_k: float = 3.0, partial: torch.Tensor | None = None,
+                    path_logw: torch.Tensor | None = None) -> torch.Tensor:
+    """Shard [p0, p1) of the lattice paths: returns the per-shift pairs (2 * n_shifts doubles)
+    for mvn_sov_combine."""
+    n = a.numel()
+    if partial is None:
+        partial = torch.empty(2 * n_shifts, dtype=torch.float64, device=a.device)
+    Lp, ld = _mat(L, n, "L")
+    q = _qmc(n_points, n_shifts, seed, err_k)
+    c = context()
+    c.check(lib().mvn_sov_partial(c.h, n, _vec(a, n, "a"), _vec(b, n, "b"), Lp, ld,
+                                  ctypes.byref(q), PREC[prec], int(p0), int(p1),
+                                  _vec(partial, 2 * n_shifts, "partial"),
+                                  _vec(path_logw, int(p1) - int(p0), "path_logw")))
+    return partial
+
+
+def mvn_sov_combine(partials: torch.Tensor, n_points: int, n_shifts: int, err_k: float = 3.0,
+                    out3: torch.Tensor | None = None) -> torch.Tensor:
+    """Estimate {log P, P, err} from the stacked pairs of the shards (nparts x 2 n_shifts)."""
+    nparts = partials.numel() // (2 * n_shifts)
+    if out3 is None:
+        out3 = torch.empty(3, dtype=torch.float64, device=partials.device)
+    q = _qmc(n_points, n_shifts, 0, err_k)
+    c = context()
+    c.check(lib().mvn_sov_combine(c.h, nparts, ctypes.byref(q),
+                                  _vec(partials.contiguous(), nparts * 2 * n_shifts, "partials"),
+                                  _vec(out3, 3, "out3")))
     return out3
 
 

@@ -94,10 +94,11 @@ def test_mixed_tc_ragged_vs_oracle(mvn, n, Ns, M):
     assert abs(out[0] - est[0]) <= 1e-4, (out, est, d.max())
     # per path: each dimension's factor carries the FP32 step's error (~2e-7 relative in a',
     # times the Mills ratio) and the limit shift the two-slice GEMM's (~2^-21 of sum |L||y|),
-    # accumulated over the path's n factors; stated bound 1e-4 max(1, |logw|)
+    # accumulated over the path's n factors; stated bound 1e-6 max(1, |logw|) (measured up to
+    # 3.4e-8 relative at n = 300)
     rel = d / np.maximum(1.0, np.abs(ref))
     print(f"n={n}: mixed per-path max |d logw| {d.max():.3e}, max relative {rel.max():.3e}")
-    assert rel.max() <= 1e-4
+    assert rel.max() <= 1e-6
 
 
 def test_mixed_tc_batched_and_excursion(mvn):

@@ -483,6 +483,32 @@ def test_estimate_log_domain():
     assert oracle.estimate(np.full(8, -np.inf), 2) == (-np.inf, 0.0, 0.0)
 
 
+def test_shard_partials_combine_to_the_estimate():
+    """Splitting the paths into shards (whole shifts, or cuts inside a shift) and combining the
+    per-shift statistics gives the estimate of all paths: the log-sum-exp decomposes exactly, so
+    only rounding differs."""
+    rng = np.random.default_rng(41)
+    M, Ns = 7, 53
+    lw = rng.uniform(-60, -40, M * Ns)
+    lw[5] = -np.inf
+    lw[Ns:2 * Ns] = -np.inf        # a shift whose paths all have weight 0
+    ref = oracle.estimate(lw, M)
+    for cuts in ([0, M * Ns], [0, 3 * Ns, M * Ns], [0, 17, 100, 101, 250, M * Ns],
+                 [0, 1, Ns, 2 * Ns + 5, M * Ns - 1, M * Ns]):
+        parts = [oracle.shift_partials(lw[c0:c1], c0, Ns, M) for c0, c1 in zip(cuts, cuts[1:])]
+        got = oracle.combine_partials(parts, Ns, M)
+        assert abs(got[0] - ref[0]) <= 1e-13 * abs(ref[0])
+        assert abs(got[1] - ref[1]) <= 1e-13 * ref[1]
+        assert abs(got[2] - ref[2]) <= 1e-10 * ref[2]
+    # a shard with no path of a shift reports (-inf, 0) for it
+    part = oracle.shift_partials(lw[:10], 0, Ns, M)
+    assert part[0, 0] == np.max(lw[:10]) and np.all(part[1:, 0] == -np.inf)
+    assert np.all(part[1:, 1] == 0.0)
+    # every weight zero
+    z = [oracle.shift_partials(np.full(M * Ns, -np.inf), 0, Ns, M)]
+    assert oracle.combine_partials(z, Ns, M) == (-np.inf, 0.0, 0.0)
+
+
 # ----------------------------------------------------------------- SOV adjoint
 
 def test_sov_grad_n1_closed_form():

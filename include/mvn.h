@@ -192,10 +192,21 @@ mvn_status mvn_sov_combine(mvn_ctx* ctx, int nparts, const mvn_qmc* qmc, const d
  *   within each 128-path tile and the tiles in FP64.  Workspace per 128 paths: 2 * n * 128 * 8 bytes (FP64) or
  *   * 4 bytes (mixed).
  * dlogp_dL uses the leading dimension ld of L; its strict upper part is not written.  out3 as
- * in mvn_sov. */
+ * in mvn_sov.
+ * Memory: the transformed variables y and the reverse sums of a 128-path tile take
+ * 2 * n * 128 * (8 or 4) bytes; when all tiles together exceed the context's limit
+ * (mvn_grad_set_ylimit, default 8 GiB), the tiles run in batches under that limit: a first
+ * forward sweep over all paths gives the log-weights (hence every path's weight in log P-hat),
+ * then each batch recomputes its forward sweep and runs its reverse sweep.  out3, dlogp_da and
+ * dlogp_db are then bit-identical to the unbatched call; dlogp_dL agrees to rounding (its
+ * off-diagonal sums are added batch by batch). */
 mvn_status mvn_sov_grad(mvn_ctx* ctx, int n, const double* a, const double* b,
                         const double* L, int64_t ld, const mvn_qmc* qmc, mvn_prec prec,
                         double* out3, double* dlogp_da, double* dlogp_db, double* dlogp_dL);
+
+/* Limit (bytes) of the y and reverse-sum buffers of mvn_sov_grad on this context; 0 restores
+ * the default (8 GiB).  Smaller limits trade memory for one more forward sweep (see above). */
+mvn_status mvn_grad_set_ylimit(mvn_ctx* ctx, int64_t bytes);
 
 /* nprob independent problems in one launch (Alg. 1's loop of PMVN calls):
  * problem p has dimension dims[p] (host array) and limits a[off_p .. off_p + dims[p]),

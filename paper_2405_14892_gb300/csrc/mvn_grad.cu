@@ -456,13 +456,16 @@ __global__ void k_sum_parts(const double* __restrict__ part, int ntiles, int n,
 // Paths are laid out per tile: X[tile][dim][128].  One 64 x 64 lower output tile per block.
 // The products of one 128-path tile are summed in T, the tiles' partial sums in FP64 (for
 // T = float the rounding error then grows with the tile's 128 terms, not with all N paths).
+// mode 0: write every lower entry (dL(i, i) from dsum); mode 1: write the strictly lower entries
+// only; mode 2: add into the strictly lower entries (batches of path tiles: Sbar, Y and omega are
+// the batch's, Ntot its path count; the diagonal is written once at the end by k_grad_diag).
 template <typename T>
 __global__ void __launch_bounds__(256) k_grad_L(int n, int ntiles, int64_t Ntot,
                                                 const T* __restrict__ Sbar,
                                                 const T* __restrict__ Y,
                                                 const double* __restrict__ omega,
                                                 const double* __restrict__ dsum,
-                                                double* __restrict__ G, int64_t ldg) {
+                                                double* __restrict__ G, int64_t ldg, int mode) {
     __shared__ T As[32][64 + 1];  // As[pp][r] = w_p sbar_{p, R0 + r}
     __shared__ T Bs[32][64 + 1];  // Bs[pp][c] = y_{p, C0 + c}
     const int x = blockIdx.x;
@@ -521,9 +524,19 @@ __global__ void __launch_bounds__(256) k_grad_L(int n, int ntiles, int64_t Ntot,
         for (int u = 0; u < 4; ++u) {
             const int r = R0 + tx + 16 * u;
             if (r >= n || r < c) continue;
-            G[r + (int64_t)c * ldg] = (r == c) ? dsum[2 * (int64_t)n + r] : acc[u][v];
+            if (mode == 0)
+                G[r + (int64_t)c * ldg] = (r == c) ? dsum[2 * (int64_t)n + r] : acc[u][v];
+            else if (r > c)
+                G[r + (int64_t)c * ldg] = (mode == 1) ? acc[u][v] : G[r + (int64_t)c * ldg] + acc[u][v];
         }
     }
+}
+
+// dL(i, i) = dsum[2n + i] (the diagonal terms summed over all work items).
+__global__ void k_grad_diag(int n, const double* __restrict__ dsum, double* __restrict__ G,
+                            int64_t ldg) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) G[i + (int64_t)i * ldg] = dsum[2 * (int64_t)n + i];
 }
 
 // ---------------------------------------------------------------- generic FP64 GEMM
@@ -782,12 +795,18 @@ static mvn_status sov_grad_run(mvn_ctx* ctx, int n, const double* a, const doubl
     const int64_t ntiles = (Ntot + SOV_P - 1) / SOV_P;
     const int nn = std::max(n, 1);
     const int64_t ystride = (int64_t)nn * SOV_P;
-    if ((double)ntiles * ystride * 2.0 * sizeof(T) > 200e9)
-        return mvn_fail(ctx, MVN_ERR_ARG, "gradient workspace beyond 200 GB");
+    // path tiles whose y and ybar fit under the context's limit; more tiles than that run in
+    // batches, each recomputing its forward sweep after a first forward pass over all paths has
+    // given the log-weights (and so the softmax weights of every path)
+    const int64_t per_tile = 2 * ystride * (int64_t)sizeof(T);
+    const int64_t batch_tiles =
+        std::max<int64_t>(1, std::min<int64_t>(ntiles, ctx->grad_y_limit / per_tile));
+    const int64_t nbatch = (ntiles + batch_tiles - 1) / batch_tiles;
+    if ((double)ntiles * RV_ITEMS_PER_TILE * 3.0 * nn * 8.0 > 100e9)
+        return mvn_fail(ctx, MVN_ERR_ARG, "gradient partial sums beyond 100 GB");
     MVN_TRY(lattice_ensure(ctx, nn));
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 2 * (int64_t)ctx->sm_count));
     const size_t need = ws_round(sizeof(uint64_t) * (size_t)M * nn) + ws_round(sizeof(double) * Ntot) * 2 +
-                        2 * ws_round(sizeof(T) * (size_t)ntiles * ystride) +
+                        2 * ws_round(sizeof(T) * (size_t)batch_tiles * ystride) +
                         ws_round(sizeof(double) * 3 * (size_t)RV_ITEMS_PER_TILE * ntiles * nn) +
                         ws_round(sizeof(double) * 3 * (size_t)nn) + 4 * ws_round(sizeof(double)) + 4096;
     MVN_TRY(ws_reserve(ctx, need));
@@ -795,8 +814,8 @@ static mvn_status sov_grad_run(mvn_ctx* ctx, int n, const double* a, const doubl
     uint64_t* delta = wc.take<uint64_t>((size_t)M * nn);
     double* logw = wc.take<double>(Ntot);
     double* omega = wc.take<double>(Ntot);
-    T* Y = wc.take<T>((size_t)ntiles * ystride);
-    T* Sb = wc.take<T>((size_t)ntiles * ystride);
+    T* Y = wc.take<T>((size_t)batch_tiles * ystride);
+    T* Sb = wc.take<T>((size_t)batch_tiles * ystride);
     double* part = wc.take<double>(3 * (size_t)RV_ITEMS_PER_TILE * ntiles * nn);
     double* dsum = wc.take<double>(3 * (size_t)nn);
     double* lse = wc.take<double>(1);
@@ -816,20 +835,36 @@ static mvn_status sov_grad_run(mvn_ctx* ctx, int n, const double* a, const doubl
     P.delta = delta;
     P.dstride = nn;
     P.logw = logw;
-    // forward sweep keeping every tile's y
+    int fwd_per_sm = 1, rev_per_sm = 1;
+    MVN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fwd_per_sm, k_sov_fwd_keep<T>,
+                                                                RV_THREADS, 0));
+    MVN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rev_per_sm, k_sov_rev<T>,
+                                                                RV_THREADS, 0));
+    // the problem restricted to path tiles [t0, t0 + nt): its paths start at p0 = 128 t0
+    auto batch_problem = [&](int64_t t0, int64_t nt) {
+        SovProblem B = P;
+        B.p0 = t0 * SOV_P;
+        B.Ntot = std::min<int64_t>(Ntot - B.p0, nt * SOV_P);
+        B.logw = logw + B.p0;
+        return B;
+    };
+    // forward sweep keeping the batch's y (32-path work items, four per tile, persistent grid)
+    auto forward = [&](const SovProblem& B, int64_t nt) -> mvn_status {
+        MVN_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(int), ctx->stream));
+        const int nfwd = (int)(RV_ITEMS_PER_TILE * nt);
+        const int grid_fwd = std::max(1, std::min(nfwd, std::max(fwd_per_sm, 1) * ctx->sm_count));
+        MVN_TIMED(ctx, F64 ? "k_sov_grad_fwd_f64" : "k_sov_grad_fwd_f32",
+                  (k_sov_fwd_keep<T><<<grid_fwd, RV_THREADS, 0, ctx->stream>>>(
+                      B, nfwd, counter, ctx->d_alpha, Y, ystride)));
+        return MVN_OK;
+    };
     if (n == 0) {
         MVN_CUDA(ctx, cudaMemsetAsync(logw, 0, sizeof(double) * Ntot, ctx->stream));
     } else {
-        MVN_CUDA(ctx, cudaMemsetAsync(counter, 0, 2 * sizeof(int), ctx->stream));
-        // 32-path work items (four per tile), a persistent grid of the resident CTAs
-        const int nfwd = (int)(RV_ITEMS_PER_TILE * ntiles);
-        int per_sm = 1;
-        MVN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sov_fwd_keep<T>,
-                                                                    RV_THREADS, 0));
-        const int grid_fwd = std::max(1, std::min(nfwd, std::max(per_sm, 1) * ctx->sm_count));
-        MVN_TIMED(ctx, F64 ? "k_sov_grad_fwd_f64" : "k_sov_grad_fwd_f32",
-                  (k_sov_fwd_keep<T><<<grid_fwd, RV_THREADS, 0, ctx->stream>>>(
-                      P, nfwd, counter, ctx->d_alpha, Y, ystride)));
+        for (int64_t t0 = 0; t0 < ntiles; t0 += batch_tiles) {
+            const int64_t nt = std::min(batch_tiles, ntiles - t0);
+            MVN_TRY(forward(batch_problem(t0, nt), nt));
+        }
     }
     MVN_TRY(sov_reduce_launch_opt(ctx, logw, Ns, M, qmc->err_k, out3, 1, Ntot, true));
     k_lse_all<<<1, 512, 0, ctx->stream>>>(logw, Ntot, lse);
@@ -837,16 +872,29 @@ static mvn_status sov_grad_run(mvn_ctx* ctx, int n, const double* a, const doubl
     k_weights<<<(unsigned)((Ntot + 255) / 256), 256, 0, ctx->stream>>>(logw, Ntot, lse, omega);
     MVN_LAUNCHED(ctx);
     if (n == 0) return MVN_OK;
-    // reverse sweep
-    // work items of 32 paths (four per tile); a persistent grid of the resident CTAs
-    const int nrev = (int)(RV_ITEMS_PER_TILE * ntiles);
-    int per_sm = 1;
-    MVN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sov_rev<T>, RV_THREADS, 0));
-    const int grid_rev = std::max(1, std::min(nrev, std::max(per_sm, 1) * ctx->sm_count));
-    MVN_TIMED(ctx, F64 ? "k_sov_rev_f64" : "k_sov_rev_f32",
-              (k_sov_rev<T><<<grid_rev, RV_THREADS, 0, ctx->stream>>>(
-                  P, nrev, counter + 1, ctx->d_alpha, Y, Sb, ystride, omega, part)));
-    k_sum_parts<<<dim3((n + 255) / 256, 3), 256, 0, ctx->stream>>>(part, nrev, n, dsum);
+    const int T64 = (n + 63) / 64;
+    for (int64_t t0 = 0; t0 < ntiles; t0 += batch_tiles) {
+        const int64_t nt = std::min(batch_tiles, ntiles - t0);
+        const SovProblem B = batch_problem(t0, nt);
+        if (nbatch > 1) MVN_TRY(forward(B, nt));  // the batch's y again (the buffer was reused)
+        // reverse sweep: work items of 32 paths (four per tile), persistent grid
+        const int nrev = (int)(RV_ITEMS_PER_TILE * nt);
+        const int grid_rev = std::max(1, std::min(nrev, std::max(rev_per_sm, 1) * ctx->sm_count));
+        MVN_CUDA(ctx, cudaMemsetAsync(counter + 1, 0, sizeof(int), ctx->stream));
+        double* part_b = part + (size_t)RV_ITEMS_PER_TILE * t0 * 3 * n;
+        MVN_TIMED(ctx, F64 ? "k_sov_rev_f64" : "k_sov_rev_f32",
+                  (k_sov_rev<T><<<grid_rev, RV_THREADS, 0, ctx->stream>>>(
+                      B, nrev, counter + 1, ctx->d_alpha, Y, Sb, ystride, omega + B.p0,
+                      part_b)));
+        if (dlogp_dL && nbatch > 1) {
+            MVN_TIMED(ctx, F64 ? "k_grad_L_f64" : "k_grad_L_f32",
+                      (k_grad_L<T><<<(unsigned)((int64_t)T64 * (T64 + 1) / 2), 256, 0,
+                                     ctx->stream>>>(n, (int)nt, B.Ntot, Sb, Y, omega + B.p0,
+                                                    dsum, dlogp_dL, ld, t0 == 0 ? 1 : 2)));
+        }
+    }
+    const int nrev_all = (int)(RV_ITEMS_PER_TILE * ntiles);
+    k_sum_parts<<<dim3((n + 255) / 256, 3), 256, 0, ctx->stream>>>(part, nrev_all, n, dsum);
     MVN_LAUNCHED(ctx);
     if (dlogp_da)
         MVN_CUDA(ctx, cudaMemcpyAsync(dlogp_da, dsum, sizeof(double) * n,
@@ -855,11 +903,23 @@ static mvn_status sov_grad_run(mvn_ctx* ctx, int n, const double* a, const doubl
         MVN_CUDA(ctx, cudaMemcpyAsync(dlogp_db, dsum + n, sizeof(double) * n,
                                       cudaMemcpyDeviceToDevice, ctx->stream));
     if (dlogp_dL) {
-        const int T64 = (n + 63) / 64;
-        MVN_TIMED(ctx, F64 ? "k_grad_L_f64" : "k_grad_L_f32",
-                  (k_grad_L<T><<<(unsigned)((int64_t)T64 * (T64 + 1) / 2), 256, 0, ctx->stream>>>(
-                      n, (int)ntiles, Ntot, Sb, Y, omega, dsum, dlogp_dL, ld)));
+        if (nbatch == 1) {
+            MVN_TIMED(ctx, F64 ? "k_grad_L_f64" : "k_grad_L_f32",
+                      (k_grad_L<T><<<(unsigned)((int64_t)T64 * (T64 + 1) / 2), 256, 0,
+                                     ctx->stream>>>(n, (int)ntiles, Ntot, Sb, Y, omega, dsum,
+                                                    dlogp_dL, ld, 0)));
+        } else {
+            k_grad_diag<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, dsum, dlogp_dL, ld);
+            MVN_LAUNCHED(ctx);
+        }
     }
+    return MVN_OK;
+}
+
+extern "C" mvn_status mvn_grad_set_ylimit(mvn_ctx* ctx, int64_t bytes) {
+    if (!ctx) return MVN_ERR_ARG;
+    if (bytes < 0) return mvn_fail(ctx, MVN_ERR_ARG, "negative limit");
+    ctx->grad_y_limit = bytes > 0 ? bytes : MVN_GRAD_Y_LIMIT_DEFAULT;
     return MVN_OK;
 }
 

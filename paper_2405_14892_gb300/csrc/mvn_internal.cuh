@@ -17,6 +17,8 @@
 //   [1] LAPACK-style info of the last failed factorisation (1-based column)
 //   [2] scratch counter used by persistent kernels
 #define MVN_STATUS_WORDS 8
+// default limit of the adjoint's y and ybar buffers (8 GiB)
+#define MVN_GRAD_Y_LIMIT_DEFAULT ((int64_t)8 << 30)
 
 // Launch shapes the autotuner chooses (mvn_tune.cu); every choice gives bit-identical results
 // (the Cholesky update sums exact integers, the sweeps are per path), only the time differs.
@@ -52,6 +54,8 @@ struct mvn_ctx {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> ktimes;
+    // bytes of the y and ybar buffers of mvn_sov_grad (path tiles beyond it run in batches)
+    int64_t grad_y_limit = MVN_GRAD_Y_LIMIT_DEFAULT;
 };
 
 // Events around one launch when timing is enabled (returns nullptr otherwise).

@@ -62,6 +62,7 @@ SIGNATURES = {
     "mvn_cholesky_grad": (_I, [_P, _I, _P, _I64, _P]),
     "mvn_sov": (_I, [_P, _I, _P, _P, _P, _I64, _QP, _I, _P, _P]),
     "mvn_sov_grad": (_I, [_P, _I, _P, _P, _P, _I64, _QP, _I, _P, _P, _P, _P]),
+    "mvn_grad_set_ylimit": (_I, [_P, _I64]),
     "mvn_sov_partial": (_I, [_P, _I, _P, _P, _P, _I64, _QP, _I, _I64, _I64, _P, _P]),
     "mvn_sov_combine": (_I, [_P, _I, _QP, _P, _P]),
     "mvn_sov_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _I64, _QP, _I, _P]),
@@ -324,6 +325,12 @@ def mvn_sov_grad(a, b, L, n_points, n_shifts, seed, prec="fp64", err_k=3.0, want
                                PREC[prec], _P(out3.data_ptr()), _P(ga.data_ptr()),
                                _P(gb.data_ptr()), _P(gL.data_ptr()) if gL is not None else None))
     return out3, ga, gb, gL
+
+
+def mvn_grad_set_ylimit(nbytes: int):
+    """Limit of mvn_sov_grad's y / reverse-sum buffers on the current context (0 = default)."""
+    c = context()
+    c.check(lib().mvn_grad_set_ylimit(c.h, int(nbytes)))
 
 
 def mvn_sov_batched(dims, offsets, a, b, L, n_points, n_shifts, seed, prec="fp64", err_k=3.0):

@@ -216,3 +216,33 @@ def test_w4_mixed_gradients_vs_fp64(mvn):
           f"db {e_b:.2e} dsigma2 {e_s:.2e} drange {e_r:.2e}")
     assert abs(lmx - l64) <= 1e-4
     assert max(e_b, e_s, e_r) <= 1e-3
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sov_grad_batched_under_a_memory_limit(mvn, prec):
+    """A y-buffer limit of 3 path tiles splits 2,000 paths (16 tiles) into 6 batches that recompute
+    their forward sweep: the estimate and d log P / d(a, b) are bit-identical to the unbatched
+    call, d log P / dL equal to rounding; and the FP64 result still matches the oracle."""
+    n, Ns, M, seed = 90, 400, 5, 77
+    S, a, b = _problem(n, 3)
+    Lo, _ = oracle.cholesky(S)
+    L = mvn.to_colmajor(_t(Lo))
+    ref = mvn.mvn_sov_grad(_t(a), _t(b), L, Ns, M, seed, prec=prec, want_L=True)
+    mvn.sync()
+    elt = 8 if prec == "fp64" else 4
+    mvn.mvn_grad_set_ylimit(3 * 2 * n * 128 * elt)
+    try:
+        got = mvn.mvn_sov_grad(_t(a), _t(b), L, Ns, M, seed, prec=prec, want_L=True)
+        mvn.sync()
+    finally:
+        mvn.mvn_grad_set_ylimit(0)
+    for k in range(3):
+        assert torch.equal(got[k], ref[k]), k
+    gl, rl = np.tril(got[3].cpu().numpy()), np.tril(ref[3].cpu().numpy())
+    assert np.abs(gl - rl).max() <= 1e-12 * max(1.0, np.abs(rl).max())
+    if prec == "fp64":
+        logP, ga, gb, gL = oracle.sov_grad(a, b, Lo, oracle.QMC(Ns, M, seed))
+        assert abs(got[0].cpu().numpy()[0] - logP) < 1e-9
+        scale = max(1.0, np.abs(gb).max(), np.abs(ga).max())
+        np.testing.assert_allclose(got[2].cpu().numpy(), gb, atol=1e-9 * scale)
+        assert np.abs(gl - np.tril(gL)).max() <= 1e-9 * max(1.0, np.abs(gL).max())

@@ -77,6 +77,8 @@ def _load():
     lib.orc_sov_paths.restype = None
     lib.orc_sov_paths.argtypes = [i32, P, P, P, i64, i64, P, P, i64, i64, P, P, P, i32, P, P,
                                   i32]
+    lib.orc_cholesky_reorder.restype = i32
+    lib.orc_cholesky_reorder.argtypes = [i32, P, P, i64, P, P, P]
     lib.orc_sov_step_vec.restype = None
     lib.orc_sov_step_vec.argtypes = [i64, P, P, P, P, P, P, P]
     lib.orc_sov_grad.restype = None
@@ -247,6 +249,24 @@ def cholesky(A: np.ndarray):
     info = _load().orc_cholesky(n, _ptr(F), max(n, 1))
     L = np.tril(F)
     return L, int(info)
+
+
+def cholesky_reorder(A: np.ndarray, a, b):
+    """Cholesky factor with the univariate variable reordering (Gibson, Glasbey and Elston 1994;
+    Genz and Bretz 2009, Sec. 4.1.3; not in the paper: a variance-reducing variant of the SOV
+    estimator of Eq. 2): at step i the variable with the smallest conditional interval
+    probability given the truncated-normal means of the variables already placed goes next.
+    Returns (L, perm, a[perm], b[perm], info) with L the lower factor of A[perm, perm]."""
+    n = A.shape[0]
+    S = np.asfortranarray(np.array(A, dtype=np.float64, copy=True))
+    S = np.asfortranarray(np.tril(S) + np.tril(S, -1).T)
+    L = np.zeros((n, n), order="F")
+    ap = np.ascontiguousarray(a, dtype=np.float64).copy()
+    bp = np.ascontiguousarray(b, dtype=np.float64).copy()
+    perm = np.zeros(n, dtype=np.int32)
+    info = _load().orc_cholesky_reorder(n, _ptr(S), _ptr(L), max(n, 1), _ptr(ap), _ptr(bp),
+                                        _ptr(perm))
+    return np.array(L), perm, ap, bp, int(info)
 
 
 def cholesky_grad(L: np.ndarray, Lbar: np.ndarray) -> np.ndarray:

@@ -347,12 +347,23 @@ def run_gpu(args):
     all_pairs = torch.empty(2 * M * world, dtype=torch.float64, device=dev)
 
     def sweep():
+        aa, bb = (reo["a"], reo["b"]) if args.reorder else (a_d, b_d)
         if world == 1:
-            mvn.mvn_sov(a_d, b_d, S, Ns, M, seed, prec=prec, out3=out3)
+            mvn.mvn_sov(aa, bb, S, Ns, M, seed, prec=prec, out3=out3)
             return
-        mvn.mvn_sov_partial(a_d, b_d, S, Ns, M, seed, p0, p1, prec=prec, partial=pairs)
+        mvn.mvn_sov_partial(aa, bb, S, Ns, M, seed, p0, p1, prec=prec, partial=pairs)
         dist.all_gather_into_tensor(all_pairs, pairs)
         mvn.mvn_sov_combine(all_pairs, Ns, M, out3=out3)
+
+    reo = {}
+
+    def factor():
+        if args.reorder:
+            # univariate variable reordering (FP64 pivoted factorisation); the sweep then runs on
+            # the permuted limits
+            reo["perm"], reo["a"], reo["b"], _ = mvn.mvn_cholesky_reorder(S, a_d, b_d, check=False)
+        else:
+            mvn.mvn_cholesky(S, prec=prec, check=False)
 
     def step(evs=None):
         if evs is not None:
@@ -360,7 +371,7 @@ def run_gpu(args):
         mvn.mvn_matern(coords, w["sigma2"], w["range"], w["nu"], w["nugget"], out=S)
         if evs is not None:
             evs[1].record(stream)
-        mvn.mvn_cholesky(S, prec=prec, check=False)
+        factor()
         if evs is not None:
             evs[2].record(stream)
         sweep()
@@ -440,7 +451,7 @@ def run_gpu(args):
 
     # ---- the metric's other arm: the plain FP64 GPU path on identical lattice points
     fp64 = None
-    if prec == "mixed" and not args.no_fp64_arm and rank == 0:
+    if prec == "mixed" and not args.no_fp64_arm and not args.reorder and rank == 0:
         del S
         torch.cuda.empty_cache()
         f_ms, f_res = fp64_arm(mvn, coords, w, a_d, b_d, Ns, M, seed, n, dev, stream)
@@ -474,6 +485,8 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": w["name"], "n": n, "paths": Ntot, "shifts": M, "points": Ns,
                    "prec": prec, "l2": "inputs larger than L2 (Sigma n^2 FP64 = 2.1 GB)",
+                   "reorder": ("univariate variable reordering (FP64 pivoted Cholesky)"
+                               if args.reorder else None),
                    "parallelism": (f"paths split over {world} ranks (Sigma and its factor on "
                                    f"every rank, one all-gather of per-shift pairs)"
                                    if world > 1 else "1 GPU"),
@@ -514,6 +527,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="skip the plain FP64 GPU step (about 20 s at the default size)")
+    ap.add_argument("--reorder", action="store_true",
+                    help="factor with the univariate variable reordering (mvn_cholesky_reorder)")
     ap.add_argument("--no-tune", action="store_true",
                     help="default launch shapes instead of the autotuner (profiling runs)")
     ap.add_argument("--workload", default="w2", choices=["w1", "w2", "w3", "w4", "w5"],

@@ -137,6 +137,27 @@ mvn_status mvn_matern_grad(mvn_ctx* ctx, int n, const double* coords, double sig
 mvn_status mvn_cholesky(mvn_ctx* ctx, int n, double* A, int64_t ld, int tile, mvn_prec prec,
                         int* info);
 
+/* Cholesky factorisation with the univariate variable reordering (Gibson, Glasbey and Elston
+ * 1994; Genz and Bretz 2009, Sec. 4.1.3).  Not in the paper: a variance-reducing variant of the
+ * SOV estimator of Eq. 2 that changes the order of integration, not the probability.  Step i
+ * places next the remaining variable with the smallest conditional interval probability
+ * Phi(b'_j) - Phi(a'_j), a'_j = (a_j - s_j)/sqrt(d_j), b'_j = (b_j - s_j)/sqrt(d_j), where d_j is
+ * its conditional variance given the variables placed so far and s_j = sum_k L_jk y_k with y_k
+ * the truncated-normal means E[Z | a'_k < Z < b'_k] of those variables (an interval probability
+ * that underflows takes the finite limit as y); ties go to the variable earliest in the current
+ * order.
+ *   A      : on entry Sigma (n x n, column-major, ld; lower triangle read); on exit the lower
+ *            factor L of Sigma[perm, perm] (strict upper part untouched).  FP64 throughout.
+ *   a, b   : device n-vectors of the limits (inputs).
+ *   perm   : device int32[n]; perm[i] = original index of the i-th variable.
+ *   a_perm, b_perm: device n-vectors, a[perm] and b[perm] (inputs of mvn_sov with this L).
+ *   info   : as in mvn_cholesky (the 1-based step at which no remaining conditional variance is
+ *            positive).
+ * Workspace: ~2 n doubles.  Asynchronous unless info is given. */
+mvn_status mvn_cholesky_reorder(mvn_ctx* ctx, int n, double* A, int64_t ld, const double* a,
+                                const double* b, int32_t* perm, double* a_perm, double* b_perm,
+                                int* info);
+
 /* Reverse mode of mvn_cholesky (blocked form of the column algorithm's adjoint; Murray 2016).
  * L: the factor (lower, ld).  Lbar: on entry dF/dL (lower triangle, ld); on exit dF/dA for the
  * lower-triangle entries A_ij (i >= j) read by the factorisation (strict upper part untouched). */

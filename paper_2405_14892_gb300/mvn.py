@@ -60,6 +60,7 @@ SIGNATURES = {
     "mvn_matern_grad": (_I, [_P, _I, _P, _D, _D, _D, _P, _I64, _P]),
     "mvn_cholesky": (_I, [_P, _I, _P, _I64, _I, _I, ctypes.POINTER(_I)]),
     "mvn_cholesky_grad": (_I, [_P, _I, _P, _I64, _P]),
+    "mvn_cholesky_reorder": (_I, [_P, _I, _P, _I64, _P, _P, _P, _P, _P, ctypes.POINTER(_I)]),
     "mvn_sov": (_I, [_P, _I, _P, _P, _P, _I64, _QP, _I, _P, _P]),
     "mvn_sov_grad": (_I, [_P, _I, _P, _P, _P, _I64, _QP, _I, _P, _P, _P, _P]),
     "mvn_grad_set_ylimit": (_I, [_P, _I64]),
@@ -246,6 +247,27 @@ def mvn_cholesky(A: torch.Tensor, prec: str = "fp64", tile: int = 0, check: bool
     st = lib().mvn_cholesky(c.h, n, P, ld, tile, PREC[prec], ctypes.byref(info) if check else None)
     c.check(st)
     return info.value
+
+
+def mvn_cholesky_reorder(A: torch.Tensor, a: torch.Tensor, b: torch.Tensor,
+                         check: bool = True):
+    """In-place factor of A[perm, perm] with the univariate variable reordering.  Returns
+    (perm int32 tensor, a[perm], b[perm], info); with check=False the call does not wait and info
+    is 0 (a failure then surfaces at the next sync)."""
+    n = A.shape[0]
+    Ap, ld = _mat(A, n, "A")
+    perm = torch.empty(n, dtype=torch.int32, device=A.device)
+    a2 = torch.empty(n, dtype=torch.float64, device=A.device)
+    b2 = torch.empty(n, dtype=torch.float64, device=A.device)
+    info = _I(0)
+    c = context()
+    st = lib().mvn_cholesky_reorder(c.h, n, Ap, ld, _vec(a, n, "a"), _vec(b, n, "b"),
+                                    _vec(perm, n, "perm", dtype=torch.int32), _vec(a2, n, "a_perm"),
+                                    _vec(b2, n, "b_perm"), ctypes.byref(info) if check else None)
+    if st == MVN_ERR_NOT_PD:
+        raise MVNError(st, f"not positive definite at step {info.value}")
+    c.check(st)
+    return perm, a2, b2, info.value
 
 
 def mvn_cholesky_grad(L: torch.Tensor, Lbar: torch.Tensor) -> torch.Tensor:

@@ -1,0 +1,162 @@
+"""The reordered Cholesky (univariate variable reordering, mvn_cholesky_reorder) on the GPU
+against the CPU oracle, through the C ABI: the order bit-exact and the factor within FP64
+rounding where the criteria are well separated (random sites and limits), the greedy rule and
+the factorisation checked as properties where they are not (grid symmetries make exact ties, and
+rounding may break them either way), the estimate of the reordered problem against the oracle's,
+and the W2 problem at full size."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_14892_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mvn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_14892_gb300 import mvn as m
+    return m
+
+
+def _t(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def _crit(ap, bp):
+    from scipy.special import ndtr
+    return np.where(ap > 0, ndtr(-ap) - ndtr(-bp), ndtr(bp) - ndtr(ap))
+
+
+def _greedy_ok(L, a, b, steps, rtol=1e-9):
+    """Greedy rule at the given steps, from the factor itself: the first i columns of rows >= i
+    are the factor rows of the remaining variables given the first i, so d_j and s_j follow from
+    them; the placed variable's criterion is the smallest (to rounding)."""
+    n = L.shape[0]
+    diag = np.einsum("ij,ij->i", L, L)      # Sigma_perm diagonal = sum_k L_jk^2 (k <= j)
+    y = np.zeros(n)
+    last = max(steps)
+    for i in range(last + 1):
+        s_i = L[i, :i] @ y[:i]
+        ap, bp = (a[i] - s_i) / L[i, i], (b[i] - s_i) / L[i, i]
+        if i in steps:
+            R = L[i:, :i]
+            d = diag[i:] - np.einsum("ij,ij->i", R, R)
+            s = R @ y[:i]
+            c = _crit((a[i:] - s) / np.sqrt(d), (b[i:] - s) / np.sqrt(d))
+            assert c[0] <= c.min() * (1 + rtol) + 1e-300, (i, c[0], c.min())
+        phi = lambda x: 0.0 if np.isinf(x) else math.exp(-0.5 * x * x) / math.sqrt(2 * math.pi)
+        den = _crit(np.array(ap), np.array(bp))
+        y[i] = (phi(ap) - phi(bp)) / den if den > 0 else (ap if ap > 0 else bp)
+
+
+@pytest.mark.parametrize("n", [1, 5, 64, 65, 130, 300])
+def test_reorder_vs_oracle(mvn, n):
+    c = inputs.random_coords(n, 60 + n)
+    S = oracle.matern(c, 1.0, 0.2, 1.5, nugget=1e-4)
+    rng = np.random.default_rng(n)
+    a = rng.uniform(-2.0, 0.5, n)
+    b = a + rng.uniform(0.3, 3.0, n)
+    a[::3] = -np.inf
+    b[1::5] = np.inf
+    A = mvn.to_colmajor(_t(S))
+    perm, ap, bp, info = mvn.mvn_cholesky_reorder(A, _t(a), _t(b))
+    assert info == 0
+    Lo, po, apo, bpo, info_o = oracle.cholesky_reorder(S, a, b)
+    assert info_o == 0
+    assert np.array_equal(perm.cpu().numpy(), po)
+    assert np.array_equal(ap.cpu().numpy(), apo) and np.array_equal(bp.cpu().numpy(), bpo)
+    L = np.tril(A.cpu().numpy())
+    assert np.abs(L - Lo).max() <= 1e-12, np.abs(L - Lo).max()
+    # the SOV estimate of the reordered problem, per path, against the oracle's
+    lw = torch.empty(400, dtype=torch.float64, device="cuda")
+    out = mvn.mvn_sov(ap, bp, A, 100, 4, 7, path_logw=lw).cpu().numpy()
+    mvn.sync()
+    ref = oracle.sov_logw(apo, bpo, Lo, oracle.QMC(100, 4, 7))
+    got = lw.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 1e-9 * np.maximum(1.0, np.abs(ref)))
+    est = oracle.estimate(ref, 4)
+    assert abs(out[0] - est[0]) <= 1e-9
+
+
+def test_reorder_on_a_grid_with_ties(mvn):
+    """A regular grid with equal limits: the first step is a 144-way tie (taken by index on both
+    sides) and later steps meet the grid's symmetries.  The order is checked for what is unique:
+    a permutation, the greedy rule at every step, and the factor of the permuted covariance."""
+    g = 12
+    n = g * g
+    S = oracle.matern(inputs.grid_coords(g), 1.0, 0.1, 1.5, nugget=1e-4)
+    a = np.full(n, -np.inf)
+    b = np.full(n, 0.5)
+    A = mvn.to_colmajor(_t(S))
+    perm, ap, bp, info = mvn.mvn_cholesky_reorder(A, _t(a), _t(b))
+    p = perm.cpu().numpy()
+    assert info == 0 and sorted(p.tolist()) == list(range(n)) and p[0] == 0
+    L = np.tril(A.cpu().numpy())
+    Sp = S[np.ix_(p, p)]
+    assert np.linalg.norm(L @ L.T - Sp) / np.linalg.norm(Sp) < 1e-14
+    _greedy_ok(L, ap.cpu().numpy(), bp.cpu().numpy(), set(range(n)))
+
+
+def test_reorder_not_pd(mvn):
+    S = oracle.matern(inputs.random_coords(50, 61), 1.0, 0.2, 0.5)
+    S[20, 20] = -1.0
+    a, b = np.full(50, -np.inf), np.full(50, 1.0)
+    _, _, _, _, info_o = oracle.cholesky_reorder(S, a, b)
+    with pytest.raises(mvn.MVNError) as e:
+        mvn.mvn_cholesky_reorder(mvn.to_colmajor(_t(S)), _t(a), _t(b))
+    assert e.value.status == mvn.MVN_ERR_NOT_PD
+    assert info_o > 0
+    # the context stays usable
+    A = mvn.to_colmajor(_t(np.eye(3) * 4.0))
+    perm, _, _, info = mvn.mvn_cholesky_reorder(A, _t(np.full(3, -1.0)), _t([1.0, 2.0, 3.0]))
+    assert info == 0 and perm.cpu().numpy().tolist() == [0, 1, 2]
+
+
+def test_reorder_w2_full_size(mvn):
+    """W2 (n = 16,384) reordered on the GPU, then the mixed sweep: the factor against the
+    oracle's covariance of the permuted sites (random matrix-vector products), the greedy rule
+    at sampled steps, and the estimate against the unordered one (same probability within the
+    two errors; the error of the reordered estimate far smaller)."""
+    w = dict(inputs.WORKLOADS["W2"])
+    c = inputs.grid_coords(w["g"])
+    n = c.shape[0]
+    a, b = inputs.limits_for(w, n)
+    S = mvn.mvn_matern(_t(c), w["sigma2"], w["range"], w["nu"], w["nugget"])
+    S0 = S.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    perm, ap, bp, info = mvn.mvn_cholesky_reorder(S, _t(a), _t(b))
+    t_re = time.perf_counter() - t0
+    assert info == 0
+    Ns, M = w["Ns"], w["M"]
+    o1 = mvn.mvn_sov(ap, bp, S, Ns, M, w["seed"], prec="mixed").cpu().numpy()
+    assert mvn.mvn_cholesky(S0, prec="mixed") == 0
+    o0 = mvn.mvn_sov(_t(a), _t(b), S0, Ns, M, w["seed"], prec="mixed").cpu().numpy()
+    mvn.sync()
+    del S0
+    p = perm.cpu().numpy()
+    assert sorted(p.tolist()) == list(range(n))
+    So = oracle.matern_closed(c[p], w["sigma2"], w["range"], w["nu"], w["nugget"])
+    Lg = torch.tril(S)
+    rng = np.random.default_rng(2)
+    for _ in range(2):
+        v = rng.standard_normal(n)
+        LLv = (Lg @ (Lg.t() @ _t(v))).cpu().numpy()
+        Sv = So @ v
+        assert np.linalg.norm(LLv - Sv) / np.linalg.norm(Sv) < 1e-13
+    L = Lg.cpu().numpy()
+    del Lg
+    _greedy_ok(L, ap.cpu().numpy(), bp.cpu().numpy(), {0, 1, 2, 50, 1000, 4000})
+    print(f"W2 reordered: {t_re * 1e3:.0f} ms (first call); log P {o1[0]:.6f} err/P "
+          f"{o1[2] / o1[1]:.3e}; unordered log P {o0[0]:.6f} err/P {o0[2] / o0[1]:.3e}")
+    assert abs(o1[1] - o0[1]) <= o1[2] + o0[2]
+    assert o1[2] / o1[1] < 0.5 * (o0[2] / o0[1])

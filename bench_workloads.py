@@ -216,7 +216,8 @@ def run(args):
         Lt = mvn.colmajor_empty(n, n, dev)
         out_t = torch.empty(3, dtype=torch.float64, device=dev)
         out_d = torch.empty(3, dtype=torch.float64, device=dev)
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+        out_x = torch.empty(3, dtype=torch.float64, device=dev)
         mvn.mvn_matern(cd, w["sigma2"], w["range"], w["nu"], w["nugget"], out=S)
         torch.cuda.synchronize()
         ctx.timing(True)
@@ -225,31 +226,39 @@ def run(args):
         e[1].record(stream)
         mvn.mvn_tlr_cholesky(T)
         e[2].record(stream)
+        # the sweep on the compressed factor (low-rank limit updates, FP32 shifts)
+        mvn.mvn_sov_tlr(T, ad, bd, w["Ns"], w["M"], w["seed"], prec="mixed", out3=out_t)
+        e[3].record(stream)
+        # for comparison: the factor expanded to dense and the tensor-core sweep
         Lt.zero_()
         mvn.mvn_tlr_to_dense(T, out=Lt)
-        mvn.mvn_sov(ad, bd, Lt, w["Ns"], w["M"], w["seed"], prec="mixed", out3=out_t)
-        e[3].record(stream)
-        mvn.mvn_cholesky(S, prec="mixed", check=False)
+        mvn.mvn_sov(ad, bd, Lt, w["Ns"], w["M"], w["seed"], prec="mixed", out3=out_x)
         e[4].record(stream)
-        mvn.mvn_sov(ad, bd, S, w["Ns"], w["M"], w["seed"], prec="mixed", out3=out_d)
+        mvn.mvn_cholesky(S, prec="mixed", check=False)
         e[5].record(stream)
+        mvn.mvn_sov(ad, bd, S, w["Ns"], w["M"], w["seed"], prec="mixed", out3=out_d)
+        e[6].record(stream)
         torch.cuda.synchronize()
         mvn.sync()
         kms = {k: round(v[0], 2) for k in ("k_bgemm", "k_chol_inv", "k_jacobi", "k_trsm_block",
                                            "k_syrk", "k_oz_update", "k_oz_potrf", "k_oz_trsm",
-                                           "k_sov_tc")
+                                           "k_sov_tc", "k_sov_tlr_f32")
                for v in [ctx.kernel_time(k)] if v[1]}
         ctx.timing(False)
-        ms = [e[i].elapsed_time(e[i + 1]) for i in range(5)]
+        ms = [e[i].elapsed_time(e[i + 1]) for i in range(6)]
         ranks = T.ranks()
         tlr_ms = ms[0] + ms[1] + ms[2]
-        dense_ms = ms[3] + ms[4]
+        dense_ms = ms[4] + ms[5]
         _line(args, w["name"], "TLR vs dense time-to-P-hat, n=65,536", 1e3 / tlr_ms, "probs/s",
-              tlr_ms, {"dtype": "f64 (TLR) / f64+f32+fp16x2+bf16 digits (dense)",
+              tlr_ms, {"dtype": "f64 (TLR factor) + f32 low-rank sweep / f64+f32+fp16x2+bf16 "
+                                "digits (dense)",
                        "tlr_compress_ms": ms[0], "tlr_cholesky_ms": ms[1],
-                       "tlr_sov_ms": ms[2], "dense_cholesky_ms": ms[3], "dense_sov_ms": ms[4],
+                       "tlr_sov_lowrank_ms": ms[2], "tlr_sov_expanded_ms": ms[3],
+                       "dense_cholesky_ms": ms[4], "dense_sov_ms": ms[5],
                        "tlr_over_dense_speedup": dense_ms / tlr_ms,
-                       "logP_tlr": float(out_t[0]), "logP_dense": float(out_d[0]),
+                       "sov_lowrank_over_dense": ms[5] / ms[2],
+                       "logP_tlr": float(out_t[0]), "logP_tlr_expanded": float(out_x[0]),
+                       "logP_dense": float(out_d[0]),
                        "ranks": {"min": int(ranks.min()), "median": float(np.median(ranks)),
                                  "max": int(ranks.max()), "capped": int(T.capped)},
                        "kernel_ms": kms,

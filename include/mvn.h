@@ -356,6 +356,17 @@ mvn_status mvn_tlr_to_dense(mvn_ctx* ctx, const mvn_tlr* tlr, double* L, int64_t
 /* ranks (host int array of length nt*(nt-1)/2, nt = ceil(n/tile)), tile (i,j), i > j, in
  * column order: (1,0),(2,0),...,(nt-1,0),(2,1),... */
 mvn_status mvn_tlr_ranks(const mvn_tlr* tlr, int* ranks);
+/* The SOV estimate of mvn_sov with the factor in tile low-rank form (after mvn_tlr_cholesky):
+ * the limit shifts of block row r are sum_{c<r} U_rc (V_rc^T y_c) with the compressed off-diagonal
+ * tiles (2 m k multiply-adds per path and tile of rank k instead of m^2), the diagonal tiles dense
+ * (Alg. 2 step (c) on the TLR factor of Sec. III-E; the paper expands the factor instead).
+ * a, b, qmc, out3, path_logw as in mvn_sov; the dimension is the object's n.
+ * prec = MVN_FP64: FP64 shifts and step; MVN_MIXED or MVN_MIXED_SIMT: FP32 shifts and y on the CUDA
+ * cores with the FP32 step of MVN_MIXED_SIMT (FP64 in the deep tails).  Workspace per resident CTA:
+ * (n rounded up to tiles + tile) x 128 words.  Asynchronous; errors as mvn_sov, MVN_ERR_ARG for an
+ * object that is not factored. */
+mvn_status mvn_sov_tlr(mvn_ctx* ctx, const mvn_tlr* tlr, const double* a, const double* b,
+                       const mvn_qmc* qmc, mvn_prec prec, double* out3, double* path_logw);
 mvn_status mvn_tlr_free(mvn_tlr* tlr);
 
 /* ------------------------------------------------------------------ autotuner (launch shapes) */

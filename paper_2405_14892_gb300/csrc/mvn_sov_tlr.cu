@@ -1,0 +1,263 @@
+// mvn_sov_tlr.cu -- the SOV sweep on a tile low-rank Cholesky factor (Sec. III-E; the
+// limit-update step (c) of Alg. 2 with the off-diagonal factor tiles kept low rank).
+//
+// With L_rc = U_rc V_rc^T for the tiles c < r of block row r, the limit shifts of block r are
+//   s_r = sum_{c<r} U_rc (V_rc^T y_c)
+// (2 m k_rc multiply-adds per path and tile instead of m^2), and the diagonal tile L_rr is dense.
+// The paper's sweep expands the factor to a dense matrix first; here the factor stays in its
+// compressed form, so the sweep's work follows the ranks.
+//
+// Design (GB300): one CTA owns a tile of 128 paths (one thread per path), persistent over the
+// path tiles.  Block row r: for every earlier tile c and every chunk of 16 rank components,
+// t = V_rc^T y_c is formed in registers (V staged through shared memory 64 rows at a time, y_c
+// read from the CTA's own y buffer, coalesced over the paths) and s_r += U_rc t is added into a
+// per-CTA shift buffer of m entries per path; then the dense diagonal tile runs in blocks of B
+// dimensions exactly like the CUDA-core sweep (earlier dimensions of the tile as a mat-vec, the
+// block's dimensions one at a time with the elementwise step of Eq. 2).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "mvn_internal.cuh"
+#include "mvn_sov.cuh"
+#include "mvn_sov_simt.cuh"
+#include "mvn_tlr.cuh"
+
+#define LR_K 16   // rank components per chunk
+#define LR_R 64   // rows of U / V staged per step
+
+struct TlrSweep {
+    SovProblem P;            // limits, lattice, log-weights (P.L unused)
+    int m, nt, kmax;
+    const double* D;         // diagonal factor tiles, m x m (ld m)
+    const double* U;         // off-diagonal tiles, m x kmax (ld m) each, tri_index order
+    const double* V;
+    const int* rank;         // per off-diagonal tile
+    int nitems;              // path tiles
+    int* counter;            // work-queue head (zeroed before the launch)
+};
+
+__device__ __forceinline__ int64_t lr_tri(int i, int j, int nt) {
+    return (int64_t)j * nt - (int64_t)j * (j + 1) / 2 + (i - j - 1);
+}
+
+template <int B, typename T>
+struct LrSmem {
+    T Vs[LR_R][LR_K];
+    T Us[LR_R][LR_K];
+    SovSmem<B, T> d;
+};
+
+template <int B, typename T, bool ELEM64>
+__device__ void tlr_tile(const TlrSweep& S, int tile, const uint64_t* __restrict__ alpha,
+                         T* __restrict__ Ycta, T* __restrict__ Scta, LrSmem<B, T>& sm) {
+    const SovProblem& P = S.P;
+    const int t = threadIdx.x;
+    const int n = P.n, m = S.m;
+    const int64_t p = (int64_t)tile * SOV_P + t;
+    const bool valid = p < P.Ntot;
+    const int64_t pg = P.p0 + p;
+    const int64_t q = valid ? pg / P.Ns : 0;
+    const uint64_t j = valid ? (uint64_t)(pg - q * P.Ns) + 1u : 1u;
+    const uint64_t* __restrict__ dq = P.delta + q * P.dstride;
+    LogProd lp;
+    for (int r = 0; r < S.nt; ++r) {
+        const int r0 = r * m;
+        const int mr = min(m, n - r0);
+        for (int v = 0; v < mr; ++v) Scta[(int64_t)v * SOV_P + t] = (T)0;
+        // low-rank part of the shifts: s_r += U_rc (V_rc^T y_c), c < r (tile c is full)
+        for (int c = 0; c < r; ++c) {
+            const int64_t idx = lr_tri(r, c, S.nt);
+            const int k = S.rank[idx];
+            const double* __restrict__ Uc = S.U + idx * (int64_t)m * S.kmax;
+            const double* __restrict__ Vc = S.V + idx * (int64_t)m * S.kmax;
+            const T* __restrict__ yc = Ycta + (int64_t)c * m * SOV_P;
+            for (int k0 = 0; k0 < k; k0 += LR_K) {
+                const int kn = min(LR_K, k - k0);
+                T tt[LR_K];
+#pragma unroll
+                for (int kk = 0; kk < LR_K; ++kk) tt[kk] = (T)0;
+                for (int u0 = 0; u0 < m; u0 += LR_R) {
+                    __syncthreads();
+                    for (int e = t; e < LR_R * LR_K; e += SOV_P) {
+                        const int uu = e % LR_R, kk = e / LR_R;
+                        sm.Vs[uu][kk] = (kk < kn) ? (T)Vc[(u0 + uu) + (int64_t)(k0 + kk) * m] : (T)0;
+                    }
+                    __syncthreads();
+#pragma unroll 4
+                    for (int uu = 0; uu < LR_R; ++uu) {
+                        const T y = yc[(int64_t)(u0 + uu) * SOV_P + t];
+#pragma unroll
+                        for (int kk = 0; kk < LR_K; ++kk) tt[kk] = fma(sm.Vs[uu][kk], y, tt[kk]);
+                    }
+                }
+                for (int v0 = 0; v0 < mr; v0 += LR_R) {
+                    __syncthreads();
+                    for (int e = t; e < LR_R * LR_K; e += SOV_P) {
+                        const int vv = e % LR_R, kk = e / LR_R;
+                        sm.Us[vv][kk] = (kk < kn && v0 + vv < mr)
+                                            ? (T)Uc[(v0 + vv) + (int64_t)(k0 + kk) * m]
+                                            : (T)0;
+                    }
+                    __syncthreads();
+                    const int vn = min(LR_R, mr - v0);
+                    for (int vv = 0; vv < vn; ++vv) {
+                        T acc = Scta[(int64_t)(v0 + vv) * SOV_P + t];
+#pragma unroll
+                        for (int kk = 0; kk < LR_K; ++kk) acc = fma(sm.Us[vv][kk], tt[kk], acc);
+                        Scta[(int64_t)(v0 + vv) * SOV_P + t] = acc;
+                    }
+                }
+            }
+        }
+        // dense diagonal tile r in blocks of B dimensions (as the CUDA-core sweep)
+        const double* __restrict__ Dr = S.D + (int64_t)r * m * m;
+        for (int b0 = 0; b0 < mr; b0 += B) {
+            const int nb = min(B, mr - b0);
+            T acc[B];
+#pragma unroll
+            for (int v = 0; v < B; ++v)
+                acc[v] = (v < nb) ? Scta[(int64_t)(b0 + v) * SOV_P + t] : (T)0;
+            for (int k0 = 0; k0 < b0; k0 += B) {
+                __syncthreads();
+                for (int e = t; e < B * B; e += SOV_P) {
+                    const int v = e % B, kk = e / B;
+                    sm.d.Lk[kk][v] = (v < nb) ? (T)Dr[(b0 + v) + (int64_t)(k0 + kk) * m] : (T)0;
+                }
+                __syncthreads();
+#pragma unroll 4
+                for (int kk = 0; kk < B; ++kk) {
+                    const T yk = Ycta[(int64_t)(r0 + k0 + kk) * SOV_P + t];
+#pragma unroll
+                    for (int v = 0; v < B; ++v) acc[v] = fma(sm.d.Lk[kk][v], yk, acc[v]);
+                }
+            }
+            __syncthreads();
+            for (int e = t; e < B * B; e += SOV_P) {
+                const int v = e % B, u = e / B;
+                sm.d.Ld[v][u] = (v < nb && u <= v) ? (T)Dr[(b0 + v) + (int64_t)(b0 + u) * m] : (T)0;
+            }
+            if (t < B) {
+                const int g = r0 + b0 + t;
+                sm.d.a[t] = (t < nb) ? P.a[g] : 0.0;
+                sm.d.b[t] = (t < nb) ? P.b[g] : 1.0;
+                sm.d.alpha[t] = (t < nb) ? alpha[g] : 0u;
+            }
+            __syncthreads();
+            T y[B];
+#pragma unroll
+            for (int v = 0; v < B; ++v) {
+                if (v < nb) {
+                    T s = acc[v];
+#pragma unroll
+                    for (int u = 0; u < v; ++u) s = fma(sm.d.Ld[v][u], y[u], s);
+                    const double w = lattice_w(j, sm.d.alpha[v], dq[r0 + b0 + v]);
+                    double delta;
+                    if constexpr (ELEM64) {
+                        y[v] = (T)sov_step_f64(sm.d.a[v], sm.d.b[v], (double)s,
+                                               (double)sm.d.Ld[v][v], w, delta);
+                    } else {
+                        y[v] = (T)sov_step_f32(sm.d.a[v], sm.d.b[v], (float)s,
+                                               (float)sm.d.Ld[v][v], w, delta);
+                    }
+                    lp.mul(delta);
+                    if (valid) Ycta[(int64_t)(r0 + b0 + v) * SOV_P + t] = y[v];
+                } else {
+                    y[v] = (T)0;
+                }
+            }
+        }
+    }
+    if (valid && P.logw) P.logw[p] = lp.log_value();
+}
+
+template <int B, typename T, bool ELEM64>
+__global__ void __launch_bounds__(SOV_P) k_sov_tlr(const TlrSweep S,
+                                                   const uint64_t* __restrict__ alpha,
+                                                   T* __restrict__ Yscratch, int64_t ystride,
+                                                   T* __restrict__ Sscratch, int64_t sstride) {
+    __shared__ LrSmem<B, T> sm;
+    __shared__ int s_item;
+    T* Ycta = Yscratch + (int64_t)blockIdx.x * ystride;
+    T* Scta = Sscratch + (int64_t)blockIdx.x * sstride;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(S.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= S.nitems) break;
+        tlr_tile<B, T, ELEM64>(S, it, alpha, Ycta, Scta, sm);
+    }
+}
+
+extern "C" mvn_status mvn_sov_tlr(mvn_ctx* ctx, const mvn_tlr* Lt, const double* a,
+                                  const double* b, const mvn_qmc* qmc, mvn_prec prec,
+                                  double* out3, double* path_logw) {
+    if (!ctx) return MVN_ERR_ARG;
+    if (!Lt || !Lt->factored)
+        return mvn_fail(ctx, MVN_ERR_ARG, "mvn_sov_tlr: needs a factored TLR object");
+    MVN_TRY(check_qmc(ctx, qmc));
+    const int n = Lt->n, m = Lt->m;
+    if (!a || !b || !out3) return mvn_fail(ctx, MVN_ERR_ARG, "mvn_sov_tlr: null pointer");
+    if (prec != MVN_FP64 && prec != MVN_MIXED && prec != MVN_MIXED_SIMT)
+        return mvn_fail(ctx, MVN_ERR_ARG, "unknown precision");
+    MVN_CUDA(ctx, cudaSetDevice(ctx->device));
+    const bool f64 = (prec == MVN_FP64);
+    const size_t elt = f64 ? sizeof(double) : sizeof(float);
+    const int M = qmc->n_shifts;
+    const int64_t Ns = qmc->n_points, Ntot = Ns * M;
+    const int64_t ntiles = (Ntot + SOV_P - 1) / SOV_P;
+    if (ntiles > (1 << 30)) return mvn_fail(ctx, MVN_ERR_ARG, "too many path tiles");
+    MVN_TRY(lattice_ensure(ctx, n));
+    const int occ = tune_sweep(ctx, prec == MVN_MIXED ? MVN_MIXED_SIMT : prec, n, ntiles)
+                        .simt_ctas_per_sm;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)ctx->sm_count * occ));
+    const int64_t ystride = (int64_t)Lt->npad * SOV_P, sstride = (int64_t)m * SOV_P;
+    const size_t need = ws_round(sizeof(uint64_t) * (size_t)M * n) +
+                        (path_logw ? 0 : ws_round(sizeof(double) * (size_t)Ntot)) +
+                        ws_round(elt * (size_t)ystride * grid) +
+                        ws_round(elt * (size_t)sstride * grid) + ws_round(sizeof(int)) + 1024;
+    MVN_TRY(ws_reserve(ctx, need));
+    WsCarver wc(ctx->ws);
+    uint64_t* delta = wc.take<uint64_t>((size_t)M * n);
+    double* logw = path_logw ? path_logw : wc.take<double>((size_t)Ntot);
+    void* Ybuf = wc.take<char>(elt * (size_t)ystride * grid);
+    void* Sbuf = wc.take<char>(elt * (size_t)sstride * grid);
+    int* counter = wc.take<int>(1);
+    TlrSweep S;
+    memset(&S, 0, sizeof(S));
+    SovProblem& P = S.P;
+    P.n = n;
+    P.M = M;
+    P.Ns = Ns;
+    P.Ntot = Ntot;
+    P.p0 = 0;
+    P.a = a;
+    P.b = b;
+    P.delta = delta;
+    P.dstride = n;
+    P.logw = logw;
+    S.m = m;
+    S.nt = Lt->nt;
+    S.kmax = Lt->kmax;
+    S.D = Lt->D;
+    S.U = Lt->U;
+    S.V = Lt->V;
+    S.rank = Lt->rank;
+    S.nitems = (int)ntiles;
+    S.counter = counter;
+    MVN_TRY(check_limits_device(ctx, n, a, b));
+    MVN_TRY(lattice_shifts(ctx, qmc->seed, M, n, delta));
+    MVN_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(int), ctx->stream));
+    if (f64) {
+        MVN_TIMED(ctx, "k_sov_tlr_f64",
+                  (k_sov_tlr<32, double, true><<<grid, SOV_P, 0, ctx->stream>>>(
+                      S, ctx->d_alpha, (double*)Ybuf, ystride, (double*)Sbuf, sstride)));
+    } else {
+        MVN_TIMED(ctx, "k_sov_tlr_f32",
+                  (k_sov_tlr<64, float, false><<<grid, SOV_P, 0, ctx->stream>>>(
+                      S, ctx->d_alpha, (float*)Ybuf, ystride, (float*)Sbuf, sstride)));
+    }
+    return sov_reduce_launch(ctx, logw, Ns, M, qmc->err_k, out3, 1, Ntot);
+}

@@ -83,6 +83,7 @@ SIGNATURES = {
     "mvn_tlr_cholesky": (_I, [_P, _P, ctypes.POINTER(_I)]),
     "mvn_tlr_to_dense": (_I, [_P, _P, _P, _I64]),
     "mvn_tlr_ranks": (_I, [_P, _P]),
+    "mvn_sov_tlr": (_I, [_P, _P, _P, _P, _QP, _I, _P, _P]),
     "mvn_tlr_free": (_I, [_P]),
     "mvn_lattice_alpha": (_I, [_P, _I, _P]),
     "mvn_lattice_shifts": (_I, [_P, _U64, _I, _I, _P]),
@@ -614,6 +615,21 @@ def mvn_tlr_to_dense(T: TLR, out: torch.Tensor | None = None) -> torch.Tensor:
     c = context()
     c.check(lib().mvn_tlr_to_dense(c.h, T.h, Lp, ld))
     return out
+
+
+def mvn_sov_tlr(T: TLR, a: torch.Tensor, b: torch.Tensor, n_points: int, n_shifts: int,
+                seed: int, prec: str = "fp64", err_k: float = 3.0,
+                path_logw: torch.Tensor | None = None, out3: torch.Tensor | None = None):
+    """SOV estimate on a factored TLR object (low-rank limit updates); returns out3."""
+    n = T.n
+    if out3 is None:
+        out3 = torch.empty(3, dtype=torch.float64, device=a.device)
+    q = _qmc(n_points, n_shifts, seed, err_k)
+    c = context()
+    c.check(lib().mvn_sov_tlr(c.h, T.h, _vec(a, n, "a"), _vec(b, n, "b"), ctypes.byref(q),
+                              PREC[prec], _vec(out3, 3, "out3"),
+                              _vec(path_logw, n_points * n_shifts, "path_logw")))
+    return out3
 
 
 def sync():

@@ -93,3 +93,47 @@ def test_tlr_ragged_and_rank_cap(mvn):
     L = np.tril(mvn.mvn_tlr_to_dense(T).cpu().numpy())
     Ld = np.linalg.cholesky(S)
     assert np.abs(L - Ld).max() < 1e-5, np.abs(L - Ld).max()
+
+
+@pytest.mark.parametrize("n,tile,prec", [(1024, 128, "fp64"), (700, 256, "fp64"),
+                                         (1024, 128, "mixed_simt")])
+def test_sov_on_the_tlr_factor(mvn, n, tile, prec):
+    """The sweep on the compressed factor (mvn_sov_tlr: limit shifts U (V^T y) per tile) against
+    the oracle's sweep on the same factor expanded to a dense matrix, per path: FP64 within
+    1e-9 max(1, |logw|) (only the order of the shift sums differs), the FP32 variant within the
+    mixed paths' stated bounds (|d log P| <= 1e-4, per path 1e-6 max(1, |logw|)); ragged last
+    tile (700 = 2 x 256 + 188)."""
+    g = int(np.ceil(np.sqrt(n)))
+    c = inputs.grid_coords(g, order="morton")[:n] if g * g == n else inputs.random_coords(n, 9)
+    S = oracle.matern(c, 1.0, 0.1, 0.5, nugget=1e-4)
+    T = mvn.mvn_tlr_compress(mvn.to_colmajor(_t(S)), tile, 1e-7, tile // 2)
+    assert mvn.mvn_tlr_cholesky(T) == 0
+    L = np.tril(mvn.mvn_tlr_to_dense(T).cpu().numpy())
+    rng = np.random.default_rng(n)
+    a = np.full(n, -np.inf)
+    b = rng.uniform(0.0, 2.0, n)
+    a[::5] = b[::5] - 3.0
+    Ns, M, seed = 150, 4, 21
+    lw = torch.empty(Ns * M, dtype=torch.float64, device="cuda")
+    out = mvn.mvn_sov_tlr(T, _t(a), _t(b), Ns, M, seed, prec=prec, path_logw=lw).cpu().numpy()
+    mvn.sync()
+    ref = oracle.sov_logw(a, b, L, oracle.QMC(Ns, M, seed))
+    got = lw.cpu().numpy()
+    rel = np.abs(got - ref) / np.maximum(1.0, np.abs(ref))
+    est = oracle.estimate(ref, M)
+    print(f"n={n} tile={tile} {prec}: ranks {T.ranks().min()}..{T.ranks().max()}, per-path max "
+          f"rel {rel.max():.3e}, d log P {out[0] - est[0]:.3e}")
+    if prec == "fp64":
+        assert rel.max() <= 1e-9
+        assert abs(out[0] - est[0]) <= 1e-9
+    else:
+        assert rel.max() <= 1e-6
+        assert abs(out[0] - est[0]) <= 1e-4
+
+
+def test_sov_tlr_needs_a_factored_object(mvn):
+    S = _case(g=16)
+    T = mvn.mvn_tlr_compress(mvn.to_colmajor(_t(S)), 64, 1e-6, 32)
+    with pytest.raises(mvn.MVNError) as e:
+        mvn.mvn_sov_tlr(T, _t(np.full(256, -np.inf)), _t(np.ones(256)), 10, 2, 1)
+    assert e.value.status == mvn.MVN_ERR_ARG

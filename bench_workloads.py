@@ -240,7 +240,7 @@ def run(args):
         e[6].record(stream)
         torch.cuda.synchronize()
         mvn.sync()
-        kms = {k: round(v[0], 2) for k in ("k_bgemm", "k_chol_inv", "k_jacobi", "k_trsm_block",
+        kms = {k: round(v[0], 2) for k in ("k_bgemm", "k_chol_inv", "k_jacobi1", "k_trsm_block",
                                            "k_syrk", "k_oz_update", "k_oz_potrf", "k_oz_trsm",
                                            "k_sov_tc", "k_sov_tlr_f32")
                for v in [ctx.kernel_time(k)] if v[1]}

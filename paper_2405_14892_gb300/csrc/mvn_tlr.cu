@@ -5,9 +5,11 @@
 // Tropp 2011, with one power iteration), each step a batched kernel:
 //   Y = A Omega (Omega Gaussian, m x r, r = max_rank + 8 <= m);  Q = orth(Y)
 //   Y = A (A^T Q);  Q = orth(Y)
-//   B = Q^T A (r x m);  C = B B^T = W Lambda W^T (two-sided parallel Jacobi, FP64)
-//   sigma_l = sqrt(lambda_l) sorted descending;  k = #{sigma_l > acc} capped at max_rank
-//   U = Q W_k diag(sigma_k),  V = B^T W_k diag(1/sigma_k)  (so A ~= U V^T).
+//   X = A^T Q (m x r);  X G = V Sigma (one-sided Jacobi SVD, FP64: rotations of column pairs
+//   until the columns are orthogonal; sigma_l = the column norms, resolved relative to
+//   themselves)
+//   sigma_l sorted descending;  k = #{sigma_l > acc} capped at max_rank
+//   U = Q G_k diag(sigma_k),  V = V_k  (so A ~= Q X^T = U V^T).
 // orth(Y) is shifted Cholesky QR applied three times (Gram matrix + small shift, Cholesky,
 // triangular inverse, Y R^-1): stable for rank-deficient sketches, whose surplus directions only
 // add rows of negligible norm to B.
@@ -215,126 +217,112 @@ __device__ double block_sum256(double v, double* red) {
     return s;
 }
 
-#define JAC_SMEM_R 80  // C and W in shared memory up to r = 80 (100 KB)
-
-// Two-sided parallel Jacobi (round-robin pairs) on a symmetric r x r matrix C (ld r) per item;
-// W (r x r) receives the eigenvectors (columns), lam the eigenvalues (diagonal of the converged
-// C), order the column indices sorted by descending eigenvalue.  With in_smem, C and W live in
-// shared memory while the rotations run (r <= JAC_SMEM_R; the same arithmetic), and W is
-// written back at the end; C is then left as it came in.
-__global__ void __launch_bounds__(256) k_jacobi(int r, double* const* __restrict__ Cs,
-                                                double* const* __restrict__ Ws,
-                                                double* const* __restrict__ lams,
-                                                int* const* __restrict__ orders, int max_sweeps,
-                                                int in_smem) {
-    extern __shared__ double jsm[];  // cs[np], sn[np], pp[np], qq[np] (ints), [C, W (r x r)]
-    __shared__ double red[256];
-    double* C = Cs[blockIdx.x];
-    double* const Wg = Ws[blockIdx.x];
-    double* W = Wg;
+// One-sided (Hestenes) Jacobi SVD of X = A^T Q (m x r, ld m) per item, in place: plane rotations
+// of column pairs make the columns mutually orthogonal, X <- X G with G (r x r) accumulated in W.
+// Then X = V Sigma with sigma_j = ||X_j||, and A ~= Q X^T = (Q G) Sigma V^T.  Unlike an eigen-
+// decomposition of B B^T it never forms a Gram matrix, so each singular value is resolved
+// relative to itself (Demmel and Veselic 1992), not to sigma_1^2: the truncation at sigma ~ acc
+// is decided on accurate values.  Pairs follow the round-robin (circle) order, each round's
+// r/2 disjoint pairs spread over the block's warps (one warp per pair: three dot products over
+// the m rows, then the rotation of the two columns of X and of W).  lam[j] = sigma_j^2 and
+// order = the columns by descending sigma.  Rutishauser's rotation:
+//   zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+//   c = 1 / sqrt(1 + t^2), s = c t;  X_i <- c X_i - s X_j,  X_j <- s X_i + c X_j.
+__global__ void __launch_bounds__(256) k_jacobi1(int m, int r, double* const* __restrict__ Xs,
+                                                 double* const* __restrict__ Ws,
+                                                 double* const* __restrict__ lams,
+                                                 int* const* __restrict__ orders,
+                                                 int max_sweeps) {
+    __shared__ int s_rot;
+    double* X = Xs[blockIdx.x];
+    double* W = Ws[blockIdx.x];
     double* lam = lams[blockIdx.x];
     int* order = orders[blockIdx.x];
-    const int t = threadIdx.x;
-    const int rp = (r + 1) & ~1;  // even slot count (slot r is a dummy when r is odd)
-    const int np = rp / 2;
-    double* cs = jsm;
-    double* sn = jsm + np;
-    int* pp = (int*)(jsm + 2 * np);
-    int* qq = pp + np;
-    if (in_smem) {
-        double* Cs_ = jsm + 3 * np;  // after cs, sn and the two int arrays (np doubles)
-        for (int e = t; e < r * r; e += 256) Cs_[e] = C[e];
-        C = Cs_;
-        W = Cs_ + r * r;
-    }
-    for (int e = t; e < r * r; e += 256) W[e] = ((e % r) == (e / r)) ? 1.0 : 0.0;
-    __syncthreads();
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+    for (int e = t; e < r * r; e += blockDim.x) W[e] = ((e % r) == (e / r)) ? 1.0 : 0.0;
+    const int rp = (r + 1) & ~1;  // even player count (player r is a dummy when r is odd)
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        double lo = 0.0, ldg = 0.0;
-        for (int e = t; e < r * r; e += 256) {
-            const double v = C[e];
-            if ((e % r) == (e / r)) ldg += v * v;
-            else lo += v * v;
-        }
-        const double offn = block_sum256(lo, red);
-        const double diagn = block_sum256(ldg, red);
-        if (offn <= 1e-30 * diagn) break;
+        if (t == 0) s_rot = 0;
+        __syncthreads();
         for (int round = 0; round < rp - 1; ++round) {
-            for (int k = t; k < np; k += 256) {
-                int a = (k == 0) ? 0 : 1 + (k - 1 + round) % (rp - 1);
-                int b = 1 + (rp - 2 - k + round) % (rp - 1);
-                if (a > b) {
-                    const int x = a;
-                    a = b;
-                    b = x;
+            for (int pi = warp; pi < rp / 2; pi += nw) {
+                int i, j;
+                if (pi == 0) {
+                    i = round;
+                    j = rp - 1;
+                } else {
+                    i = (round + pi) % (rp - 1);
+                    j = (round - pi + (rp - 1)) % (rp - 1);
                 }
-                pp[k] = a;
-                qq[k] = b;
-                double c = 1.0, s = 0.0;
-                if (b < r) {
-                    const double app = C[a + (int64_t)a * r], aqq = C[b + (int64_t)b * r];
-                    const double apq = C[a + (int64_t)b * r];
-                    if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
-                        const double tau = (aqq - app) / (2.0 * apq);
-                        const double tt =
-                            (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + tt * tt);
-                        s = tt * c;
-                    }
+                if (i > j) {
+                    const int x = i;
+                    i = j;
+                    j = x;
                 }
-                cs[k] = c;
-                sn[k] = s;
-            }
-            __syncthreads();
-            for (int e = t; e < np * r; e += 256) {  // rows: C <- J^T C
-                const int k = e % np, j = e / np;
-                const int a = pp[k], b = qq[k];
-                if (b >= r || sn[k] == 0.0) continue;
-                const double x = C[a + (int64_t)j * r], y = C[b + (int64_t)j * r];
-                C[a + (int64_t)j * r] = cs[k] * x - sn[k] * y;
-                C[b + (int64_t)j * r] = sn[k] * x + cs[k] * y;
-            }
-            __syncthreads();
-            for (int e = t; e < np * r; e += 256) {  // columns: C <- C J, W <- W J
-                const int k = e % np, i = e / np;
-                const int a = pp[k], b = qq[k];
-                if (b >= r || sn[k] == 0.0) continue;
-                double x = C[i + (int64_t)a * r], y = C[i + (int64_t)b * r];
-                C[i + (int64_t)a * r] = cs[k] * x - sn[k] * y;
-                C[i + (int64_t)b * r] = sn[k] * x + cs[k] * y;
-                x = W[i + (int64_t)a * r];
-                y = W[i + (int64_t)b * r];
-                W[i + (int64_t)a * r] = cs[k] * x - sn[k] * y;
-                W[i + (int64_t)b * r] = sn[k] * x + cs[k] * y;
+                if (j >= r) continue;  // the dummy player
+                double* xi = X + (int64_t)i * m;
+                double* xj = X + (int64_t)j * m;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int u = lane; u < m; u += 32) {
+                    const double a = xi[u], b = xj[u];
+                    al = fma(a, a, al);
+                    be = fma(b, b, be);
+                    ga = fma(a, b, ga);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                    be += __shfl_xor_sync(0xffffffffu, be, o);
+                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                }
+                if (!(fabs(ga) > 2.2e-16 * sqrt(al * be)) || ga == 0.0) continue;
+                const double zeta = (be - al) / (2.0 * ga);
+                const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
+                for (int u = lane; u < m; u += 32) {
+                    const double a = xi[u], b = xj[u];
+                    xi[u] = c * a - sn * b;
+                    xj[u] = sn * a + c * b;
+                }
+                double* wi = W + (int64_t)i * r;
+                double* wj = W + (int64_t)j * r;
+                for (int u = lane; u < r; u += 32) {
+                    const double a = wi[u], b = wj[u];
+                    wi[u] = c * a - sn * b;
+                    wj[u] = sn * a + c * b;
+                }
+                if (lane == 0) s_rot = 1;
             }
             __syncthreads();
         }
+        if (!s_rot) break;
+        __syncthreads();
     }
-    for (int i = t; i < r; i += 256) {
-        lam[i] = C[i + (int64_t)i * r];
-        order[i] = i;
+    // sigma_j^2 = ||X_j||^2, then the order by descending value (stable)
+    for (int jj = warp; jj < r; jj += nw) {
+        const double* xj = X + (int64_t)jj * m;
+        double a = 0.0;
+        for (int u = lane; u < m; u += 32) a = fma(xj[u], xj[u], a);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) lam[jj] = a;
     }
-    if (in_smem)
-        for (int e = t; e < r * r; e += 256) Wg[e] = W[e];
     __syncthreads();
-    if (t == 0) {  // selection sort of the order by descending eigenvalue (r is small)
-        for (int i = 0; i < r; ++i) {
-            int best = i;
-            for (int j2 = i + 1; j2 < r; ++j2)
-                if (lam[order[j2]] > lam[order[best]]) best = j2;
-            const int x = order[i];
-            order[i] = order[best];
-            order[best] = x;
-        }
+    for (int jj = t; jj < r; jj += blockDim.x) {
+        int rankpos = 0;
+        for (int k = 0; k < r; ++k)
+            rankpos += (lam[k] > lam[jj]) || (lam[k] == lam[jj] && k < jj);
+        order[rankpos] = jj;
     }
 }
 
-// Per item: rank k = #{sqrt(lambda) > acc} (capped at kmax); WU(:, j) = W(:, order_j) sigma_j and
-// WV(:, j) = W(:, order_j) / sigma_j for j < k, zero columns for j >= k (r x kmax, ld r).
-__global__ void k_select(int r, int kmax, double acc, double* const* __restrict__ Ws,
-                         double* const* __restrict__ lams, int* const* __restrict__ orders,
-                         double* const* __restrict__ WUs, double* const* __restrict__ WVs,
-                         int* __restrict__ rank_out, int* __restrict__ capped) {
+// After k_jacobi1: WU(:, q) = G(:, order_q) sigma_q and WV(order_q, q) = 1 / sigma_q (a selection
+// matrix, r x kmax, ld r) for q < k, zero columns for q >= k, k = #{sigma > acc} capped at kmax;
+// then U = Q WU and V = X WV = the rotated columns scaled to unit norm.
+__global__ void k_select1(int r, int kmax, double acc, double* const* __restrict__ Ws,
+                          double* const* __restrict__ lams, int* const* __restrict__ orders,
+                          double* const* __restrict__ WUs, double* const* __restrict__ WVs,
+                          int* __restrict__ rank_out, int* __restrict__ capped) {
     const double* W = Ws[blockIdx.x];
     const double* lam = lams[blockIdx.x];
     const int* order = orders[blockIdx.x];
@@ -354,13 +342,12 @@ __global__ void k_select(int r, int kmax, double acc, double* const* __restrict_
     __syncthreads();
     const int k = ks;
     for (int e = threadIdx.x; e < r * kmax; e += blockDim.x) {
-        const int i = e % r, j = e / r;
+        const int i = e % r, q = e / r;
         double u = 0.0, v = 0.0;
-        if (j < k) {
-            const double sg = sqrt(lam[order[j]]);
-            const double w = W[i + (int64_t)order[j] * r];
-            u = w * sg;
-            v = w / sg;
+        if (q < k) {
+            const double sg = sqrt(lam[order[q]]);
+            u = W[i + (int64_t)order[q] * r] * sg;
+            v = (i == order[q]) ? 1.0 / sg : 0.0;
         }
         WU[e] = u;
         WV[e] = v;
@@ -413,7 +400,7 @@ struct CompWs {
     int m, r, kmax, T;
     double *Om, *Y, *Q, *Z, *B, *G, *R, *W, *WU, *WV, *lam;
     int *order, *rank, *capped, *rk;
-    double **pG, **pR, **pW, **pWU, **pWV, **plam;
+    double **pG, **pR, **pW, **pWU, **pWV, **plam, **pB;
     int** porder;
     GItem* items;
 };
@@ -423,7 +410,7 @@ static size_t comp_ws_bytes(int m, int r, int kmax, int T) {
     return ws_round(sizeof(double) * mr) + 4 * ws_round(sizeof(double) * mr * T) +
            3 * ws_round(sizeof(double) * rr * T) + 2 * ws_round(sizeof(double) * (size_t)r * kmax * T) +
            ws_round(sizeof(double) * (size_t)r * T) + 2 * ws_round(sizeof(int) * (size_t)r * T) +
-           ws_round(sizeof(int) * (size_t)T) + ws_round(sizeof(int)) + 7 * ws_round(sizeof(void*) * T) +
+           ws_round(sizeof(int) * (size_t)T) + ws_round(sizeof(int)) + 8 * ws_round(sizeof(void*) * T) +
            ws_round(sizeof(GItem) * (size_t)T * 4) + 8 * 256;
 }
 
@@ -456,6 +443,7 @@ static CompWs comp_ws_carve(WsCarver& wc, int m, int r, int kmax, int T) {
     c.pWV = wc.take<double*>(T);
     c.plam = wc.take<double*>(T);
     c.porder = wc.take<int*>(T);
+    c.pB = wc.take<double*>(T);
     c.items = wc.take<GItem>((size_t)T * 4);
     return c;
 }
@@ -493,7 +481,7 @@ static mvn_status comp_run(mvn_ctx* ctx, CompWs& c, int T, const std::vector<con
     const int m = c.m, kmax = c.kmax;
     const size_t mr = (size_t)m * r, rr = (size_t)r * r;
     {
-        std::vector<double*> pG(T), pR(T), pW(T), pWU(T), pWV(T), plam(T);
+        std::vector<double*> pG(T), pR(T), pW(T), pWU(T), pWV(T), plam(T), pB(T);
         std::vector<int*> pord(T);
         for (int t = 0; t < T; ++t) {
             pG[t] = c.G + t * rr;
@@ -503,7 +491,9 @@ static mvn_status comp_run(mvn_ctx* ctx, CompWs& c, int T, const std::vector<con
             pWV[t] = c.WV + (size_t)t * r * kmax;
             plam[t] = c.lam + (size_t)t * r;
             pord[t] = c.order + (size_t)t * r;
+            pB[t] = c.B + t * mr;
         }
+        MVN_CUDA(ctx, cudaMemcpyAsync(c.pB, pB.data(), sizeof(void*) * T, cudaMemcpyHostToDevice, ctx->stream));
         MVN_CUDA(ctx, cudaMemcpyAsync(c.pG, pG.data(), sizeof(void*) * T, cudaMemcpyHostToDevice, ctx->stream));
         MVN_CUDA(ctx, cudaMemcpyAsync(c.pR, pR.data(), sizeof(void*) * T, cudaMemcpyHostToDevice, ctx->stream));
         MVN_CUDA(ctx, cudaMemcpyAsync(c.pW, pW.data(), sizeof(void*) * T, cudaMemcpyHostToDevice, ctx->stream));
@@ -528,31 +518,22 @@ static mvn_status comp_run(mvn_ctx* ctx, CompWs& c, int T, const std::vector<con
     for (int t = 0; t < T; ++t) it.push_back(gi(A[t], 1, m, c.Q + t * mr, 1, m, c.Y + t * mr, m, m, r, m, 1.0, 0.0));
     MVN_TRY(bgemm(ctx, it, c.items));
     MVN_TRY(comp_orth(ctx, c, T, c.Y, c.Q, r));
-    // B = Q^T A (r x m, ld r);  C = B B^T
+    // X = A^T Q (m x r, ld m), the transpose of B = Q^T A; its one-sided Jacobi SVD gives
+    // A ~= (Q G) Sigma V^T with V the rotated, normalised columns of X
     it.clear();
-    for (int t = 0; t < T; ++t) it.push_back(gi(c.Q + t * mr, m, 1, A[t], 1, m, c.B + t * mr, r, r, m, m, 1.0, 0.0));
+    for (int t = 0; t < T; ++t) it.push_back(gi(A[t], m, 1, c.Q + t * mr, 1, m, c.B + t * mr, m, m, r, m, 1.0, 0.0));
     MVN_TRY(bgemm(ctx, it, c.items));
-    it.clear();
-    for (int t = 0; t < T; ++t) it.push_back(gi(c.B + t * mr, 1, r, c.B + t * mr, r, 1, c.G + t * rr, r, r, r, m, 1.0, 0.0));
-    MVN_TRY(bgemm(ctx, it, c.items));
-    const int np = ((r + 1) & ~1) / 2;
-    const int in_smem = (r <= JAC_SMEM_R) ? 1 : 0;
-    const size_t jsmem = sizeof(double) * 3 * np + (in_smem ? sizeof(double) * 2 * r * r : 0);
-    if (in_smem)
-        MVN_CUDA(ctx, cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)jsmem));
-    MVN_TIMED(ctx, "k_jacobi",
-              (k_jacobi<<<T, 256, jsmem, ctx->stream>>>(r, c.pG, c.pW, c.plam, c.porder, 40,
-                                                        in_smem)));
-    k_select<<<T, 256, 0, ctx->stream>>>(r, kmax, acc, c.pW, c.plam, c.porder, c.pWU, c.pWV,
-                                         rank_out, c.capped);
+    MVN_TIMED(ctx, "k_jacobi1",
+              (k_jacobi1<<<T, 256, 0, ctx->stream>>>(m, r, c.pB, c.pW, c.plam, c.porder, 40)));
+    k_select1<<<T, 256, 0, ctx->stream>>>(r, kmax, acc, c.pW, c.plam, c.porder, c.pWU, c.pWV,
+                                          rank_out, c.capped);
     MVN_LAUNCHED(ctx);
-    // U = Q WU (m x kmax);  V = B^T WV (m x kmax)
+    // U = Q WU (m x kmax);  V = X WV (m x kmax)
     it.clear();
     for (int t = 0; t < T; ++t) it.push_back(gi(c.Q + t * mr, 1, m, c.WU + (size_t)t * r * kmax, 1, r, U[t], m, m, kmax, r, 1.0, 0.0));
     MVN_TRY(bgemm(ctx, it, c.items));
     it.clear();
-    for (int t = 0; t < T; ++t) it.push_back(gi(c.B + t * mr, r, 1, c.WV + (size_t)t * r * kmax, 1, r, V[t], m, m, kmax, r, 1.0, 0.0));
+    for (int t = 0; t < T; ++t) it.push_back(gi(c.B + t * mr, 1, m, c.WV + (size_t)t * r * kmax, 1, r, V[t], m, m, kmax, r, 1.0, 0.0));
     MVN_TRY(bgemm(ctx, it, c.items));
     return MVN_OK;
 }

@@ -38,20 +38,26 @@ def test_tlr_compress_vs_oracle(mvn, tile, acc, kmax):
     ref = oracle.tlr_compress(S, tile, acc, kmax)
     L = mvn.mvn_tlr_to_dense(T).cpu().numpy()
     nt = n // tile
-    # ranks: equal except where a singular value sits within 5% of the threshold
+    # ranks: equal except where a singular value sits within 1% of the threshold (the singular
+    # values come from a one-sided Jacobi SVD of the sketched tile, each to ~1e-12 relative; the
+    # sketch itself can lose a little of the values near the truncation)
+    nmiss = 0
     for t, (i, j) in enumerate((i, j) for j in range(nt) for i in range(j + 1, nt)):
         A = S[i * tile:(i + 1) * tile, j * tile:(j + 1) * tile]
         s = np.linalg.svd(A, compute_uv=False)
         k_ref = ref["ranks"][t]
         if ranks[t] != k_ref:
+            nmiss += 1
             lo, hi = sorted((ranks[t], k_ref))
-            assert np.all(np.abs(s[lo:hi] / acc - 1.0) < 0.05), (i, j, ranks[t], k_ref, s[lo:hi + 1])
+            dev = np.abs(s[lo:hi] / acc - 1.0)
+            print(f"tile ({i},{j}): rank {ranks[t]} vs {k_ref}, sigma/acc - 1 = {dev}")
+            assert np.all(dev < 0.01), (i, j, ranks[t], k_ref, s[lo:hi + 1])
         err = np.linalg.norm(A - L[i * tile:(i + 1) * tile, j * tile:(j + 1) * tile], 2)
         # Eckart-Young bound of the exact truncation plus the randomised range finder's slack
         assert err <= 2.0 * max(acc, s[min(kmax, len(s) - 1)] if ranks[t] == kmax else acc), (i, j, err)
     assert np.allclose(np.tril(L[:tile, :tile]), np.tril(S[:tile, :tile]))
     print(f"tile {tile}: ranks gpu {ranks.min()}..{ranks.max()} oracle "
-          f"{ref['ranks'].min()}..{ref['ranks'].max()}, capped {T.capped}")
+          f"{ref['ranks'].min()}..{ref['ranks'].max()}, capped {T.capped}, {nmiss} ranks differ")
 
 
 def test_tlr_cholesky_vs_oracle_and_dense(mvn):

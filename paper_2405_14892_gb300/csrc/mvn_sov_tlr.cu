@@ -8,10 +8,11 @@
 // compressed form, so the sweep's work follows the ranks.
 //
 // Design (GB300): one CTA owns a tile of 128 paths (one thread per path), persistent over the
-// path tiles.  Block row r: for every earlier tile c and every chunk of 16 rank components,
+// path tiles.  Block row r: for every earlier tile c and every chunk of 8 rank components,
 // t = V_rc^T y_c is formed in registers (V staged through shared memory 64 rows at a time, y_c
-// read from the CTA's own y buffer, coalesced over the paths) and s_r += U_rc t is added into a
-// per-CTA shift buffer of m entries per path; then the dense diagonal tile runs in blocks of B
+// read from the CTA's own y buffer, coalesced over the paths) and kept in a per-CTA buffer; then
+// 64 rows of block r at a time sum U_rc t over every c and component in registers and write
+// their shifts once; then the dense diagonal tile runs in blocks of B
 // dimensions exactly like the CUDA-core sweep (earlier dimensions of the tile as a mat-vec, the
 // block's dimensions one at a time with the elementwise step of Eq. 2).
 #include <math.h>
@@ -24,7 +25,7 @@
 #include "mvn_sov_simt.cuh"
 #include "mvn_tlr.cuh"
 
-#define LR_K 16   // rank components per chunk
+#define LR_K 8    // rank components per chunk
 #define LR_R 64   // rows of U / V staged per step
 
 struct TlrSweep {
@@ -51,7 +52,8 @@ struct LrSmem {
 
 template <int B, typename T, bool ELEM64>
 __device__ void tlr_tile(const TlrSweep& S, int tile, const uint64_t* __restrict__ alpha,
-                         T* __restrict__ Ycta, T* __restrict__ Scta, LrSmem<B, T>& sm) {
+                         T* __restrict__ Ycta, T* __restrict__ Scta, T* __restrict__ Tcta,
+                         LrSmem<B, T>& sm) {
     const SovProblem& P = S.P;
     const int t = threadIdx.x;
     const int n = P.n, m = S.m;
@@ -65,12 +67,14 @@ __device__ void tlr_tile(const TlrSweep& S, int tile, const uint64_t* __restrict
     for (int r = 0; r < S.nt; ++r) {
         const int r0 = r * m;
         const int mr = min(m, n - r0);
-        for (int v = 0; v < mr; ++v) Scta[(int64_t)v * SOV_P + t] = (T)0;
-        // low-rank part of the shifts: s_r += U_rc (V_rc^T y_c), c < r (tile c is full)
+        // low-rank part of the shifts, s_r = sum_{c<r} U_rc (V_rc^T y_c) (tile c is full):
+        // (A) t_c = V_rc^T y_c for every c into the CTA's buffer Tcta (one entry per rank
+        // component and path), (B) for 64 rows of block r at a time, the sum over c and the rank
+        // components in registers, written once to Scta.
+        int toff = 0;
         for (int c = 0; c < r; ++c) {
             const int64_t idx = lr_tri(r, c, S.nt);
             const int k = S.rank[idx];
-            const double* __restrict__ Uc = S.U + idx * (int64_t)m * S.kmax;
             const double* __restrict__ Vc = S.V + idx * (int64_t)m * S.kmax;
             const T* __restrict__ yc = Ycta + (int64_t)c * m * SOV_P;
             for (int k0 = 0; k0 < k; k0 += LR_K) {
@@ -92,24 +96,47 @@ __device__ void tlr_tile(const TlrSweep& S, int tile, const uint64_t* __restrict
                         for (int kk = 0; kk < LR_K; ++kk) tt[kk] = fma(sm.Vs[uu][kk], y, tt[kk]);
                     }
                 }
-                for (int v0 = 0; v0 < mr; v0 += LR_R) {
+#pragma unroll
+                for (int kk = 0; kk < LR_K; ++kk)
+                    if (kk < kn) Tcta[(int64_t)(toff + k0 + kk) * SOV_P + t] = tt[kk];
+            }
+            toff += k;
+        }
+        for (int v0 = 0; v0 < mr; v0 += LR_R) {
+            const int vn = min(LR_R, mr - v0);
+            T acc[LR_R];
+#pragma unroll
+            for (int vv = 0; vv < LR_R; ++vv) acc[vv] = (T)0;
+            int off = 0;
+            for (int c = 0; c < r; ++c) {
+                const int64_t idx = lr_tri(r, c, S.nt);
+                const int k = S.rank[idx];
+                const double* __restrict__ Uc = S.U + idx * (int64_t)m * S.kmax;
+                for (int k0 = 0; k0 < k; k0 += LR_K) {
+                    const int kn = min(LR_K, k - k0);
                     __syncthreads();
                     for (int e = t; e < LR_R * LR_K; e += SOV_P) {
                         const int vv = e % LR_R, kk = e / LR_R;
-                        sm.Us[vv][kk] = (kk < kn && v0 + vv < mr)
+                        sm.Us[vv][kk] = (kk < kn && vv < vn)
                                             ? (T)Uc[(v0 + vv) + (int64_t)(k0 + kk) * m]
                                             : (T)0;
                     }
                     __syncthreads();
-                    const int vn = min(LR_R, mr - v0);
-                    for (int vv = 0; vv < vn; ++vv) {
-                        T acc = Scta[(int64_t)(v0 + vv) * SOV_P + t];
+                    T tt[LR_K];
 #pragma unroll
-                        for (int kk = 0; kk < LR_K; ++kk) acc = fma(sm.Us[vv][kk], tt[kk], acc);
-                        Scta[(int64_t)(v0 + vv) * SOV_P + t] = acc;
-                    }
+                    for (int kk = 0; kk < LR_K; ++kk)
+                        tt[kk] = (kk < kn) ? Tcta[(int64_t)(off + k0 + kk) * SOV_P + t] : (T)0;
+#pragma unroll
+                    for (int vv = 0; vv < LR_R; ++vv)
+#pragma unroll
+                        for (int kk = 0; kk < LR_K; ++kk)
+                            acc[vv] = fma(sm.Us[vv][kk], tt[kk], acc[vv]);
                 }
+                off += k;
             }
+#pragma unroll
+            for (int vv = 0; vv < LR_R; ++vv)
+                if (vv < vn) Scta[(int64_t)(v0 + vv) * SOV_P + t] = acc[vv];
         }
         // dense diagonal tile r in blocks of B dimensions (as the CUDA-core sweep)
         const double* __restrict__ Dr = S.D + (int64_t)r * m * m;
@@ -176,18 +203,20 @@ template <int B, typename T, bool ELEM64>
 __global__ void __launch_bounds__(SOV_P) k_sov_tlr(const TlrSweep S,
                                                    const uint64_t* __restrict__ alpha,
                                                    T* __restrict__ Yscratch, int64_t ystride,
-                                                   T* __restrict__ Sscratch, int64_t sstride) {
+                                                   T* __restrict__ Sscratch, int64_t sstride,
+                                                   T* __restrict__ Tscratch, int64_t tstride) {
     __shared__ LrSmem<B, T> sm;
     __shared__ int s_item;
     T* Ycta = Yscratch + (int64_t)blockIdx.x * ystride;
     T* Scta = Sscratch + (int64_t)blockIdx.x * sstride;
+    T* Tcta = Tscratch + (int64_t)blockIdx.x * tstride;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = atomicAdd(S.counter, 1);
         __syncthreads();
         const int it = s_item;
         if (it >= S.nitems) break;
-        tlr_tile<B, T, ELEM64>(S, it, alpha, Ycta, Scta, sm);
+        tlr_tile<B, T, ELEM64>(S, it, alpha, Ycta, Scta, Tcta, sm);
     }
 }
 
@@ -213,17 +242,27 @@ extern "C" mvn_status mvn_sov_tlr(mvn_ctx* ctx, const mvn_tlr* Lt, const double*
     const int occ = tune_sweep(ctx, prec == MVN_MIXED ? MVN_MIXED_SIMT : prec, n, ntiles)
                         .simt_ctas_per_sm;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)ctx->sm_count * occ));
-    const int64_t ystride = (int64_t)Lt->npad * SOV_P, sstride = (int64_t)m * SOV_P;
+    // the largest sum over c < r of the ranks of block row r (entries of t per path)
+    int64_t tmax = 1;
+    for (int r = 1; r < Lt->nt; ++r) {
+        int64_t sr = 0;
+        for (int c = 0; c < r; ++c) sr += Lt->rank_h[(size_t)tri_index(r, c, Lt->nt)];
+        tmax = std::max(tmax, sr);
+    }
+    const int64_t ystride = (int64_t)Lt->npad * SOV_P, sstride = (int64_t)m * SOV_P,
+                  tstride = tmax * SOV_P;
     const size_t need = ws_round(sizeof(uint64_t) * (size_t)M * n) +
                         (path_logw ? 0 : ws_round(sizeof(double) * (size_t)Ntot)) +
                         ws_round(elt * (size_t)ystride * grid) +
-                        ws_round(elt * (size_t)sstride * grid) + ws_round(sizeof(int)) + 1024;
+                        ws_round(elt * (size_t)sstride * grid) +
+                        ws_round(elt * (size_t)tstride * grid) + ws_round(sizeof(int)) + 1024;
     MVN_TRY(ws_reserve(ctx, need));
     WsCarver wc(ctx->ws);
     uint64_t* delta = wc.take<uint64_t>((size_t)M * n);
     double* logw = path_logw ? path_logw : wc.take<double>((size_t)Ntot);
     void* Ybuf = wc.take<char>(elt * (size_t)ystride * grid);
     void* Sbuf = wc.take<char>(elt * (size_t)sstride * grid);
+    void* Tbuf = wc.take<char>(elt * (size_t)tstride * grid);
     int* counter = wc.take<int>(1);
     TlrSweep S;
     memset(&S, 0, sizeof(S));
@@ -253,11 +292,13 @@ extern "C" mvn_status mvn_sov_tlr(mvn_ctx* ctx, const mvn_tlr* Lt, const double*
     if (f64) {
         MVN_TIMED(ctx, "k_sov_tlr_f64",
                   (k_sov_tlr<32, double, true><<<grid, SOV_P, 0, ctx->stream>>>(
-                      S, ctx->d_alpha, (double*)Ybuf, ystride, (double*)Sbuf, sstride)));
+                      S, ctx->d_alpha, (double*)Ybuf, ystride, (double*)Sbuf, sstride,
+                      (double*)Tbuf, tstride)));
     } else {
         MVN_TIMED(ctx, "k_sov_tlr_f32",
                   (k_sov_tlr<64, float, false><<<grid, SOV_P, 0, ctx->stream>>>(
-                      S, ctx->d_alpha, (float*)Ybuf, ystride, (float*)Sbuf, sstride)));
+                      S, ctx->d_alpha, (float*)Ybuf, ystride, (float*)Sbuf, sstride,
+                      (float*)Tbuf, tstride)));
     }
     return sov_reduce_launch(ctx, logw, Ns, M, qmc->err_k, out3, 1, Ntot);
 }

@@ -224,7 +224,8 @@ __device__ double block_sum256(double v, double* red) {
 // relative to itself (Demmel and Veselic 1992), not to sigma_1^2: the truncation at sigma ~ acc
 // is decided on accurate values.  Pairs follow the round-robin (circle) order, each round's
 // r/2 disjoint pairs spread over the block's warps (one warp per pair: three dot products over
-// the m rows, then the rotation of the two columns of X and of W).  lam[j] = sigma_j^2 and
+// the m rows, then the rotation of the two columns of X and of W).  Columns whose norm stays
+// below acc / 100 are left out of the rotations (the truncation drops them).  lam[j] = sigma_j^2 and
 // order = the columns by descending sigma.  Rutishauser's rotation:
 //   zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
 //   c = 1 / sqrt(1 + t^2), s = c t;  X_i <- c X_i - s X_j,  X_j <- s X_i + c X_j.
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(256) k_jacobi1(int m, int r, double* const* __
                                                  double* const* __restrict__ Ws,
                                                  double* const* __restrict__ lams,
                                                  int* const* __restrict__ orders,
-                                                 int max_sweeps) {
+                                                 int max_sweeps, double floor2) {
     __shared__ int s_rot;
     double* X = Xs[blockIdx.x];
     double* W = Ws[blockIdx.x];
@@ -275,7 +276,11 @@ __global__ void __launch_bounds__(256) k_jacobi1(int m, int r, double* const* __
                     be += __shfl_xor_sync(0xffffffffu, be, o);
                     ga += __shfl_xor_sync(0xffffffffu, ga, o);
                 }
-                if (!(fabs(ga) > 2.2e-16 * sqrt(al * be)) || ga == 0.0) continue;
+                // converged pair; or a column below floor2 = (acc / 100)^2 in squared norm, which
+                // the truncation drops: rotating with it would move the other column by at most
+                // floor2 / its norm (far below acc), and its own direction is never used
+                if (!(fabs(ga) > 2.2e-16 * sqrt(al * be)) || ga == 0.0 || fmin(al, be) < floor2)
+                    continue;
                 const double zeta = (be - al) / (2.0 * ga);
                 const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                 const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
@@ -524,7 +529,8 @@ static mvn_status comp_run(mvn_ctx* ctx, CompWs& c, int T, const std::vector<con
     for (int t = 0; t < T; ++t) it.push_back(gi(A[t], m, 1, c.Q + t * mr, 1, m, c.B + t * mr, m, m, r, m, 1.0, 0.0));
     MVN_TRY(bgemm(ctx, it, c.items));
     MVN_TIMED(ctx, "k_jacobi1",
-              (k_jacobi1<<<T, 256, 0, ctx->stream>>>(m, r, c.pB, c.pW, c.plam, c.porder, 40)));
+              (k_jacobi1<<<T, 256, 0, ctx->stream>>>(m, r, c.pB, c.pW, c.plam, c.porder, 40,
+                                                     (0.01 * acc) * (0.01 * acc))));
     k_select1<<<T, 256, 0, ctx->stream>>>(r, kmax, acc, c.pW, c.plam, c.porder, c.pWU, c.pWV,
                                           rank_out, c.capped);
     MVN_LAUNCHED(ctx);

@@ -38,9 +38,9 @@ def test_tlr_compress_vs_oracle(mvn, tile, acc, kmax):
     ref = oracle.tlr_compress(S, tile, acc, kmax)
     L = mvn.mvn_tlr_to_dense(T).cpu().numpy()
     nt = n // tile
-    # ranks: equal except where a singular value sits within 1% of the threshold (the singular
-    # values come from a one-sided Jacobi SVD of the sketched tile, each to ~1e-12 relative; the
-    # sketch itself can lose a little of the values near the truncation)
+    # ranks: equal except where a singular value sits within 1e-6 relative of the threshold (the
+    # singular values come from a one-sided Jacobi SVD of the sketched tile, each resolved
+    # relative to itself; measured: every rank equal to the oracle's)
     nmiss = 0
     for t, (i, j) in enumerate((i, j) for j in range(nt) for i in range(j + 1, nt)):
         A = S[i * tile:(i + 1) * tile, j * tile:(j + 1) * tile]
@@ -51,7 +51,7 @@ def test_tlr_compress_vs_oracle(mvn, tile, acc, kmax):
             lo, hi = sorted((ranks[t], k_ref))
             dev = np.abs(s[lo:hi] / acc - 1.0)
             print(f"tile ({i},{j}): rank {ranks[t]} vs {k_ref}, sigma/acc - 1 = {dev}")
-            assert np.all(dev < 0.01), (i, j, ranks[t], k_ref, s[lo:hi + 1])
+            assert np.all(dev < 1e-6), (i, j, ranks[t], k_ref, s[lo:hi + 1])
         err = np.linalg.norm(A - L[i * tile:(i + 1) * tile, j * tile:(j + 1) * tile], 2)
         # Eckart-Young bound of the exact truncation plus the randomised range finder's slack
         assert err <= 2.0 * max(acc, s[min(kmax, len(s) - 1)] if ranks[t] == kmax else acc), (i, j, err)
@@ -74,7 +74,9 @@ def test_tlr_cholesky_vs_oracle_and_dense(mvn):
     print(f"TLR Cholesky: ||LL^T - S|| gpu {e_bwd:.3e} oracle {e_ref:.3e}; max|L - L_oracle| "
           f"{np.abs(L - ref).max():.3e}; max|L - L_dense| {np.abs(L - Ld).max():.3e}")
     assert e_bwd < 100 * acc
-    assert np.abs(L - ref).max() < 1e-3
+    # the same ranks as the oracle's exact SVD and the same tile algorithm: the factors agree to
+    # rounding (measured 1.6e-12)
+    assert np.abs(L - ref).max() < 1e-9
     # SOV with the TLR factor vs the dense factor on identical points (stated difference)
     a = np.full(n, -np.inf)
     b = np.full(n, 1.0)
@@ -83,7 +85,9 @@ def test_tlr_cholesky_vs_oracle_and_dense(mvn):
     P_d = mvn.mvn_sov(_t(a), _t(b), mvn.to_colmajor(_t(Ld)), *q).cpu().numpy()
     mvn.sync()
     print(f"log P with TLR factor {P_t[0]:.8f} vs dense {P_d[0]:.8f}")
-    assert abs(P_t[0] - P_d[0]) < 1e-2
+    # the factor differs from the dense one by ~acc-sized truncations (max |L - L_dense| ~5e-7);
+    # log P moves by 3.9e-7 (measured)
+    assert abs(P_t[0] - P_d[0]) < 1e-5
 
 
 def test_tlr_ragged_and_rank_cap(mvn):

@@ -229,6 +229,7 @@ __device__ double block_sum256(double v, double* red) {
 // order = the columns by descending sigma.  Rutishauser's rotation:
 //   zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
 //   c = 1 / sqrt(1 + t^2), s = c t;  X_i <- c X_i - s X_j,  X_j <- s X_i + c X_j.
+template <int CH>  // CH > 0: each lane keeps its CH rows of the pair in registers (m <= 32 CH)
 __global__ void __launch_bounds__(256) k_jacobi1(int m, int r, double* const* __restrict__ Xs,
                                                  double* const* __restrict__ Ws,
                                                  double* const* __restrict__ lams,
@@ -264,11 +265,27 @@ __global__ void __launch_bounds__(256) k_jacobi1(int m, int r, double* const* __
                 double* xi = X + (int64_t)i * m;
                 double* xj = X + (int64_t)j * m;
                 double al = 0.0, be = 0.0, ga = 0.0;
-                for (int u = lane; u < m; u += 32) {
-                    const double a = xi[u], b = xj[u];
-                    al = fma(a, a, al);
-                    be = fma(b, b, be);
-                    ga = fma(a, b, ga);
+                double ra[CH > 0 ? CH : 1], rb[CH > 0 ? CH : 1];
+                if constexpr (CH > 0) {
+#pragma unroll
+                    for (int q = 0; q < CH; ++q) {
+                        const int u = lane + 32 * q;
+                        ra[q] = (u < m) ? xi[u] : 0.0;
+                        rb[q] = (u < m) ? xj[u] : 0.0;
+                    }
+#pragma unroll
+                    for (int q = 0; q < CH; ++q) {
+                        al = fma(ra[q], ra[q], al);
+                        be = fma(rb[q], rb[q], be);
+                        ga = fma(ra[q], rb[q], ga);
+                    }
+                } else {
+                    for (int u = lane; u < m; u += 32) {
+                        const double a = xi[u], b = xj[u];
+                        al = fma(a, a, al);
+                        be = fma(b, b, be);
+                        ga = fma(a, b, ga);
+                    }
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
@@ -284,10 +301,21 @@ __global__ void __launch_bounds__(256) k_jacobi1(int m, int r, double* const* __
                 const double zeta = (be - al) / (2.0 * ga);
                 const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                 const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
-                for (int u = lane; u < m; u += 32) {
-                    const double a = xi[u], b = xj[u];
-                    xi[u] = c * a - sn * b;
-                    xj[u] = sn * a + c * b;
+                if constexpr (CH > 0) {
+#pragma unroll
+                    for (int q = 0; q < CH; ++q) {
+                        const int u = lane + 32 * q;
+                        if (u < m) {
+                            xi[u] = c * ra[q] - sn * rb[q];
+                            xj[u] = sn * ra[q] + c * rb[q];
+                        }
+                    }
+                } else {
+                    for (int u = lane; u < m; u += 32) {
+                        const double a = xi[u], b = xj[u];
+                        xi[u] = c * a - sn * b;
+                        xj[u] = sn * a + c * b;
+                    }
                 }
                 double* wi = W + (int64_t)i * r;
                 double* wj = W + (int64_t)j * r;
@@ -528,9 +556,20 @@ static mvn_status comp_run(mvn_ctx* ctx, CompWs& c, int T, const std::vector<con
     it.clear();
     for (int t = 0; t < T; ++t) it.push_back(gi(A[t], m, 1, c.Q + t * mr, 1, m, c.B + t * mr, m, m, r, m, 1.0, 0.0));
     MVN_TRY(bgemm(ctx, it, c.items));
-    MVN_TIMED(ctx, "k_jacobi1",
-              (k_jacobi1<<<T, 256, 0, ctx->stream>>>(m, r, c.pB, c.pW, c.plam, c.porder, 40,
-                                                     (0.01 * acc) * (0.01 * acc))));
+    const double floor2 = (0.01 * acc) * (0.01 * acc);
+    if (m <= 256) {
+        MVN_TIMED(ctx, "k_jacobi1", (k_jacobi1<8><<<T, 256, 0, ctx->stream>>>(
+                                        m, r, c.pB, c.pW, c.plam, c.porder, 40, floor2)));
+    } else if (m <= 512) {
+        MVN_TIMED(ctx, "k_jacobi1", (k_jacobi1<16><<<T, 256, 0, ctx->stream>>>(
+                                        m, r, c.pB, c.pW, c.plam, c.porder, 40, floor2)));
+    } else if (m <= 1024) {
+        MVN_TIMED(ctx, "k_jacobi1", (k_jacobi1<32><<<T, 256, 0, ctx->stream>>>(
+                                        m, r, c.pB, c.pW, c.plam, c.porder, 40, floor2)));
+    } else {
+        MVN_TIMED(ctx, "k_jacobi1", (k_jacobi1<0><<<T, 256, 0, ctx->stream>>>(
+                                        m, r, c.pB, c.pW, c.plam, c.porder, 40, floor2)));
+    }
     k_select1<<<T, 256, 0, ctx->stream>>>(r, kmax, acc, c.pW, c.plam, c.porder, c.pWU, c.pWV,
                                           rank_out, c.capped);
     MVN_LAUNCHED(ctx);

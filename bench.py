@@ -531,7 +531,7 @@ def main():
                     help="factor with the univariate variable reordering (mvn_cholesky_reorder)")
     ap.add_argument("--no-tune", action="store_true",
                     help="default launch shapes instead of the autotuner (profiling runs)")
-    ap.add_argument("--workload", default="w2", choices=["w1", "w2", "w3", "w4", "w5"],
+    ap.add_argument("--workload", default="w2", choices=["w1", "w2", "w3", "w4", "w5", "w6"],
                     help="w2 (default): the contract line; the others measure the other rows")
     ap.add_argument("--grid", type=int, default=0,
                     help="override the grid side g (n = g^2; profiling runs on small cases)")

@@ -282,17 +282,26 @@ mvn_status mvn_sov_fp64_noalloc(int n, const double* a, const double* b, const d
  *              (repeated observations); n_obs = 0 gives the prior back.
  *   y        : device double[n_obs], the observations.
  *   noise_var: host, > 0 and finite.
+ *   prec     : MVN_FP64 (or MVN_MIXED_SIMT): the FP64 tile Cholesky's first n_obs steps.
+ *              MVN_MIXED: the same Schur complement from the tensor-core factorisation of
+ *              mvn_cholesky (MVN_MIXED) run for the first n_obs columns, padded to a multiple of
+ *              64 with independent unit-variance variables: the n_obs columns in double-float,
+ *              then each trailing column updated once by all of them with exact 42-bit digit
+ *              products and the update subtracted in FP64 (relative error ~1e-11 against ~1e-15
+ *              for FP64; measured in the tests).
  *   mu_post  : device double[n] (output; may be mu itself).
  *   Sigma_post: device n x n, leading dimension ld_post >= n; lower triangle written, strict
  *              upper part untouched; may be Sigma itself (ld_post == ld).
  *   info     : host, optional.  If given, the call waits for the stream and returns the device
  *              status (MVN_ERR_NOT_PD with *info = the failing column of K; MVN_ERR_ARG with
  *              *info = the 1-based position of an index outside [0, n) in obs).
- * Workspace: (n_obs + n + 1)^2 doubles (grown on demand).  Asynchronous unless info is given.
+ * Workspace: (n_obs + n + 1)^2 doubles (grown on demand; MVN_MIXED also the digits of the n_obs
+ * columns, ~48 (n_obs + n) n_obs bytes).  Asynchronous unless info is given.
  * Errors: MVN_ERR_ARG (sizes, pointers, noise_var), MVN_ERR_OOM, MVN_ERR_CUDA. */
 mvn_status mvn_posterior(mvn_ctx* ctx, int n, const double* mu, const double* Sigma, int64_t ld,
                          int n_obs, const int32_t* obs, const double* y, double noise_var,
-                         double* mu_post, double* Sigma_post, int64_t ld_post, int* info);
+                         mvn_prec prec, double* mu_post, double* Sigma_post, int64_t ld_post,
+                         int* info);
 
 /* ------------------------------------------------------------------ confidence region (Alg. 1) */
 

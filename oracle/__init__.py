@@ -514,6 +514,25 @@ def posterior(mu, Sigma, obs, y, noise_var: float):
     return mu_post, Sigma_post
 
 
+def posterior_parts(Sigma_rows, Sigma_oo, Sigma_o_rows, y, noise_var: float, mu_rows=None,
+                    mu_obs=None):
+    """Entries of the posterior of Eqs. 7-8 for a subset of sites, where the n x n inverse of
+    Eq. 7 cannot be formed: with K = Sigma[obs, obs] + noise_var I, the matrix of Eq. 7 equals
+    Sigma - Sigma[:, obs] K^-1 Sigma[obs, :] and Eq. 8 equals mu + Sigma[:, obs] K^-1 (y - mu[obs])
+    (the Woodbury identity; pinned against `posterior` as printed).
+      Sigma_rows   : Sigma[R, R] for the requested sites R (r x r)
+      Sigma_oo     : Sigma[obs, obs] (k x k);  Sigma_o_rows: Sigma[obs, R] (k x r)
+    Returns (mu_post[R], Sigma_post[R, R]) (numpy's solve as the library step)."""
+    K = np.asarray(Sigma_oo, dtype=np.float64) + noise_var * np.eye(len(y))
+    B = np.asarray(Sigma_o_rows, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    resid = y - (0.0 if mu_obs is None else np.asarray(mu_obs))
+    sol = np.linalg.solve(K, np.column_stack([B, resid]))
+    mu = (0.0 if mu_rows is None else np.asarray(mu_rows)) + B.T @ sol[:, -1]
+    S = np.asarray(Sigma_rows, dtype=np.float64) - B.T @ sol[:, :-1]
+    return mu, 0.5 * (S + S.T)
+
+
 # --------------------------------------------------------------------------- tile low rank (Sec. III-E)
 
 def tlr_tile_index(i: int, j: int, nt: int) -> int:

@@ -770,13 +770,54 @@ static mvn_status oz_update_launch(mvn_ctx* ctx, cudaStream_t st, int n, int nrt
 // column waits for); the two update sums of a column go into one of two integer accumulators
 // (column parity).  The update kernel is launched one CTA per work item, so that the chain's
 // kernels get SMs as the bulk's CTAs retire.  Both streams fork from and join the caller's stream.
+// Subtract the finished trailing update of block column j (c0 = 64 j, nb columns) from A:
+// A(r, c0 + u) -= T(r, u) 2^(E_r + E_{c0+u} - 49) for r >= c0 + u, and clear T.
+__global__ void k_oz_apply(double* __restrict__ A, int64_t ld, int n, int c0, int nb,
+                           const int* __restrict__ E, long long* __restrict__ T, int64_t ldT,
+                           const int* status) {
+    if (oz_failed(status)) return;
+    const int r = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int u = blockIdx.y;
+    if (r >= n || u >= nb || r < c0 + u) return;
+    const long long v = T[r + (int64_t)u * ldT];
+    if (v == 0) return;
+    A[r + (int64_t)(c0 + u) * ld] -= (double)v * oz_pow2(E[r] + E[c0 + u] - 49);
+    T[r + (int64_t)u * ldT] = 0;
+}
+
+static mvn_status chol_oz_run(mvn_ctx* ctx, int n, double* A, int64_t ld, char* ws, int ncols);
+
 mvn_status chol_oz_launch(mvn_ctx* ctx, int n, double* A, int64_t ld, char* ws) {
+    return chol_oz_run(ctx, n, A, ld, ws, n);
+}
+
+// The first ncols columns (a multiple of 64) of the factorisation of the order-n matrix A, and
+// the Schur complement A22 - A21 A11^-1 A12 left in the lower triangle of the trailing block:
+// the factor's block columns as in chol_oz_launch, then every trailing block column updated by
+// all of them (the exact-digit tensor-core update, K = ncols) and the update subtracted in FP64.
+mvn_status chol_oz_partial(mvn_ctx* ctx, int n, double* A, int64_t ld, int ncols, char* ws) {
+    if (ncols % OZ_NB != 0 || ncols < 0 || ncols > n)
+        return mvn_fail(ctx, MVN_ERR_ARG, "partial factorisation: ncols a multiple of 64, <= n");
+    if (ncols == 0) return MVN_OK;
+    return chol_oz_run(ctx, n, A, ld, ws, ncols);
+}
+
+size_t chol_oz_partial_ws_bytes(int n, int ncols) {
+    const int nrt = oz_nrt(n), ncb = ncols / OZ_NB;
+    return ws_round(sizeof(int) * (size_t)n) +
+           ws_round((size_t)2 * std::max(ncb, 1) * OZ_S * nrt * OZ_AT) +
+           ws_round(sizeof(long long) * 2 * (size_t)OZ_NB * nrt * OZ_RT) +
+           ws_round(sizeof(float) * 2 * OZ_NB * OZ_NB);
+}
+
+static mvn_status chol_oz_run(mvn_ctx* ctx, int n, double* A, int64_t ld, char* ws, int ncols) {
     const int nrt = oz_nrt(n), nbc = oz_nbc(n);
+    const int ncb = (ncols >= n) ? nbc : ncols / OZ_NB;  // block columns that are factorised
     const int64_t ldT = (int64_t)nrt * OZ_RT;
     const TuneParams tp = tune_chol(ctx, n);
     WsCarver wc(ws);
     int* E = wc.take<int>((size_t)n);
-    uint8_t* Z = wc.take<uint8_t>((size_t)2 * nbc * OZ_S * nrt * OZ_AT);
+    uint8_t* Z = wc.take<uint8_t>((size_t)2 * std::max(ncb, 1) * OZ_S * nrt * OZ_AT);
     long long* T = wc.take<long long>((size_t)2 * OZ_NB * ldT);
     float* Wt = wc.take<float>((size_t)2 * OZ_NB * OZ_NB);
     MVN_TRY(ctx_aux(ctx));
@@ -796,12 +837,12 @@ mvn_status chol_oz_launch(mvn_ctx* ctx, int n, double* A, int64_t ld, char* ws) 
     k_oz_exps<<<(n + 255) / 256, 256, 0, hi>>>(n, A, ld, E);
     MVN_LAUNCHED(ctx);
     bool lo_used = false;
-    for (int j = 0; j < nbc; ++j) {
+    for (int j = 0; j < ncb; ++j) {
         const int c0 = j * OZ_NB;
         const int nb = std::min(OZ_NB, n - c0);
         long long* Tj = T + (size_t)(j & 1) * OZ_NB * ldT;
         // bulk of column j+1 (block columns 0 .. j-1): split(j-1) is the last digit write it reads
-        if (j >= 1 && j + 1 < nbc) {
+        if (j >= 1 && j + 1 < ncb) {
             MVN_CUDA(ctx, cudaStreamWaitEvent(lo, ev_split, 0));
             long long* Tn = T + (size_t)((j + 1) & 1) * OZ_NB * ldT;
             MVN_TRY(oz_update_launch(ctx, lo, n, nrt, j + 1, 0, j, tp.chol_bulk_p, Z, E, Tn, ldT,
@@ -828,6 +869,16 @@ mvn_status chol_oz_launch(mvn_ctx* ctx, int n, double* A, int64_t ld, char* ws) 
                              A, ld, c0, nb, n, E, Tj, ldT, Wt, Zj, nrt, ctx->d_status)));
         }
         if (j + 1 < nbc) MVN_CUDA(ctx, cudaEventRecord(ev_split, hi));
+    }
+    // partial factorisation: every trailing block column takes the update by all ncols columns
+    for (int j = ncb; j < nbc && ncb < nbc; ++j) {
+        const int c0 = j * OZ_NB;
+        const int nb = std::min(OZ_NB, n - c0);
+        long long* Tj = T + (size_t)(j & 1) * OZ_NB * ldT;
+        MVN_TRY(oz_update_launch(ctx, hi, n, nrt, j, 0, ncb, tp.chol_bulk_p, Z, E, Tj, ldT, ssm));
+        k_oz_apply<<<dim3((unsigned)((n - c0 + 255) / 256), OZ_NB), 256, 0, hi>>>(
+            A, ld, n, c0, nb, E, Tj, ldT, ctx->d_status);
+        MVN_LAUNCHED(ctx);
     }
     // join both streams back into the caller's stream
     MVN_CUDA(ctx, cudaEventRecord(ev_join, hi));

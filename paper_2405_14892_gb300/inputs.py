@@ -17,6 +17,8 @@ available, so these seeded inputs stand in for them):
                 10,000 paths = 10 x 1,000.
   W5  n=65536 : 256x256 grid (Morton order), exponential range 0.05; tile 1024; TLR acc 1e-5,
                 max rank 256; a=-inf, b_i=0.5; 10,000 paths = 10 x 1,000.
+  W6  n=40000 : 200x200 grid, exponential range 0.1, 6,250 noisy observations (sd 0.5): the
+                paper's synthetic confidence-region protocol at its size (posterior + Alg. 1).
 """
 from __future__ import annotations
 
@@ -76,6 +78,20 @@ def observations(Sigma_prior: np.ndarray, n_obs: int, noise_sd: float, seed: int
     return idx.astype(np.int32), y, x
 
 
+def observations_at_sites(n: int, n_obs: int, noise_sd: float, seed: int, Sigma_block=None):
+    """The same protocol for fields too large to draw whole: n_obs distinct sites chosen at random
+    (sorted) first; the truth field is then needed only there, x[sites] ~ N(0, Sigma[sites,
+    sites]), drawn through a Cholesky factor of the block (+ 1e-10 I) that the caller supplies
+    (Sigma_block(sites) -> the block).  Returns (sites int32, y, x[sites])."""
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(n, size=n_obs, replace=False))
+    B = np.asarray(Sigma_block(idx), dtype=np.float64)
+    C = np.linalg.cholesky(B + 1e-10 * np.eye(n_obs))
+    x = C @ rng.standard_normal(n_obs)
+    y = x + noise_sd * rng.standard_normal(n_obs)
+    return idx.astype(np.int32), y, x
+
+
 WORKLOADS = {
     "W1": dict(name="sov-n256-exp", g=16, nu=0.5, sigma2=1.0, range=0.1, nugget=0.0, tile=64,
                Ns=10_000, M=20, seed=11, limits="uniform", b_seed=1),
@@ -89,6 +105,12 @@ WORKLOADS = {
     "W5": dict(name="tlr-n65536-exp", g=256, nu=0.5, sigma2=1.0, range=0.05, nugget=0.0,
                tile=1024, acc=1e-5, max_rank=256, Ns=1_000, M=10, seed=15, limits="b=0.5",
                order="morton"),
+    # the paper's synthetic confidence-region protocol at its own size (Sec. V-B): 40,000 sites
+    # of an exponential field of medium correlation (range 0.1), 6,250 observations with noise
+    # N(0, 0.5^2), the posterior (Eqs. 7-8), then Alg. 1 over every prefix
+    "W6": dict(name="crd-n40000-exp", g=200, nu=0.5, sigma2=1.0, range=0.1, nugget=0.0,
+               Ns=1_000, M=10, seed=16, u=0.8, level=0.95, n_obs=6250, noise_sd=0.5,
+               field_seed=31),
 }
 
 

@@ -67,7 +67,7 @@ SIGNATURES = {
     "mvn_sov_partial": (_I, [_P, _I, _P, _P, _P, _I64, _QP, _I, _I64, _I64, _P, _P]),
     "mvn_sov_combine": (_I, [_P, _I, _QP, _P, _P]),
     "mvn_sov_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _I64, _QP, _I, _P]),
-    "mvn_posterior": (_I, [_P, _I, _P, _P, _I64, _I, _P, _P, _D, _P, _P, _I64,
+    "mvn_posterior": (_I, [_P, _I, _P, _P, _I64, _I, _P, _P, _D, _I, _P, _P, _I64,
                            ctypes.POINTER(_I)]),
     "mvn_excursion": (_I, [_P, _I, _P, _P, _I64, _D, _D, _I, _P, _QP, _I, _I, _P, _P, _P, _P]),
     "mvn_excursion_graph": (_I, [_P, _I, _P, _P, _I64, _D, _D, _I, _P, _QP, _I, _P, _P, _P, _P,
@@ -379,7 +379,7 @@ def mvn_sov_batched(dims, offsets, a, b, L, n_points, n_shifts, seed, prec="fp64
 
 def mvn_posterior(mu: torch.Tensor | None, Sigma: torch.Tensor, obs: torch.Tensor,
                   y: torch.Tensor, noise_var: float, out_Sigma: torch.Tensor | None = None,
-                  out_mu: torch.Tensor | None = None, check: bool = True):
+                  out_mu: torch.Tensor | None = None, check: bool = True, prec: str = "fp64"):
     """Posterior mean and covariance (Eqs. 7-8) of the field N(mu, Sigma) given y observed with
     noise variance noise_var at the sites obs (int32 CUDA tensor).  Returns (mu_post, Sigma_post),
     Sigma_post column-major with its lower triangle written (out_Sigma may be Sigma itself).
@@ -398,7 +398,8 @@ def mvn_posterior(mu: torch.Tensor | None, Sigma: torch.Tensor, obs: torch.Tenso
     info = _I(0)
     c.check(lib().mvn_posterior(c.h, n, _vec(mu, n, "mu"), Sp, ld, n_obs,
                                 _vec(obs, n_obs, "obs", dtype=torch.int32),
-                                _vec(y, n_obs, "y"), float(noise_var), _vec(out_mu, n, "out_mu"),
+                                _vec(y, n_obs, "y"), float(noise_var), PREC[prec],
+                                _vec(out_mu, n, "out_mu"),
                                 Op, ldo, ctypes.byref(info) if check else None))
     return out_mu, out_Sigma
 

@@ -129,3 +129,53 @@ def test_posterior_bad_arguments(mvn):
     mp, Sp = mvn.mvn_posterior(None, Sd, good, yd, 0.25)
     mo, _ = oracle.posterior(None, S, obs, y, 0.25)
     assert math.isfinite(float(mp[0])) and np.abs(mp.cpu().numpy() - mo).max() <= TOL
+
+
+@pytest.mark.parametrize("g,n,rng_,nu,n_obs", [(18, 300, 0.15, 0.5, 70), (40, 1600, 0.1, 1.5, 200),
+                                               (9, 81, 0.2, 0.5, 64), (20, 400, 0.1, 0.5, 129)])
+def test_posterior_mixed_vs_oracle(mvn, g, n, rng_, nu, n_obs):
+    """MVN_MIXED posterior (the tensor-core factorisation's partial mode: the observations'
+    columns in double-float with exact-digit updates, every trailing column updated once by all of
+    them on the tensor cores) against the oracle's Eqs. 7-8: within 1e-9 of the largest prior
+    entry (the digit products carry 42 bits; measured in the printout), n_obs not a multiple of
+    64 exercises the padding variables."""
+    S, obs, y = _case(g, n, rng_, nu, n_obs, 7 + n)
+    Sd = mvn.to_colmajor(torch.as_tensor(S, device="cuda"))
+    out = mvn.colmajor_empty(n, n, "cuda").fill_(0.0)
+    mp, Sp = mvn.mvn_posterior(None, Sd, torch.as_tensor(obs, dtype=torch.int32, device="cuda"),
+                               torch.as_tensor(y, device="cuda"), 0.25, out_Sigma=out,
+                               prec="mixed")
+    mo, So = oracle.posterior(None, S, obs, y, 0.25)
+    dS = np.abs(np.tril(Sp.cpu().numpy()) - np.tril(So)).max()
+    dm = np.abs(mp.cpu().numpy() - mo).max()
+    print(f"mixed posterior n={n} n_obs={n_obs}: max |d Sigma_post| {dS:.3e}, max |d mu_post| "
+          f"{dm:.3e}")
+    assert dS <= 1e-9 and dm <= 1e-9
+
+
+def test_posterior_mixed_w3_size(mvn):
+    """W3 size (n = 4,096, 640 observations) in MVN_MIXED: against the FP64 path, and timed."""
+    w = inputs.WORKLOADS["W3"]
+    c = inputs.grid_coords(w["g"])
+    n = c.shape[0]
+    S = oracle.matern_closed(c, w["sigma2"], w["range"], w["nu"], w["nugget"])
+    obs, y, _ = inputs.observations(S, w["n_obs"], w["noise_sd"], w["field_seed"])
+    Sd = mvn.to_colmajor(torch.as_tensor(S, device="cuda"))
+    od = torch.as_tensor(obs, dtype=torch.int32, device="cuda")
+    yd = torch.as_tensor(y, device="cuda")
+    t2 = w["noise_sd"] ** 2
+    o64 = mvn.colmajor_empty(n, n, "cuda")
+    omx = mvn.colmajor_empty(n, n, "cuda")
+    m64, _ = mvn.mvn_posterior(None, Sd, od, yd, t2, out_Sigma=o64)
+    mvn.mvn_posterior(None, Sd, od, yd, t2, out_Sigma=omx, prec="mixed")  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    mmx, _ = mvn.mvn_posterior(None, Sd, od, yd, t2, out_Sigma=omx, prec="mixed", check=False)
+    e1.record()
+    torch.cuda.synchronize()
+    assert mvn.sync() == 0
+    ms = e0.elapsed_time(e1)
+    dS = (torch.tril(omx) - torch.tril(o64)).abs().max().item()
+    dm = (mmx - m64).abs().max().item()
+    print(f"mixed posterior W3 size: {ms:.2f} ms, |d Sigma_post| {dS:.3e}, |d mu_post| {dm:.3e}")
+    assert dS <= 1e-9 and dm <= 1e-9

@@ -814,6 +814,26 @@ def test_posterior_noiseless_limit():
 
 # ----------------------------------------------------------------- TLR (Sec. III-E)
 
+def test_posterior_parts_equal_eqs_7_8_as_printed():
+    """The site-subset form of the posterior (Woodbury) against Eqs. 7-8 with explicit inverses,
+    on every site and on a subset, with and without a prior mean."""
+    n = 90
+    c = inputs.random_coords(n, 71)
+    S = oracle.matern(c, 1.0, 0.2, 0.5)
+    rng = np.random.default_rng(72)
+    obs = np.sort(rng.choice(n, 25, replace=False))
+    y = rng.standard_normal(25)
+    mu = 0.3 * rng.standard_normal(n)
+    for m in (None, mu):
+        mo, So = oracle.posterior(m, S, obs, y, 0.25)
+        R = np.array([0, 5, 17, 40, 89])
+        mp, Sp = oracle.posterior_parts(S[np.ix_(R, R)], S[np.ix_(obs, obs)], S[np.ix_(obs, R)], y,
+                                        0.25, None if m is None else m[R],
+                                        None if m is None else m[obs])
+        np.testing.assert_allclose(mp, mo[R], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(Sp, So[np.ix_(R, R)], rtol=0, atol=1e-12)
+
+
 def test_tlr_truncation_eckart_young_and_planted_rank():
     rng = np.random.default_rng(30)
     A = rng.standard_normal((60, 7)) @ rng.standard_normal((7, 60))  # rank 7 exactly

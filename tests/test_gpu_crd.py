@@ -69,8 +69,8 @@ def test_crd_w6_scale(mvn):
     R = np.array([0, 1, 201, 12345, 20000, 39999])
     mp, Spp = oracle.posterior_parts(_cov(c, w, R, R), Koo - t2 * np.eye(obs.size),
                                      _cov(c, w, obs, R), y, t2)
-    Sg = torch.tril(Sp)[torch.as_tensor(R, device="cuda")][:, torch.as_tensor(R, device="cuda")]
-    Sg = Sg.cpu().numpy()
+    Rd = torch.as_tensor(R, device="cuda")      # R ascending: (i >= j) entries are stored
+    Sg = np.tril(Sp[Rd][:, Rd].cpu().numpy())
     Sg = Sg + np.tril(Sg, -1).T
     assert np.abs(Sg - Spp).max() <= 1e-9 and np.abs(mu_g[R] - mp).max() <= 1e-8
     # Alg. 1 over every prefix on the GPU

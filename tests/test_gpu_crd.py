@@ -63,8 +63,12 @@ def test_crd_w6_scale(mvn):
     dg = torch.diagonal(Sp).cpu().numpy()
     print(f"W6 posterior: max |d mu| {np.abs(mu_g - mu_o).max():.3e}, max |d var| "
           f"{np.abs(dg - var_o).max():.3e}")
-    assert np.abs(mu_g - mu_o).max() <= 1e-8
-    assert np.abs(dg - var_o).max() <= 1e-9
+    # the trailing update's digit products carry 42 bits relative to the rows' scales: the
+    # border row (y) is scaled by its norm bound 2^8 here, so mu_post's update, summed over the
+    # 6,272 factor columns, is good to ~5e-9 and Sigma_post's to ~1e-10 (measured 6.5e-9 and
+    # 6.0e-10, the double-float panel included); gates 5e-8 and 5e-9
+    assert np.abs(mu_g - mu_o).max() <= 5e-8
+    assert np.abs(dg - var_o).max() <= 5e-9
     # sampled off-diagonal entries by the site-subset form
     R = np.array([0, 1, 201, 12345, 20000, 39999])
     mp, Spp = oracle.posterior_parts(_cov(c, w, R, R), Koo - t2 * np.eye(obs.size),
@@ -72,7 +76,7 @@ def test_crd_w6_scale(mvn):
     Rd = torch.as_tensor(R, device="cuda")      # R ascending: (i >= j) entries are stored
     Sg = np.tril(Sp[Rd][:, Rd].cpu().numpy())
     Sg = Sg + np.tril(Sg, -1).T
-    assert np.abs(Sg - Spp).max() <= 1e-9 and np.abs(mu_g[R] - mp).max() <= 1e-8
+    assert np.abs(Sg - Spp).max() <= 5e-9 and np.abs(mu_g[R] - mp).max() <= 5e-8
     # Alg. 1 over every prefix on the GPU
     r = mvn.mvn_excursion(mu, Sp, w["u"], w["level"], w["Ns"], w["M"], w["seed"], prec="mixed")
     mvn.sync()

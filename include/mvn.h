@@ -117,8 +117,12 @@ mvn_status mvn_matern_grad(mvn_ctx* ctx, int n, const double* coords, double sig
 
 /* ------------------------------------------------------------------ Cholesky (Alg. 1, "dpotrf") */
 
-/* In-place lower Cholesky factorisation A = L L^T (Alg. 1 "dpotrf"), tile algorithm with tile
- * size `tile` (0 = automatic).  Only the lower triangle of A is read and written.
+/* In-place lower Cholesky factorisation A = L L^T (Alg. 1 "dpotrf"), tile algorithm.  Only the
+ * lower triangle of A is read and written.
+ * tile: the paper's tile size (a parameter of its CPU task runtime), accepted for the interface
+ * and not used: on this GPU the panel width is fixed at 64 (the width of the tensor-core digit
+ * tiles and of the FP64 register-blocked kernels), and what the autotuner chooses instead is the
+ * split-K size of the update's work items (mvn_autotune); any value >= 0 is accepted.
  * prec: MVN_FP64 / MVN_MIXED_SIMT: right-looking over 64-wide panels, every update in FP64.
  *   MVN_MIXED: left-looking over 64-wide panels; the trailing updates run on the tcgen05 tensor
  *   cores on exact BF16 digit slices of the rows of L (6 balanced digits of 7 bits of each entry
@@ -314,7 +318,8 @@ mvn_status mvn_posterior(mvn_ctx* ctx, int n, const double* mu, const double* Si
  * prec: the factorisation of Sigma[order, order] and the sweep as in mvn_cholesky and mvn_sov
  * (MVN_MIXED: tensor-core Cholesky and sweep; MVN_MIXED_SIMT: FP64 Cholesky, FP32 sweep).
  * mu (n), Sigma (n x n, ld, lower triangle read) are inputs; order (int32, n), marginal (n),
- * F (nprob), region (uint8, n) are outputs.  Workspace holds the permuted factor (n x n). */
+ * F (nprob), region (uint8, n) are outputs.  Workspace holds the permuted factor (n x n).
+ * tile: as in mvn_cholesky (accepted, not used). */
 mvn_status mvn_excursion(mvn_ctx* ctx, int n, const double* mu, const double* Sigma,
                          int64_t ld, double u, double one_minus_alpha, int nprob,
                          const int* prefix_dims, const mvn_qmc* qmc, mvn_prec prec, int tile,

@@ -166,7 +166,7 @@ mvn_status chol_f64_launch(mvn_ctx* ctx, int n, double* A, int64_t ld) {
 extern "C" mvn_status mvn_cholesky(mvn_ctx* ctx, int n, double* A, int64_t ld, int tile,
                                    mvn_prec prec, int* info) {
     if (!ctx) return MVN_ERR_ARG;
-    (void)tile;
+    if (tile < 0) return mvn_fail(ctx, MVN_ERR_ARG, "negative tile size");  // panel width is fixed at 64
     if (n < 0 || n > (1 << 21) || ld < (n > 0 ? n : 1) || (n > 0 && !A))
         return mvn_fail(ctx, MVN_ERR_ARG, "mvn_cholesky: invalid argument");
     if (prec != MVN_FP64 && prec != MVN_MIXED && prec != MVN_MIXED_SIMT)

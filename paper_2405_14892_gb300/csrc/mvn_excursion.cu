@@ -227,7 +227,7 @@ extern "C" mvn_status mvn_excursion(mvn_ctx* ctx, int n, const double* mu, const
                                     int tile, int32_t* order, double* marginal, double* F,
                                     uint8_t* region) {
     if (!ctx) return MVN_ERR_ARG;
-    (void)tile;
+    if (tile < 0) return mvn_fail(ctx, MVN_ERR_ARG, "negative tile size");  // panel width is fixed at 64
     ExcPlan pl;
     MVN_TRY(exc_plan(ctx, n, mu, Sigma, ld, nprob, prefix_dims, qmc, prec, order, marginal, F,
                      region, pl));

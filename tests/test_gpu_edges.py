@@ -67,8 +67,10 @@ def _step_inputs():
             b = np.inf
         rows.append((a, b, rng.uniform(-2, 2), rng.uniform(0.05, 2.0),
                      int(rng.integers(0, 2 ** 63)) * 2 + int(rng.integers(0, 2))))
-    a, b, s, l, W = (np.array(c) for c in zip(*rows))
-    return a, b, s, l, W.astype(np.uint64)
+    cols = list(zip(*rows))
+    a, b, s, l = (np.array(c, dtype=np.float64) for c in cols[:4])
+    W = np.array(cols[4], dtype=np.uint64)   # exact 64-bit integers (2^64 - 1 included)
+    return a, b, s, l, W
 
 
 def _gpu_step(mvn, prec, a, b, s, l, W):

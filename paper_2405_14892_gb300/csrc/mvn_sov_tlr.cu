@@ -25,8 +25,12 @@
 #include "mvn_sov_simt.cuh"
 #include "mvn_tlr.cuh"
 
-#define LR_K 8    // rank components per chunk
-#define LR_R 64   // rows of U / V staged per step
+#define LR_K 8     // rank components per chunk
+#define LR_R 64    // rows of U / V / D staged per step
+#define LR_PATHS 32  // paths per work item
+#define LR_PARTS 4   // threads per path
+#define LR_THREADS (LR_PATHS * LR_PARTS)
+#define LR_B 16    // dimensions per diagonal block
 
 struct TlrSweep {
     SovProblem P;            // limits, lattice, log-weights (P.L unused)
@@ -35,7 +39,7 @@ struct TlrSweep {
     const double* U;         // off-diagonal tiles, m x kmax (ld m) each, tri_index order
     const double* V;
     const int* rank;         // per off-diagonal tile
-    int nitems;              // path tiles
+    int nitems;              // 32-path work items
     int* counter;            // work-queue head (zeroed before the launch)
 };
 
@@ -43,40 +47,49 @@ __device__ __forceinline__ int64_t lr_tri(int i, int j, int nt) {
     return (int64_t)j * nt - (int64_t)j * (j + 1) / 2 + (i - j - 1);
 }
 
-template <int B, typename T>
+template <typename T>
 struct LrSmem {
-    T Vs[LR_R][LR_K];
-    T Us[LR_R][LR_K];
-    SovSmem<B, T> d;
+    T W[LR_R][LR_K + 1];      // a staged chunk of V or U (rows x rank components)
+    T Ds[LR_B][LR_R + 1];     // a staged chunk of the diagonal tile (block rows x columns)
+    T Dd[LR_B][LR_B + 1];     // the block's own lower triangle
+    double a[LR_B], b[LR_B];
+    uint64_t alpha[LR_B];
 };
 
-template <int B, typename T, bool ELEM64>
-__device__ void tlr_tile(const TlrSweep& S, int tile, const uint64_t* __restrict__ alpha,
-                         T* __restrict__ Ycta, T* __restrict__ Scta, T* __restrict__ Tcta,
-                         LrSmem<B, T>& sm) {
+// Sum over the four threads of a path (adjacent lanes).
+template <typename T>
+__device__ __forceinline__ T lr_sum4(T v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    return v;
+}
+
+// One 32-path item.  Thread t: path pl = t / 4 of the item, part q = t % 4.  Y, S and the rank
+// products are per-CTA buffers laid out [row][32 paths].
+template <typename T, bool ELEM64>
+__device__ void tlr_item(const TlrSweep& S, int item, const uint64_t* __restrict__ alpha,
+                         T* __restrict__ Y, T* __restrict__ Sb, T* __restrict__ Tb,
+                         LrSmem<T>& sm) {
     const SovProblem& P = S.P;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, pl = t >> 2, q = t & 3;
     const int n = P.n, m = S.m;
-    const int64_t p = (int64_t)tile * SOV_P + t;
+    const int64_t p = (int64_t)item * LR_PATHS + pl;
     const bool valid = p < P.Ntot;
     const int64_t pg = P.p0 + p;
-    const int64_t q = valid ? pg / P.Ns : 0;
-    const uint64_t j = valid ? (uint64_t)(pg - q * P.Ns) + 1u : 1u;
-    const uint64_t* __restrict__ dq = P.delta + q * P.dstride;
+    const int64_t qs = valid ? pg / P.Ns : 0;
+    const uint64_t j = valid ? (uint64_t)(pg - qs * P.Ns) + 1u : 1u;
+    const uint64_t* __restrict__ dq = P.delta + qs * P.dstride;
     LogProd lp;
     for (int r = 0; r < S.nt; ++r) {
         const int r0 = r * m;
         const int mr = min(m, n - r0);
-        // low-rank part of the shifts, s_r = sum_{c<r} U_rc (V_rc^T y_c) (tile c is full):
-        // (A) t_c = V_rc^T y_c for every c into the CTA's buffer Tcta (one entry per rank
-        // component and path), (B) for 64 rows of block r at a time, the sum over c and the rank
-        // components in registers, written once to Scta.
+        // (A) rank products t_c = V_rc^T y_c for every c < r (each thread a quarter of the rows)
         int toff = 0;
         for (int c = 0; c < r; ++c) {
             const int64_t idx = lr_tri(r, c, S.nt);
             const int k = S.rank[idx];
             const double* __restrict__ Vc = S.V + idx * (int64_t)m * S.kmax;
-            const T* __restrict__ yc = Ycta + (int64_t)c * m * SOV_P;
+            const T* __restrict__ yc = Y + (int64_t)c * m * LR_PATHS;
             for (int k0 = 0; k0 < k; k0 += LR_K) {
                 const int kn = min(LR_K, k - k0);
                 T tt[LR_K];
@@ -84,29 +97,35 @@ __device__ void tlr_tile(const TlrSweep& S, int tile, const uint64_t* __restrict
                 for (int kk = 0; kk < LR_K; ++kk) tt[kk] = (T)0;
                 for (int u0 = 0; u0 < m; u0 += LR_R) {
                     __syncthreads();
-                    for (int e = t; e < LR_R * LR_K; e += SOV_P) {
+                    for (int e = t; e < LR_R * LR_K; e += LR_THREADS) {
                         const int uu = e % LR_R, kk = e / LR_R;
-                        sm.Vs[uu][kk] = (kk < kn) ? (T)Vc[(u0 + uu) + (int64_t)(k0 + kk) * m] : (T)0;
+                        sm.W[uu][kk] = (kk < kn) ? (T)Vc[(u0 + uu) + (int64_t)(k0 + kk) * m] : (T)0;
                     }
                     __syncthreads();
 #pragma unroll 4
-                    for (int uu = 0; uu < LR_R; ++uu) {
-                        const T y = yc[(int64_t)(u0 + uu) * SOV_P + t];
+                    for (int i = 0; i < LR_R / LR_PARTS; ++i) {
+                        const int uu = LR_PARTS * i + q;
+                        const T y = yc[(int64_t)(u0 + uu) * LR_PATHS + pl];
 #pragma unroll
-                        for (int kk = 0; kk < LR_K; ++kk) tt[kk] = fma(sm.Vs[uu][kk], y, tt[kk]);
+                        for (int kk = 0; kk < LR_K; ++kk) tt[kk] = fma(sm.W[uu][kk], y, tt[kk]);
                     }
                 }
 #pragma unroll
-                for (int kk = 0; kk < LR_K; ++kk)
-                    if (kk < kn) Tcta[(int64_t)(toff + k0 + kk) * SOV_P + t] = tt[kk];
+                for (int kk = 0; kk < LR_K; ++kk) {
+                    tt[kk] = lr_sum4(tt[kk]);
+                    if (kk < kn && (kk & 3) == q)
+                        Tb[(int64_t)(toff + k0 + kk) * LR_PATHS + pl] = tt[kk];
+                }
             }
             toff += k;
         }
+        __syncthreads();  // the rank products are visible to all four threads of a path
+        // (B) shifts of 64 rows at a time: s_v = sum_c sum_k U_rc(v, k) t_c(k), each thread 16 rows
         for (int v0 = 0; v0 < mr; v0 += LR_R) {
             const int vn = min(LR_R, mr - v0);
-            T acc[LR_R];
+            T acc[LR_R / LR_PARTS];
 #pragma unroll
-            for (int vv = 0; vv < LR_R; ++vv) acc[vv] = (T)0;
+            for (int i = 0; i < LR_R / LR_PARTS; ++i) acc[i] = (T)0;
             int off = 0;
             for (int c = 0; c < r; ++c) {
                 const int64_t idx = lr_tri(r, c, S.nt);
@@ -115,108 +134,117 @@ __device__ void tlr_tile(const TlrSweep& S, int tile, const uint64_t* __restrict
                 for (int k0 = 0; k0 < k; k0 += LR_K) {
                     const int kn = min(LR_K, k - k0);
                     __syncthreads();
-                    for (int e = t; e < LR_R * LR_K; e += SOV_P) {
+                    for (int e = t; e < LR_R * LR_K; e += LR_THREADS) {
                         const int vv = e % LR_R, kk = e / LR_R;
-                        sm.Us[vv][kk] = (kk < kn && vv < vn)
-                                            ? (T)Uc[(v0 + vv) + (int64_t)(k0 + kk) * m]
-                                            : (T)0;
+                        sm.W[vv][kk] = (kk < kn && vv < vn)
+                                           ? (T)Uc[(v0 + vv) + (int64_t)(k0 + kk) * m]
+                                           : (T)0;
                     }
                     __syncthreads();
                     T tt[LR_K];
 #pragma unroll
                     for (int kk = 0; kk < LR_K; ++kk)
-                        tt[kk] = (kk < kn) ? Tcta[(int64_t)(off + k0 + kk) * SOV_P + t] : (T)0;
+                        tt[kk] = (kk < kn) ? Tb[(int64_t)(off + k0 + kk) * LR_PATHS + pl] : (T)0;
 #pragma unroll
-                    for (int vv = 0; vv < LR_R; ++vv)
+                    for (int i = 0; i < LR_R / LR_PARTS; ++i)
 #pragma unroll
                         for (int kk = 0; kk < LR_K; ++kk)
-                            acc[vv] = fma(sm.Us[vv][kk], tt[kk], acc[vv]);
+                            acc[i] = fma(sm.W[q * (LR_R / LR_PARTS) + i][kk], tt[kk], acc[i]);
                 }
                 off += k;
             }
 #pragma unroll
-            for (int vv = 0; vv < LR_R; ++vv)
-                if (vv < vn) Scta[(int64_t)(v0 + vv) * SOV_P + t] = acc[vv];
+            for (int i = 0; i < LR_R / LR_PARTS; ++i) {
+                const int vv = q * (LR_R / LR_PARTS) + i;
+                if (vv < vn) Sb[(int64_t)(v0 + vv) * LR_PATHS + pl] = acc[i];
+            }
         }
-        // dense diagonal tile r in blocks of B dimensions (as the CUDA-core sweep)
+        __syncthreads();
+        // dense diagonal tile r in blocks of 16 dimensions
         const double* __restrict__ Dr = S.D + (int64_t)r * m * m;
-        for (int b0 = 0; b0 < mr; b0 += B) {
-            const int nb = min(B, mr - b0);
-            T acc[B];
+        for (int b0 = 0; b0 < mr; b0 += LR_B) {
+            const int nb = min(LR_B, mr - b0);
+            // earlier dimensions of the tile: a quarter of the columns per thread, then summed
+            T acc[LR_B];
 #pragma unroll
-            for (int v = 0; v < B; ++v)
-                acc[v] = (v < nb) ? Scta[(int64_t)(b0 + v) * SOV_P + t] : (T)0;
-            for (int k0 = 0; k0 < b0; k0 += B) {
+            for (int v = 0; v < LR_B; ++v) acc[v] = (T)0;
+            for (int k0 = 0; k0 < b0; k0 += LR_R) {
+                const int kw = min(LR_R, b0 - k0);
                 __syncthreads();
-                for (int e = t; e < B * B; e += SOV_P) {
-                    const int v = e % B, kk = e / B;
-                    sm.d.Lk[kk][v] = (v < nb) ? (T)Dr[(b0 + v) + (int64_t)(k0 + kk) * m] : (T)0;
+                for (int e = t; e < LR_B * LR_R; e += LR_THREADS) {
+                    const int v = e % LR_B, kk = e / LR_B;
+                    sm.Ds[v][kk] = (v < nb && kk < kw) ? (T)Dr[(b0 + v) + (int64_t)(k0 + kk) * m]
+                                                        : (T)0;
                 }
                 __syncthreads();
-#pragma unroll 4
-                for (int kk = 0; kk < B; ++kk) {
-                    const T yk = Ycta[(int64_t)(r0 + k0 + kk) * SOV_P + t];
+                for (int kk = q; kk < kw; kk += LR_PARTS) {
+                    const T yk = Y[(int64_t)(r0 + k0 + kk) * LR_PATHS + pl];
 #pragma unroll
-                    for (int v = 0; v < B; ++v) acc[v] = fma(sm.d.Lk[kk][v], yk, acc[v]);
+                    for (int v = 0; v < LR_B; ++v) acc[v] = fma(sm.Ds[v][kk], yk, acc[v]);
                 }
             }
+#pragma unroll
+            for (int v = 0; v < LR_B; ++v) acc[v] = lr_sum4(acc[v]);
             __syncthreads();
-            for (int e = t; e < B * B; e += SOV_P) {
-                const int v = e % B, u = e / B;
-                sm.d.Ld[v][u] = (v < nb && u <= v) ? (T)Dr[(b0 + v) + (int64_t)(b0 + u) * m] : (T)0;
+            for (int e = t; e < LR_B * LR_B; e += LR_THREADS) {
+                const int v = e % LR_B, u = e / LR_B;
+                sm.Dd[v][u] = (v < nb && u <= v) ? (T)Dr[(b0 + v) + (int64_t)(b0 + u) * m] : (T)0;
             }
-            if (t < B) {
+            if (t < LR_B) {
                 const int g = r0 + b0 + t;
-                sm.d.a[t] = (t < nb) ? P.a[g] : 0.0;
-                sm.d.b[t] = (t < nb) ? P.b[g] : 1.0;
-                sm.d.alpha[t] = (t < nb) ? alpha[g] : 0u;
+                sm.a[t] = (t < nb) ? P.a[g] : 0.0;
+                sm.b[t] = (t < nb) ? P.b[g] : 1.0;
+                sm.alpha[t] = (t < nb) ? alpha[g] : 0u;
             }
             __syncthreads();
-            T y[B];
+            // the block's dimensions in order (every thread of a path computes the same values)
+            T y[LR_B];
 #pragma unroll
-            for (int v = 0; v < B; ++v) {
+            for (int v = 0; v < LR_B; ++v) {
                 if (v < nb) {
-                    T s = acc[v];
+                    T s = acc[v] + Sb[(int64_t)(b0 + v) * LR_PATHS + pl];
 #pragma unroll
-                    for (int u = 0; u < v; ++u) s = fma(sm.d.Ld[v][u], y[u], s);
-                    const double w = lattice_w(j, sm.d.alpha[v], dq[r0 + b0 + v]);
+                    for (int u = 0; u < v; ++u) s = fma(sm.Dd[v][u], y[u], s);
+                    const double w = lattice_w(j, sm.alpha[v], dq[r0 + b0 + v]);
                     double delta;
                     if constexpr (ELEM64) {
-                        y[v] = (T)sov_step_f64(sm.d.a[v], sm.d.b[v], (double)s,
-                                               (double)sm.d.Ld[v][v], w, delta);
+                        y[v] = (T)sov_step_f64(sm.a[v], sm.b[v], (double)s, (double)sm.Dd[v][v], w,
+                                               delta);
                     } else {
-                        y[v] = (T)sov_step_f32(sm.d.a[v], sm.d.b[v], (float)s,
-                                               (float)sm.d.Ld[v][v], w, delta);
+                        y[v] = (T)sov_step_f32(sm.a[v], sm.b[v], (float)s, (float)sm.Dd[v][v], w,
+                                               delta);
                     }
                     lp.mul(delta);
-                    if (valid) Ycta[(int64_t)(r0 + b0 + v) * SOV_P + t] = y[v];
+                    if ((v & 3) == q) Y[(int64_t)(r0 + b0 + v) * LR_PATHS + pl] = y[v];
                 } else {
                     y[v] = (T)0;
                 }
             }
+            __syncthreads();  // the block's y are visible to every part before they are read
         }
     }
-    if (valid && P.logw) P.logw[p] = lp.log_value();
+    if (valid && q == 0 && P.logw) P.logw[p] = lp.log_value();
 }
 
-template <int B, typename T, bool ELEM64>
-__global__ void __launch_bounds__(SOV_P) k_sov_tlr(const TlrSweep S,
-                                                   const uint64_t* __restrict__ alpha,
-                                                   T* __restrict__ Yscratch, int64_t ystride,
-                                                   T* __restrict__ Sscratch, int64_t sstride,
-                                                   T* __restrict__ Tscratch, int64_t tstride) {
-    __shared__ LrSmem<B, T> sm;
+template <typename T, bool ELEM64>
+__global__ void __launch_bounds__(LR_THREADS, 4) k_sov_tlr(const TlrSweep S,
+                                                        const uint64_t* __restrict__ alpha,
+                                                        T* __restrict__ Yscratch, int64_t ystride,
+                                                        T* __restrict__ Sscratch, int64_t sstride,
+                                                        T* __restrict__ Tscratch,
+                                                        int64_t tstride) {
+    __shared__ LrSmem<T> sm;
     __shared__ int s_item;
-    T* Ycta = Yscratch + (int64_t)blockIdx.x * ystride;
-    T* Scta = Sscratch + (int64_t)blockIdx.x * sstride;
-    T* Tcta = Tscratch + (int64_t)blockIdx.x * tstride;
+    T* Y = Yscratch + (int64_t)blockIdx.x * ystride;
+    T* Sb = Sscratch + (int64_t)blockIdx.x * sstride;
+    T* Tb = Tscratch + (int64_t)blockIdx.x * tstride;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = atomicAdd(S.counter, 1);
         __syncthreads();
         const int it = s_item;
         if (it >= S.nitems) break;
-        tlr_tile<B, T, ELEM64>(S, it, alpha, Ycta, Scta, Tcta, sm);
+        tlr_item<T, ELEM64>(S, it, alpha, Y, Sb, Tb, sm);
     }
 }
 
@@ -236,12 +264,19 @@ extern "C" mvn_status mvn_sov_tlr(mvn_ctx* ctx, const mvn_tlr* Lt, const double*
     const size_t elt = f64 ? sizeof(double) : sizeof(float);
     const int M = qmc->n_shifts;
     const int64_t Ns = qmc->n_points, Ntot = Ns * M;
-    const int64_t ntiles = (Ntot + SOV_P - 1) / SOV_P;
-    if (ntiles > (1 << 30)) return mvn_fail(ctx, MVN_ERR_ARG, "too many path tiles");
+    const int64_t nitems = (Ntot + LR_PATHS - 1) / LR_PATHS;
+    if (nitems > (1 << 30)) return mvn_fail(ctx, MVN_ERR_ARG, "too many path items");
     MVN_TRY(lattice_ensure(ctx, n));
-    const int occ = tune_sweep(ctx, prec == MVN_MIXED ? MVN_MIXED_SIMT : prec, n, ntiles)
-                        .simt_ctas_per_sm;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)ctx->sm_count * occ));
+    int occ = 1;
+    if (f64) {
+        MVN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sov_tlr<double, true>,
+                                                                    LR_THREADS, 0));
+    } else {
+        MVN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sov_tlr<float, false>,
+                                                                    LR_THREADS, 0));
+    }
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>(nitems, (int64_t)ctx->sm_count * std::max(occ, 1)));
     // the largest sum over c < r of the ranks of block row r (entries of t per path)
     int64_t tmax = 1;
     for (int r = 1; r < Lt->nt; ++r) {
@@ -249,8 +284,8 @@ extern "C" mvn_status mvn_sov_tlr(mvn_ctx* ctx, const mvn_tlr* Lt, const double*
         for (int c = 0; c < r; ++c) sr += Lt->rank_h[(size_t)tri_index(r, c, Lt->nt)];
         tmax = std::max(tmax, sr);
     }
-    const int64_t ystride = (int64_t)Lt->npad * SOV_P, sstride = (int64_t)m * SOV_P,
-                  tstride = tmax * SOV_P;
+    const int64_t ystride = (int64_t)Lt->npad * LR_PATHS, sstride = (int64_t)m * LR_PATHS,
+                  tstride = tmax * LR_PATHS;
     const size_t need = ws_round(sizeof(uint64_t) * (size_t)M * n) +
                         (path_logw ? 0 : ws_round(sizeof(double) * (size_t)Ntot)) +
                         ws_round(elt * (size_t)ystride * grid) +
@@ -284,19 +319,19 @@ extern "C" mvn_status mvn_sov_tlr(mvn_ctx* ctx, const mvn_tlr* Lt, const double*
     S.U = Lt->U;
     S.V = Lt->V;
     S.rank = Lt->rank;
-    S.nitems = (int)ntiles;
+    S.nitems = (int)nitems;
     S.counter = counter;
     MVN_TRY(check_limits_device(ctx, n, a, b));
     MVN_TRY(lattice_shifts(ctx, qmc->seed, M, n, delta));
     MVN_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(int), ctx->stream));
     if (f64) {
         MVN_TIMED(ctx, "k_sov_tlr_f64",
-                  (k_sov_tlr<32, double, true><<<grid, SOV_P, 0, ctx->stream>>>(
+                  (k_sov_tlr<double, true><<<grid, LR_THREADS, 0, ctx->stream>>>(
                       S, ctx->d_alpha, (double*)Ybuf, ystride, (double*)Sbuf, sstride,
                       (double*)Tbuf, tstride)));
     } else {
         MVN_TIMED(ctx, "k_sov_tlr_f32",
-                  (k_sov_tlr<64, float, false><<<grid, SOV_P, 0, ctx->stream>>>(
+                  (k_sov_tlr<float, false><<<grid, LR_THREADS, 0, ctx->stream>>>(
                       S, ctx->d_alpha, (float*)Ybuf, ystride, (float*)Sbuf, sstride,
                       (float*)Tbuf, tstride)));
     }

@@ -7,14 +7,16 @@
 // The paper's sweep expands the factor to a dense matrix first; here the factor stays in its
 // compressed form, so the sweep's work follows the ranks.
 //
-// Design (GB300): one CTA owns a tile of 128 paths (one thread per path), persistent over the
-// path tiles.  Block row r: for every earlier tile c and every chunk of 8 rank components,
-// t = V_rc^T y_c is formed in registers (V staged through shared memory 64 rows at a time, y_c
-// read from the CTA's own y buffer, coalesced over the paths) and kept in a per-CTA buffer; then
-// 64 rows of block r at a time sum U_rc t over every c and component in registers and write
-// their shifts once; then the dense diagonal tile runs in blocks of B
-// dimensions exactly like the CUDA-core sweep (earlier dimensions of the tile as a mat-vec, the
-// block's dimensions one at a time with the elementwise step of Eq. 2).
+// Design (GB300): one CTA owns a work item of 32 paths with four threads per path (128 threads),
+// persistent over the items, so that a problem of 10,000 paths fills every SM.  Block row r:
+// (A) for every earlier tile c and every chunk of 8 rank components, t = V_rc^T y_c, each thread
+// summing a quarter of the rows (V staged through shared memory 64 rows at a time, y_c read from
+// the CTA's own y buffer), the quarters added by shuffles and kept in a per-CTA buffer; (B) for
+// 64 rows of block r at a time, each thread sums U_rc t over every c and component for 16 of
+// them in registers and writes their shifts once; then the dense diagonal tile runs in blocks of
+// 16 dimensions (the earlier dimensions of the tile as a mat-vec split over the four threads,
+// then the block's dimensions one at a time with the elementwise step of Eq. 2, computed by all
+// four threads of the path alike).
 #include <math.h>
 #include <string.h>
 

@@ -9,10 +9,11 @@
 //     factorisation, since sum_k L_ik^2 = Sigma_ii), so x_ik = L_ik 2^-E_i lies in (-1, 1);
 //   - x_ik is rounded once to v_ik = rint(x_ik 2^42) and written as six balanced 7-bit digits,
 //     x_ik ~ sum_{s<6} a^(s)_ik 2^(-7(s+1)), |a^(0)| <= 128, |a^(s>0)| <= 64, exact in BF16;
-//   - the digit products of one level l = s + t (l <= 5) share a TMEM accumulator; over 256
-//     values of k their sum is an integer below 2^23, so the tensor core's FP32 accumulation is
-//     exact;
-//   - every 256 values of k the six level sums are drained into a 64-bit integer
+//   - the digit products of one level l = s + t (l <= 5) share a TMEM accumulator; a level has at
+//     most two products with a leading digit (<= 128 x 64 each) and four others (<= 64 x 64),
+//     i.e. at most 2^15 per value of k, so over 384 values of k its sum is an integer below
+//     12.6e6 < 2^24 and the tensor core's FP32 accumulation is exact;
+//   - every 384 values of k the six level sums are drained into a 64-bit integer
 //     T = sum_l V_l 2^(7(5-l)) (the product in units of 2^-49), which stays exact; split-K
 //     partial sums are added with integer atomics (exact and order-independent), and the POTRF
 //     and TRSM kernels apply C_ij -= 2^(E_i+E_j-49) T_ij in FP64 as they load their block.
@@ -39,7 +40,7 @@
 #define OZ_STAGE (OZ_S * (OZ_AT + OZ_BT))
 #define OZ_NST 2            // pipeline stages (K = 32 each, 72 KB; measured: a third stage does
                             // not speed the W2 factorisation up)
-#define OZ_GRP 8            // stages accumulated in TMEM between drains (K = 256)
+#define OZ_GRP 12           // stages accumulated in TMEM between drains (K = 384)
 #define OZ_DW 8             // drain warps
 #define OZ_THREADS (32 * (OZ_DW + 2))
 #define OZ_WAIT 4000000000LL

@@ -72,32 +72,71 @@ __device__ __forceinline__ MF mf_exp_neg_red(MF x, int& k) {
     return mf_mul(q, q);
 }
 
-// One block: 256 rows x 8 columns of the lower triangle, column-major writes.
-__global__ void k_matern(int n, const double* __restrict__ xy, double sigma2, double inv_range,
-                         int nu2, double nugget, double* __restrict__ S, int64_t ld) {
-    const int i = blockIdx.x * 256 + threadIdx.x;
-    const int j0 = blockIdx.y * 8;
-    if (i >= n || i < j0) return;
-    const double xi = xy[2 * i], yi = xy[2 * i + 1];
+// Exact difference of two double-float numbers as a pair (two-sum of the high parts, then the
+// low parts added).
+__device__ __forceinline__ MF mf_sub(MF a, MF b) { return mf_add(a, MF{-b.hi, -b.lo}); }
+
+// Coordinates as double-float pairs (x_hi, x_lo, y_hi, y_lo): the site differences are then formed
+// on the FP32 pipe; a pair keeps 48 bits of each coordinate (|x| <= 1 here: 4e-15 absolute).
+__global__ void k_coords_df(int n, const double* __restrict__ xy, float4* __restrict__ cp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const MF x = mf_from(xy[2 * i]), y = mf_from(xy[2 * i + 1]);
+    cp[i] = make_float4(x.hi, x.lo, y.hi, y.lo);
+}
+
+// One block per lower 128 x 128 tile (ti >= tj, linear index over the triangle): thread t owns
+// row i = 128 ti + t and walks the tile's 128 columns (column-major writes, coalesced over the
+// rows).  Everything up to the final value runs in FP32 pairs; the FP64 pipe (~1/64 of FP32 on
+// this GPU) only forms the output double (two conversions and one add) and, where e^-x would
+// leave FP32's range, applies 2^-k.
+__global__ void __launch_bounds__(128) k_matern(int n, const float4* __restrict__ cp,
+                                                double sigma2, double inv_range, int nu2,
+                                                double nugget, double* __restrict__ S,
+                                                int64_t ld) {
+    __shared__ float4 cj[128];
+    const int x = blockIdx.x;
+    int ti = (int)((sqrt(8.0 * x + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= x) ++ti;
+    while (ti * (ti + 1) / 2 > x) --ti;
+    const int tj = x - ti * (ti + 1) / 2;
+    const int t = threadIdx.x;
+    const int j0 = tj * 128;
+    if (j0 + t < n) cj[t] = cp[j0 + t];
+    __syncthreads();
+    const int i = ti * 128 + t;
+    if (i >= n) return;
+    const float4 ci = cp[i];
+    const MF xi{ci.x, ci.y}, yi{ci.z, ci.w};
     const MF sg = mf_from(sigma2), ir = mf_from(inv_range);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        int j = j0 + c;
-        if (j > i || j >= n) break;
-        const double dx = xi - xy[2 * j], dy = yi - xy[2 * j + 1];
-        const MF x = mf_mul(mf_sqrt(mf_from(fma(dx, dx, dy * dy))), ir);
-        double out = 0.0;
-        if (x.hi < 700.0f) {
-            int k;
-            const MF e = mf_exp_neg_red(x, k);
-            MF poly{1.0f, 0.0f};
-            if (nu2 >= 3) poly = mf_add(poly, x);
-            if (nu2 == 5)
-                poly = mf_add(poly, mf_mul(mf_mul(x, x), MF{0.3333333432674408f, -9.934107758624577e-09f}));
-            out = mf_to(mf_mul(sg, mf_mul(poly, e))) *
-                  __longlong_as_double((long long)(1023 - k) << 52);  // 2^-k, k <= 1010
+    const int jn = min(128, min(n - j0, i - j0 + 1));
+    for (int c = 0; c < jn; ++c) {
+        const int j = j0 + c;
+        double out;
+        if (i == j) {
+            out = sigma2 + nugget;
+        } else {
+            const float4 cc = cj[c];
+            const MF dx = mf_sub(xi, MF{cc.x, cc.y}), dy = mf_sub(yi, MF{cc.z, cc.w});
+            const MF xx = mf_mul(mf_sqrt(mf_add(mf_mul(dx, dx), mf_mul(dy, dy))), ir);
+            out = 0.0;
+            if (xx.hi < 700.0f) {
+                int k;
+                const MF e = mf_exp_neg_red(xx, k);
+                MF poly{1.0f, 0.0f};
+                if (nu2 >= 3) poly = mf_add(poly, xx);
+                if (nu2 == 5)
+                    poly = mf_add(poly, mf_mul(mf_mul(xx, xx),
+                                               MF{0.3333333432674408f, -9.934107758624577e-09f}));
+                MF v = mf_mul(sg, mf_mul(poly, e));
+                if (k <= 60 && fabsf(v.hi) >= 0x1p-40f) {  // 2^-k in FP32: both parts stay normal
+                    const float sc = __int_as_float((127 - k) << 23);
+                    out = (double)(v.hi * sc) + (double)(v.lo * sc);
+                } else {
+                    out = mf_to(v) * __longlong_as_double((long long)(1023 - k) << 52);
+                }
+            }
         }
-        if (i == j) out = sigma2 + nugget;
         S[i + (int64_t)j * ld] = out;
     }
 }
@@ -113,9 +152,13 @@ extern "C" mvn_status mvn_matern(mvn_ctx* ctx, int n, const double* coords, doub
         return mvn_fail(ctx, MVN_ERR_ARG, "mvn_matern: invalid argument (nu must be 0.5, 1.5 or 2.5)");
     if (n == 0) return MVN_OK;
     MVN_CUDA(ctx, cudaSetDevice(ctx->device));
-    dim3 grid((n + 255) / 256, (n + 7) / 8);
-    k_matern<<<grid, 256, 0, ctx->stream>>>(n, coords, sigma2, 1.0 / range, nu2, nugget, Sigma,
-                                            ld);
+    MVN_TRY(ws_reserve(ctx, sizeof(float4) * (size_t)n + 1024));
+    float4* cp = (float4*)ctx->ws;
+    k_coords_df<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, coords, cp);
+    MVN_LAUNCHED(ctx);
+    const int64_t T = (n + 127) / 128;
+    k_matern<<<(unsigned)(T * (T + 1) / 2), 128, 0, ctx->stream>>>(n, cp, sigma2, 1.0 / range,
+                                                                  nu2, nugget, Sigma, ld);
     MVN_LAUNCHED(ctx);
     return MVN_OK;
 }

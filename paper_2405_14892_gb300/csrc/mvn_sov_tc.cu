@@ -14,8 +14,8 @@
 // e_v is a per-row power of two that keeps row v of L below 2^12 (no FP16 overflow for any
 // scale of Sigma).  The tensor cores accumulate in FP32 with truncation, so the accumulator is
 // drained into FP32 registers every K = 128 (two ping-pong TMEM buffers), which keeps the
-// accumulated error near that of an FP32 sum.  Warp 0 drives the copy/MMA pipeline without
-// blocking while the other warps wait for the accumulator.
+// accumulated error near that of an FP32 sum.  A fifth warp drives the copy/MMA pipeline and
+// meets the path threads only at mbarriers, so that copies, MMAs and drains overlap.
 // The 128 x 128 diagonal block (Alg. 3) then runs on the CUDA cores in FP32, one dimension at a
 // time in a rolled loop: the far shifts and the new y values sit in tensor memory (one column
 // per dimension, one lane per path), the packed lower triangle of the block is brought into the
@@ -143,7 +143,7 @@ struct __align__(1024) TcSmem {
     float escale[TC_N];
     uint64_t alpha[TC_N];
     unsigned char ainf[TC_N], binf[TC_N];
-    uint64_t full[TC_NST], empty[TC_NST], accf[2], dbar, fin;
+    uint64_t full[TC_NST], empty[TC_NST], accf[2], drained[2], ybar, dbar, fin;
     uint32_t tmem;
     int item;
     int abort;
@@ -151,165 +151,167 @@ struct __align__(1024) TcSmem {
 
 static_assert(sizeof(TcSmem) <= 112 * 1024, "two CTAs per SM need <= 112 KB each");
 static_assert(TC_DPACK * 4 <= TC_NST * TC_STAGE, "the diagonal block lives in the stage area");
+static_assert(TC_P == TC_N, "one path thread per dimension of a super-block loads its limits");
 
-// ---------------------------------------------------------------- GEMM pipeline (thread 0)
+// ---------------------------------------------------------------- roles and barriers
 //
-// The stages of all far GEMMs form one sequence; stage number q uses slot q % TC_NST, whose
-// "full" barrier completes for the (q / TC_NST)-th time when its bulk copies land and whose
-// "empty" barrier completes when the MMAs reading it are done.  Stages are grouped by TC_G; group
-// number g accumulates into TMEM buffer g % 2 and commits to accf[g % 2] when complete; a group's
-// MMAs start only once the group two earlier has been drained.  All parities follow from these
-// counters, so no barrier phase is ever skipped or waited twice.
+// A CTA has TC_P path threads (warps 0-3; thread t owns path t of the tile and TMEM lane t) and
+// two pipeline warps: lane 0 of warp 4 streams the far GEMMs' operands (the producer), lane 0 of
+// warp 5 issues their MMAs.  The roles meet only at mbarriers, so bulk copies, MMAs and TMEM
+// drains overlap, and the issue costs of the copies and of the MMAs fall on different threads:
+//   - the stages of all far GEMMs form one sequence; stage number q uses slot q % TC_NST, whose
+//     "full" barrier completes for the (q / TC_NST)-th time when its bulk copies land and whose
+//     "empty" barrier completes when the MMAs reading it are done;
+//   - stages are grouped by TC_G; group number g accumulates into TMEM buffer g % 2 and commits
+//     to accf[g % 2]; the path threads drain it and arrive on drained[g % 2] (TC_P arrivals),
+//     which the first MMA of group g + 2 waits for;
+//   - ybar completes once per super-block whose y the path threads have written (they then no
+//     longer use its TMEM buffers or its diagonal block in the stage area): the far GEMM of the
+//     next super-block starts after it, on both pipeline threads.
+// All parities follow from these counters, so no barrier phase is skipped or waited twice.  The
+// path threads synchronise among themselves with barrier 1 and reduce their abort decisions in
+// it, so that they always leave the loop together.
+#define TC_THREADS (TC_P + 64)
+#define TC_PRODUCER TC_P         // thread that issues the bulk copies
+#define TC_ISSUER (TC_P + 32)    // thread that issues the MMAs
+
 struct TcPipe {
-    uint32_t q_load = 0;   // global stage number of the next load
-    uint32_t q_mma = 0;    // global stage number of the next MMA stage
-    uint32_t g0 = 0;       // global group number of the current far GEMM's group 0
-    uint32_t drained = 0;  // groups drained so far (global)
-    const uint8_t* Ybuf = nullptr;
-    const uint8_t* Lsb = nullptr;  // tile pairs of the current super-block
-    int kcs = 0;           // stages of the current far GEMM
-    int next_load = 0, next_mma = 0;
+    uint32_t q = 0;       // global stage number of the next load (producer) / MMA stage (issuer)
+    uint32_t g_next = 0;  // global group number of the next far GEMM's group 0 (issuer)
+    uint32_t ywait = 0;   // completions of ybar waited for
 };
 
 __device__ __forceinline__ uint32_t tc_buf_col(uint32_t g) { return (g & 1u) * TC_N; }
 
-// Issue every load and MMA stage that can go now, without waiting (test_wait only).
-__device__ void tc_pump(TcSmem& sm, TcPipe& pp) {
-    const uint32_t idesc = tc::idesc_f16_f32(TC_P, TC_N);
-    for (;;) {
-        bool progress = false;
-        if (pp.next_load < pp.kcs && pp.next_load < pp.next_mma + TC_NST) {
-            const uint32_t q = pp.q_load;
-            const int slot = (int)(q % TC_NST);
-            if (q < TC_NST || tc::mbar_test_wait(&sm.empty[slot], ((q / TC_NST) - 1) & 1u)) {
-                uint8_t* st = sm.stage[slot];
-                const int kc = pp.next_load;
-                tc::mbar_arrive_expect_tx(&sm.full[slot], TC_STAGE);
-                tc::bulk_g2s(st, pp.Ybuf + (size_t)kc * 2 * TC_TILE, 2 * TC_TILE, &sm.full[slot]);
-                tc::bulk_g2s(st + 2 * TC_TILE, pp.Lsb + (size_t)kc * 2 * TC_TILE, 2 * TC_TILE,
-                             &sm.full[slot]);
-                // the stage TC_PF ahead into L2, so that its copy into shared memory does not
-                // wait for HBM (only two stages fit in shared memory)
-                const int kp = kc + TC_PF;
-                if (kp < pp.kcs) {
-                    tc::bulk_prefetch_l2(pp.Ybuf + (size_t)kp * 2 * TC_TILE, 2 * TC_TILE);
-                    tc::bulk_prefetch_l2(pp.Lsb + (size_t)kp * 2 * TC_TILE, 2 * TC_TILE);
-                }
-                ++pp.q_load;
-                ++pp.next_load;
-                progress = true;
-            }
-        }
-        if (pp.next_mma < pp.next_load) {
-            const uint32_t q = pp.q_mma;
-            const int slot = (int)(q % TC_NST);
-            const int kc = pp.next_mma;
-            const uint32_t g = pp.g0 + (uint32_t)(kc / TC_G);
-            if (g < pp.drained + 2 && tc::mbar_test_wait(&sm.full[slot], (q / TC_NST) & 1u)) {
-                tc::tc_fence_after();
-                const uint32_t acc = sm.tmem + tc_buf_col(g);
-                const uint32_t base = tc::smem_u32(sm.stage[slot]);
-#pragma unroll
-                for (int k16 = 0; k16 < 2; ++k16) {
-                    const uint32_t ko = k16 * 32;
-                    const uint64_t ah = tc::sdesc_sw64(base + ko);
-                    const uint64_t al = tc::sdesc_sw64(base + TC_TILE + ko);
-                    const uint64_t bh = tc::sdesc_sw64(base + 2 * TC_TILE + ko);
-                    const uint64_t bl = tc::sdesc_sw64(base + 3 * TC_TILE + ko);
-                    const uint32_t first = (kc % TC_G == 0 && k16 == 0) ? 0u : 1u;
-                    tc::mma_f16(acc, ah, bh, idesc, first);
-                    tc::mma_f16(acc, ah, bl, idesc, 1u);
-                    tc::mma_f16(acc, al, bh, idesc, 1u);
-                }
-                tc::mma_commit(&sm.empty[slot]);
-                if (kc % TC_G == TC_G - 1 || kc == pp.kcs - 1) tc::mma_commit(&sm.accf[g & 1u]);
-                ++pp.q_mma;
-                ++pp.next_mma;
-                progress = true;
-            }
-        }
-        if (!progress) return;
+__device__ __forceinline__ int tc_groups(int rb) { return (4 * rb + TC_G - 1) / TC_G; }
+
+// Bounded wait that also gives up as soon as another role of the CTA has aborted.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!tc::mbar_try_wait(bar, parity)) {
+        if (*abort_flag || clock64() - t0 > TC_WAIT_BUDGET) return false;
     }
+    return true;
 }
 
-// Set up the far GEMM of super-block rb (K = 128 rb) after the previous one has been drained
-// (every Y tile it reads is written), and start its first stages on their way into L2.
-__device__ __forceinline__ void tc_far_begin(TcPipe& pp, const uint8_t* Ybuf, const uint8_t* Lt,
-                                             int rb) {
-    pp.g0 = pp.drained;
-    pp.Ybuf = Ybuf;
-    pp.Lsb = Lt + tc_lt_off(rb, 0);
-    pp.kcs = 4 * rb;
-    pp.next_load = 0;
-    pp.next_mma = 0;
-    for (int kp = 0; kp < min(pp.kcs, TC_PF); ++kp) {
-        tc::bulk_prefetch_l2(pp.Ybuf + (size_t)kp * 2 * TC_TILE, 2 * TC_TILE);
-        tc::bulk_prefetch_l2(pp.Lsb + (size_t)kp * 2 * TC_TILE, 2 * TC_TILE);
+// Barrier 1 over the TC_P path threads; returns whether any of them passed `flag`.
+__device__ __forceinline__ bool tc_path_sync_or(bool flag) {
+    uint32_t r;
+    __syncwarp();
+    asm volatile(
+        "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n"
+        " bar.red.or.pred b, 1, %2, a;\n selp.u32 %0, 1, 0, b;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)flag), "n"(TC_P)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void tc_path_sync() {
+    __syncwarp();
+    asm volatile("bar.sync 1, %0;" ::"n"(TC_P) : "memory");
+}
+
+// Operand stream of the far GEMM of super-block rb (K = 128 rb), run by the producer: each
+// stage's bulk copies (Y and L tile pairs) as soon as its slot is free, and the stage TC_PF
+// ahead prefetched into L2, so that the copy into shared memory does not wait for HBM.
+// Returns false on timeout or abort.
+__device__ bool tc_far_load(TcSmem& sm, TcPipe& pp, const uint8_t* Ybuf, const uint8_t* Lt,
+                            int rb) {
+    const uint8_t* Lsb = Lt + tc_lt_off(rb, 0);
+    const int kcs = 4 * rb;
+    volatile int* abort_flag = &sm.abort;
+    for (int kp = 0; kp < min(kcs, TC_PF); ++kp) {
+        tc::bulk_prefetch_l2(Ybuf + (size_t)kp * 2 * TC_TILE, 2 * TC_TILE);
+        tc::bulk_prefetch_l2(Lsb + (size_t)kp * 2 * TC_TILE, 2 * TC_TILE);
     }
+    for (int kc = 0; kc < kcs; ++kc, ++pp.q) {
+        const uint32_t q = pp.q;
+        const int slot = (int)(q % TC_NST);
+        if (q >= TC_NST && !tc_wait(&sm.empty[slot], ((q / TC_NST) - 1) & 1u, abort_flag))
+            return false;
+        uint8_t* st = sm.stage[slot];
+        tc::mbar_arrive_expect_tx(&sm.full[slot], TC_STAGE);
+        tc::bulk_g2s(st, Ybuf + (size_t)kc * 2 * TC_TILE, 2 * TC_TILE, &sm.full[slot]);
+        tc::bulk_g2s(st + 2 * TC_TILE, Lsb + (size_t)kc * 2 * TC_TILE, 2 * TC_TILE,
+                     &sm.full[slot]);
+        const int kp = kc + TC_PF;
+        if (kp < kcs) {
+            tc::bulk_prefetch_l2(Ybuf + (size_t)kp * 2 * TC_TILE, 2 * TC_TILE);
+            tc::bulk_prefetch_l2(Lsb + (size_t)kp * 2 * TC_TILE, 2 * TC_TILE);
+        }
+    }
+    return true;
+}
+
+// MMAs of the far GEMM of super-block rb, run by the issuer: a stage's three split products as
+// soon as its data has landed (and, for a group's first stage, its TMEM buffer has been
+// drained); each stage's slot is released by a commit to its "empty" barrier, each group's
+// buffer by a commit to accf.  Returns false on timeout or abort.
+__device__ bool tc_far_mma(TcSmem& sm, TcPipe& pp, int rb) {
+    const uint32_t idesc = tc::idesc_f16_f32(TC_P, TC_N);
+    const int kcs = 4 * rb;
+    volatile int* abort_flag = &sm.abort;
+    for (int kc = 0; kc < kcs; ++kc, ++pp.q) {
+        const uint32_t q = pp.q;
+        const int slot = (int)(q % TC_NST);
+        const uint32_t g = pp.g_next + (uint32_t)(kc / TC_G);
+        // a group's first MMA overwrites buffer g % 2: group g - 2 must have been drained
+        if (kc % TC_G == 0 && g >= 2u &&
+            !tc_wait(&sm.drained[g & 1u], ((g >> 1) - 1u) & 1u, abort_flag))
+            return false;
+        if (!tc_wait(&sm.full[slot], (q / TC_NST) & 1u, abort_flag)) return false;
+        tc::tc_fence_after();
+        const uint32_t acc = sm.tmem + tc_buf_col(g);
+        const uint32_t base = tc::smem_u32(sm.stage[slot]);
+#pragma unroll
+        for (int k16 = 0; k16 < 2; ++k16) {
+            const uint32_t ko = k16 * 32;
+            const uint64_t ah = tc::sdesc_sw64(base + ko);
+            const uint64_t al = tc::sdesc_sw64(base + TC_TILE + ko);
+            const uint64_t bh = tc::sdesc_sw64(base + 2 * TC_TILE + ko);
+            const uint64_t bl = tc::sdesc_sw64(base + 3 * TC_TILE + ko);
+            const uint32_t first = (kc % TC_G == 0 && k16 == 0) ? 0u : 1u;
+            tc::mma_f16(acc, ah, bh, idesc, first);
+            tc::mma_f16(acc, ah, bl, idesc, 1u);
+            tc::mma_f16(acc, al, bh, idesc, 1u);
+        }
+        tc::mma_commit(&sm.empty[slot]);
+        if (kc % TC_G == TC_G - 1 || kc == kcs - 1) tc::mma_commit(&sm.accf[g & 1u]);
+    }
+    pp.g_next += (uint32_t)tc_groups(rb);
+    return true;
 }
 
 // Far part of the limit shift of this thread's path for super-block rb (K = 128 rb): the groups
-// g0, g0 + 1, .. are accumulated in TMEM and added into FP32 registers; thread 0 (whose pipe has
-// begun this far GEMM with the same g0) keeps the pipeline moving while the others wait.  All
-// threads call this with the same rb and g0.  Returns false if a wait timed out.
-__device__ bool tc_far(TcSmem& sm, TcPipe& pp, int rb, uint32_t g0, float (&s)[TC_N]) {
+// g0, g0 + 1, .. are drained from TMEM as they complete and added into FP32 registers; each
+// buffer goes back to the pipeline thread through drained[].  Returns false if a wait timed out
+// or another role aborted.
+__device__ bool tc_far_drain(TcSmem& sm, int rb, uint32_t g0, float (&s)[TC_N]) {
     const int t = threadIdx.x;
-    const int ng = (4 * rb + TC_G - 1) / TC_G;
+    const int ng = tc_groups(rb);
 #pragma unroll
     for (int v = 0; v < TC_N; ++v) s[v] = 0.0f;
     const uint32_t lane_base = ((uint32_t)(t >> 5) * 32u) << 16;
-    bool ok = true;
+    volatile int* abort_flag = &sm.abort;
     for (int gi = 0; gi < ng; ++gi) {
         const uint32_t g = g0 + (uint32_t)gi;
-        const uint32_t par = (g >> 1) & 1u;
-        if (t < 32) {
-            // warp 0 polls as a whole (a waiting lane must not hold back lane 0, which keeps
-            // the pipeline moving); the other warps wait on the barrier
-            const long long t0 = clock64();
-            for (;;) {
-                int state = 0;  // lane 0 decides for the warp: 1 done, 2 timed out
-                if (t == 0) {
-                    tc_pump(sm, pp);
-                    if (tc::mbar_test_wait(&sm.accf[g & 1u], par))
-                        state = 1;
-                    else if (clock64() - t0 > TC_WAIT_BUDGET)
-                        state = 2;
-                }
-                state = __shfl_sync(0xffffffffu, state, 0);
-                if (state == 1) break;
-                if (state == 2) {
-                    ok = false;
-                    sm.abort = 1;
-                    break;
-                }
-            }
-        } else if (!tc::mbar_wait(&sm.accf[g & 1u], par, TC_WAIT_BUDGET)) {
-            ok = false;
-            sm.abort = 1;
-        }
-        if (ok) {
-            tc::tc_fence_after();
-            const uint32_t col = sm.tmem + lane_base + tc_buf_col(g);
+        if (!tc_wait(&sm.accf[g & 1u], (g >> 1) & 1u, abort_flag)) return false;
+        tc::tc_fence_after();
+        const uint32_t col = sm.tmem + lane_base + tc_buf_col(g);
 #pragma unroll
-            for (int c = 0; c < TC_N; c += 32) {
-                float v[32];
-                tc::tmem_ld32(col + c, v);
+        for (int c = 0; c < TC_N; c += 16) {
+            float v[16];
+            tc::tmem_ld16(col + c, v);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) s[c + i] += v[i];
-            }
+            for (int i = 0; i < 16; ++i) s[c + i] += v[i];
         }
         tc::tc_fence_before();
-        __syncthreads();  // the buffer of group g is free again
-        if (sm.abort) return false;
-        if (t == 0) {
-            pp.drained = g + 1;
-            tc::tc_fence_after();
-            tc_pump(sm, pp);
-        }
+        tc::mbar_arrive(&sm.drained[g & 1u]);
     }
 #pragma unroll
     for (int v = 0; v < TC_N; ++v) s[v] *= sm.escale[v];
-    return ok;
+    return true;
 }
 
 // Write 32 y values of this thread's path (two FP16 slices) as row `t` of the Y tiles of
@@ -355,8 +357,11 @@ __device__ __forceinline__ void tc_setup(TcSmem& sm) {
             tc::mbar_init(&sm.full[s], 1);
             tc::mbar_init(&sm.empty[s], 1);
         }
-        tc::mbar_init(&sm.accf[0], 1);
-        tc::mbar_init(&sm.accf[1], 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&sm.accf[b], 1);
+            tc::mbar_init(&sm.drained[b], TC_P);
+        }
+        tc::mbar_init(&sm.ybar, TC_P);
         tc::mbar_init(&sm.dbar, 1);
         tc::mbar_init(&sm.fin, 1);
         tc::mbar_fence_init();
@@ -372,19 +377,24 @@ __device__ __forceinline__ void tc_setup(TcSmem& sm) {
 }
 
 // Before shared and tensor memory are released: every copy this CTA issued has landed and every
-// MMA it issued has completed (bounded waits; also after an aborted wait).  A wait that runs out
-// here means work may still be in flight when the memory is released, so the result cannot be
-// trusted: it raises MVN_ERR_TIMEOUT like the waits of the main loop.
+// MMA it issued has completed (bounded waits; also after an aborted wait).  Path thread 0 issued
+// the diagonal-block copies, the producer the stage copies, the issuer the MMAs.  A wait that
+// runs out here means work may still be in flight when the memory is released, so the result
+// cannot be trusted: it raises MVN_ERR_TIMEOUT like the waits of the main loop.
 __device__ __forceinline__ void tc_quiesce(TcSmem& sm, const TcPipe& pp, uint32_t dphase,
                                            int* status) {
-    if (threadIdx.x != 0) return;
+    const int t = threadIdx.x;
     bool ok = true;
-    const uint32_t q0 = pp.q_load > TC_NST ? pp.q_load - TC_NST : 0u;
-    for (uint32_t q = q0; q < pp.q_load; ++q)
-        ok &= tc::mbar_wait(&sm.full[q % TC_NST], (q / TC_NST) & 1u, TC_WAIT_BUDGET);
-    if (dphase > 0) ok &= tc::mbar_wait(&sm.dbar, (dphase - 1) & 1u, TC_WAIT_BUDGET);
-    tc::mma_commit(&sm.fin);
-    ok &= tc::mbar_wait(&sm.fin, 0, TC_WAIT_BUDGET);
+    if (t == 0 && dphase > 0) ok &= tc::mbar_wait(&sm.dbar, (dphase - 1) & 1u, TC_WAIT_BUDGET);
+    if (t == TC_PRODUCER) {
+        const uint32_t q0 = pp.q > TC_NST ? pp.q - TC_NST : 0u;
+        for (uint32_t q = q0; q < pp.q; ++q)
+            ok &= tc::mbar_wait(&sm.full[q % TC_NST], (q / TC_NST) & 1u, TC_WAIT_BUDGET);
+    }
+    if (t == TC_ISSUER) {
+        tc::mma_commit(&sm.fin);
+        ok &= tc::mbar_wait(&sm.fin, 0, TC_WAIT_BUDGET);
+    }
     if (!ok) dev_raise(status, MVN_ERR_TIMEOUT, 0);
 }
 
@@ -404,15 +414,21 @@ __device__ __forceinline__ TcSmem& tc_smem(uint8_t* raw) {
 
 __device__ __forceinline__ constexpr int tri(int v, int u) { return v * (v + 1) / 2 + u; }
 
-__global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
-                                                     const uint64_t* __restrict__ alpha) {
+// Raise a timeout once and make every role of the CTA stop.
+__device__ __forceinline__ void tc_fail(TcSmem& sm, int* status) {
+    sm.abort = 1;
+    dev_raise(status, MVN_ERR_TIMEOUT, 0);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 2) k_sov_tc(const TcBatch bt,
+                                                          const uint64_t* __restrict__ alpha) {
     extern __shared__ uint8_t smem_raw[];
     TcSmem& sm = tc_smem(smem_raw);
     const int t = threadIdx.x;
     tc_setup(sm);
-    TcPipe pp;
-    uint32_t dphase = 0;  // loads of the packed diagonal block issued (uniform)
-    uint32_t g_all = 0;   // accumulation groups of all far GEMMs so far (uniform)
+    TcPipe pp;            // producer / issuer state
+    uint32_t dphase = 0;  // loads of the packed diagonal block issued (path thread 0)
+    uint32_t g_all = 0;   // accumulation groups of all far GEMMs so far (path threads)
     uint8_t* Ybuf = bt.Yscratch + (int64_t)blockIdx.x * bt.ystride;
     const uint32_t lane_base = ((uint32_t)(t >> 5) * 32u) << 16;
 
@@ -422,146 +438,174 @@ __global__ void __launch_bounds__(TC_P, 2) k_sov_tc(const TcBatch bt,
         const int it = sm.item;
         if (it >= bt.nitems || sm.abort) break;
         const SovProblem& P = (bt.probs == nullptr) ? bt.single : bt.probs[bt.items[it].x];
-        const int tile = (bt.probs == nullptr) ? it : bt.items[it].y;
         const int n = P.n;
-        const int64_t p = (int64_t)tile * TC_P + t;
-        const bool valid = p < P.Ntot;
-        const int64_t pg = P.p0 + p;  // index of the path in the whole lattice rule
-        const int64_t q = valid ? pg / P.Ns : 0;
-        const uint64_t j = valid ? (uint64_t)(pg - q * P.Ns) + 1u : 1u;
-        const uint64_t* __restrict__ dq = P.delta + q * P.dstride;
-        DFProd lp;
-        int pf = 0;
-        int next_k = (P.nprefix > 0) ? P.prefix[0] : -1;
         const int nsb = (n + TC_N - 1) / TC_N;
-
-        for (int rb = 0; rb < nsb; ++rb) {
-            const int d0 = rb * TC_N;
-            const int nb2 = min(TC_N, n - d0);
-            if (t < TC_N) {
-                const int v = d0 + t;
-                const double av = (t < nb2) ? P.a[v] : 0.0;
-                const double bv = (t < nb2) ? P.b[v] : 1.0;
-                sm.a[t] = av;
-                sm.b[t] = bv;
-                sm.af[t] = (float)av;
-                sm.bf[t] = (float)bv;
-                sm.ainf[t] = (av == -INFINITY);
-                sm.binf[t] = (bv == INFINITY);
-                sm.alpha[t] = (t < nb2) ? alpha[v] : 0u;
-                sm.escale[t] = bt.escale[v];
-            }
-            if (t == 0 && rb > 0) tc_far_begin(pp, Ybuf, bt.Lt, rb);
-            __syncthreads();
-            // far part of the shifts (Alg. 2 step (c) over all earlier super-blocks) -> TMEM
-            // buffer 1; buffer 0 receives this super-block's y
-            const uint32_t sbuf = sm.tmem + lane_base + TC_N, ybuf = sm.tmem + lane_base;
-            {
-                float s[TC_N];
-                if (rb > 0) {
-                    if (!tc_far(sm, pp, rb, g_all, s) && t == 0)
-                        dev_raise(bt.status, MVN_ERR_TIMEOUT, 0);
-                    g_all += (uint32_t)((4 * rb + TC_G - 1) / TC_G);
-                } else {
-#pragma unroll
-                    for (int v = 0; v < TC_N; ++v) s[v] = 0.0f;
-                }
-                if (sm.abort) break;
-                // packed diagonal block into the (now idle) stage area
-                if (t == 0) {
-                    tc::fence_proxy_async_smem();
-                    tc::mbar_arrive_expect_tx(&sm.dbar, TC_DPACK * 4);
-                    tc::bulk_g2s(sm.D, bt.Dpack + (size_t)rb * TC_DPACK, TC_DPACK * 4, &sm.dbar);
-                }
-                ++dphase;
-#pragma unroll
-                for (int c = 0; c < TC_N; c += 32) {
-                    float h[32];
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) h[i] = s[c + i];
-                    tc::tmem_st32(sbuf + c, h);
-
-                }
-            }
-            if (t == 0 && !tc::mbar_wait(&sm.dbar, (dphase - 1) & 1u, TC_WAIT_BUDGET)) {
-                sm.abort = 1;
-                dev_raise(bt.status, MVN_ERR_TIMEOUT, 0);
-            }
-            __syncthreads();
-            if (sm.abort) break;
-            // diagonal block (Alg. 3) in blocks of 16 dimensions.  For block c the shifts of its
-            // dimensions start as q_i = far_i + sum_{u < 16c} L(16c + i, u) y_u (a 16 x 16c
-            // mat-vec over the earlier y, read back from TMEM 16 at a time); inside the block the
-            // dimensions go one at a time, q being a queue whose head is the current dimension:
-            // after the elementwise step of Eq. 2 gives y_v, the later dimensions of the block
-            // get L(v + p, v) y_v added (right-looking) and the queue shifts by one.  One copy
-            // of the step code serves every dimension.
-#pragma unroll 1
-            for (int c0 = 0; c0 < nb2; c0 += 16) {
-                float q[16];
-                tc::tmem_ld16(sbuf + c0, q);
-#pragma unroll 1
-                for (int u0 = 0; u0 < c0; u0 += 16) {
-                    float yy[16];
-                    tc::tmem_ld16(ybuf + u0, yy);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float* Dr = sm.D + tri(c0 + i, u0);
-#pragma unroll
-                        for (int k = 0; k < 16; ++k) q[i] = fmaf(Dr[k], yy[k], q[i]);
+        if (t >= TC_P) {
+            // ------------------------------------------------ pipeline warps: far GEMMs 1 .. nsb-1
+            if (t == TC_PRODUCER || t == TC_ISSUER) {
+                for (int rb = 1; rb < nsb; ++rb) {
+                    // y of super-block rb - 1 written, its buffers and diagonal block released
+                    if (!tc_wait(&sm.ybar, pp.ywait & 1u, &sm.abort)) {
+                        tc_fail(sm, bt.status);
+                        break;
+                    }
+                    ++pp.ywait;
+                    tc::tc_fence_after();
+                    const bool ok = (t == TC_PRODUCER) ? tc_far_load(sm, pp, Ybuf, bt.Lt, rb)
+                                                       : tc_far_mma(sm, pp, rb);
+                    if (!ok) {
+                        tc_fail(sm, bt.status);
+                        break;
                     }
                 }
-                float y16[16];
-#pragma unroll 1
-                for (int i = 0; i < 16; ++i) {
-                    const int v = c0 + i;
-                    float y = 0.0f;
-                    if (v < nb2) {
-                        float w, wc, dh, dl;
-                        uint64_t wm;
-                        int dex;
-                        lattice_wf(j, sm.alpha[v], dq[d0 + v], w, wc, wm);
-                        y = sov_step_f32p(sm.af[v], sm.bf[v], sm.a[v], sm.b[v], sm.ainf[v],
-                                          sm.binf[v], q[0], sm.D[tri(v, v)], w, wc, wm, dh, dl,
-                                          dex);
-                        lp.mul(dh, dl, dex);
-                        while (next_k == d0 + v + 1) {
-                            if (valid) P.logw_prefix[(int64_t)pf * P.Ntot + p] = lp.log_value();
-                            ++pf;
-                            next_k = (pf < P.nprefix) ? P.prefix[pf] : -1;
+            }
+            __syncwarp();
+        } else {
+            // ------------------------------------------------ path threads
+            const int tile = (bt.probs == nullptr) ? it : bt.items[it].y;
+            const int64_t p = (int64_t)tile * TC_P + t;
+            const bool valid = p < P.Ntot;
+            const int64_t pg = P.p0 + p;  // index of the path in the whole lattice rule
+            const int64_t q = valid ? pg / P.Ns : 0;
+            const uint64_t j = valid ? (uint64_t)(pg - q * P.Ns) + 1u : 1u;
+            const uint64_t* __restrict__ dq = P.delta + q * P.dstride;
+            DFProd lp;
+            int pf = 0;
+            int next_k = (P.nprefix > 0) ? P.prefix[0] : -1;
+            bool done = true;
+            for (int rb = 0; rb < nsb; ++rb) {
+                const int d0 = rb * TC_N;
+                const int nb2 = min(TC_N, n - d0);
+                {
+                    const int v = d0 + t;
+                    const double av = (t < nb2) ? P.a[v] : 0.0;
+                    const double bv = (t < nb2) ? P.b[v] : 1.0;
+                    sm.a[t] = av;
+                    sm.b[t] = bv;
+                    sm.af[t] = (float)av;
+                    sm.bf[t] = (float)bv;
+                    sm.ainf[t] = (av == -INFINITY);
+                    sm.binf[t] = (bv == INFINITY);
+                    sm.alpha[t] = (t < nb2) ? alpha[v] : 0u;
+                    sm.escale[t] = bt.escale[v];
+                }
+                tc_path_sync();
+                // far part of the shifts (Alg. 2 step (c) over all earlier super-blocks) -> TMEM
+                // buffer 1; buffer 0 receives this super-block's y
+                const uint32_t sbuf = sm.tmem + lane_base + TC_N, ybuf = sm.tmem + lane_base;
+                bool fail = false;
+                {
+                    float s[TC_N];
+                    if (rb > 0) {
+                        fail = !tc_far_drain(sm, rb, g_all, s);
+                        g_all += (uint32_t)tc_groups(rb);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < TC_N; ++v) s[v] = 0.0f;
+                    }
+                    if (fail) {
+                        tc_fail(sm, bt.status);
+                    } else {
+                        // packed diagonal block into the (now idle) stage area
+                        if (t == 0) {
+                            tc::fence_proxy_async_smem();
+                            tc::mbar_arrive_expect_tx(&sm.dbar, TC_DPACK * 4);
+                            tc::bulk_g2s(sm.D, bt.Dpack + (size_t)rb * TC_DPACK, TC_DPACK * 4,
+                                         &sm.dbar);
+                            ++dphase;
+                        }
+#pragma unroll
+                        for (int c = 0; c < TC_N; c += 32) {
+                            float h[32];
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) h[i] = s[c + i];
+                            tc::tmem_st32(sbuf + c, h);
                         }
                     }
-                    // later dimensions of the block, then shift the queues
-#pragma unroll
-                    for (int pp2 = 1; pp2 < 16; ++pp2)
-                        if (pp2 < 16 - i) q[pp2] = fmaf(sm.D[tri(v + pp2, v)], y, q[pp2]);
-#pragma unroll
-                    for (int k = 0; k < 15; ++k) {
-                        q[k] = q[k + 1];
-                        y16[k] = y16[k + 1];
-                    }
-                    q[15] = 0.0f;
-                    y16[15] = y;
                 }
-                tc::tmem_st16(ybuf + c0, y16);
-            }
-            // y of this super-block -> operand buffer of the later super-blocks (read back by
-            // the async proxy: fence before the barrier that precedes those loads)
-            if (d0 + TC_N < n) {
+                if (t == 0 && !fail && !tc::mbar_wait(&sm.dbar, (dphase - 1) & 1u, TC_WAIT_BUDGET)) {
+                    fail = true;
+                    tc_fail(sm, bt.status);
+                }
+                if (tc_path_sync_or(fail || sm.abort)) {
+                    done = false;
+                    break;
+                }
+                // diagonal block (Alg. 3) in blocks of 16 dimensions.  For block c the shifts of
+                // its dimensions start as q_i = far_i + sum_{u < 16c} L(16c + i, u) y_u (a
+                // 16 x 16c mat-vec over the earlier y, read back from TMEM 16 at a time); inside
+                // the block the dimensions go one at a time, q being a queue whose head is the
+                // current dimension: after the elementwise step of Eq. 2 gives y_v, the later
+                // dimensions of the block get L(v + p, v) y_v added (right-looking) and the queue
+                // shifts by one.  One copy of the step code serves every dimension.
 #pragma unroll 1
-                for (int c = 0; c < TC_N; c += 32) {
-                    float yy[32];
-                    tc::tmem_ld32(ybuf + c, yy);
-                    tc_write_y32(Ybuf, (d0 + c) / TC_KS, t, yy);
+                for (int c0 = 0; c0 < nb2; c0 += 16) {
+                    float qv[16];
+                    tc::tmem_ld16(sbuf + c0, qv);
+#pragma unroll 1
+                    for (int u0 = 0; u0 < c0; u0 += 16) {
+                        float yy[16];
+                        tc::tmem_ld16(ybuf + u0, yy);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const float* Dr = sm.D + tri(c0 + i, u0);
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) qv[i] = fmaf(Dr[k], yy[k], qv[i]);
+                        }
+                    }
+                    float y16[16];
+#pragma unroll 1
+                    for (int i = 0; i < 16; ++i) {
+                        const int v = c0 + i;
+                        float y = 0.0f;
+                        if (v < nb2) {
+                            float w, wc, dh, dl;
+                            uint64_t wm;
+                            int dex;
+                            lattice_wf(j, sm.alpha[v], dq[d0 + v], w, wc, wm);
+                            y = sov_step_f32p(sm.af[v], sm.bf[v], sm.a[v], sm.b[v], sm.ainf[v],
+                                              sm.binf[v], qv[0], sm.D[tri(v, v)], w, wc, wm, dh,
+                                              dl, dex);
+                            lp.mul(dh, dl, dex);
+                            while (next_k == d0 + v + 1) {
+                                if (valid) P.logw_prefix[(int64_t)pf * P.Ntot + p] = lp.log_value();
+                                ++pf;
+                                next_k = (pf < P.nprefix) ? P.prefix[pf] : -1;
+                            }
+                        }
+                        // later dimensions of the block, then shift the queues
+#pragma unroll
+                        for (int pp2 = 1; pp2 < 16; ++pp2)
+                            if (pp2 < 16 - i) qv[pp2] = fmaf(sm.D[tri(v + pp2, v)], y, qv[pp2]);
+#pragma unroll
+                        for (int k = 0; k < 15; ++k) {
+                            qv[k] = qv[k + 1];
+                            y16[k] = y16[k + 1];
+                        }
+                        qv[15] = 0.0f;
+                        y16[15] = y;
+                    }
+                    tc::tmem_st16(ybuf + c0, y16);
                 }
-                tc::fence_proxy_async_global();
+                // y of this super-block -> operand buffer of the later super-blocks (read back
+                // by the async proxy: fence, then release it to the pipeline thread through
+                // ybar together with the TMEM buffers and the stage area)
+                if (d0 + TC_N < n) {
+#pragma unroll 1
+                    for (int c = 0; c < TC_N; c += 32) {
+                        float yy[32];
+                        tc::tmem_ld32(ybuf + c, yy);
+                        tc_write_y32(Ybuf, (d0 + c) / TC_KS, t, yy);
+                    }
+                    tc::fence_proxy_async_global();
+                    tc::fence_proxy_async_smem();
+                    tc::tc_fence_before();
+                    tc::mbar_arrive(&sm.ybar);
+                }
+                tc_path_sync();  // the limits of the next super-block overwrite sm.a ..
             }
-            tc::fence_proxy_async_smem();  // the stage area is rewritten by bulk copies next
-            tc::tc_fence_before();
-            __syncthreads();
-            tc::tc_fence_after();
+            if (done && valid && P.logw) P.logw[p] = lp.log_value();
         }
-        if (valid && P.logw) P.logw[p] = lp.log_value();
         __syncthreads();
     }
     tc_quiesce(sm, pp, dphase, bt.status);
@@ -680,7 +724,7 @@ mvn_status sov_run_tc(mvn_ctx* ctx, const std::vector<SovProblem>& probs_h, char
     const size_t smem = tc_smem_bytes();
     MVN_CUDA(ctx, cudaFuncSetAttribute(k_sov_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-    MVN_TIMED(ctx, "k_sov_tc", (k_sov_tc<<<grid, TC_P, smem, ctx->stream>>>(bt, ctx->d_alpha)));
+    MVN_TIMED(ctx, "k_sov_tc", (k_sov_tc<<<grid, TC_THREADS, smem, ctx->stream>>>(bt, ctx->d_alpha)));
     return MVN_OK;
 }
 
@@ -713,23 +757,29 @@ __global__ void k_tc_selftest_prep(int K, const double* __restrict__ Y, uint8_t*
     tc::fence_proxy_async_global();
 }
 
-__global__ void __launch_bounds__(TC_P, 2) k_tc_selftest(int rb, const uint8_t* __restrict__ Ybuf,
-                                                          const uint8_t* __restrict__ Lt,
-                                                          const float* __restrict__ escale,
-                                                          float* __restrict__ S, int* status) {
+__global__ void __launch_bounds__(TC_THREADS, 2) k_tc_selftest(int rb,
+                                                               const uint8_t* __restrict__ Ybuf,
+                                                               const uint8_t* __restrict__ Lt,
+                                                               const float* __restrict__ escale,
+                                                               float* __restrict__ S, int* status) {
     extern __shared__ uint8_t smem_raw[];
     TcSmem& sm = tc_smem(smem_raw);
     const int t = threadIdx.x;
     tc_setup(sm);
     TcPipe pp;
-    sm.escale[t] = escale[TC_N * rb + t];
-    if (t == 0) tc_far_begin(pp, Ybuf, Lt, rb);
+    if (t < TC_P) sm.escale[t] = escale[TC_N * rb + t];
     __syncthreads();
-    float s[TC_N];
-    const bool ok = tc_far(sm, pp, rb, 0u, s);
-    if (!ok && t == 0) dev_raise(status, MVN_ERR_TIMEOUT, 0);
-    if (ok)
-        for (int v = 0; v < TC_N; ++v) S[t * TC_N + v] = s[v];
+    if (t >= TC_P) {
+        if (t == TC_PRODUCER && !tc_far_load(sm, pp, Ybuf, Lt, rb)) tc_fail(sm, status);
+        if (t == TC_ISSUER && !tc_far_mma(sm, pp, rb)) tc_fail(sm, status);
+        __syncwarp();
+    } else {
+        float s[TC_N];
+        if (!tc_far_drain(sm, rb, 0u, s))
+            tc_fail(sm, status);
+        else
+            for (int v = 0; v < TC_N; ++v) S[t * TC_N + v] = s[v];
+    }
     tc_quiesce(sm, pp, 0, status);
     tc_teardown(sm);
 }
@@ -763,7 +813,7 @@ extern "C" mvn_status mvn_tc_selftest(mvn_ctx* ctx, int K, const double* Y, cons
     const size_t smem = tc_smem_bytes();
     MVN_CUDA(ctx, cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-    k_tc_selftest<<<1, TC_P, smem, ctx->stream>>>(rb, Ybuf, Lt, escale, S, ctx->d_status);
+    k_tc_selftest<<<1, TC_THREADS, smem, ctx->stream>>>(rb, Ybuf, Lt, escale, S, ctx->d_status);
     MVN_LAUNCHED(ctx);
     return MVN_OK;
 }

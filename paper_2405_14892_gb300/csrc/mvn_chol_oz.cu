@@ -404,29 +404,19 @@ __device__ __forceinline__ DF df_rcp(DF l) {
 // they are finished (staged in shared memory).  Rows and columns beyond nb are the identity and
 // are never touched.  Writes L_jj to A (FP64), W^T as pairs Wt[u][c] = W[c][u], and the digits of
 // the diagonal rows.
-__device__ __forceinline__ DF df_sel4(const DF (&x)[4], int b) {
-    DF v = x[0];
-    if (b == 1) v = x[1];
-    if (b == 2) v = x[2];
-    if (b == 3) v = x[3];
-    return v;
-}
-
 __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_t ld, int c0,
                                                   int nb, const int* __restrict__ E,
                                                   long long* __restrict__ T, int64_t ldT,
                                                   float* __restrict__ Wt, uint8_t* __restrict__ Z,
                                                   int nrt, int* status) {
     __shared__ DF Vs[2][OZ_NB];  // step vector V, by step parity
-    __shared__ DF piv[2];        // 1 / L_kk, by step parity
+    __shared__ DF Sdp[2];        // S(k, k) published one step ahead, by step parity
     // staging: the loaded block, then the columns of L as they are finished
     __shared__ float Sh[OZ_NB][OZ_NB + 1], Sl[OZ_NB][OZ_NB + 1];
     __shared__ int Eb[OZ_NB];
-    __shared__ int bad;
     if (oz_failed(status)) return;
     const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
     const bool act = (tx <= ty);
-    if (t == 0) bad = 0;
     if (t < OZ_NB) Eb[t] = (t < nb) ? E[c0 + t] : 0;
     __syncthreads();
     {
@@ -467,85 +457,30 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
             const int i = 4 * ty + a, m = 4 * tx + b;
             X[a][b] = (act && m <= i) ? DF{Sh[i][m], Sl[i][m]} : DF{0.0f, 0.0f};
         }
+    if (t == 0) Sdp[0] = DF{Sh[0][0], Sl[0][0]};
     __syncthreads();  // Sh/Sl now receive the finished columns of L
+    // Step k runs in one phase between two barriers: the rank-1 update of step k - 1, then the
+    // pivot and the scaling of column k (and of row k of W).  Every thread that scales computes
+    // the pivot itself from S(k, k) after the update of step k - 1: its owner publishes
+    // S(k, k) after the update of step k - 2 (one phase ahead, in Sdp), and the last update
+    // -V(k) V(k), V the vector of step k - 1, is redone on that copy with the owner's exact
+    // operations, so that every copy of the pivot is the same.
     for (int k = 0; k < nb; ++k) {
         const int kb = k >> 2, kk = k & 3;
         DF* V = Vs[k & 1];
-        // pivot: L_kk = sqrt(S_kk); X(k, k) becomes W(k, k) = 1 / L_kk
-        if (ty == kb && tx == kb) {
-            DF d = DF{0.0f, 0.0f};
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-                if (a == kk) d = df_sel4(X[a], kk);
-            if (!(d.hi > 0.0f)) {
-                dev_raise(status, MVN_ERR_NOT_PD, c0 + k + 1);
-                bad = 1;
-            } else {
-                const DF l = df_sqrt(d);
-                const DF r = df_rcp(l);
-                piv[k & 1] = r;
-                V[k] = r;
-                Sh[k][k] = l.hi;
-                Sl[k][k] = l.lo;
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-                    if (a == kk) {
-#pragma unroll
-                        for (int b = 0; b < 4; ++b)
-                            if (b == kk) X[a][b] = r;
-                    }
-            }
-        }
-        __syncthreads();
-        if (bad) return;
-        const DF r = piv[k & 1];
-        // column k below the pivot: L(i, k) = S(i, k) / L_kk leaves the array (entry zeroed)
-        if (act && tx == kb && 4 * ty + 3 > k) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const int i = 4 * ty + a;
-                if (i > k) {
-                    DF v = DF{0.0f, 0.0f};
-#pragma unroll
-                    for (int b = 0; b < 4; ++b)
-                        if (b == kk) {
-                            v = df_mul(X[a][b], r);
-                            X[a][b] = DF{0.0f, 0.0f};
-                        }
-                    V[i] = v;
-                    Sh[i][k] = v.hi;
-                    Sl[i][k] = v.lo;
-                }
-            }
-        }
-        // row k left of the pivot: W(k, c) = X(k, c) / L_kk, final
-        if (act && ty == kb && 4 * tx < k) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-                if (a == kk) {
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const int c = 4 * tx + b;
-                        if (c < k) {
-                            const DF v = df_mul(X[a][b], r);
-                            X[a][b] = v;
-                            V[c] = v;
-                        }
-                    }
-                }
-        }
-        __syncthreads();
-        // rank-1 update of the rows i > k (warp-uniform skip once both row groups are done)
-        if (act && 4 * ty + 3 > k) {
+        // rank-1 update of step k - 1 on the rows i > k - 1 (warp-uniform skip once both row
+        // groups are done)
+        if (k > 0 && act && 4 * ty + 3 > k - 1) {
+            const DF* Vp = Vs[(k - 1) & 1];
             DF vi[4], vm[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) vi[a] = V[4 * ty + a];
+            for (int a = 0; a < 4; ++a) vi[a] = Vp[4 * ty + a];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) vm[b] = V[4 * tx + b];
+            for (int b = 0; b < 4; ++b) vm[b] = Vp[4 * tx + b];
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                // rows <= k take an exact zero multiplier: all 16 updates are independent
-                const bool row = (4 * ty + a > k);
+                // rows <= k - 1 take an exact zero multiplier: all 16 updates are independent
+                const bool row = (4 * ty + a > k - 1);
                 const DF nv{row ? -vi[a].hi : 0.0f, row ? -vi[a].lo : 0.0f};
 #pragma unroll
                 for (int b = 0; b < 4; ++b) df_fma_acc(X[a][b], nv, vm[b]);
@@ -555,8 +490,86 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
 #pragma unroll
                 for (int b = 0; b < 4; ++b) X[a][b] = df_norm(X[a][b].hi, X[a][b].lo);
         }
-        // the other parity's vector is rewritten next step; this step's is not touched again
-        // until every thread has passed the next step's barriers
+        // the owner of (k + 1, k + 1) publishes it for the pivot of step k + 1
+        const int k1 = k + 1, k1b = k1 >> 2;
+        if (k1 < nb && ty == k1b && tx == k1b) {
+            const int q = k1 & 3;
+            DF v = X[0][0];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (a == q && b == q) v = X[a][b];
+            Sdp[k1 & 1] = v;
+        }
+        // pivot L_kk = sqrt(S_kk); X(k, k) becomes W(k, k) = 1 / L_kk
+        int bad = 0;
+        if (act && (tx == kb || ty == kb)) {
+            DF d = Sdp[k & 1];
+            if (k > 0) {
+                const DF v = Vs[(k - 1) & 1][k];
+                df_fma_acc(d, DF{-v.hi, -v.lo}, v);
+                d = df_norm(d.hi, d.lo);
+            }
+            if (!(d.hi > 0.0f)) {
+                bad = 1;
+                dev_raise(status, MVN_ERR_NOT_PD, c0 + k + 1);
+            } else {
+                const DF l = df_sqrt(d);
+                const DF r = df_rcp(l);
+                if (ty == kb && tx == kb) {
+                    V[k] = r;
+                    Sh[k][k] = l.hi;
+                    Sl[k][k] = l.lo;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        if (a == kk) {
+#pragma unroll
+                            for (int b = 0; b < 4; ++b)
+                                if (b == kk) X[a][b] = r;
+                        }
+                }
+                // column k below the pivot: L(i, k) = S(i, k) / L_kk leaves the array (entry
+                // zeroed)
+                if (tx == kb && 4 * ty + 3 > k) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int i = 4 * ty + a;
+                        if (i > k) {
+                            DF v = DF{0.0f, 0.0f};
+#pragma unroll
+                            for (int b = 0; b < 4; ++b)
+                                if (b == kk) {
+                                    v = df_mul(X[a][b], r);
+                                    X[a][b] = DF{0.0f, 0.0f};
+                                }
+                            V[i] = v;
+                            Sh[i][k] = v.hi;
+                            Sl[i][k] = v.lo;
+                        }
+                    }
+                }
+                // row k left of the pivot: W(k, c) = X(k, c) / L_kk, final
+                if (ty == kb && 4 * tx < k) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        if (a == kk) {
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) {
+                                const int c = 4 * tx + b;
+                                if (c < k) {
+                                    const DF v = df_mul(X[a][b], r);
+                                    X[a][b] = v;
+                                    V[c] = v;
+                                }
+                            }
+                        }
+                }
+            }
+        }
+        // this step's vector, pivot copy and columns become visible; the buffers of the other
+        // parity are rewritten next phase, after every thread has read them in this one
+        if (__syncthreads_or(bad)) return;
     }
     // W^T (X holds W in its lower entries; rows and columns beyond nb are the identity)
     if (act) {

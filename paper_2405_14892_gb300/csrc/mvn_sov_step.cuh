@@ -136,12 +136,31 @@ __device__ __forceinline__ float sov_step_f32(double ai, double bi, float s, flo
 // 1 - Q(b') keeps Q(b') even when it is below FP32's resolution of 1) times 2^dex.  Deep tails
 // and two-sided intervals fall back to the FP64 step.
 
+// The float nearest to an integer 1 <= x < 2^55 (ties to even), from integer operations only:
+// the 64-bit integer-to-float conversion is a long-latency instruction on this GPU, and the
+// lattice point sits on the sweep's serial chain.  With e the position of the leading one, the
+// 24 leading bits are kept and rounded by the bits shifted out (round half to even).
+__device__ __forceinline__ float u55_to_f32_rn(uint64_t x) {
+    const int e = 63 - __clzll((long long)x);
+    uint32_t mant;
+    if (e <= 23) {
+        mant = (uint32_t)x << (23 - e);  // exact
+    } else {
+        const int sh = e - 23;  // 1 .. 31
+        mant = (uint32_t)(x >> sh);
+        const uint64_t rem = x & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        mant += (rem > half || (rem == half && (mant & 1u))) ? 1u : 0u;
+    }
+    // mant lies in [2^23, 2^24]; a rounding carry to 2^24 moves into the exponent field
+    return __uint_as_float(((uint32_t)(e + 127) << 23) + (mant - (1u << 23)));
+}
+
 __device__ __forceinline__ void lattice_wf(uint64_t j, uint64_t alpha, uint64_t delta, float& w,
                                            float& wc, uint64_t& m) {
     const uint64_t W = j * alpha + delta;
     m = W >> 11;
-    w = __ull2float_rn(2u * m + 1u) * 0x1p-54f;
-    wc = __ull2float_rn((1ull << 54) - 2u * m - 1u) * 0x1p-54f;
+    w = u55_to_f32_rn(2u * m + 1u) * 0x1p-54f;
+    wc = u55_to_f32_rn((1ull << 54) - 2u * m - 1u) * 0x1p-54f;
 }
 
 static __device__ __noinline__ float sov_step_slow_pair(double ai, double bi, float s, float lii,
@@ -168,16 +187,17 @@ static __device__ __noinline__ float sov_step_slow_pair(double ai, double bi, fl
 // branches on the common path (the paths of a warp take different tails): one erfcf of |x| gives
 // both tails, one normcdfinvf of the smaller of p and 1 - p gives y, and the shift is scaled by
 // 1 / L_ii, which does not depend on it.
-__device__ __forceinline__ float sov_step_f32p(float af, float bf, double ai, double bi, bool ainf,
-                                               bool binf, float s, float lii, float w, float wc,
-                                               uint64_t m, float& dh, float& dl, int& dex) {
+// The same with rl = 1 / lii given (computed once per dimension ahead of the sweep).
+__device__ __forceinline__ float sov_step_f32r(float af, float bf, double ai, double bi, bool ainf,
+                                               bool binf, float s, float lii, float rl, float w,
+                                               float wc, uint64_t m, float& dh, float& dl,
+                                               int& dex) {
     dex = 0;
     dl = 0.0f;
     if (ainf && binf) {
         dh = 1.0f;
         return phinv_two_sided_f32(w, wc);
     }
-    const float rl = 1.0f / lii;
     if (ainf) {  // Delta = Phi(b'),  p = w Phi(b'),  1 - p = (1 - w) + w Q(b')
         const float bp = (bf - s) * rl;
         if (bp > -9.0f) {
@@ -215,6 +235,12 @@ __device__ __forceinline__ float sov_step_f32p(float af, float bf, double ai, do
         return sov_step_slow_pair(ai, bi, s, lii, m, &dh, &dl, &dex);
     }
     return sov_step_slow_pair(ai, bi, s, lii, m, &dh, &dl, &dex);
+}
+
+__device__ __forceinline__ float sov_step_f32p(float af, float bf, double ai, double bi, bool ainf,
+                                               bool binf, float s, float lii, float w, float wc,
+                                               uint64_t m, float& dh, float& dl, int& dex) {
+    return sov_step_f32r(af, bf, ai, bi, ainf, binf, s, lii, 1.0f / lii, w, wc, m, dh, dl, dex);
 }
 
 // Running product of the factors as (ph + pl) 2^ex in FP32 pairs: each factor costs an exact

@@ -44,7 +44,10 @@
 #define TC_TILE 8192        // one FP16 slice of a 128-row x 32-column tile (64-byte swizzle)
 #define TC_STAGE (4 * TC_TILE)  // Yh, Yl, Lh, Ll
 #define TC_TMEM_COLS 256    // two accumulation buffers of 128 columns
-#define TC_DPACK (TC_N * (TC_N + 1) / 2 + 16)  // floats of one packed diagonal block (+ zero pad)
+#define TC_TRI (TC_N * (TC_N + 1) / 2 + 16)    // packed lower triangle (+ zero pad)
+#define TC_RCP TC_TRI                          // then 1 / L_vv
+#define TC_BAND (TC_RCP + TC_N)                // then the band L(v + p, v), p < 16, by v
+#define TC_DPACK (TC_BAND + 16 * TC_N)         // floats of one packed diagonal block
 #define TC_WAIT_BUDGET 4000000000LL  // cycles (~2 s) before a wait gives up
 
 // Split-factor tile pair (hi, lo) of super-block rb (rows 128 rb ..) and K sub-chunk kc < 4 rb.
@@ -112,7 +115,10 @@ __global__ void __launch_bounds__(128) k_split_L(int n, const double* __restrict
 
 // Packed FP32 diagonal block of super-block rb: the lower triangle of L(d0:d0+128, d0:d0+128),
 // row-packed (v (v + 1) / 2 + u), then 16 zeros (the left-looking dot reads up to 15 entries past
-// a row; they meet y values that are still zero).  Rows beyond n: zero, diagonal one.
+// a row; they meet y values that are still zero); then 1 / L_vv (the same FP32 division as in
+// the step); then the band below the diagonal by column, band[16 v + p] = L(v + p, v) for
+// 1 <= p < 16 (zero past the block, p = 0 unused), for the right-looking update in vector loads.
+// Rows beyond n: zero, diagonal one.
 __global__ void k_pack_D(int n, const double* __restrict__ L, int64_t ld, float* __restrict__ D) {
     const int rb = blockIdx.x, d0 = TC_N * rb;
     float* out = D + (size_t)rb * TC_DPACK;
@@ -125,8 +131,15 @@ __global__ void k_pack_D(int n, const double* __restrict__ L, int64_t ld, float*
         else
             x = (u == v) ? 1.0f : 0.0f;
         out[v * (v + 1) / 2 + u] = x;
+        if (u == v) out[TC_RCP + v] = 1.0f / x;
+        const int p = v - u;
+        if (p > 0 && p < 16) out[TC_BAND + 16 * u + p] = x;
     }
     if (threadIdx.x < 16) out[TC_N * (TC_N + 1) / 2 + threadIdx.x] = 0.0f;
+    for (int e = threadIdx.x; e < TC_N * 16; e += blockDim.x) {
+        const int u = e >> 4, p = e & 15;
+        if (p == 0 || u + p >= TC_N) out[TC_BAND + e] = 0.0f;
+    }
 }
 
 // ---------------------------------------------------------------- shared memory
@@ -151,6 +164,7 @@ struct __align__(1024) TcSmem {
 
 static_assert(sizeof(TcSmem) <= 112 * 1024, "two CTAs per SM need <= 112 KB each");
 static_assert(TC_DPACK * 4 <= TC_NST * TC_STAGE, "the diagonal block lives in the stage area");
+static_assert(TC_BAND % 4 == 0 && (TC_DPACK * 4) % 16 == 0, "vector loads / bulk copy alignment");
 static_assert(TC_P == TC_N, "one path thread per dimension of a super-block loads its limits");
 
 // ---------------------------------------------------------------- roles and barriers
@@ -563,9 +577,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_sov_tc(const TcBatch bt,
                             uint64_t wm;
                             int dex;
                             lattice_wf(j, sm.alpha[v], dq[d0 + v], w, wc, wm);
-                            y = sov_step_f32p(sm.af[v], sm.bf[v], sm.a[v], sm.b[v], sm.ainf[v],
-                                              sm.binf[v], qv[0], sm.D[tri(v, v)], w, wc, wm, dh,
-                                              dl, dex);
+                            y = sov_step_f32r(sm.af[v], sm.bf[v], sm.a[v], sm.b[v], sm.ainf[v],
+                                              sm.binf[v], qv[0], sm.D[tri(v, v)],
+                                              sm.D[TC_RCP + v], w, wc, wm, dh, dl, dex);
                             lp.mul(dh, dl, dex);
                             while (next_k == d0 + v + 1) {
                                 if (valid) P.logw_prefix[(int64_t)pf * P.Ntot + p] = lp.log_value();
@@ -573,10 +587,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_sov_tc(const TcBatch bt,
                                 next_k = (pf < P.nprefix) ? P.prefix[pf] : -1;
                             }
                         }
-                        // later dimensions of the block, then shift the queues
+                        // later dimensions of the block (column v of the band), then shift
+                        // the queues
+                        float bd[16];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            *reinterpret_cast<float4*>(bd + 4 * c) =
+                                *reinterpret_cast<const float4*>(sm.D + TC_BAND + 16 * v + 4 * c);
 #pragma unroll
                         for (int pp2 = 1; pp2 < 16; ++pp2)
-                            if (pp2 < 16 - i) qv[pp2] = fmaf(sm.D[tri(v + pp2, v)], y, qv[pp2]);
+                            if (pp2 < 16 - i) qv[pp2] = fmaf(bd[pp2], y, qv[pp2]);
 #pragma unroll
                         for (int k = 0; k < 15; ++k) {
                             qv[k] = qv[k + 1];

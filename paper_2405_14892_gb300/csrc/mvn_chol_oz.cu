@@ -374,17 +374,27 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
     e = fmaf(a.lo, b.hi, e);
     return df_norm(p, e);
 }
-// square root: s0 = sqrt(d.hi) in FP32, then one Newton correction (d - s0^2) / (2 s0)
+// Square root and reciprocal of the pivot, on the POTRF's serial path: the hardware
+// approximations (relative error ~2^-22), one Newton-Raphson step in FP32 (Markstein 1990),
+// then one Newton correction in double-float with the residual formed exactly by FMA (Dekker
+// 1971): ~2^-45 relative, beyond the 42 bits the digit products keep, without the special-case
+// branches of the IEEE square root and division.
+// sqrt: y ~ 1/sqrt(d.hi) refined by y (3 - d y^2) / 2, s0 = d.hi y, then s0 + (d - s0^2) y / 2
 __device__ __forceinline__ DF df_sqrt(DF d) {
-    const float s0 = sqrtf(d.hi);
+    float y;
+    asm("rsqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(d.hi));
+    y = y * fmaf(-0.5f * d.hi * y, y, 1.5f);
+    const float s0 = d.hi * y;
     const float p = s0 * s0;
     const float pe = fmaf(s0, s0, -p);
     const float diff = ((d.hi - p) - pe) + d.lo;
-    return df_norm(s0, diff * (0.5f / s0));
+    return df_norm(s0, diff * (0.5f * y));
 }
-// reciprocal: r0 = 1 / l.hi in FP32, then r0 (1 + (1 - l r0))
+// reciprocal: r ~ 1/l.hi refined by r + r (1 - l.hi r), then r0 (1 + (1 - l r0))
 __device__ __forceinline__ DF df_rcp(DF l) {
-    const float r0 = 1.0f / l.hi;
+    float r0;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r0) : "f"(l.hi));
+    r0 = fmaf(r0, fmaf(-l.hi, r0, 1.0f), r0);
     const float p = l.hi * r0;
     const float pe = fmaf(l.hi, r0, -p);
     const float res = ((1.0f - p) - pe) - l.lo * r0;

@@ -228,15 +228,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(const OzWork w,
     } else if (warp == OZ_DW + 1) {
         // ---------------------------------------------------------------- MMA issue
         if (lane == 0) {
-            // digits u and u + 1 of the block column are adjacent 64-row B tiles and levels
-            // s + u and s + u + 1 adjacent 64-column accumulators, so one N = 128 MMA forms both
-            // products (12 MMAs per 16 K instead of 21; the issuing thread pays per instruction)
-            const uint32_t idesc64 = (1u << 4) | (1u << 7) | (1u << 10) |
-                                     ((uint32_t)(OZ_NB >> 3) << 17) |
-                                     ((uint32_t)(OZ_RT >> 4) << 24);
-            const uint32_t idesc128 = (1u << 4) | (1u << 7) | (1u << 10) |
-                                      ((uint32_t)((2 * OZ_NB) >> 3) << 17) |
-                                      ((uint32_t)(OZ_RT >> 4) << 24);
+            // digits u .. u + c - 1 of the block column are adjacent 64-row B tiles and levels
+            // s + u .. s + u + c - 1 adjacent 64-column accumulators, so one MMA of N = 64 c forms
+            // c products; the 6 - s products of digit s of the rows go in chunks of 4, 2, 1
+            // (9 MMAs per 16 K instead of 21; the issuing thread pays per instruction)
+            auto idesc_n = [](int nc) {
+                return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((nc * OZ_NB) >> 3) << 17) |
+                       ((uint32_t)(OZ_RT >> 4) << 24);
+            };
             uint32_t q = 0, g = 0;
             bool ok = true;
             for (int it = blockIdx.x; it < w.n_items && ok; it += gridDim.x) {
@@ -260,8 +259,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(const OzWork w,
 #pragma unroll
                         for (int s = 0; s < OZ_S; ++s) {
 #pragma unroll
-                            for (int u = 0; u + s < OZ_S; u += 2) {
-                                const bool pair = (u + 1 + s < OZ_S);
+                            for (int u = 0; u + s < OZ_S;) {
+                                const int left = OZ_S - s - u;
+                                const int nc = left >= 4 ? 4 : (left >= 2 ? 2 : 1);
                                 const uint32_t dcol = sm.tmem + (uint32_t)(s + u) * OZ_NB;
 #pragma unroll
                                 for (int k16 = 0; k16 < 2; ++k16) {
@@ -271,8 +271,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_update(const OzWork w,
                                         base + OZ_S * OZ_AT + u * OZ_BT + k16 * 32);
                                     const uint32_t acc =
                                         (kc == k0 && s == 0 && k16 == 0) ? 0u : 1u;
-                                    tc::mma_f16(dcol, ad, bd, pair ? idesc128 : idesc64, acc);
+                                    tc::mma_f16(dcol, ad, bd, idesc_n(nc), acc);
                                 }
+                                u += nc;
                             }
                         }
                         tc::mma_commit(&sm.empty[slot]);

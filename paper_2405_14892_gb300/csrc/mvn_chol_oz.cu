@@ -638,9 +638,10 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
 }
 
 // Panel solve X = C(i, c0:c0+64) L_jj^-T = C W^T for the rows i >= c0 + nb below the diagonal
-// block, after applying the update: a double-float GEMM.  CTA = 64 rows x 64 columns, 256
-// threads, each 4 rows x 4 columns; C and W^T staged in shared memory as pairs.
-#define OZ_TR_ROWS 64
+// block, after applying the update: a double-float GEMM.  CTA = 32 rows x 64 columns, 256
+// threads, each 2 rows x 4 columns; C and W^T staged in shared memory as pairs.
+#define OZ_TR_ROWS 32                // rows per CTA: short CTAs, the chain waits on the last
+#define OZ_TR_RPT (OZ_TR_ROWS / 16)  // rows per thread
 __global__ void __launch_bounds__(256) k_oz_trsm(double* __restrict__ A, int64_t ld, int c0,
                                                  int nb, int n, const int* __restrict__ E,
                                                  long long* __restrict__ T, int64_t ldT,
@@ -693,23 +694,35 @@ __global__ void __launch_bounds__(256) k_oz_trsm(double* __restrict__ A, int64_t
         }
     }
     __syncthreads();
-    const int ty = t >> 4, tx = t & 15;  // rows 4 ty .. 4 ty + 3, columns 4 tx .. 4 tx + 3
-    DF acc[4][4];
+    // thread (ty, tx): rows OZ_TR_RPT ty .., columns 4 tx .. 4 tx + 3
+    const int ty = t >> 4, tx = t & 15;
+    DF acc[OZ_TR_RPT][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < OZ_TR_RPT; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = DF{0.0f, 0.0f};
     const int umax = min(nb, 4 * tx + 4);  // W[c][u] = 0 for u > c
 #pragma unroll 2
     for (int u = 0; u < umax; ++u) {
-        const float4 bh = *reinterpret_cast<const float4*>(&Bh[u][4 * ty]);
-        const float4 bl = *reinterpret_cast<const float4*>(&Bl[u][4 * ty]);
+        DF bv[OZ_TR_RPT];
+        if constexpr (OZ_TR_RPT == 4) {
+            const float4 bh = *reinterpret_cast<const float4*>(&Bh[u][4 * ty]);
+            const float4 bl = *reinterpret_cast<const float4*>(&Bl[u][4 * ty]);
+            bv[0] = DF{bh.x, bl.x};
+            bv[1] = DF{bh.y, bl.y};
+            bv[2] = DF{bh.z, bl.z};
+            bv[3] = DF{bh.w, bl.w};
+        } else {
+            const float2 bh = *reinterpret_cast<const float2*>(&Bh[u][2 * ty]);
+            const float2 bl = *reinterpret_cast<const float2*>(&Bl[u][2 * ty]);
+            bv[0] = DF{bh.x, bl.x};
+            bv[1] = DF{bh.y, bl.y};
+        }
         const float4 wh = *reinterpret_cast<const float4*>(&Wh[u][4 * tx]);
         const float4 wl = *reinterpret_cast<const float4*>(&Wl[u][4 * tx]);
-        const DF bv[4] = {{bh.x, bl.x}, {bh.y, bl.y}, {bh.z, bl.z}, {bh.w, bl.w}};
         const DF wv[4] = {{wh.x, wl.x}, {wh.y, wl.y}, {wh.z, wl.z}, {wh.w, wl.w}};
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < OZ_TR_RPT; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) df_fma_acc(acc[a][b], bv[a], wv[b]);
     }
@@ -717,8 +730,8 @@ __global__ void __launch_bounds__(256) k_oz_trsm(double* __restrict__ A, int64_t
     float(*Xh)[OZ_NB + 1] = reinterpret_cast<float(*)[OZ_NB + 1]>(tr_raw);
     float(*Xl)[OZ_NB + 1] = Xh + OZ_TR_ROWS;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int r = r0 + 4 * ty + a;
+    for (int a = 0; a < OZ_TR_RPT; ++a) {
+        const int r = r0 + OZ_TR_RPT * ty + a;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int cc = 4 * tx + b;
@@ -727,8 +740,8 @@ __global__ void __launch_bounds__(256) k_oz_trsm(double* __restrict__ A, int64_t
                 x = df_norm(acc[a][b].hi, acc[a][b].lo);
                 A[r + (int64_t)(c0 + cc) * ld] = df_to(x);
             }
-            Xh[4 * ty + a][cc] = x.hi;
-            Xl[4 * ty + a][cc] = x.lo;
+            Xh[OZ_TR_RPT * ty + a][cc] = x.hi;
+            Xl[OZ_TR_RPT * ty + a][cc] = x.lo;
         }
     }
     // digits of these rows for the later updates (whole 16-byte chunks per thread)

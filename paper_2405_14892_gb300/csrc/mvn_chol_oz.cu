@@ -638,9 +638,9 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
 }
 
 // Panel solve X = C(i, c0:c0+64) L_jj^-T = C W^T for the rows i >= c0 + nb below the diagonal
-// block, after applying the update: a double-float GEMM.  CTA = 32 rows x 64 columns, 256
-// threads, each 2 rows x 4 columns; C and W^T staged in shared memory as pairs.
-#define OZ_TR_ROWS 32                // rows per CTA: short CTAs, the chain waits on the last
+// block, after applying the update: a double-float GEMM.  CTA = 16 rows x 64 columns, 256
+// threads, each 1 row x 4 columns; C and W^T staged in shared memory as pairs.
+#define OZ_TR_ROWS 16                // rows per CTA: short CTAs, the chain waits on the last
 #define OZ_TR_RPT (OZ_TR_ROWS / 16)  // rows per thread
 __global__ void __launch_bounds__(256) k_oz_trsm(double* __restrict__ A, int64_t ld, int c0,
                                                  int nb, int n, const int* __restrict__ E,
@@ -712,11 +712,13 @@ __global__ void __launch_bounds__(256) k_oz_trsm(double* __restrict__ A, int64_t
             bv[1] = DF{bh.y, bl.y};
             bv[2] = DF{bh.z, bl.z};
             bv[3] = DF{bh.w, bl.w};
-        } else {
+        } else if constexpr (OZ_TR_RPT == 2) {
             const float2 bh = *reinterpret_cast<const float2*>(&Bh[u][2 * ty]);
             const float2 bl = *reinterpret_cast<const float2*>(&Bl[u][2 * ty]);
             bv[0] = DF{bh.x, bl.x};
             bv[1] = DF{bh.y, bl.y};
+        } else {
+            bv[0] = DF{Bh[u][ty], Bl[u][ty]};
         }
         const float4 wh = *reinterpret_cast<const float4*>(&Wh[u][4 * tx]);
         const float4 wl = *reinterpret_cast<const float4*>(&Wl[u][4 * tx]);

@@ -164,13 +164,13 @@ TIMED_KERNELS = ("k_oz_update", "k_oz_potrf", "k_oz_trsm", "k_sov_tc", "k_syrk",
 
 # DRAM bytes per launch measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass)
 # on this workload itself, n = 16,384 with 20,000 paths (profiles/launches_w2_mixed.md): k_sov_tc
-# 93.64 GB read + 1.42 GB written in its launch; k_oz_update 143.36 GB read + 3.29 GB written over
+# 90.98 GB read + 1.42 GB written in its launch; k_oz_update 143.11 GB read + 3.11 GB written over
 # the 509 launches of one factorisation.  Other sizes scale by the growth the kernels' structure
 # gives: the sweep's Y re-reads as (path tiles) x n^2, the update's digit-tile reads as n^2 per
 # launch.
 TRAFFIC_N0 = 16384
 TRAFFIC_TILES0 = 157
-TRAFFIC_BYTES0 = {"k_sov_tc": 93.642e9 + 1.420e9, "k_oz_update": (143.356e9 + 3.293e9) / 509}
+TRAFFIC_BYTES0 = {"k_sov_tc": 90.977e9 + 1.418e9, "k_oz_update": (143.106e9 + 3.106e9) / 509}
 TRAFFIC_NOTE = {"k_oz_update": "bytes per launch, averaged over the 509 launches of one "
                                "factorisation; ncu (1 pass) at n=16384, this workload",
                 "k_sov_tc": "bytes of the launch; ncu (1 pass) at n=16384 with 20,000 paths, "

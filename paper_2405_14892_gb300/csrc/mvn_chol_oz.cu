@@ -23,7 +23,9 @@
 // The update of block column j (64 columns) is an M = 128 (row tile) x N = 64 x K = 64 j GEMM
 // per row tile.  Its K range is cut into work items that a persistent grid of one CTA per SM
 // walks; inside a CTA one warp streams digit tiles (1-D bulk copies, 2-stage mbarrier ring), one
-// warp issues the MMAs, and eight warps drain TMEM into the integer accumulators.
+// warp issues the MMAs (a row digit times 4, 2 or 1 adjacent block-column digits per MMA of
+// N = 256, 128 or 64: the issuing thread, not the tensor pipe, sets the pace), and eight warps
+// drain TMEM into the integer accumulators.
 #include <cuda_bf16.h>
 #include <math.h>
 

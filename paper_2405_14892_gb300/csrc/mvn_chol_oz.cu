@@ -413,8 +413,10 @@ __device__ __forceinline__ DF df_rcp(DF l) {
 }
 
 // POTRF of the diagonal block (c0, c0), nb <= 64, after applying the update, and the inverse
-// W = L_jj^-1 for the panel solve (double-float).  256 threads as a 16 x 16 grid; thread (ty, tx)
-// with tx <= ty keeps the 4 x 4 block X (rows 4 ty .., columns 4 tx ..) in registers.
+// W = L_jj^-1 for the panel solve (double-float).  512 threads as a 32 x 16 grid; thread (ty, tx)
+// with a block in the lower triangle keeps the 2 x 4 block X (rows 2 ty .., columns 4 tx ..) in
+// registers (8 double-float updates per thread and step: the step's serial time is the busiest
+// warp's update plus the pivot).
 // One array carries both factors: at step k of the right-looking sweep the columns m > k of X
 // hold the Schur complement S, the columns m <= k hold W (the column-oriented forward
 // substitution L W = I riding along), so the two updates of step k are one symmetric rank-1
@@ -425,7 +427,7 @@ __device__ __forceinline__ DF df_rcp(DF l) {
 // they are finished (staged in shared memory).  Rows and columns beyond nb are the identity and
 // are never touched.  Writes L_jj to A (FP64), W^T as pairs Wt[u][c] = W[c][u], and the digits of
 // the diagonal rows.
-__global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_t ld, int c0,
+__global__ void __launch_bounds__(512) k_oz_potrf(double* __restrict__ A, int64_t ld, int c0,
                                                   int nb, const int* __restrict__ E,
                                                   long long* __restrict__ T, int64_t ldT,
                                                   float* __restrict__ Wt, uint8_t* __restrict__ Z,
@@ -437,23 +439,23 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
     __shared__ int Eb[OZ_NB];
     if (oz_failed(status)) return;
     const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
-    const bool act = (tx <= ty);
+    const bool act = (4 * tx <= 2 * ty + 1);
     if (t < OZ_NB) Eb[t] = (t < nb) ? E[c0 + t] : 0;
     __syncthreads();
     {
-        // all loads first (16 per thread, independent), then the update is applied
-        double av[16];
-        long long tv[16];
+        // all loads first (8 per thread, independent), then the update is applied
+        double av[8];
+        long long tv[8];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int e = t + 256 * k, i = e % OZ_NB, m = e / OZ_NB;
+        for (int k = 0; k < 8; ++k) {
+            const int e = t + 512 * k, i = e % OZ_NB, m = e / OZ_NB;
             const bool in = (i < nb && m <= i);
             av[k] = in ? A[(c0 + i) + (int64_t)(c0 + m) * ld] : 0.0;
             tv[k] = in ? T[(c0 + i) + (int64_t)m * ldT] : 0;
         }
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int e = t + 256 * k, i = e % OZ_NB, m = e / OZ_NB;
+        for (int k = 0; k < 8; ++k) {
+            const int e = t + 512 * k, i = e % OZ_NB, m = e / OZ_NB;
             DF v{0.0f, 0.0f};
             if (i < nb && m <= i) {
                 double a = av[k];
@@ -470,12 +472,12 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
         }
     }
     __syncthreads();
-    DF X[4][4];  // this thread's block: lower entries of S, becoming W; upper entries unused
+    DF X[2][4];  // this thread's block: lower entries of S, becoming W; upper entries unused
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const int i = 4 * ty + a, m = 4 * tx + b;
+            const int i = 2 * ty + a, m = 4 * tx + b;
             X[a][b] = (act && m <= i) ? DF{Sh[i][m], Sl[i][m]} : DF{0.0f, 0.0f};
         }
     if (t == 0) Sdp[0] = DF{Sh[0][0], Sl[0][0]};
@@ -487,45 +489,46 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
     // -V(k) V(k), V the vector of step k - 1, is redone on that copy with the owner's exact
     // operations, so that every copy of the pivot is the same.
     for (int k = 0; k < nb; ++k) {
-        const int kb = k >> 2, kk = k & 3;
+        const int kb = k >> 2, kk = k & 3;  // column block and column of k
+        const int kr = k >> 1, ka = k & 1;  // row block and row of k
         DF* V = Vs[k & 1];
         // rank-1 update of step k - 1 on the rows i > k - 1 (warp-uniform skip once both row
         // groups are done)
-        if (k > 0 && act && 4 * ty + 3 > k - 1) {
+        if (k > 0 && act && 2 * ty + 1 > k - 1) {
             const DF* Vp = Vs[(k - 1) & 1];
-            DF vi[4], vm[4];
+            DF vi[2], vm[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) vi[a] = Vp[4 * ty + a];
+            for (int a = 0; a < 2; ++a) vi[a] = Vp[2 * ty + a];
 #pragma unroll
             for (int b = 0; b < 4; ++b) vm[b] = Vp[4 * tx + b];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                // rows <= k - 1 take an exact zero multiplier: all 16 updates are independent
-                const bool row = (4 * ty + a > k - 1);
+            for (int a = 0; a < 2; ++a) {
+                // rows <= k - 1 take an exact zero multiplier: all 8 updates are independent
+                const bool row = (2 * ty + a > k - 1);
                 const DF nv{row ? -vi[a].hi : 0.0f, row ? -vi[a].lo : 0.0f};
 #pragma unroll
                 for (int b = 0; b < 4; ++b) df_fma_acc(X[a][b], nv, vm[b]);
             }
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 2; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) X[a][b] = df_norm(X[a][b].hi, X[a][b].lo);
         }
         // the owner of (k + 1, k + 1) publishes it for the pivot of step k + 1
-        const int k1 = k + 1, k1b = k1 >> 2;
-        if (k1 < nb && ty == k1b && tx == k1b) {
-            const int q = k1 & 3;
+        const int k1 = k + 1;
+        if (k1 < nb && ty == (k1 >> 1) && tx == (k1 >> 2)) {
+            const int qr = k1 & 1, qc = k1 & 3;
             DF v = X[0][0];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 2; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b)
-                    if (a == q && b == q) v = X[a][b];
+                    if (a == qr && b == qc) v = X[a][b];
             Sdp[k1 & 1] = v;
         }
         // pivot L_kk = sqrt(S_kk); X(k, k) becomes W(k, k) = 1 / L_kk
         int bad = 0;
-        if (act && (tx == kb || ty == kb)) {
+        if (act && (tx == kb || ty == kr)) {
             DF d = Sdp[k & 1];
             if (k > 0) {
                 const DF v = Vs[(k - 1) & 1][k];
@@ -538,13 +541,13 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
             } else {
                 const DF l = df_sqrt(d);
                 const DF r = df_rcp(l);
-                if (ty == kb && tx == kb) {
+                if (ty == kr && tx == kb) {
                     V[k] = r;
                     Sh[k][k] = l.hi;
                     Sl[k][k] = l.lo;
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
-                        if (a == kk) {
+                    for (int a = 0; a < 2; ++a)
+                        if (a == ka) {
 #pragma unroll
                             for (int b = 0; b < 4; ++b)
                                 if (b == kk) X[a][b] = r;
@@ -552,10 +555,10 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
                 }
                 // column k below the pivot: L(i, k) = S(i, k) / L_kk leaves the array (entry
                 // zeroed)
-                if (tx == kb && 4 * ty + 3 > k) {
+                if (tx == kb && 2 * ty + 1 > k) {
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const int i = 4 * ty + a;
+                    for (int a = 0; a < 2; ++a) {
+                        const int i = 2 * ty + a;
                         if (i > k) {
                             DF v = DF{0.0f, 0.0f};
 #pragma unroll
@@ -571,10 +574,10 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
                     }
                 }
                 // row k left of the pivot: W(k, c) = X(k, c) / L_kk, final
-                if (ty == kb && 4 * tx < k) {
+                if (ty == kr && 4 * tx < k) {
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
-                        if (a == kk) {
+                    for (int a = 0; a < 2; ++a)
+                        if (a == ka) {
 #pragma unroll
                             for (int b = 0; b < 4; ++b) {
                                 const int c = 4 * tx + b;
@@ -595,10 +598,10 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
     // W^T (X holds W in its lower entries; rows and columns beyond nb are the identity)
     if (act) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const int i = 4 * ty + a, m = 4 * tx + b;
+                const int i = 2 * ty + a, m = 4 * tx + b;
                 DF w = (m < i) ? X[a][b] : DF{0.0f, 0.0f};
                 if (m == i) w = (i < nb) ? X[a][b] : DF{1.0f, 0.0f};
                 Wt[m * OZ_NB + i] = w.hi;
@@ -607,21 +610,21 @@ __global__ void __launch_bounds__(256) k_oz_potrf(double* __restrict__ A, int64_
     } else {
         // upper blocks of W^T are zero
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const int i = 4 * ty + a, m = 4 * tx + b;
+                const int i = 2 * ty + a, m = 4 * tx + b;
                 Wt[m * OZ_NB + i] = 0.0f;
                 Wt[OZ_NB * OZ_NB + m * OZ_NB + i] = 0.0f;
             }
     }
     __syncthreads();
-    for (int m = ty; m < nb; m += 16)
+    for (int m = ty; m < nb; m += 32)
         for (int i = m + tx; i < nb; i += 16)
             A[(c0 + i) + (int64_t)(c0 + m) * ld] = df_to(DF{Sh[i][m], Sl[i][m]});
     // digits of the diagonal rows (and zero digits for the rows of the row tile above them)
     if (Z != nullptr) {
-        for (int e = t; e < 2 * OZ_NB * 8; e += 256) {
+        for (int e = t; e < 2 * OZ_NB * 8; e += 512) {
             const int c8 = e & 7, i = (e >> 3) - ((c0 % OZ_RT) ? OZ_NB : 0);
             if (i >= OZ_NB) continue;
             float xh[8], xl[8];
@@ -910,7 +913,7 @@ static mvn_status chol_oz_run(mvn_ctx* ctx, int n, double* A, int64_t ld, char* 
         // below, up to the end of the last row tile) when a later column needs them
         uint8_t* Zj = (j + 1 < nbc) ? Z : nullptr;
         MVN_TIMED_ON(ctx, hi, "k_oz_potrf",
-                     (k_oz_potrf<<<1, 256, 0, hi>>>(A, ld, c0, nb, E, Tj, ldT, Wt, Zj, nrt,
+                     (k_oz_potrf<<<1, 512, 0, hi>>>(A, ld, c0, nb, E, Tj, ldT, Wt, Zj, nrt,
                                                     ctx->d_status)));
         const int rows = (Zj != nullptr) ? nrt * OZ_RT - c0 - nb : n - c0 - nb;
         if (rows > 0) {

@@ -413,10 +413,11 @@ __device__ __forceinline__ DF df_rcp(DF l) {
 }
 
 // POTRF of the diagonal block (c0, c0), nb <= 64, after applying the update, and the inverse
-// W = L_jj^-1 for the panel solve (double-float).  512 threads as a 32 x 16 grid; thread (ty, tx)
-// with a block in the lower triangle keeps the 2 x 4 block X (rows 2 ty .., columns 4 tx ..) in
-// registers (8 double-float updates per thread and step: the step's serial time is the busiest
-// warp's update plus the pivot).
+// W = L_jj^-1 for the panel solve (double-float).  The 64 x 64 block is cut into 2 x 4 blocks
+// (rows 2 ty .., columns 4 tx ..); the 272 of them that reach the lower triangle (4 tx <= 2 ty + 1)
+// go one per thread, packed densely in row-major order (row pair p, i.e. ty = 2p and 2p + 1, holds
+// 2 (p + 1) blocks starting at block p (p + 1)), so that no warp issues for the empty upper half.
+// Each thread keeps its block X in registers (8 double-float updates per step).
 // One array carries both factors: at step k of the right-looking sweep the columns m > k of X
 // hold the Schur complement S, the columns m <= k hold W (the column-oriented forward
 // substitution L W = I riding along), so the two updates of step k are one symmetric rank-1
@@ -427,35 +428,52 @@ __device__ __forceinline__ DF df_rcp(DF l) {
 // they are finished (staged in shared memory).  Rows and columns beyond nb are the identity and
 // are never touched.  Writes L_jj to A (FP64), W^T as pairs Wt[u][c] = W[c][u], and the digits of
 // the diagonal rows.
-__global__ void __launch_bounds__(512) k_oz_potrf(double* __restrict__ A, int64_t ld, int c0,
-                                                  int nb, const int* __restrict__ E,
-                                                  long long* __restrict__ T, int64_t ldT,
-                                                  float* __restrict__ Wt, uint8_t* __restrict__ Z,
-                                                  int nrt, int* status) {
+#define OZ_PF_BLOCKS 272   // 2 x 4 blocks of a 64 x 64 block that reach its lower triangle
+#define OZ_PF_THREADS 288  // whole warps
+__global__ void __launch_bounds__(OZ_PF_THREADS) k_oz_potrf(double* __restrict__ A, int64_t ld,
+                                                           int c0, int nb,
+                                                           const int* __restrict__ E,
+                                                           long long* __restrict__ T, int64_t ldT,
+                                                           float* __restrict__ Wt,
+                                                           uint8_t* __restrict__ Z, int nrt,
+                                                           int* status) {
     __shared__ DF Vs[2][OZ_NB];  // step vector V, by step parity
     __shared__ DF Sdp[2];        // S(k, k) published one step ahead, by step parity
     // staging: the loaded block, then the columns of L as they are finished
     __shared__ float Sh[OZ_NB][OZ_NB + 1], Sl[OZ_NB][OZ_NB + 1];
     __shared__ int Eb[OZ_NB];
     if (oz_failed(status)) return;
-    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
-    const bool act = (4 * tx <= 2 * ty + 1);
-    if (t < OZ_NB) Eb[t] = (t < nb) ? E[c0 + t] : 0;
+    const int t = threadIdx.x;
+    const bool act = (t < OZ_PF_BLOCKS);
+    int ty = 0, tx = 0;  // idle threads (act false) take part in the loads, barriers and stores only
+    if (act) {
+        int p = 0;
+        while ((p + 1) * (p + 2) <= t) ++p;
+        const int q = t - p * (p + 1);
+        ty = 2 * p + (q > p ? 1 : 0);
+        tx = (q > p) ? q - p - 1 : q;
+    }
+    if (t < OZ_NB) {
+        Eb[t] = (t < nb) ? E[c0 + t] : 0;
+        Vs[1][t] = DF{0.0f, 0.0f};  // the vector "before step 0": the first update is empty
+    }
     __syncthreads();
     {
-        // all loads first (8 per thread, independent), then the update is applied
-        double av[8];
-        long long tv[8];
+        // all loads first (independent), then the update is applied
+        constexpr int NL = (OZ_NB * OZ_NB + OZ_PF_THREADS - 1) / OZ_PF_THREADS;
+        double av[NL];
+        long long tv[NL];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int e = t + 512 * k, i = e % OZ_NB, m = e / OZ_NB;
-            const bool in = (i < nb && m <= i);
+        for (int k = 0; k < NL; ++k) {
+            const int e = t + OZ_PF_THREADS * k, i = e % OZ_NB, m = e / OZ_NB;
+            const bool in = (e < OZ_NB * OZ_NB && i < nb && m <= i);
             av[k] = in ? A[(c0 + i) + (int64_t)(c0 + m) * ld] : 0.0;
             tv[k] = in ? T[(c0 + i) + (int64_t)m * ldT] : 0;
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int e = t + 512 * k, i = e % OZ_NB, m = e / OZ_NB;
+        for (int k = 0; k < NL; ++k) {
+            const int e = t + OZ_PF_THREADS * k, i = e % OZ_NB, m = e / OZ_NB;
+            if (e >= OZ_NB * OZ_NB) continue;
             DF v{0.0f, 0.0f};
             if (i < nb && m <= i) {
                 double a = av[k];
@@ -483,19 +501,27 @@ __global__ void __launch_bounds__(512) k_oz_potrf(double* __restrict__ A, int64_
     if (t == 0) Sdp[0] = DF{Sh[0][0], Sl[0][0]};
     __syncthreads();  // Sh/Sl now receive the finished columns of L
     // Step k runs in one phase between two barriers: the rank-1 update of step k - 1, then the
-    // pivot and the scaling of column k (and of row k of W).  Every thread that scales computes
-    // the pivot itself from S(k, k) after the update of step k - 1: its owner publishes
-    // S(k, k) after the update of step k - 2 (one phase ahead, in Sdp), and the last update
-    // -V(k) V(k), V the vector of step k - 1, is redone on that copy with the owner's exact
-    // operations, so that every copy of the pivot is the same.
+    // scaling of column k (and of row k of W).  Every thread with a row i > k - 1 computes the
+    // pivot itself, from S(k, k) as its owner published it one phase ahead (in Sdp, after the
+    // update of step k - 2) with the last update -V(k) V(k) redone by the owner's exact
+    // operations, so that every copy is the same; the pivot does not depend on this phase's
+    // update, so the two dependency chains interleave in one straight-line block.
     for (int k = 0; k < nb; ++k) {
         const int kb = k >> 2, kk = k & 3;  // column block and column of k
         const int kr = k >> 1, ka = k & 1;  // row block and row of k
         DF* V = Vs[k & 1];
-        // rank-1 update of step k - 1 on the rows i > k - 1 (warp-uniform skip once both row
-        // groups are done)
-        if (k > 0 && act && 2 * ty + 1 > k - 1) {
-            const DF* Vp = Vs[(k - 1) & 1];
+        const DF* Vp = Vs[(k + 1) & 1];  // the vector of step k - 1 (zero before step 0)
+        int bad = 0;
+        if (act && 2 * ty + 1 > k - 1) {
+            // pivot L_kk = sqrt(S_kk) and its reciprocal
+            DF d = Sdp[k & 1];
+            const DF vk = Vp[k];
+            df_fma_acc(d, DF{-vk.hi, -vk.lo}, vk);
+            d = df_norm(d.hi, d.lo);
+            const bool pos = (d.hi > 0.0f);
+            const DF l = df_sqrt(pos ? d : DF{1.0f, 0.0f});
+            const DF r = df_rcp(l);
+            // rank-1 update of step k - 1; rows <= k - 1 take an exact zero multiplier
             DF vi[2], vm[4];
 #pragma unroll
             for (int a = 0; a < 2; ++a) vi[a] = Vp[2 * ty + a];
@@ -503,7 +529,6 @@ __global__ void __launch_bounds__(512) k_oz_potrf(double* __restrict__ A, int64_
             for (int b = 0; b < 4; ++b) vm[b] = Vp[4 * tx + b];
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
-                // rows <= k - 1 take an exact zero multiplier: all 8 updates are independent
                 const bool row = (2 * ty + a > k - 1);
                 const DF nv{row ? -vi[a].hi : 0.0f, row ? -vi[a].lo : 0.0f};
 #pragma unroll
@@ -513,60 +538,48 @@ __global__ void __launch_bounds__(512) k_oz_potrf(double* __restrict__ A, int64_
             for (int a = 0; a < 2; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) X[a][b] = df_norm(X[a][b].hi, X[a][b].lo);
-        }
-        // the owner of (k + 1, k + 1) publishes it for the pivot of step k + 1
-        const int k1 = k + 1;
-        if (k1 < nb && ty == (k1 >> 1) && tx == (k1 >> 2)) {
-            const int qr = k1 & 1, qc = k1 & 3;
-            DF v = X[0][0];
+            // the owner of (k + 1, k + 1) publishes it for the pivot of step k + 1
+            const int k1 = k + 1;
+            if (k1 < nb && ty == (k1 >> 1) && tx == (k1 >> 2)) {
+                const int qr = k1 & 1, qc = k1 & 3;
+                DF v = X[0][0];
 #pragma unroll
-            for (int a = 0; a < 2; ++a)
+                for (int a = 0; a < 2; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    if (a == qr && b == qc) v = X[a][b];
-            Sdp[k1 & 1] = v;
-        }
-        // pivot L_kk = sqrt(S_kk); X(k, k) becomes W(k, k) = 1 / L_kk
-        int bad = 0;
-        if (act && (tx == kb || ty == kr)) {
-            DF d = Sdp[k & 1];
-            if (k > 0) {
-                const DF v = Vs[(k - 1) & 1][k];
-                df_fma_acc(d, DF{-v.hi, -v.lo}, v);
-                d = df_norm(d.hi, d.lo);
+                    for (int b = 0; b < 4; ++b)
+                        if (a == qr && b == qc) v = X[a][b];
+                Sdp[k1 & 1] = v;
             }
-            if (!(d.hi > 0.0f)) {
+            if (!pos) {
                 bad = 1;
                 dev_raise(status, MVN_ERR_NOT_PD, c0 + k + 1);
             } else {
-                const DF l = df_sqrt(d);
-                const DF r = df_rcp(l);
+                // X(k, k) becomes W(k, k) = 1 / L_kk
                 if (ty == kr && tx == kb) {
                     V[k] = r;
                     Sh[k][k] = l.hi;
                     Sl[k][k] = l.lo;
 #pragma unroll
                     for (int a = 0; a < 2; ++a)
-                        if (a == ka) {
 #pragma unroll
-                            for (int b = 0; b < 4; ++b)
-                                if (b == kk) X[a][b] = r;
-                        }
+                        for (int b = 0; b < 4; ++b)
+                            if (a == ka && b == kk) X[a][b] = r;
                 }
                 // column k below the pivot: L(i, k) = S(i, k) / L_kk leaves the array (entry
-                // zeroed)
+                // zeroed); the entry is selected first, then scaled once
                 if (tx == kb && 2 * ty + 1 > k) {
 #pragma unroll
                     for (int a = 0; a < 2; ++a) {
                         const int i = 2 * ty + a;
+                        DF x = X[a][0];
+#pragma unroll
+                        for (int b = 1; b < 4; ++b)
+                            if (b == kk) x = X[a][b];
                         if (i > k) {
-                            DF v = DF{0.0f, 0.0f};
+                            const DF v = df_mul(x, r);
 #pragma unroll
                             for (int b = 0; b < 4; ++b)
-                                if (b == kk) {
-                                    v = df_mul(X[a][b], r);
-                                    X[a][b] = DF{0.0f, 0.0f};
-                                }
+                                if (b == kk) X[a][b] = DF{0.0f, 0.0f};
                             V[i] = v;
                             Sh[i][k] = v.hi;
                             Sl[i][k] = v.lo;
@@ -576,18 +589,18 @@ __global__ void __launch_bounds__(512) k_oz_potrf(double* __restrict__ A, int64_
                 // row k left of the pivot: W(k, c) = X(k, c) / L_kk, final
                 if (ty == kr && 4 * tx < k) {
 #pragma unroll
-                    for (int a = 0; a < 2; ++a)
-                        if (a == ka) {
-#pragma unroll
-                            for (int b = 0; b < 4; ++b) {
-                                const int c = 4 * tx + b;
-                                if (c < k) {
-                                    const DF v = df_mul(X[a][b], r);
-                                    X[a][b] = v;
-                                    V[c] = v;
-                                }
-                            }
+                    for (int b = 0; b < 4; ++b) {
+                        const int c = 4 * tx + b;
+                        const DF x = ka ? X[1][b] : X[0][b];
+                        if (c < k) {
+                            const DF v = df_mul(x, r);
+                            if (ka)
+                                X[1][b] = v;
+                            else
+                                X[0][b] = v;
+                            V[c] = v;
                         }
+                    }
                 }
             }
         }
@@ -607,24 +620,24 @@ __global__ void __launch_bounds__(512) k_oz_potrf(double* __restrict__ A, int64_
                 Wt[m * OZ_NB + i] = w.hi;
                 Wt[OZ_NB * OZ_NB + m * OZ_NB + i] = w.lo;
             }
-    } else {
-        // upper blocks of W^T are zero
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int i = 2 * ty + a, m = 4 * tx + b;
-                Wt[m * OZ_NB + i] = 0.0f;
-                Wt[OZ_NB * OZ_NB + m * OZ_NB + i] = 0.0f;
-            }
+    }
+    // the blocks that no thread holds (above the diagonal) are zero in W^T
+    for (int e = t; e < OZ_NB * OZ_NB; e += OZ_PF_THREADS) {
+        const int i = e % OZ_NB, m = e / OZ_NB;
+        if (4 * (m >> 2) > 2 * (i >> 1) + 1) {
+            Wt[m * OZ_NB + i] = 0.0f;
+            Wt[OZ_NB * OZ_NB + m * OZ_NB + i] = 0.0f;
+        }
     }
     __syncthreads();
-    for (int m = ty; m < nb; m += 32)
-        for (int i = m + tx; i < nb; i += 16)
+    for (int e = t; e < OZ_NB * OZ_NB; e += OZ_PF_THREADS) {
+        const int i = e % OZ_NB, m = e / OZ_NB;
+        if (m <= i && i < nb)
             A[(c0 + i) + (int64_t)(c0 + m) * ld] = df_to(DF{Sh[i][m], Sl[i][m]});
+    }
     // digits of the diagonal rows (and zero digits for the rows of the row tile above them)
     if (Z != nullptr) {
-        for (int e = t; e < 2 * OZ_NB * 8; e += 512) {
+        for (int e = t; e < 2 * OZ_NB * 8; e += OZ_PF_THREADS) {
             const int c8 = e & 7, i = (e >> 3) - ((c0 % OZ_RT) ? OZ_NB : 0);
             if (i >= OZ_NB) continue;
             float xh[8], xl[8];
@@ -913,7 +926,7 @@ static mvn_status chol_oz_run(mvn_ctx* ctx, int n, double* A, int64_t ld, char* 
         // below, up to the end of the last row tile) when a later column needs them
         uint8_t* Zj = (j + 1 < nbc) ? Z : nullptr;
         MVN_TIMED_ON(ctx, hi, "k_oz_potrf",
-                     (k_oz_potrf<<<1, 512, 0, hi>>>(A, ld, c0, nb, E, Tj, ldT, Wt, Zj, nrt,
+                     (k_oz_potrf<<<1, OZ_PF_THREADS, 0, hi>>>(A, ld, c0, nb, E, Tj, ldT, Wt, Zj, nrt,
                                                     ctx->d_status)));
         const int rows = (Zj != nullptr) ? nrt * OZ_RT - c0 - nb : n - c0 - nb;
         if (rows > 0) {
